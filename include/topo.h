@@ -1,0 +1,172 @@
+/*
+ * topo.h -- C-ABI of the GB300 SIMP hot-path library (libtopo.so).
+ *
+ * The calls follow the problem statement of arXiv 2012.08208 (Section 4: the
+ * program main(nelx, nely[, nelz], volfrac, penal, rmin); Section 5: 3D,
+ * other supports, several load cases, passive elements) on structured grids of
+ * unit Q4 (2D, plane stress) / H8 (3D) elements.
+ *
+ * Conventions shared by every call
+ *   - Numbering: node (i,j[,k]) = i + (nelx+1)*(j + (nely+1)*k); element
+ *     (i,j[,k]) = i + nelx*(j + nely*k); DOF = dim*node + component.
+ *   - Host arrays are borrowed for the duration of the call only.  Where a call
+ *     takes `on_device`, a nonzero value means the pointer is device memory of
+ *     the problem's device (e.g. a PyTorch tensor on the problem's stream);
+ *     zero means host memory.
+ *   - Ownership: the library allocates and owns every device buffer of a
+ *     problem; tp_destroy_problem frees them.
+ *   - Errors: every call returns a tp_status; no exception crosses the ABI.
+ *     After an error the handle stays valid and tp_last_error() describes it.
+ *     Calls on one handle are not thread-safe.  All work is enqueued on the
+ *     stream given at creation; calls that return scalars synchronise it.
+ *   - Order: create, set_fixed, set_loads, [set_passive], set_density, then per
+ *     SIMP iteration solve, sensitivities, filter, oc_update (or tp_simp_step).
+ *     A call whose inputs are not ready returns TP_ERR_STATE.
+ */
+#ifndef TOPO_H
+#define TOPO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TP_OK = 0,
+  TP_ERR_ARG = 1,            /* invalid argument (size, range, NaN, null pointer) */
+  TP_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  TP_ERR_OOM = 3,            /* device allocation failed */
+  TP_ERR_NOT_CONVERGED = 4,  /* solve hit max_it before the tolerance */
+  TP_ERR_BREAKDOWN = 5,      /* CG breakdown (p^T K p <= 0 or not finite) */
+  TP_ERR_TIMEOUT = 6,        /* a bounded device-side wait expired */
+  TP_ERR_STATE = 7           /* call out of order (inputs not set) */
+} tp_status;
+
+/* Problem parameters (Section 4: nelx, nely, volfrac, penal, rmin; Section 5.1
+ * adds nelz).  E0/Emin/nu: modified-SIMP moduli and Poisson ratio;
+ * move/dmin: OC move limit and lower density bound (Eq. "update");
+ * n_cases: number of load cases (Section 5.3), 1..8. */
+typedef struct tp_params {
+  int dim;      /* 2 (Q4, plane stress) or 3 (H8) */
+  int nelx, nely, nelz;  /* elements per axis; nelz ignored in 2D */
+  double E0, Emin, nu, penal, volfrac, rmin, move, dmin;
+  int n_cases;
+} tp_params;
+
+enum { TP_PREC_F64 = 0, TP_PREC_MIXED = 1 };
+enum { TP_WARM_ZERO = 0, TP_WARM_PREVIOUS = 1, TP_WARM_USER = 2 };
+enum { TP_FILTER_SENSITIVITY = 0 };
+/* Quantities for tp_get / tp_set (all FP64):
+ *   TP_RHO   design densities rho[n_el]
+ *   TP_U     displacements u[n_cases][n_dof] (the solution, or the warm start)
+ *   TP_DC    raw sensitivities dc[n_el] (after tp_sensitivities)
+ *   TP_DCF   filtered sensitivities dc~[n_el] (after tp_filter)
+ *   TP_CE    element energies sum_k u_e^T K0 u_e [n_el] (after tp_sensitivities)
+ *   TP_RHO_PHYS  physical densities used for stiffness [n_el] */
+enum { TP_RHO = 0, TP_U = 1, TP_DC = 2, TP_DCF = 3, TP_CE = 4, TP_RHO_PHYS = 5 };
+
+/* Solver options.  tol: target TRUE relative residual ||f - K u||_2 / ||f||_2
+ * per case, checked in FP64 at exit.  max_it: maximum CG iterations.
+ * precision TP_PREC_F64: all vectors and the operator in FP64.
+ * precision TP_PREC_MIXED: operator and CG vectors in FP32, dot products in FP64,
+ * and the solution accumulated in FP64 with reliable updates: whenever the FP32
+ * recurrence residual has dropped by `update_drop` (e.g. 1e-2) since the last
+ * update, the FP64 true residual f - K u replaces it.  warm_start: TP_WARM_*.
+ * TP_WARM_USER uses the displacement set by tp_set(TP_U, ...). */
+typedef struct tp_solve_opts {
+  double tol;
+  int max_it;
+  int precision;
+  int warm_start;
+  double update_drop;
+} tp_solve_opts;
+
+typedef struct tp_solve_info {
+  int iters;            /* CG iterations (shared by all cases) */
+  int updates;          /* FP64 true-residual evaluations */
+  int converged;        /* 1 if every case met tol */
+  int status;           /* tp_status of the solve */
+  double rel_res[8];    /* final true relative residual per case */
+  double ms;            /* device time of the solve */
+} tp_solve_info;
+
+typedef struct tp_step_info {
+  tp_solve_info solve;
+  double compliance;    /* sum_k f_k^T u_k */
+  double lambda;        /* OC multiplier */
+  double volume;        /* sum rho_new */
+  double change;        /* max |rho_new - rho| */
+} tp_step_info;
+
+typedef struct tp_problem tp_problem;
+
+/* Create a problem on the current CUDA device.  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Validates sizes and ranges:
+ * dim in {2,3}, element counts >= 1, 0 < volfrac <= 1, rmin > 0, penal >= 1,
+ * 0 <= nu < 0.5, 0 < Emin < E0, 0 < dmin < 1, move > 0, 1 <= n_cases <= 8. */
+tp_status tp_create_problem(const tp_params* params, void* cuda_stream, tp_problem** out);
+void tp_destroy_problem(tp_problem* p);
+const char* tp_last_error(const tp_problem* p);
+
+/* Dirichlet DOFs (Section 4.2; DirichletBC): fixed[n_dof] (host), nonzero = u = 0.
+ * Rejected if no DOF is fixed (K would be singular). */
+tp_status tp_set_fixed(tp_problem* p, const uint8_t* fixed);
+/* Nodal loads f[n_cases][n_dof] (host, FP64; Section 4.2 loads, Section 5.3 load
+ * cases).  Loads on fixed DOFs are ignored.  Rejects NaN/Inf and an all-zero case. */
+tp_status tp_set_loads(tp_problem* p, const double* f);
+/* Passive elements passive[n_el] (host; Section 5.4): 1 = void, held at dmin. */
+tp_status tp_set_passive(tp_problem* p, const int8_t* passive);
+/* Design densities rho[n_el] (FP64, host or device).  Must lie in (0, 1]. */
+tp_status tp_set_density(tp_problem* p, const double* rho, int on_device);
+
+/* Solve K(rho) u_k = f_k for every case (replaces the sparse LU of Section 4.3)
+ * by Jacobi-preconditioned CG in one persistent launch.  Fills `info` (may be
+ * NULL).  Returns TP_ERR_NOT_CONVERGED / TP_ERR_BREAKDOWN / TP_ERR_TIMEOUT when the
+ * solve did not reach opts->tol (the solution is still stored). */
+tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info);
+
+/* Compliance c = sum_k f_k^T u_k and sensitivities
+ * dc_e = -p rho_e^(p-1) (E0 - Emin) sum_k u_e^T K0 u_e (Section 3.2 sensitivity,
+ * Section 4.4, Section 5.3).  `compliance` (host, may be NULL) receives c. */
+tp_status tp_sensitivities(tp_problem* p, double* compliance);
+
+/* Mesh-independency filter (Section 3.2.2, Eq. "filter", "filter_cond"; Eq.
+ * "filter_mat"): W_ab = max(0, rmin - |x_a - x_b|) over element midpoints, rows
+ * truncated at the mesh boundary.
+ * mode TP_FILTER_SENSITIVITY: dc~_a = sum_b W_ab rho_b dc_b / (rho_a sum_b W_ab).
+ * Any other mode returns TP_ERR_ARG. */
+tp_status tp_filter(tp_problem* p, int mode);
+
+/* OC update with bisection on lambda (Section 3.2, Eq. "update", Section 3.2.1):
+ * rho_new = max(dmin, max(rho - m, min(1, min(rho + m, rho sqrt(-dc~ / lambda))))),
+ * lambda such that sum rho_new = volfrac * n_el (passive held at dmin), bracket
+ * [0, 1e9] widened x10 as needed, stopped at width <= 1e-10 (l1 + l2).  Replaces
+ * rho by rho_new.  Outputs (host, each may be NULL): lambda, volume, change. */
+tp_status tp_oc_update(tp_problem* p, double* lambda, double* volume, double* change);
+
+/* One SIMP iteration: solve, sensitivities, sensitivity filter, OC update. */
+tp_status tp_simp_step(tp_problem* p, const tp_solve_opts* opts, tp_step_info* info);
+
+/* Copy a quantity out (TP_RHO, TP_U, TP_DC, TP_DCF, TP_CE, TP_RHO_PHYS) to `dst`. */
+tp_status tp_get(tp_problem* p, int what, void* dst, int on_device);
+/* Set a quantity: TP_U (warm start for TP_WARM_USER / TP_WARM_PREVIOUS),
+ * TP_DC (raw sensitivities, e.g. to filter given values), TP_DCF (filtered
+ * sensitivities, e.g. to run the OC update on given values). */
+tp_status tp_set(tp_problem* p, int what, const void* src, int on_device);
+
+/* Apply the boundary-conditioned operator: y = K(rho) u on free DOFs with the
+ * fixed entries of u read as 0, and y_i = u_i on fixed DOFs.  precision
+ * TP_PREC_F64: u, y are double[n_dof]; TP_PREC_MIXED: float[n_dof] (FP32 operator).
+ * `ncopies` > 1 applies it to that many consecutive vectors (stride n_dof). */
+tp_status tp_matvec(tp_problem* p, const void* u, void* y, int precision, int ncopies,
+                    int on_device);
+
+/* Launch accounting: number of kernels this library enqueued since creation. */
+long long tp_launch_count(const tp_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOPO_H */

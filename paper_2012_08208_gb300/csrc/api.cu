@@ -1,0 +1,519 @@
+// C-ABI of the GB300 SIMP library (declared in include/topo.h).
+// Host-side state machine, argument validation and kernel launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/topo.h"
+#include "host.h"
+
+using namespace tp;
+
+struct tp_problem {
+  tp_params prm;
+  cudaStream_t stream = nullptr;
+  int dev = 0, nsm = 0;
+  Grid g;
+  long long nn = 0, ne = 0, ndof = 0;
+  int nc = 1, dim = 2, nv = 2;
+  std::vector<double> K0;
+  FilterLaunch* flt = nullptr;
+
+  double* rho = nullptr;
+  double* rho_new = nullptr;
+  float* E32 = nullptr;
+  double* E64 = nullptr;
+  uint8_t* mask = nullptr;
+  int8_t* passive = nullptr;
+  double* f = nullptr;
+  double* x64 = nullptr;
+  float* inv32 = nullptr;
+  double* inv64 = nullptr;
+  void* w[6] = {};  // xl, r, z, p0, p1, q (sized for double)
+  double* part = nullptr;
+  GridBar* bar = nullptr;
+  PcgStatus* st = nullptr;
+  OcStatus* ost = nullptr;
+  double* scal = nullptr;
+  double* dc = nullptr;
+  double* dcf = nullptr;
+  double* ce = nullptr;
+  double* bscr = nullptr;
+  double* abi = nullptr;
+
+  bool has_fixed = false, has_loads = false, has_density = false, has_u = false;
+  bool has_dc = false, has_dcf = false, E_dirty = true, has_passive = false;
+  double ff[kMaxCases] = {};
+  std::string err;
+  long long launches = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int last_grid = 0;
+};
+
+namespace {
+
+constexpr int kMaxGridPerSm = 16;
+
+tp_status fail(tp_problem* p, tp_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+tp_status cuda_fail(tp_problem* p, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(p, e == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA, m);
+}
+
+#define TPCK(call, what)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(p, e_, what);  \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** ptr, size_t count) {
+  return cudaMalloc((void**)ptr, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+}
+
+void free_all(tp_problem* p) {
+  void* ptrs[] = {p->rho, p->rho_new, p->E32, p->E64, p->mask, p->passive, p->f, p->x64,
+                  p->inv32, p->inv64, p->w[0], p->w[1], p->w[2], p->w[3], p->w[4], p->w[5],
+                  p->part, p->bar, p->st, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  delete p->flt;
+}
+
+bool finite_all(const double* a, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+tp_status ensure_E(tp_problem* p) {
+  if (!p->E_dirty) return TP_OK;
+  TPCK(launch_young(p->stream, p->rho, p->E32, p->E64, p->ne, p->prm.E0, p->prm.Emin, p->prm.penal),
+       "young kernel");
+  TPCK(launch_diag(p->stream, p->g, p->K0.data(), p->E64, p->mask, p->inv32, p->inv64), "diag kernel");
+  p->launches += 2;
+  p->E_dirty = false;
+  return TP_OK;
+}
+
+cudaMemcpyKind kind_of(int on_device, bool to_device) {
+  if (on_device) return cudaMemcpyDeviceToDevice;
+  return to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+tp_status tp_create_problem(const tp_params* params, void* cuda_stream, tp_problem** out) {
+  if (!params || !out) return TP_ERR_ARG;
+  *out = nullptr;
+  const tp_params& q = *params;
+  if (q.dim != 2 && q.dim != 3) return TP_ERR_ARG;
+  if (q.nelx < 1 || q.nely < 1 || (q.dim == 3 && q.nelz < 1)) return TP_ERR_ARG;
+  if (!(q.volfrac > 0.0 && q.volfrac <= 1.0) || !(q.rmin > 0.0) || !(q.penal >= 1.0)) return TP_ERR_ARG;
+  if (!(q.nu >= 0.0 && q.nu < 0.5) || !(q.Emin > 0.0 && q.Emin < q.E0)) return TP_ERR_ARG;
+  if (!(q.dmin > 0.0 && q.dmin < 1.0) || !(q.move > 0.0)) return TP_ERR_ARG;
+  if (q.n_cases < 1 || q.n_cases > kMaxCases) return TP_ERR_ARG;
+  const long long nx = q.nelx + 1, ny = q.nely + 1, nz = q.dim == 3 ? q.nelz + 1 : 1;
+  if (nx * ny * nz * q.dim * q.n_cases > (1LL << 31) - 1) return TP_ERR_ARG;
+
+  tp_problem* p = new tp_problem();
+  p->prm = q;
+  if (q.dim == 2) p->prm.nelz = 0;
+  p->stream = (cudaStream_t)cuda_stream;
+  p->dim = q.dim;
+  p->nc = q.n_cases;
+  p->nv = q.dim * q.n_cases;
+  p->g.dim = q.dim;
+  p->g.ex = q.nelx;
+  p->g.ey = q.nely;
+  p->g.ez = q.dim == 3 ? q.nelz : 1;
+  p->g.nx = (int)nx;
+  p->g.ny = (int)ny;
+  p->g.nz = (int)nz;
+  p->g.nn = nx * ny * nz;
+  p->g.ne = (long long)p->g.ex * p->g.ey * p->g.ez;
+  p->nn = p->g.nn;
+  p->ne = p->g.ne;
+  p->ndof = p->nn * q.dim;
+  const int nd = q.dim == 2 ? 8 : 24;
+  p->K0.resize(nd * nd);
+  element_k0(q.dim, q.nu, p->K0.data());
+  p->flt = new FilterLaunch();
+  p->flt->g = p->g;
+  p->flt->ntaps = filter_taps(q.dim, q.rmin, kMaxTaps, p->flt->off, p->flt->w);
+  if (p->flt->ntaps < 1) {
+    delete p->flt;
+    delete p;
+    return TP_ERR_ARG;
+  }
+
+  cudaError_t e = cudaGetDevice(&p->dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
+  const size_t nvals = (size_t)p->nn * p->nv;
+  const size_t maxgrid = (size_t)p->nsm * kMaxGridPerSm;
+  if (e == cudaSuccess) e = dalloc(&p->rho, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->rho_new, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->E32, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->E64, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->mask, p->nn);
+  if (e == cudaSuccess) e = dalloc(&p->passive, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->f, nvals);
+  if (e == cudaSuccess) e = dalloc(&p->x64, nvals);
+  if (e == cudaSuccess) e = dalloc(&p->inv32, p->ndof);
+  if (e == cudaSuccess) e = dalloc(&p->inv64, p->ndof);
+  for (int i = 0; i < 6 && e == cudaSuccess; i++) e = dalloc((double**)&p->w[i], nvals);
+  if (e == cudaSuccess) e = dalloc(&p->part, (size_t)48 * maxgrid);
+  if (e == cudaSuccess) e = dalloc(&p->bar, 1);
+  if (e == cudaSuccess) e = dalloc(&p->st, 1);
+  if (e == cudaSuccess) e = dalloc(&p->ost, 1);
+  if (e == cudaSuccess) e = dalloc(&p->scal, 16);
+  if (e == cudaSuccess) e = dalloc(&p->dc, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->dcf, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->ce, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->bscr, p->ne);
+  if (e == cudaSuccess) e = dalloc(&p->abi, nvals);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->mask, 0, p->nn, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->passive, 0, p->ne, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->x64, 0, nvals * sizeof(double), p->stream);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&p->ev1);
+  if (e != cudaSuccess) {
+    const tp_status s = e == cudaErrorMemoryAllocation ? TP_ERR_OOM : TP_ERR_CUDA;
+    cudaGetLastError();
+    free_all(p);
+    delete p;
+    return s;
+  }
+  *out = p;
+  return TP_OK;
+}
+
+void tp_destroy_problem(tp_problem* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->stream);
+  free_all(p);
+  delete p;
+}
+
+const char* tp_last_error(const tp_problem* p) { return p ? p->err.c_str() : "null problem"; }
+
+long long tp_launch_count(const tp_problem* p) { return p ? p->launches : 0; }
+
+tp_status tp_set_fixed(tp_problem* p, const uint8_t* fixed) {
+  if (!p || !fixed) return fail(p, TP_ERR_ARG, "null argument");
+  std::vector<uint8_t> m(p->nn, 0);
+  long long nfix = 0;
+  for (long long i = 0; i < p->ndof; i++)
+    if (fixed[i]) {
+      m[i / p->dim] |= (uint8_t)(1u << (i % p->dim));
+      nfix++;
+    }
+  if (nfix == 0) return fail(p, TP_ERR_ARG, "no fixed DOF: the stiffness would be singular");
+  TPCK(cudaMemcpyAsync(p->mask, m.data(), p->nn, cudaMemcpyHostToDevice, p->stream), "copy mask");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  p->has_fixed = true;
+  p->has_loads = false;
+  p->has_u = false;
+  p->E_dirty = true;
+  return TP_OK;
+}
+
+tp_status tp_set_loads(tp_problem* p, const double* f) {
+  if (!p || !f) return fail(p, TP_ERR_ARG, "null argument");
+  if (!p->has_fixed) return fail(p, TP_ERR_STATE, "tp_set_fixed must precede tp_set_loads");
+  const size_t n = (size_t)p->nc * p->ndof;
+  if (!finite_all(f, n)) return fail(p, TP_ERR_ARG, "loads contain NaN or Inf");
+  std::vector<uint8_t> m(p->nn);
+  TPCK(cudaMemcpyAsync(m.data(), p->mask, p->nn, cudaMemcpyDeviceToHost, p->stream), "copy mask");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  for (int c = 0; c < p->nc; c++) {
+    double s = 0.0;
+    for (long long i = 0; i < p->ndof; i++) {
+      const double v = f[(size_t)c * p->ndof + i];
+      if (!((m[i / p->dim] >> (i % p->dim)) & 1)) s += v * v;
+    }
+    if (!(s > 0.0)) return fail(p, TP_ERR_ARG, "a load case has no load on free DOFs");
+    p->ff[c] = s;
+  }
+  TPCK(cudaMemcpyAsync(p->abi, f, n * sizeof(double), cudaMemcpyHostToDevice, p->stream), "copy loads");
+  TPCK(launch_to_internal(p->stream, p->abi, p->f, p->nn, p->dim, p->nc, p->mask, 1), "layout kernel");
+  p->launches++;
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  p->has_loads = true;
+  return TP_OK;
+}
+
+tp_status tp_set_passive(tp_problem* p, const int8_t* passive) {
+  if (!p || !passive) return fail(p, TP_ERR_ARG, "null argument");
+  for (long long e = 0; e < p->ne; e++)
+    if (passive[e] != 0 && passive[e] != 1) return fail(p, TP_ERR_ARG, "passive entries must be 0 or 1");
+  TPCK(cudaMemcpyAsync(p->passive, passive, p->ne, cudaMemcpyHostToDevice, p->stream), "copy passive");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  p->has_passive = true;
+  return TP_OK;
+}
+
+tp_status tp_set_density(tp_problem* p, const double* rho, int on_device) {
+  if (!p || !rho) return fail(p, TP_ERR_ARG, "null argument");
+  if (!on_device) {
+    for (long long e = 0; e < p->ne; e++)
+      if (!(rho[e] > 0.0 && rho[e] <= 1.0)) return fail(p, TP_ERR_ARG, "densities must lie in (0, 1]");
+  }
+  TPCK(cudaMemcpyAsync(p->rho, rho, p->ne * sizeof(double), kind_of(on_device, true), p->stream),
+       "copy density");
+  if (!on_device) TPCK(cudaStreamSynchronize(p->stream), "sync");
+  p->has_density = true;
+  p->E_dirty = true;
+  p->has_dc = p->has_dcf = false;
+  return TP_OK;
+}
+
+tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info) {
+  if (!p || !opts) return fail(p, TP_ERR_ARG, "null argument");
+  if (!p->has_fixed || !p->has_loads || !p->has_density)
+    return fail(p, TP_ERR_STATE, "fixed DOFs, loads and density must be set before tp_solve");
+  if (!(opts->tol > 0.0) || opts->max_it < 1) return fail(p, TP_ERR_ARG, "tol must be > 0, max_it >= 1");
+  if (opts->precision != TP_PREC_F64 && opts->precision != TP_PREC_MIXED)
+    return fail(p, TP_ERR_ARG, "unknown precision");
+  if (opts->warm_start < TP_WARM_ZERO || opts->warm_start > TP_WARM_USER)
+    return fail(p, TP_ERR_ARG, "unknown warm_start");
+  if (opts->warm_start == TP_WARM_USER && !p->has_u)
+    return fail(p, TP_ERR_STATE, "TP_WARM_USER needs tp_set(TP_U, ...) first");
+  double drop = opts->update_drop;
+  if (opts->precision == TP_PREC_MIXED) {
+    if (drop == 0.0) drop = 1e-2;
+    if (!(drop > 0.0 && drop < 1.0)) return fail(p, TP_ERR_ARG, "update_drop must lie in (0, 1)");
+  }
+  tp_status s = ensure_E(p);
+  if (s != TP_OK) return s;
+  const bool f64 = opts->precision == TP_PREC_F64;
+  const size_t nvals = (size_t)p->nn * p->nv;
+  if (opts->warm_start == TP_WARM_ZERO || (opts->warm_start == TP_WARM_PREVIOUS && !p->has_u))
+    TPCK(cudaMemsetAsync(p->x64, 0, nvals * sizeof(double), p->stream), "memset");
+  TPCK(cudaMemsetAsync(p->w[0], 0, nvals * (f64 ? 8 : 4), p->stream), "memset");
+  TPCK(cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream), "memset");
+  PcgLaunch L;
+  L.g = p->g;
+  L.nc = p->nc;
+  L.E = f64 ? (const void*)p->E64 : (const void*)p->E32;
+  L.E64 = p->E64;
+  L.mask = p->mask;
+  L.invdiag = f64 ? (const void*)p->inv64 : (const void*)p->inv32;
+  L.f = p->f;
+  L.x64 = p->x64;
+  L.xl = p->w[0];
+  L.r = p->w[1];
+  L.z = p->w[2];
+  L.p0 = p->w[3];
+  L.p1 = p->w[4];
+  L.q = p->w[5];
+  L.part = p->part;
+  L.bar = p->bar;
+  L.st = p->st;
+  for (int c = 0; c < kMaxCases; c++) L.tol2ff[c] = c < p->nc ? opts->tol * opts->tol * p->ff[c] : 0.0;
+  L.drop2 = f64 ? 0.0 : drop * drop;
+  L.max_it = opts->max_it;
+  L.K0 = p->K0.data();
+  TPCK(cudaEventRecord(p->ev0, p->stream), "event");
+  TPCK(launch_pcg(p->stream, L, f64, p->nsm, &p->last_grid), "cg kernel");
+  p->launches++;
+  TPCK(cudaEventRecord(p->ev1, p->stream), "event");
+  PcgStatus st;
+  TPCK(cudaMemcpyAsync(&st, p->st, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "copy status");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  p->has_u = true;
+  p->has_dc = p->has_dcf = false;
+  bool conv = true, brk = false;
+  for (int c = 0; c < p->nc; c++) {
+    conv &= st.state[c] == 1;
+    brk |= st.state[c] == 2;
+  }
+  tp_status rs = TP_OK;
+  if (st.flags & ERR_TIMEOUT) rs = TP_ERR_TIMEOUT;
+  else if (brk) rs = TP_ERR_BREAKDOWN;
+  else if (!conv) rs = TP_ERR_NOT_CONVERGED;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->iters = st.iters;
+    info->updates = st.updates;
+    info->converged = conv ? 1 : 0;
+    info->status = rs;
+    for (int c = 0; c < p->nc; c++) info->rel_res[c] = std::sqrt(st.rr_true[c] / p->ff[c]);
+    info->ms = ms;
+  }
+  if (rs == TP_ERR_TIMEOUT) return fail(p, rs, "a device-side wait timed out in the CG kernel");
+  if (rs == TP_ERR_BREAKDOWN) return fail(p, rs, "CG breakdown (p^T K p <= 0 or not finite)");
+  if (rs == TP_ERR_NOT_CONVERGED) return fail(p, rs, "CG reached max_it before the tolerance");
+  return TP_OK;
+}
+
+tp_status tp_sensitivities(tp_problem* p, double* compliance) {
+  if (!p) return TP_ERR_ARG;
+  if (!p->has_u) return fail(p, TP_ERR_STATE, "tp_solve must precede tp_sensitivities");
+  const double dE = p->prm.E0 - p->prm.Emin;
+  TPCK(launch_sens(p->stream, p->g, p->nc, p->K0.data(), p->x64, p->f, p->rho, p->prm.penal, dE, p->ce,
+                   p->dc, p->part, p->scal),
+       "sensitivity kernel");
+  p->launches += 2;
+  if (compliance) {
+    TPCK(cudaMemcpyAsync(compliance, p->scal, sizeof(double), cudaMemcpyDeviceToHost, p->stream), "copy");
+    TPCK(cudaStreamSynchronize(p->stream), "sync");
+  }
+  p->has_dc = true;
+  p->has_dcf = false;
+  return TP_OK;
+}
+
+tp_status tp_filter(tp_problem* p, int mode) {
+  if (!p) return TP_ERR_ARG;
+  if (mode != TP_FILTER_SENSITIVITY) return fail(p, TP_ERR_ARG, "only the sensitivity filter (mode 0) is available");
+  if (!p->has_dc || !p->has_density) return fail(p, TP_ERR_STATE, "tp_sensitivities must precede tp_filter");
+  TPCK(launch_filter(p->stream, *p->flt, 0, p->rho, p->dc, p->dcf), "filter kernel");
+  p->launches++;
+  p->has_dcf = true;
+  return TP_OK;
+}
+
+tp_status tp_oc_update(tp_problem* p, double* lambda, double* volume, double* change) {
+  if (!p) return TP_ERR_ARG;
+  if (!p->has_dcf) return fail(p, TP_ERR_STATE, "tp_filter (or tp_set(TP_DCF)) must precede tp_oc_update");
+  TPCK(cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream), "memset");
+  int grid = 0;
+  TPCK(launch_oc(p->stream, p->ne, p->rho, p->dcf, p->has_passive ? p->passive : nullptr, p->prm.volfrac,
+                 p->prm.move, p->prm.dmin, p->rho_new, p->bscr, p->part, p->bar, p->ost, p->nsm, &grid),
+       "oc kernel");
+  p->launches++;
+  OcStatus st;
+  TPCK(cudaMemcpyAsync(&st, p->ost, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "copy status");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  if (st.flags & ERR_TIMEOUT) return fail(p, TP_ERR_TIMEOUT, "a device-side wait timed out in the OC kernel");
+  if (st.flags & ERR_NAN) return fail(p, TP_ERR_ARG, "no multiplier bracket found (non-finite sensitivities?)");
+  std::swap(p->rho, p->rho_new);
+  p->E_dirty = true;
+  p->has_dc = p->has_dcf = false;
+  if (lambda) *lambda = st.lambda;
+  if (volume) *volume = st.volume;
+  if (change) *change = st.change;
+  return TP_OK;
+}
+
+tp_status tp_simp_step(tp_problem* p, const tp_solve_opts* opts, tp_step_info* info) {
+  if (!p || !opts) return fail(p, TP_ERR_ARG, "null argument");
+  tp_step_info loc;
+  memset(&loc, 0, sizeof(loc));
+  tp_status s = tp_solve(p, opts, &loc.solve);
+  if (s != TP_OK && s != TP_ERR_NOT_CONVERGED) {
+    if (info) *info = loc;
+    return s;
+  }
+  tp_status s2 = tp_sensitivities(p, &loc.compliance);
+  if (s2 == TP_OK) s2 = tp_filter(p, TP_FILTER_SENSITIVITY);
+  if (s2 == TP_OK) s2 = tp_oc_update(p, &loc.lambda, &loc.volume, &loc.change);
+  if (info) *info = loc;
+  if (s2 != TP_OK) return s2;
+  return s;
+}
+
+tp_status tp_get(tp_problem* p, int what, void* dst, int on_device) {
+  if (!p || !dst) return fail(p, TP_ERR_ARG, "null argument");
+  const cudaMemcpyKind k = kind_of(on_device, false);
+  switch (what) {
+    case TP_RHO:
+    case TP_RHO_PHYS:
+      if (!p->has_density) return fail(p, TP_ERR_STATE, "density not set");
+      TPCK(cudaMemcpyAsync(dst, p->rho, p->ne * sizeof(double), k, p->stream), "copy");
+      break;
+    case TP_U:
+      if (!p->has_u) return fail(p, TP_ERR_STATE, "no displacement yet");
+      TPCK(launch_to_abi(p->stream, p->x64, p->abi, p->nn, p->dim, p->nc), "layout kernel");
+      p->launches++;
+      TPCK(cudaMemcpyAsync(dst, p->abi, (size_t)p->nc * p->ndof * sizeof(double), k, p->stream), "copy");
+      break;
+    case TP_DC:
+      if (!p->has_dc) return fail(p, TP_ERR_STATE, "no sensitivities yet");
+      TPCK(cudaMemcpyAsync(dst, p->dc, p->ne * sizeof(double), k, p->stream), "copy");
+      break;
+    case TP_CE:
+      if (!p->has_dc) return fail(p, TP_ERR_STATE, "no sensitivities yet");
+      TPCK(cudaMemcpyAsync(dst, p->ce, p->ne * sizeof(double), k, p->stream), "copy");
+      break;
+    case TP_DCF:
+      if (!p->has_dcf) return fail(p, TP_ERR_STATE, "no filtered sensitivities yet");
+      TPCK(cudaMemcpyAsync(dst, p->dcf, p->ne * sizeof(double), k, p->stream), "copy");
+      break;
+    default:
+      return fail(p, TP_ERR_ARG, "unknown quantity");
+  }
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  return TP_OK;
+}
+
+tp_status tp_set(tp_problem* p, int what, const void* src, int on_device) {
+  if (!p || !src) return fail(p, TP_ERR_ARG, "null argument");
+  const cudaMemcpyKind k = kind_of(on_device, true);
+  switch (what) {
+    case TP_U:
+      if (!p->has_fixed) return fail(p, TP_ERR_STATE, "fixed DOFs not set");
+      if (!on_device && !finite_all((const double*)src, (size_t)p->nc * p->ndof))
+        return fail(p, TP_ERR_ARG, "displacement contains NaN or Inf");
+      TPCK(cudaMemcpyAsync(p->abi, src, (size_t)p->nc * p->ndof * sizeof(double), k, p->stream), "copy");
+      TPCK(launch_to_internal(p->stream, p->abi, p->x64, p->nn, p->dim, p->nc, p->mask, 1), "layout kernel");
+      p->launches++;
+      p->has_u = true;
+      break;
+    case TP_DC:
+      TPCK(cudaMemcpyAsync(p->dc, src, p->ne * sizeof(double), k, p->stream), "copy");
+      p->has_dc = true;
+      break;
+    case TP_DCF:
+      TPCK(cudaMemcpyAsync(p->dcf, src, p->ne * sizeof(double), k, p->stream), "copy");
+      p->has_dcf = true;
+      break;
+    default:
+      return fail(p, TP_ERR_ARG, "unknown quantity");
+  }
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  return TP_OK;
+}
+
+tp_status tp_matvec(tp_problem* p, const void* u, void* y, int precision, int ncopies, int on_device) {
+  if (!p || !u || !y || ncopies < 1) return fail(p, TP_ERR_ARG, "bad argument");
+  if (!p->has_fixed || !p->has_density) return fail(p, TP_ERR_STATE, "fixed DOFs and density must be set");
+  if (precision != TP_PREC_F64 && precision != TP_PREC_MIXED) return fail(p, TP_ERR_ARG, "unknown precision");
+  tp_status s = ensure_E(p);
+  if (s != TP_OK) return s;
+  const bool f64 = precision == TP_PREC_F64;
+  const size_t bytes = (size_t)ncopies * p->ndof * (f64 ? 8 : 4);
+  const void* du = u;
+  void* dy = y;
+  void* tmp = nullptr;
+  if (!on_device) {
+    TPCK(cudaMalloc(&tmp, 2 * bytes), "alloc");
+    TPCK(cudaMemcpyAsync(tmp, u, bytes, cudaMemcpyHostToDevice, p->stream), "copy");
+    du = tmp;
+    dy = (char*)tmp + bytes;
+  }
+  cudaError_t e = launch_matvec(p->stream, p->g, p->K0.data(), f64, f64 ? (const void*)p->E64 : (const void*)p->E32,
+                                p->mask, du, dy, ncopies);
+  p->launches++;
+  if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(p, e, "matvec");
+  return TP_OK;
+}
+
+}  // extern "C"

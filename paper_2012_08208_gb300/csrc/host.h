@@ -1,0 +1,87 @@
+// Internal host-side interface between the C-ABI (api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tp {
+
+constexpr int kMaxCases = 8;
+constexpr int kMaxTaps = 512;
+
+// Element stiffness (host, FP64) and filter stencil.
+void element_k0(int dim, double nu, double* K);
+int filter_taps(int dim, double rmin, int max_taps, int* off, double* wts);
+
+// Per-solve status written by the persistent CG kernel.
+struct PcgStatus {
+  int iters;
+  int updates;
+  int flags;          // ERR_* bits
+  int state[kMaxCases];  // 0 = not converged, 1 = converged, 2 = breakdown
+  double rr_true[kMaxCases];  // final true ||f - K u||^2 per case
+};
+
+struct PcgLaunch {
+  Grid g;
+  int nc;
+  const void* E;        // operator moduli in the CG precision
+  const double* E64;    // FP64 moduli for the true residual
+  const uint8_t* mask;  // per-node fixed bits
+  const void* invdiag;  // per DOF, CG precision
+  const double* f;      // internal layout [node][case][comp]
+  double* x64;
+  void* xl;
+  void* r;
+  void* z;
+  void* p0;
+  void* p1;
+  void* q;
+  double* part;
+  GridBar* bar;
+  PcgStatus* st;
+  double tol2ff[kMaxCases];
+  double drop2;
+  int max_it;
+  const double* K0;  // host FP64 K0 (copied into the kernel parameters)
+};
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t launch_young(cudaStream_t s, const double* rho, float* E32, double* E64, long long ne,
+                         double E0, double Emin, double penal);
+cudaError_t launch_diag(cudaStream_t s, const Grid& g, const double* K0, const double* E64,
+                        const uint8_t* mask, float* inv32, double* inv64);
+cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* K0, bool f64, const void* E,
+                          const uint8_t* mask, const void* u, void* y, int ncopies);
+cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch& L, bool f64, int nsm, int* grid_out);
+cudaError_t launch_sens(cudaStream_t s, const Grid& g, int nc, const double* K0, const double* x64,
+                        const double* f, const double* rho, double penal, double dE, double* ce,
+                        double* dc, double* part, double* out_c);
+cudaError_t launch_to_internal(cudaStream_t s, const double* src, double* dst, long long nn, int dim,
+                               int nc, const uint8_t* mask, int zero_fixed);
+cudaError_t launch_to_abi(cudaStream_t s, const double* src, double* dst, long long nn, int dim, int nc);
+
+// Filter / OC (opt_kernels.cu).
+struct FilterLaunch {
+  Grid g;
+  int ntaps;
+  int off[3 * kMaxTaps];
+  double w[kMaxTaps];
+};
+cudaError_t launch_filter(cudaStream_t s, const FilterLaunch& F, int mode, const double* rho,
+                          const double* dc, double* out);
+struct OcStatus {
+  double lambda;
+  double volume;
+  double change;
+  int passes;
+  int flags;
+};
+cudaError_t launch_oc(cudaStream_t s, long long ne, const double* rho, const double* dcf,
+                      const int8_t* passive, double volfrac, double move, double dmin,
+                      double* rho_new, double* bscratch, double* part, GridBar* bar, OcStatus* st,
+                      int nsm, int* grid_out);
+
+}  // namespace tp

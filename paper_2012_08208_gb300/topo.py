@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libtopo.so (C-ABI declared in include/topo.h).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA
+kernels.  Arrays may be NumPy arrays (host) or CUDA torch tensors (device); the
+binding passes their pointers through.  If the library has not been built the
+import fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libtopo.so")
+
+TP_OK, TP_ERR_ARG, TP_ERR_CUDA, TP_ERR_OOM, TP_ERR_NOT_CONVERGED, TP_ERR_BREAKDOWN, TP_ERR_TIMEOUT, \
+    TP_ERR_STATE = range(8)
+STATUS_NAMES = ["TP_OK", "TP_ERR_ARG", "TP_ERR_CUDA", "TP_ERR_OOM", "TP_ERR_NOT_CONVERGED",
+                "TP_ERR_BREAKDOWN", "TP_ERR_TIMEOUT", "TP_ERR_STATE"]
+TP_PREC_F64, TP_PREC_MIXED = 0, 1
+TP_WARM_ZERO, TP_WARM_PREVIOUS, TP_WARM_USER = 0, 1, 2
+TP_FILTER_SENSITIVITY = 0
+TP_RHO, TP_U, TP_DC, TP_DCF, TP_CE, TP_RHO_PHYS = range(6)
+
+
+class tp_params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nelx", C.c_int), ("nely", C.c_int), ("nelz", C.c_int),
+                ("E0", C.c_double), ("Emin", C.c_double), ("nu", C.c_double), ("penal", C.c_double),
+                ("volfrac", C.c_double), ("rmin", C.c_double), ("move", C.c_double),
+                ("dmin", C.c_double), ("n_cases", C.c_int)]
+
+
+class tp_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_it", C.c_int), ("precision", C.c_int),
+                ("warm_start", C.c_int), ("update_drop", C.c_double)]
+
+
+class tp_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("updates", C.c_int), ("converged", C.c_int), ("status", C.c_int),
+                ("rel_res", C.c_double * 8), ("ms", C.c_double)]
+
+
+class tp_step_info(C.Structure):
+    _fields_ = [("solve", tp_solve_info), ("compliance", C.c_double), ("lambda_", C.c_double),
+                ("volume", C.c_double), ("change", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` "
+                          "(there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    sigs = {
+        "tp_create_problem": (C.c_int, [C.POINTER(tp_params), P, C.POINTER(P)]),
+        "tp_destroy_problem": (None, [P]),
+        "tp_last_error": (C.c_char_p, [P]),
+        "tp_launch_count": (C.c_longlong, [P]),
+        "tp_set_fixed": (C.c_int, [P, P]),
+        "tp_set_loads": (C.c_int, [P, P]),
+        "tp_set_passive": (C.c_int, [P, P]),
+        "tp_set_density": (C.c_int, [P, P, C.c_int]),
+        "tp_solve": (C.c_int, [P, C.POINTER(tp_solve_opts), C.POINTER(tp_solve_info)]),
+        "tp_sensitivities": (C.c_int, [P, C.POINTER(C.c_double)]),
+        "tp_filter": (C.c_int, [P, C.c_int]),
+        "tp_oc_update": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "tp_simp_step": (C.c_int, [P, C.POINTER(tp_solve_opts), C.POINTER(tp_step_info)]),
+        "tp_get": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "tp_set": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "tp_matvec": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+# Every name the header declares (checked by the CPU test suite).
+EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
+            "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
+            "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec"]
+
+
+class TopoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """(pointer, on_device) of a NumPy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data_as(C.c_void_p), 0
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def make_params(dim, nelx, nely, nelz=0, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0, volfrac=0.5, rmin=1.5,
+                move=0.2, dmin=1e-3, n_cases=1):
+    return tp_params(dim, nelx, nely, nelz, E0, Emin, nu, penal, volfrac, rmin, move, dmin, n_cases)
+
+
+def solve_opts(tol=1e-8, max_it=20000, precision=TP_PREC_MIXED, warm_start=TP_WARM_ZERO, update_drop=1e-2):
+    return tp_solve_opts(tol, max_it, precision, warm_start, update_drop)
+
+
+class Problem:
+    """Owns a tp_problem handle.  Method names follow the C-ABI."""
+
+    def __init__(self, params: tp_params, stream=None):
+        h = C.c_void_p()
+        s = C.c_void_p(0 if stream is None else int(stream))
+        st = lib.tp_create_problem(C.byref(params), s, C.byref(h))
+        if st != TP_OK:
+            raise TopoError(st, "tp_create_problem rejected the parameters")
+        self.h = h
+        self.params = params
+        self.dim = params.dim
+        nz = (params.nelz + 1) if params.dim == 3 else 1
+        self.n_nodes = (params.nelx + 1) * (params.nely + 1) * nz
+        self.n_dof = self.dim * self.n_nodes
+        self.n_el = params.nelx * params.nely * (params.nelz if params.dim == 3 else 1)
+        self.n_cases = params.n_cases
+
+    @classmethod
+    def from_workload(cls, w, stream=None):
+        """Create and configure from a `workloads.Problem` (fixed DOFs, loads,
+        passive mask, initial density)."""
+        prm = make_params(w.dim, w.nelx, w.nely, w.nelz, w.E0, w.Emin, w.nu, w.penal, w.volfrac, w.rmin,
+                          w.move, w.dmin, w.n_cases)
+        p = cls(prm, stream)
+        p.set_fixed(w.fixed)
+        p.set_loads(w.loads)
+        if w.passive is not None:
+            p.set_passive(w.passive)
+        p.set_density(w.initial_density())
+        return p
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.tp_destroy_problem(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != TP_OK:
+            raise TopoError(st, lib.tp_last_error(self.h).decode())
+
+    def last_error(self):
+        return lib.tp_last_error(self.h).decode()
+
+    def launch_count(self):
+        return int(lib.tp_launch_count(self.h))
+
+    def set_fixed(self, fixed):
+        a = np.ascontiguousarray(fixed, dtype=np.uint8)
+        assert a.size == self.n_dof
+        self._check(lib.tp_set_fixed(self.h, a.ctypes.data_as(C.c_void_p)))
+
+    def set_loads(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float64)
+        assert a.size == self.n_cases * self.n_dof
+        self._check(lib.tp_set_loads(self.h, a.ctypes.data_as(C.c_void_p)))
+
+    def set_passive(self, passive):
+        a = np.ascontiguousarray(passive, dtype=np.int8)
+        assert a.size == self.n_el
+        self._check(lib.tp_set_passive(self.h, a.ctypes.data_as(C.c_void_p)))
+
+    def set_density(self, rho):
+        if isinstance(rho, np.ndarray):
+            rho = np.ascontiguousarray(rho, dtype=np.float64)
+        ptr, dev = _ptr(rho)
+        self._check(lib.tp_set_density(self.h, ptr, dev))
+
+    def solve(self, opts: tp_solve_opts, check=True):
+        info = tp_solve_info()
+        st = lib.tp_solve(self.h, C.byref(opts), C.byref(info))
+        if check:
+            self._check(st)
+        return info
+
+    def sensitivities(self):
+        c = C.c_double()
+        self._check(lib.tp_sensitivities(self.h, C.byref(c)))
+        return c.value
+
+    def filter(self, mode=TP_FILTER_SENSITIVITY):
+        self._check(lib.tp_filter(self.h, mode))
+
+    def oc_update(self):
+        lam, vol, ch = C.c_double(), C.c_double(), C.c_double()
+        self._check(lib.tp_oc_update(self.h, C.byref(lam), C.byref(vol), C.byref(ch)))
+        return lam.value, vol.value, ch.value
+
+    def simp_step(self, opts: tp_solve_opts, check=True):
+        info = tp_step_info()
+        st = lib.tp_simp_step(self.h, C.byref(opts), C.byref(info))
+        if check:
+            self._check(st)
+        return info
+
+    def _size(self, what):
+        return self.n_cases * self.n_dof if what == TP_U else self.n_el
+
+    def get(self, what, out=None):
+        if out is None:
+            out = np.empty(self._size(what), dtype=np.float64)
+        ptr, dev = _ptr(out)
+        self._check(lib.tp_get(self.h, what, ptr, dev))
+        return out
+
+    def set(self, what, src):
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=np.float64)
+        ptr, dev = _ptr(src)
+        self._check(lib.tp_set(self.h, what, ptr, dev))
+
+    def matvec(self, u, precision=TP_PREC_F64, ncopies=1, out=None):
+        if isinstance(u, np.ndarray):
+            dt = np.float64 if precision == TP_PREC_F64 else np.float32
+            u = np.ascontiguousarray(u, dtype=dt)
+            if out is None:
+                out = np.empty_like(u)
+        ptr_u, dev = _ptr(u)
+        ptr_y, dev2 = _ptr(out)
+        assert dev == dev2
+        self._check(lib.tp_matvec(self.h, ptr_u, ptr_y, precision, ncopies, dev))
+        return out

@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle on the
+same seeded inputs.  Tolerances (written per test):
+  * FP64 operator:   |y - y_ref| <= 1e-12 * (|K| |u|)_i          (rounding order only)
+  * FP32 operator:   |y - y_ref| <= 2e-5 * (|K| |u|)_i           (FP32 K0, E and sums)
+  * solve / loop:    compliance rel <= 1e-8, densities max-abs <= 1e-6, lambda rel <= 1e-9
+  * filter / sens:   rel <= 1e-12 (FP64 both sides, same formula)
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem, filt, oc, sens, simp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def topo():
+    from paper_2012_08208_gb300 import topo as t
+    return t
+
+
+def _abs_product(prob, rho, u):
+    K = fem.assemble(prob, rho)
+    Ka = abs(K)
+    fixed = prob.fixed.astype(bool)
+    y = Ka @ np.abs(np.where(fixed, 0, u))
+    return np.where(fixed, np.abs(u), y)
+
+
+GRIDS = [
+    W.small2d(1, 1), W.small2d(2, 1), W.small2d(70, 20), W.small2d(33, 9, n_cases=2),
+    W.small3d(1, 1, 1), W.small3d(3, 2, 2), W.small3d(40, 9, 6), W.small3d(33, 5, 5, n_cases=2),
+]
+
+
+@pytest.mark.parametrize("prob", GRIDS, ids=lambda p: p.name + f"_nc{p.n_cases}")
+def test_matvec_f64_and_f32(topo, prob):
+    rho = W.random_density(prob.n_el, seed=31)
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    for k in range(2):
+        u = W.random_vector(prob.n_dof, seed=32 + k)
+        y_ref = fem.matvec_bc(prob, rho, u)
+        bound = _abs_product(prob, rho, u)
+        y64 = p.matvec(u, topo.TP_PREC_F64)
+        assert np.all(np.abs(y64 - y_ref) <= 1e-12 * bound + 1e-300)
+        u32 = u.astype(np.float32)
+        y32 = p.matvec(u32, topo.TP_PREC_MIXED).astype(np.float64)
+        y_ref32 = fem.matvec_bc(prob, rho, u32.astype(np.float64))
+        assert np.all(np.abs(y32 - y_ref32) <= 2e-5 * bound + 1e-30)
+    # several vectors in one call
+    U = np.stack([W.random_vector(prob.n_dof, seed=40 + k) for k in range(3)])
+    Y = p.matvec(U.ravel(), topo.TP_PREC_F64, ncopies=3).reshape(3, -1)
+    for k in range(3):
+        assert np.allclose(Y[k], fem.matvec_bc(prob, rho, U[k]), rtol=1e-12, atol=1e-12 * np.abs(Y[k]).max())
+    p.close()
+
+
+@pytest.mark.parametrize("prob", [W.small2d(37, 11, n_cases=3, passive_disk=(10, 5, 3)),
+                                  W.small3d(17, 6, 5)], ids=lambda p: p.name)
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_solve_matches_direct_solve(topo, prob, prec):
+    rho = W.random_density(prob.n_el, seed=33, lo=0.01)
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    pr = topo.TP_PREC_F64 if prec == "f64" else topo.TP_PREC_MIXED
+    info = p.solve(topo.solve_opts(tol=1e-12, max_it=100000, precision=pr))
+    assert info.converged == 1
+    U = p.get(topo.TP_U).reshape(prob.n_cases, -1)
+    U_ref = fem.solve(prob, rho)
+    res = fem.rel_residual(prob, rho, U)
+    assert np.all(res <= 1.5e-12)
+    for c in range(prob.n_cases):
+        assert info.rel_res[c] == pytest.approx(res[c], rel=1e-3, abs=1e-15)
+    c_gpu = p.sensitivities()
+    c_ref = sens.compliance(prob, U_ref)
+    assert abs(c_gpu - c_ref) <= 1e-8 * abs(c_ref)
+    p.close()
+
+
+@pytest.mark.parametrize("prob", [W.small2d(45, 13, n_cases=2), W.small3d(19, 7, 6)], ids=lambda p: p.name)
+def test_sensitivities_on_identical_displacements(topo, prob):
+    rho = W.random_density(prob.n_el, seed=34)
+    U = np.stack([W.random_vector(prob.n_dof, seed=35 + c) for c in range(prob.n_cases)])
+    U[:, prob.fixed.astype(bool)] = 0.0
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    p.set(topo.TP_U, U.ravel())
+    c_gpu = p.sensitivities()
+    c_ref, ce_ref, dc_ref = sens.sensitivities(prob, rho, U)
+    assert c_gpu == pytest.approx(c_ref, rel=1e-12)
+    assert np.allclose(p.get(topo.TP_CE), ce_ref, rtol=1e-12, atol=1e-12 * np.abs(ce_ref).max())
+    assert np.allclose(p.get(topo.TP_DC), dc_ref, rtol=1e-12, atol=1e-12 * np.abs(dc_ref).max())
+    p.close()
+
+
+@pytest.mark.parametrize("prob", [W.small2d(70, 21, rmin=1.5), W.small2d(40, 17, rmin=3.0),
+                                  W.small3d(35, 9, 7, rmin=1.5), W.small3d(33, 10, 6, rmin=2.0),
+                                  W.small2d(1, 1, rmin=3.0), W.small3d(1, 2, 1, rmin=2.0)],
+                         ids=lambda p: f"{p.name}_r{p.rmin}")
+def test_filter(topo, prob):
+    rho = W.random_density(prob.n_el, seed=36)
+    dc = W.random_sensitivity(prob.n_el, seed=37)
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    p.set(topo.TP_DC, dc)
+    p.filter()
+    got = p.get(topo.TP_DCF)
+    ref = filt.sensitivity_filter(filt.sparse_weights(prob), rho, dc)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+    p.close()
+
+
+@pytest.mark.parametrize("n,vf,passive", [(1200, 0.5, False), (4000, 0.3, True), (7, 0.6, False)])
+def test_oc_update(topo, n, vf, passive):
+    prob = W.small2d(n, 1, volfrac=vf)
+    rng = np.random.default_rng(n)
+    rho = rng.uniform(0.001, 1.0, n)
+    dcf = W.random_sensitivity(n, seed=38)
+    pas = None
+    if passive:
+        pas = (rng.uniform(size=n) < 0.1).astype(np.int8)
+        rho[pas == 1] = 0.001
+        prob.passive = pas
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    p.set(topo.TP_DCF, dcf)
+    lam, vol, ch = p.oc_update()
+    rho_new = p.get(topo.TP_RHO)
+    lam_exact = oc.exact_lambda(rho, dcf, vf, passive=pas)
+    assert lam == pytest.approx(lam_exact, rel=1e-9)
+    ref = oc.update(rho, dcf, lam_exact, passive=pas)
+    assert np.max(np.abs(rho_new - ref)) <= 1e-6
+    assert vol == pytest.approx(vf * n, rel=1e-8)
+    assert ch == pytest.approx(np.max(np.abs(rho_new - rho)), rel=1e-12)
+    if passive:
+        assert np.all(rho_new[pas == 1] == 0.001)
+    p.close()
+
+
+def test_simp_iterations_on_identical_density_mbb(topo):
+    """Config 1 (MBB 60 x 20, FP64): every iteration compared with the oracle on the
+    GPU's own density (compliance <= 1e-8, rho <= 1e-6, lambda <= 1e-9)."""
+    prob = W.mbb2d()
+    Wm = filt.weights_for(prob)
+    p = topo.Problem.from_workload(prob)
+    rho = prob.initial_density()
+    opts = topo.solve_opts(tol=1e-12, max_it=50000, precision=topo.TP_PREC_F64, warm_start=topo.TP_WARM_PREVIOUS)
+    for it in range(8):
+        info = p.simp_step(opts)
+        ref = simp.iteration(prob, rho, W=Wm)
+        assert abs(info.compliance - ref["c"]) <= 1e-8 * ref["c"]
+        rho_gpu = p.get(topo.TP_RHO)
+        lam_exact = oc.exact_lambda(rho, ref["dcf"], prob.volfrac)
+        assert info.lambda_ == pytest.approx(lam_exact, rel=1e-9)
+        assert np.max(np.abs(rho_gpu - ref["rho_new"])) <= 1e-6
+        rho = rho_gpu
+    p.close()
+
+
+def test_mbb_50_iterations_final_compliance(topo):
+    prob = W.mbb2d()
+    rho_ref, hist = simp.run(prob, n_iter=50)
+    p = topo.Problem.from_workload(prob)
+    opts = topo.solve_opts(tol=1e-10, max_it=50000, precision=topo.TP_PREC_F64, warm_start=topo.TP_WARM_PREVIOUS)
+    cs = []
+    for it in range(50):
+        cs.append(p.simp_step(opts).compliance)
+    assert abs(cs[-1] - hist[-1]["c"]) <= 1e-3 * hist[-1]["c"]
+    assert abs(cs[0] - hist[0]["c"]) <= 1e-8 * hist[0]["c"]
+    p.close()
+
+
+def test_error_paths_keep_handle_usable(topo):
+    prob = W.small2d(10, 5)
+    p = topo.Problem(topo.make_params(2, 10, 5, volfrac=0.5))
+    with pytest.raises(topo.TopoError) as e:
+        p.solve(topo.solve_opts())
+    assert e.value.status == topo.TP_ERR_STATE
+    with pytest.raises(topo.TopoError) as e:
+        p.set_fixed(np.zeros(prob.n_dof, np.uint8))
+    assert e.value.status == topo.TP_ERR_ARG
+    p.set_fixed(prob.fixed)
+    bad = prob.loads.copy()
+    bad[0, 5] = np.nan
+    with pytest.raises(topo.TopoError) as e:
+        p.set_loads(bad)
+    assert e.value.status == topo.TP_ERR_ARG
+    p.set_loads(prob.loads)
+    with pytest.raises(topo.TopoError):
+        p.set_density(np.full(prob.n_el, 1.5))
+    p.set_density(np.full(prob.n_el, 0.5))
+    info = p.solve(topo.solve_opts(tol=1e-14, max_it=3, precision=topo.TP_PREC_F64), check=False)
+    assert info.status == topo.TP_ERR_NOT_CONVERGED and info.iters == 3
+    info = p.solve(topo.solve_opts(tol=1e-10, max_it=10000, precision=topo.TP_PREC_F64))
+    assert info.converged == 1
+    p.close()
