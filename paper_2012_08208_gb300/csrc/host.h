@@ -20,7 +20,7 @@ struct PcgStatus {
   int iters;
   int updates;
   int flags;          // ERR_* bits
-  int state[kMaxCases];  // 0 = not converged, 1 = converged, 2 = breakdown
+  int state[kMaxCases];  // 0 = not converged, 1 = converged, 2 = breakdown, 3 = stagnated
   double rr_true[kMaxCases];  // final true ||f - K u||^2 per case
 };
 

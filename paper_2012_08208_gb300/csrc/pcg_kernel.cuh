@@ -49,6 +49,7 @@ constexpr int SLOT_RES = 0;   // 16: rr_true[8], rz[8]
 constexpr int SLOT_A = 16;    // 8: pq[8]
 constexpr int SLOT_B = 24;    // 16: rz[8], rr[8]
 constexpr int kPartSlots = 40;
+constexpr int kStallUpdates = 6;  // updates without progress before a case stops
 
 template <int DIM, typename T, int NCM>
 __global__ void __launch_bounds__(kThreads) pcg_kernel(const __grid_constant__ PcgArgs<DIM, T> a) {
@@ -68,10 +69,12 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const __grid_constant__ P
   // same deterministic grid totals), indexed with compile-time indices only.
   int state[NCM];
   double rz[NCM], rr_ref[NCM], beta[NCM], alpha[NCM], rr_true[NCM];
+  int stall[NCM];
 #pragma unroll
   for (int c = 0; c < NCM; c++) {
     state[c] = c < nc ? 0 : 1;
     rz[c] = rr_ref[c] = beta[c] = alpha[c] = rr_true[c] = 0.0;
+    stall[c] = 0;
   }
   auto publish = [&]() {  // block-uniform coefficients to shared memory
     __syncthreads();
@@ -288,8 +291,11 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const __grid_constant__ P
 #pragma unroll
       for (int c = 0; c < NCM; c++) {
         if (state[c] != 0) continue;
+        // stagnation: the true residual no longer halves between updates
+        stall[c] = rr_true[c] > 0.25 * rr_ref[c] ? stall[c] + 1 : 0;
         rr_ref[c] = rr_true[c];
         if (rr_true[c] <= a.tol2ff[c]) state[c] = 1;
+        else if (stall[c] >= kStallUpdates) state[c] = 3;
       }
     }
 #pragma unroll
