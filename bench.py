@@ -1,0 +1,343 @@
+"""Benchmark of the GB300 SIMP hot path.
+
+Default workload: the 2D cantilever, 600 x 200 Q4 elements (241,602 DOFs), three
+load cases, passive void disk (r = 40 at (150, 100)), volfrac 0.4, rmin 3.0,
+FP32 operator with FP64 reductions and FP64 reliable updates.  One step = one
+SIMP iteration (three-case solve, sensitivities, filter, OC update) on
+device-resident data.  Metric: SIMP iterations per second (higher is better).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the single-problem path does not shard); value = iterations of all ranks / the
+slowest rank's time.  `--impl reference` times the FP64 CPU oracle on the host
+cores for the same workload and metric (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SIMP iter/s; K(rho)u GDOF/s vs HBM roofline; learned+mixed vs plain PCG @1e-6"
+WORKLOAD = "cantilever2d_600x200_3cases_passive_disk"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._th = None
+
+    def start(self):
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def stop(self):
+        self._stop.set()
+        if self._th:
+            self._th.join(timeout=10)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "", 1).isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if "Active" in s[2 + i]
+                          and not s[2 + i].startswith("Not")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def algorithmic_bytes_pcg(info, n_dof, n_el, nc):
+    """Algorithmic bytes of one mixed-precision CG launch: per CG iteration and
+    per DOF and case 58 B (FP32 operator 10 B: read u, write y, moduli; CG vectors
+    48 B), per FP64 true-residual update 60 B (FP64 operator 20 B, f, x64, x_l,
+    r, z)."""
+    return info.iters * nc * n_dof * 58.0 + info.updates * nc * n_dof * 60.0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import workloads as W
+    from paper_2012_08208_gb300 import topo
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    w = W.cantilever2d()
+    opts = topo.solve_opts(tol=w.tol, max_it=200000, precision=topo.TP_PREC_MIXED,
+                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=1e-2)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    with torch.cuda.stream(stream):
+        p = topo.Problem.from_workload(w, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            p.simp_step(opts)
+            flush.add_(1.0)
+        barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        launches0 = p.launch_count()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        infos = []
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            infos.append(p.simp_step(opts))
+            ev[k][1].record(stream)
+            flush.add_(1.0)  # L2 flush between timed steps (outside the events)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+        launches = p.launch_count() - launches0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        # end-to-end through the public API with host buffers: H2D of the step's
+        # design from pinned memory, the step, D2H of the updated design.
+        rho_h = torch.empty(w.n_el, dtype=torch.float64, pin_memory=True)
+        rho_h.numpy()[:] = p.get(topo.TP_RHO)
+        out_h = torch.empty(w.n_el, dtype=torch.float64, pin_memory=True)
+        e2e_steps = max(2, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            p.set_density(rho_h)
+            p.simp_step(opts)
+            p.get(topo.TP_RHO, out=out_h)
+            rho_h.copy_(out_h)
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        clk = clocks.stop()
+        extras = {}
+        if not args.no_extras and rank == 0:
+            extras["matvec"] = matvec_roofline(topo, torch, dev, stream)
+        p.close()
+
+    total_ms = float(sum(step_ms))
+    tmax = torch.tensor([total_ms, t_e2e], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms, t_e2e = float(tmax[0]), float(tmax[1])
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    hbm, peak_kind = _peaks()
+    # dominant kernel: the persistent CG launch (one per step); its duration is
+    # the library's CUDA-event pair around the cooperative launch on `stream`
+    solve_ms = [i.solve.ms for i in infos]
+    byts = [algorithmic_bytes_pcg(i.solve, w.n_dof, w.n_el, w.n_cases) for i in infos]
+    avg_bytes = float(np.mean(byts))
+    avg_ms = float(np.mean(solve_ms))
+    achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
+    value = ws * args.steps / (total_ms * 1e-3)
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(w, seconds=args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": "SIMP iter/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "600x200 Q4", "n_dof": w.n_dof, "n_cases": w.n_cases,
+                   "tol": w.tol, "precision": "FP32 operator + FP64 reductions/reliable updates",
+                   "warm_start": "previous iteration's displacement", "l2": "flushed between timed steps",
+                   "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": round(ws * e2e_steps / t_e2e, 4), "unit": "SIMP iter/s",
+                "h2d_bytes_per_step": w.n_el * 8, "d2h_bytes_per_step": w.n_el * 8},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "pcg_kernel<2,float,4> (persistent CG, 3 cases)", "bound": "hbm",
+                     "achieved": round(achieved, 2), "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None,
+                     "cg_iters_per_step": float(np.mean([i.solve.iters for i in infos])),
+                     "updates_per_step": float(np.mean([i.solve.updates for i in infos])),
+                     "solve_ms_per_step": round(avg_ms, 3),
+                     "note": "working set of this workload is L2-resident within a step"},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "wall_s_timed": round(t_wall, 3),
+    }
+    line.update(extras)
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def matvec_roofline(topo, torch, dev, stream):
+    """K(rho)u in FP32 on the largest 3D grid (240 x 80 x 80 H8, 4.74M DOFs):
+    GDOF/s and fraction of the HBM roofline.  Several (u, y) pairs are rotated
+    so that the data touched between two launches exceeds L2."""
+    import workloads as W
+    w = W.cantilever3d_large()
+    p = topo.Problem(topo.make_params(3, w.nelx, w.nely, w.nelz, volfrac=w.volfrac, rmin=w.rmin),
+                     stream=stream.cuda_stream)
+    p.set_fixed(w.fixed)
+    p.set_density(W.random_density(w.n_el, seed=1))
+    npair = 4
+    us = [torch.randn(w.n_dof, dtype=torch.float32, device=dev) for _ in range(npair)]
+    ys = [torch.empty(w.n_dof, dtype=torch.float32, device=dev) for _ in range(npair)]
+    for k in range(3):
+        p.matvec(us[k % npair], topo.TP_PREC_MIXED, out=ys[k % npair])
+    reps = 40
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for k in range(reps):
+        p.matvec(us[k % npair], topo.TP_PREC_MIXED, out=ys[k % npair])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    nodes = w.n_nodes
+    byts = nodes * 12 * 2 + w.n_el * 4  # read u, write y (FP32, 3 comps), read E
+    hbm, kind = _peaks()
+    ach = byts / (ms * 1e-3) / 1e9
+    p.close()
+    return {"workload": "cantilever3d_240x80x80 H8 FP32 K(rho)u", "n_dof": w.n_dof, "us_per_apply": round(ms * 1e3, 2),
+            "gdof_s": round(w.n_dof / (ms * 1e-3) / 1e9, 3), "achieved_gbs": round(ach, 1), "peak": hbm,
+            "frac": round(ach / hbm, 4), "bytes_per_apply": byts,
+            "note": "time per launch includes the host-side ctypes call; launches are back to back"}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+
+
+def _oracle_step_fn(w):
+    from oracle import filt, simp
+    Wm = filt.sparse_weights(w)
+    state = {"rho": w.initial_density()}
+
+    def step():
+        out = simp.iteration(w, state["rho"], W=Wm)
+        state["rho"] = out["rho_new"]
+        return out
+
+    return step
+
+
+def cpu_baseline(w, seconds=20.0):
+    """The oracle as it stands (SciPy assembly + SuperLU + NumPy filter/OC),
+    timed on the host for a bounded number of SIMP iterations."""
+    step = _oracle_step_fn(w)
+    n, t = 0, 0.0
+    while t < seconds and n < 3:
+        t0 = time.perf_counter()
+        step()
+        t += time.perf_counter() - t0
+        n += 1
+    return {"value": round(n / t, 5), "unit": "SIMP iter/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} SIMP iteration(s) of the same workload from the uniform start "
+                      f"(SciPy SuperLU, single-threaded), {t:.1f} s",
+            "host_cpus": os.cpu_count()}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    import workloads as W
+    w = W.cantilever2d()
+    step = _oracle_step_fn(w)
+    # warm-up: one step at most (the oracle has no caches worth warming)
+    for _ in range(min(args.warmup, 1)):
+        step()
+    budget = 150.0
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        times.append(time.perf_counter() - t0)
+        if sum(times) > budget:
+            break
+    tot = sum(times)
+    value = len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "SIMP iter/s",
+            "n_gpus": ws, "steps": len(times), "warmup": min(args.warmup, 1),
+            "ms_per_step": round(1e3 * tot / len(times), 2), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "600x200 Q4", "n_dof": w.n_dof, "n_cases": w.n_cases},
+            "cpu_baseline": {"value": round(value, 5), "unit": "SIMP iter/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} SIMP iterations (steps capped at {budget:.0f} s)"},
+            "e2e": {"value": round(value, 5), "unit": "SIMP iter/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
