@@ -2,6 +2,7 @@
 // Host-side state machine, argument validation and kernel launches.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -19,6 +20,8 @@ struct tp_problem {
   long long nn = 0, ne = 0, ndof = 0;
   int nc = 1, dim = 2, nv = 2;
   std::vector<double> K0;
+  std::vector<double> C;  // generalised-strain matrix (K0 = G^T C G)
+  int zlen = 8;           // 3D streaming tile depth
   FilterLaunch* flt = nullptr;
 
   double* rho = nullptr;
@@ -34,7 +37,8 @@ struct tp_problem {
   void* w[6] = {};  // xl, r, z, p0, p1, q (sized for double)
   double* part = nullptr;
   GridBar* bar = nullptr;
-  PcgStatus* st = nullptr;
+  CgState* cgs = nullptr;
+  double* tol2 = nullptr;
   OcStatus* ost = nullptr;
   double* scal = nullptr;
   double* dc = nullptr;
@@ -81,7 +85,7 @@ cudaError_t dalloc(T** ptr, size_t count) {
 void free_all(tp_problem* p) {
   void* ptrs[] = {p->rho, p->rho_new, p->E32, p->E64, p->mask, p->passive, p->f, p->x64,
                   p->inv32, p->inv64, p->w[0], p->w[1], p->w[2], p->w[3], p->w[4], p->w[5],
-                  p->part, p->bar, p->st, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi};
+                  p->part, p->bar, p->cgs, p->tol2, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -149,6 +153,13 @@ tp_status tp_create_problem(const tp_params* params, void* cuda_stream, tp_probl
   const int nd = q.dim == 2 ? 8 : 24;
   p->K0.resize(nd * nd);
   element_k0(q.dim, q.nu, p->K0.data());
+  p->C.resize(18 * 18);
+  double recon = 0.0;
+  element_strain_C(q.dim, p->K0.data(), p->C.data(), &recon);
+  if (!(recon < 1e-12)) {
+    delete p;
+    return TP_ERR_ARG;
+  }
   p->flt = new FilterLaunch();
   p->flt->g = p->g;
   p->flt->ntaps = filter_taps(q.dim, q.rmin, kMaxTaps, p->flt->off, p->flt->w);
@@ -173,9 +184,14 @@ tp_status tp_create_problem(const tp_params* params, void* cuda_stream, tp_probl
   if (e == cudaSuccess) e = dalloc(&p->inv32, p->ndof);
   if (e == cudaSuccess) e = dalloc(&p->inv64, p->ndof);
   for (int i = 0; i < 6 && e == cudaSuccess; i++) e = dalloc((double**)&p->w[i], nvals);
-  if (e == cudaSuccess) e = dalloc(&p->part, (size_t)48 * maxgrid);
+  // partial sums: CG segment slots (24 per CTA) or residual tiles (16 per tile)
+  // (tile count bound: 32 x 8 node tiles, one plane deep in 3D)
+  const size_t tiles_bound = (size_t)((nx + 31) / 32) * (size_t)((ny + 7) / 8) * (size_t)nz;
+  const size_t npart = std::max<size_t>((size_t)48 * maxgrid, (size_t)16 * tiles_bound);
+  if (e == cudaSuccess) e = dalloc(&p->part, npart);
   if (e == cudaSuccess) e = dalloc(&p->bar, 1);
-  if (e == cudaSuccess) e = dalloc(&p->st, 1);
+  if (e == cudaSuccess) e = dalloc(&p->cgs, 1);
+  if (e == cudaSuccess) e = dalloc(&p->tol2, kMaxCases);
   if (e == cudaSuccess) e = dalloc(&p->ost, 1);
   if (e == cudaSuccess) e = dalloc(&p->scal, 16);
   if (e == cudaSuccess) e = dalloc(&p->dc, p->ne);
@@ -302,36 +318,50 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
   if (opts->warm_start == TP_WARM_ZERO || (opts->warm_start == TP_WARM_PREVIOUS && !p->has_u))
     TPCK(cudaMemsetAsync(p->x64, 0, nvals * sizeof(double), p->stream), "memset");
   TPCK(cudaMemsetAsync(p->w[0], 0, nvals * (f64 ? 8 : 4), p->stream), "memset");
-  TPCK(cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream), "memset");
-  PcgLaunch L;
-  L.g = p->g;
-  L.nc = p->nc;
-  L.E = f64 ? (const void*)p->E64 : (const void*)p->E32;
-  L.E64 = p->E64;
-  L.mask = p->mask;
-  L.invdiag = f64 ? (const void*)p->inv64 : (const void*)p->inv32;
-  L.f = p->f;
-  L.x64 = p->x64;
-  L.xl = p->w[0];
-  L.r = p->w[1];
-  L.z = p->w[2];
-  L.p0 = p->w[3];
-  L.p1 = p->w[4];
-  L.q = p->w[5];
-  L.part = p->part;
-  L.bar = p->bar;
-  L.st = p->st;
-  for (int c = 0; c < kMaxCases; c++) L.tol2ff[c] = c < p->nc ? opts->tol * opts->tol * p->ff[c] : 0.0;
-  L.drop2 = f64 ? 0.0 : drop * drop;
-  L.max_it = opts->max_it;
-  L.K0 = p->K0.data();
+  Solver S;
+  S.g = p->g;
+  S.nc = p->nc;
+  S.zlen = p->zlen;
+  S.E = f64 ? (const void*)p->E64 : (const void*)p->E32;
+  S.E64 = p->E64;
+  S.mask = p->mask;
+  S.invdiag = f64 ? (const void*)p->inv64 : (const void*)p->inv32;
+  S.f = p->f;
+  S.x64 = p->x64;
+  S.xl = p->w[0];
+  S.r = p->w[1];
+  S.z = p->w[2];
+  S.p0 = p->w[3];
+  S.p1 = p->w[4];
+  S.q = p->w[5];
+  S.part = p->part;
+  S.tol2ff_dev = p->tol2;
+  S.bar = p->bar;
+  S.cs = p->cgs;
+  for (int c = 0; c < kMaxCases; c++) S.tol2ff[c] = c < p->nc ? opts->tol * opts->tol * p->ff[c] : 0.0;
+  S.drop2 = f64 ? 0.0 : drop * drop;
+  S.max_it = opts->max_it;
+  S.C = p->C.data();
+  TPCK(cudaMemcpyAsync(p->tol2, S.tol2ff, sizeof(S.tol2ff), cudaMemcpyHostToDevice, p->stream), "copy");
   TPCK(cudaEventRecord(p->ev0, p->stream), "event");
-  TPCK(launch_pcg(p->stream, L, f64, p->nsm, &p->last_grid), "cg kernel");
-  p->launches++;
+  int nl = 0;
+  TPCK(launch_true_residual(p->stream, S, f64, true, &nl), "residual kernel");
+  p->launches += nl;
+  CgState st;
+  for (int guard = 0; guard < 1000000; guard++) {
+    TPCK(cudaMemcpyAsync(&st, p->cgs, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "copy state");
+    TPCK(cudaStreamSynchronize(p->stream), "sync");
+    bool active = false;
+    for (int c = 0; c < p->nc; c++) active |= st.state[c] == 0;
+    if (!active || st.it >= opts->max_it || (st.flags & ERR_TIMEOUT)) break;
+    TPCK(cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream), "memset");
+    TPCK(launch_cg_segment(p->stream, S, f64, p->nsm, &p->last_grid), "cg kernel");
+    p->launches++;
+    TPCK(launch_true_residual(p->stream, S, f64, false, &nl), "residual kernel");
+    p->launches += nl;
+  }
   TPCK(cudaEventRecord(p->ev1, p->stream), "event");
-  PcgStatus st;
-  TPCK(cudaMemcpyAsync(&st, p->st, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "copy status");
-  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  TPCK(cudaEventSynchronize(p->ev1), "sync");
   float ms = 0.f;
   cudaEventElapsedTime(&ms, p->ev0, p->ev1);
   p->has_u = true;
@@ -347,7 +377,7 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
   else if (!conv) rs = TP_ERR_NOT_CONVERGED;
   if (info) {
     memset(info, 0, sizeof(*info));
-    info->iters = st.iters;
+    info->iters = st.it;
     info->updates = st.updates;
     info->converged = conv ? 1 : 0;
     info->status = rs;
@@ -356,7 +386,8 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
   }
   if (rs == TP_ERR_TIMEOUT) return fail(p, rs, "a device-side wait timed out in the CG kernel");
   if (rs == TP_ERR_BREAKDOWN) return fail(p, rs, "CG breakdown (p^T K p <= 0 or not finite)");
-  if (rs == TP_ERR_NOT_CONVERGED) return fail(p, rs, "CG reached max_it before the tolerance");
+  if (rs == TP_ERR_NOT_CONVERGED)
+    return fail(p, rs, "CG stopped before the tolerance (max_it reached or the true residual stagnated)");
   return TP_OK;
 }
 
@@ -364,7 +395,7 @@ tp_status tp_sensitivities(tp_problem* p, double* compliance) {
   if (!p) return TP_ERR_ARG;
   if (!p->has_u) return fail(p, TP_ERR_STATE, "tp_solve must precede tp_sensitivities");
   const double dE = p->prm.E0 - p->prm.Emin;
-  TPCK(launch_sens(p->stream, p->g, p->nc, p->K0.data(), p->x64, p->f, p->rho, p->prm.penal, dE, p->ce,
+  TPCK(launch_sens(p->stream, p->g, p->nc, p->C.data(), p->x64, p->f, p->rho, p->prm.penal, dE, p->ce,
                    p->dc, p->part, p->scal),
        "sensitivity kernel");
   p->launches += 2;
@@ -506,8 +537,8 @@ tp_status tp_matvec(tp_problem* p, const void* u, void* y, int precision, int nc
     du = tmp;
     dy = (char*)tmp + bytes;
   }
-  cudaError_t e = launch_matvec(p->stream, p->g, p->K0.data(), f64, f64 ? (const void*)p->E64 : (const void*)p->E32,
-                                p->mask, du, dy, ncopies);
+  cudaError_t e = launch_matvec(p->stream, p->g, p->C.data(), f64,
+                                f64 ? (const void*)p->E64 : (const void*)p->E32, p->mask, du, dy, ncopies, p->zlen);
   p->launches++;
   if (e == cudaSuccess && !on_device) e = cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);

@@ -102,3 +102,106 @@ int filter_taps(int dim, double rmin, int max_taps, int* off, double* wts) {
 }
 
 }  // namespace tp
+
+namespace tp {
+
+// Generalised-strain factorisation K0 = G^T C G.
+//
+// G maps the element displacement vector to generalised strains: Walsh sums
+// over the element corners of each displacement component (with weights
+// s_x^a s_y^b s_z^c, s = +-1 by corner position), excluding the rigid-body
+// combinations.  Its rows are mutually orthogonal, so C follows from the
+// projection C = N^-1 G K0 G^T N^-1 with N = G G^T (diagonal).  Rigid modes lie
+// in the null space of G exactly, which keeps them exact in FP32 arithmetic.
+//
+// Row order (2D, 5 rows): a_x(10), a_y(01), a_x(01)+a_y(10), a_x(11), a_y(11)
+// Row order (3D, 18 rows), grouped by reflection-symmetry class:
+//   0..2  a_x(100), a_y(010), a_z(001)
+//   3..4  a_x(010)+a_y(100), a_z(111)
+//   5..6  a_x(001)+a_z(100), a_y(111)
+//   7..8  a_y(001)+a_z(010), a_x(111)
+//   9..10 a_y(110), a_z(101)
+//  11..12 a_x(110), a_z(011)
+//  13..14 a_x(101), a_y(011)
+//  15..17 a_x(011), a_y(101), a_z(110)
+// where a_i(abc) = sum over corners of s_x^a s_y^b s_z^c u_i(corner).
+
+static void strain_rows(int dim, std::vector<std::vector<double>>& G) {
+  const int nnode = dim == 2 ? 4 : 8, nd = dim * nnode;
+  auto walsh = [&](int comp, int a, int b, int c) {
+    std::vector<double> r(nd, 0.0);
+    for (int k = 0; k < nnode; k++) {
+      const double sx = corner_off(k, 0) ? 1.0 : -1.0, sy = corner_off(k, 1) ? 1.0 : -1.0;
+      const double sz = corner_off(k, 2) ? 1.0 : -1.0;
+      double w = 1.0;
+      if (a) w *= sx;
+      if (b) w *= sy;
+      if (c) w *= sz;
+      r[dim * k + comp] = w;
+    }
+    return r;
+  };
+  auto add = [](std::vector<double> a, const std::vector<double>& b) {
+    for (size_t i = 0; i < a.size(); i++) a[i] += b[i];
+    return a;
+  };
+  G.clear();
+  if (dim == 2) {
+    G.push_back(walsh(0, 1, 0, 0));
+    G.push_back(walsh(1, 0, 1, 0));
+    G.push_back(add(walsh(0, 0, 1, 0), walsh(1, 1, 0, 0)));
+    G.push_back(walsh(0, 1, 1, 0));
+    G.push_back(walsh(1, 1, 1, 0));
+    return;
+  }
+  G.push_back(walsh(0, 1, 0, 0));
+  G.push_back(walsh(1, 0, 1, 0));
+  G.push_back(walsh(2, 0, 0, 1));
+  G.push_back(add(walsh(0, 0, 1, 0), walsh(1, 1, 0, 0)));
+  G.push_back(walsh(2, 1, 1, 1));
+  G.push_back(add(walsh(0, 0, 0, 1), walsh(2, 1, 0, 0)));
+  G.push_back(walsh(1, 1, 1, 1));
+  G.push_back(add(walsh(1, 0, 0, 1), walsh(2, 0, 1, 0)));
+  G.push_back(walsh(0, 1, 1, 1));
+  G.push_back(walsh(1, 1, 1, 0));
+  G.push_back(walsh(2, 1, 0, 1));
+  G.push_back(walsh(0, 1, 1, 0));
+  G.push_back(walsh(2, 0, 1, 1));
+  G.push_back(walsh(0, 1, 0, 1));
+  G.push_back(walsh(1, 0, 1, 1));
+  G.push_back(walsh(0, 0, 1, 1));
+  G.push_back(walsh(1, 1, 0, 1));
+  G.push_back(walsh(2, 1, 1, 0));
+}
+
+int element_strain_C(int dim, const double* K0, double* C, double* recon_err) {
+  std::vector<std::vector<double>> G;
+  strain_rows(dim, G);
+  const int ng = (int)G.size(), nd = (int)G[0].size();
+  std::vector<double> N(ng);
+  for (int i = 0; i < ng; i++) {
+    double s = 0.0;
+    for (int k = 0; k < nd; k++) s += G[i][k] * G[i][k];
+    N[i] = s;
+  }
+  for (int i = 0; i < ng; i++)
+    for (int j = 0; j < ng; j++) {
+      double s = 0.0;
+      for (int a = 0; a < nd; a++)
+        for (int b = 0; b < nd; b++) s += G[i][a] * K0[a * nd + b] * G[j][b];
+      C[i * ng + j] = s / (N[i] * N[j]);
+    }
+  // reconstruction check: G^T C G == K0
+  double err = 0.0;
+  for (int a = 0; a < nd; a++)
+    for (int b = 0; b < nd; b++) {
+      double s = 0.0;
+      for (int i = 0; i < ng; i++)
+        for (int j = 0; j < ng; j++) s += G[i][a] * C[i * ng + j] * G[j][b];
+      err = std::fmax(err, std::fabs(s - K0[a * nd + b]));
+    }
+  if (recon_err) *recon_err = err;
+  return ng;
+}
+
+}  // namespace tp

@@ -1,18 +1,22 @@
 // Matrix-free finite-element kernels of the GB300 SIMP library:
 //   * modified-SIMP moduli E_e = Emin + rho_e^p (E0 - Emin)
-//   * the density-penalised operator y = sum_e E_e K0 u_e (Q4 / H8), node-owner
-//     gather from a shared-memory tile (no atomics, deterministic)
-//   * Jacobi diagonal
-//   * the persistent Jacobi-preconditioned CG (one cooperative launch per solve,
-//     all load cases in lock-step, FP64 dot products, FP64 reliable updates)
+//   * Jacobi diagonal of K(rho)
+//   * the boundary-conditioned operator y = K(rho) u (tile operators of tileop.cuh)
+//   * the FP64 true-residual update of the CG (x64 += x_l; r = f - K64 x64)
 //   * compliance and element sensitivities
 // The discrete system is that of Section 3.1 (Eq. "fe_form") with the SIMP
-// penalisation of Eq. "simp_fn"; the CG replaces the sparse LU of Section 4.3.
-#include <cstdio>
-
-#include "tile.cuh"
+// penalisation of Eq. "simp_fn"; the element energy u_e^T K0 u_e enters the
+// sensitivity of Section 3.2.
+#include "pcg_common.cuh"
 
 namespace tp {
+
+static int grid_for(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
 
 // ---------------------------------------------------------------------------
 // Moduli, diagonal, layout conversion.
@@ -41,7 +45,7 @@ struct DiagArgs {
 
 template <int DIM>
 __global__ void diag_kernel(const __grid_constant__ DiagArgs<DIM> a) {
-  using G = TileGeom<DIM>;
+  constexpr int NCORN = DIM == 2 ? 4 : 8;
   const Grid& g = a.g;
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < g.nn;
        n += (long long)gridDim.x * blockDim.x) {
@@ -50,7 +54,7 @@ __global__ void diag_kernel(const __grid_constant__ DiagArgs<DIM> a) {
 #pragma unroll
     for (int r = 0; r < DIM; r++) d[r] = 0.0;
 #pragma unroll
-    for (int cn = 0; cn < G::NCORN; cn++) {
+    for (int cn = 0; cn < NCORN; cn++) {
       const int ex = x - cofs(cn, 0), ey = y - cofs(cn, 1), ez = DIM == 3 ? z - cofs(cn, 2) : 0;
       if (ex < 0 || ey < 0 || ez < 0 || ex >= g.ex || ey >= g.ey || ez >= g.ez) continue;
       const double E = a.E64[ex + (long long)g.ex * (ey + (long long)g.ey * ez)];
@@ -94,50 +98,226 @@ __global__ void to_abi_kernel(const double* __restrict__ src, double* dst, long 
 }
 
 // ---------------------------------------------------------------------------
-// Standalone operator application (boundary-conditioned): y = K u on free DOFs
-// with fixed entries of u read as 0, y = u on fixed DOFs.
+// Standalone boundary-conditioned operator: y = K u on free DOFs with the fixed
+// entries of u read as 0, y = u on fixed DOFs.  One CTA per tile; blockIdx.y
+// selects the vector (stride n_dof).
 
 template <int DIM, typename T>
 struct MvArgs {
   Grid g;
-  TileMap<DIM> tm;
+  TileMapG tm;
   const T* E;
   const uint8_t* mask;
   const T* u;
   T* y;
   long long stride;
-  KMat<DIM, T> k;
+  CMat<DIM, T> C;
 };
 
 template <int DIM, typename T>
-__global__ void __launch_bounds__(kThreads) matvec_kernel(const __grid_constant__ MvArgs<DIM, T> a) {
-  using G = TileGeom<DIM>;
+__global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
+    matvec_kernel(const __grid_constant__ MvArgs<DIM, T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sP = reinterpret_cast<T*>(smem_raw);
-  T* sE = sP + G::HN * DIM;
   const T* u = a.u + blockIdx.y * a.stride;
   T* y = a.y + blockIdx.y * a.stride;
-  int x0, y0, z0;
-  tile_origin<DIM>(a.tm, blockIdx.x, x0, y0, z0);
-  load_E<DIM, T>(a.g, x0, y0, z0, a.E, sE);
-  load_halo<DIM, T>(a.g, x0, y0, z0, DIM, sP, [&](long long node, int v, bool) -> T {
-    return ((a.mask[node] >> v) & 1) ? T(0) : u[node * DIM + v];
-  });
-  __syncthreads();
-  for (int ln = threadIdx.x; ln < G::TN; ln += blockDim.x) {
-    int tx, ty, tz;
-    long long node;
-    if (!own_node<DIM>(a.g, ln, x0, y0, z0, tx, ty, tz, node)) continue;
-    T acc[DIM];
-    node_apply<DIM, T>(sP, sE, DIM, 0, tx, ty, tz, a.k, acc);
-    const uint8_t mk = a.mask[node];
+  TileOp<DIM, T>::apply(
+      a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw,
+      [&](long long node, int comp, bool) -> T {
+        return ((a.mask[node] >> comp) & 1) ? T(0) : u[node * DIM + comp];
+      },
+      [&](long long node, const T(&yv)[DIM], const T(&)[DIM]) {
+        const uint8_t mk = a.mask[node];
 #pragma unroll
-    for (int r = 0; r < DIM; r++) y[node * DIM + r] = ((mk >> r) & 1) ? u[node * DIM + r] : acc[r];
-  }
+        for (int r = 0; r < DIM; r++) y[node * DIM + r] = ((mk >> r) & 1) ? u[node * DIM + r] : yv[r];
+      });
+}
+
+template <int DIM, typename T>
+static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, const void* E,
+                               const uint8_t* mask, const void* u, void* y, int ncopies, int zlen) {
+  using Op = TileOp<DIM, T>;
+  MvArgs<DIM, T> a;
+  a.g = g;
+  a.tm = Op::map(g, zlen);
+  a.E = (const T*)E;
+  a.mask = mask;
+  a.u = (const T*)u;
+  a.y = (T*)y;
+  a.stride = g.nn * DIM;
+  fill_c<DIM, T>(a.C, C);
+  const size_t smem = Op::smem_bytes();
+  auto kern = matvec_kernel<DIM, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(a.tm.ntiles, ncopies), Op::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f64, const void* E,
+                          const uint8_t* mask, const void* u, void* y, int ncopies, int zlen) {
+  if (g.dim == 2)
+    return f64 ? matvec_impl<2, double>(s, g, C, E, mask, u, y, ncopies, zlen)
+               : matvec_impl<2, float>(s, g, C, E, mask, u, y, ncopies, zlen);
+  return f64 ? matvec_impl<3, double>(s, g, C, E, mask, u, y, ncopies, zlen)
+             : matvec_impl<3, float>(s, g, C, E, mask, u, y, ncopies, zlen);
 }
 
 // ---------------------------------------------------------------------------
-// Compliance and sensitivities (FP64).
+// FP64 true-residual update.
+
+template <typename T>
+__global__ void merge_kernel(double* x64, T* xl, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    x64[i] += (double)xl[i];
+    xl[i] = T(0);
+  }
+}
+
+template <int DIM, typename T>
+struct ResArgs {
+  Grid g;
+  TileMapG tm;
+  int nc, nv;
+  const double* E64;
+  const uint8_t* mask;
+  const T* invd;
+  const double* f;
+  const double* x64;
+  T* r;
+  T* z;
+  double* part;  // [16][gridDim.x]: rr_true[8], rz[8]
+  CMat<DIM, double> C;
+};
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(TileOp<DIM, double>::THREADS)
+    residual_kernel(const __grid_constant__ ResArgs<DIM, T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sRed[32 * 16];
+  double acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; i++) acc[i] = 0.0;
+  for (int cs = 0; cs < a.nc; cs++) {
+    double srr = 0.0, srz = 0.0;
+    TileOp<DIM, double>::apply(
+        a.g, a.tm, blockIdx.x, a.E64, a.C, smem_raw,
+        [&](long long node, int comp, bool) -> double {
+          return ((a.mask[node] >> comp) & 1) ? 0.0 : a.x64[node * a.nv + cs * DIM + comp];
+        },
+        [&](long long node, const double(&yv)[DIM], const double(&)[DIM]) {
+          const uint8_t mk = a.mask[node];
+#pragma unroll
+          for (int r = 0; r < DIM; r++) {
+            const long long idx = node * a.nv + cs * DIM + r;
+            const double r64 = ((mk >> r) & 1) ? 0.0 : a.f[idx] - yv[r];
+            const T rt = (T)r64;
+            const T zt = rt * a.invd[node * DIM + r];
+            a.r[idx] = rt;
+            a.z[idx] = zt;
+            srr += r64 * r64;
+            srz += (double)rt * (double)zt;
+          }
+        });
+    addto<16>(acc, cs, srr);
+    addto<16>(acc, 8 + cs, srz);
+  }
+  block_sum<16>(acc, sRed);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 16; i++) a.part[(size_t)i * gridDim.x + blockIdx.x] = acc[i];
+}
+
+// Sums the residual partials in block order and advances the CG state.
+__global__ void residual_finalize_kernel(const double* part, int nblocks, int nc, CgState* cs,
+                                         const double* tol2ff, int init) {
+  __shared__ double sRed[32 * 16];
+  double tot[16];
+  for (int i = 0; i < 16; i++) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += part[(size_t)i * nblocks + b];
+    tot[i] = s;
+  }
+  block_sum<16>(tot, sRed);
+  if (threadIdx.x != 0) return;
+  if (init) {
+    cs->it = 0;
+    cs->pbuf = 0;
+    cs->flags = 0;
+    cs->updates = 0;
+  }
+  cs->need = 0;
+  cs->updates += 1;
+  for (int c = 0; c < kMaxCases; c++) {
+    const double rr = tot[c], rz = tot[8 + c];
+    if (init) {
+      cs->state[c] = c < nc ? 0 : 1;
+      cs->stall[c] = 0;
+      cs->rr_ref[c] = rr;
+      cs->rr_true[c] = rr;
+      cs->beta[c] = 0.0;
+      cs->rz[c] = rz;
+      if (c < nc && rr <= tol2ff[c]) cs->state[c] = 1;
+      continue;
+    }
+    if (c >= nc) continue;
+    cs->rr_true[c] = rr;
+    if (cs->state[c] != 0) continue;
+    // stagnation: the true residual no longer halves between updates
+    cs->stall[c] = rr > 0.25 * cs->rr_ref[c] ? cs->stall[c] + 1 : 0;
+    cs->rr_ref[c] = rr;
+    const double rz_old = cs->rz[c];
+    cs->beta[c] = rz_old != 0.0 ? rz / rz_old : 0.0;
+    cs->rz[c] = rz;
+    if (rr <= tol2ff[c]) cs->state[c] = 1;
+    else if (cs->stall[c] >= 6) cs->state[c] = 3;
+  }
+}
+
+template <int DIM, typename T>
+static cudaError_t residual_impl(cudaStream_t s, const Solver& S, bool init, int* nl) {
+  using Op = TileOp<DIM, double>;
+  const long long nvals = S.g.nn * S.nc * DIM;
+  *nl = 0;
+  if (!init) {
+    merge_kernel<T><<<grid_for(nvals), 256, 0, s>>>(S.x64, (T*)S.xl, nvals);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    (*nl)++;
+  }
+  ResArgs<DIM, T> a;
+  a.g = S.g;
+  a.tm = Op::map(S.g, S.zlen);
+  a.nc = S.nc;
+  a.nv = S.nc * DIM;
+  a.E64 = S.E64;
+  a.mask = S.mask;
+  a.invd = (const T*)S.invdiag;
+  a.f = S.f;
+  a.x64 = S.x64;
+  a.r = (T*)S.r;
+  a.z = (T*)S.z;
+  a.part = S.part;
+  fill_c<DIM, double>(a.C, S.C);
+  const size_t smem = Op::smem_bytes();
+  auto kern = residual_kernel<DIM, T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<a.tm.ntiles, Op::THREADS, smem, s>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  residual_finalize_kernel<<<1, 256, 0, s>>>(S.part, a.tm.ntiles, S.nc, S.cs, S.tol2ff_dev, init ? 1 : 0);
+  *nl += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_true_residual(cudaStream_t s, const Solver& S, bool f64, bool init, int* nl) {
+  if (S.g.dim == 2)
+    return f64 ? residual_impl<2, double>(s, S, init, nl) : residual_impl<2, float>(s, S, init, nl);
+  return f64 ? residual_impl<3, double>(s, S, init, nl) : residual_impl<3, float>(s, S, init, nl);
+}
+
+// ---------------------------------------------------------------------------
+// Compliance and sensitivities (FP64).  ce_e = sum_k u_e^T K0 u_e = g^T C g.
 
 template <int DIM>
 struct SensArgs {
@@ -150,12 +330,11 @@ struct SensArgs {
   double* ce;
   double* dc;
   double* part;
-  KMat<DIM, double> kD;
+  CMat<DIM, double> C;
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(kThreads) sens_kernel(const __grid_constant__ SensArgs<DIM> a) {
-  using G = TileGeom<DIM>;
+__global__ void __launch_bounds__(256) sens_kernel(const __grid_constant__ SensArgs<DIM> a) {
   __shared__ double sRed[32];
   const Grid& g = a.g;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.ne;
@@ -164,23 +343,26 @@ __global__ void __launch_bounds__(kThreads) sens_kernel(const __grid_constant__ 
     const int ez = DIM == 3 ? (int)(e / ((long long)g.ex * g.ey)) : 0;
     double ce = 0.0;
     for (int cs = 0; cs < a.nc; cs++) {
-      double u[G::ND];
+      if constexpr (DIM == 2) {
+        double ux[4], uy[4];
 #pragma unroll
-      for (int m = 0; m < G::NCORN; m++) {
-        const long long node =
-            (ex + cofs(m, 0)) + (long long)g.nx * ((ey + cofs(m, 1)) + (long long)g.ny * (ez + (DIM == 3 ? cofs(m, 2) : 0)));
+        for (int m = 0; m < 4; m++) {
+          const long long node = (ex + cofs(m, 0)) + (long long)g.nx * (ey + cofs(m, 1));
+          ux[m] = a.x64[node * a.nv + cs * 2];
+          uy[m] = a.x64[node * a.nv + cs * 2 + 1];
+        }
+        ce += q4_energy(ux, uy, a.C);
+      } else {
+        double u[8][3];
 #pragma unroll
-        for (int s = 0; s < DIM; s++) u[DIM * m + s] = a.x64[node * a.nv + cs * DIM + s];
+        for (int m = 0; m < 8; m++) {
+          const long long node = (ex + cofs(m, 0)) +
+                                 (long long)g.nx * ((ey + cofs(m, 1)) + (long long)g.ny * (ez + cofs(m, 2)));
+#pragma unroll
+          for (int s = 0; s < 3; s++) u[m][s] = a.x64[node * a.nv + cs * 3 + s];
+        }
+        ce += h8_energy(u, a.C);
       }
-      double t = 0.0;
-#pragma unroll
-      for (int i = 0; i < G::ND; i++) {
-        double si = 0.0;
-#pragma unroll
-        for (int j = 0; j < G::ND; j++) si = fma(a.kD.k[i * G::ND + j], u[j], si);
-        t = fma(u[i], si, t);
-      }
-      ce += t;
     }
     const double r = a.rho[e];
     const double rp1 = a.penal == 3.0 ? r * r : pow(r, a.penal - 1.0);
@@ -205,8 +387,40 @@ __global__ void final_sum_kernel(const double* part, int n, double* out) {
   if (threadIdx.x == 0) out[0] = s[0];
 }
 
+template <int DIM>
+static cudaError_t sens_impl(cudaStream_t s, const Grid& g, int nc, const double* C, const double* x64,
+                             const double* f, const double* rho, double penal, double dE, double* ce,
+                             double* dc, double* part, double* out_c) {
+  SensArgs<DIM> a;
+  a.g = g;
+  a.nc = nc;
+  a.nv = nc * DIM;
+  a.x64 = x64;
+  a.f = f;
+  a.rho = rho;
+  a.penal = penal;
+  a.dE = dE;
+  a.ce = ce;
+  a.dc = dc;
+  a.part = part;
+  fill_c<DIM, double>(a.C, C);
+  const int grid = grid_for(g.ne > g.nn * nc * DIM ? g.ne : g.nn * nc * DIM);
+  sens_kernel<DIM><<<grid, 256, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  final_sum_kernel<<<1, 256, 0, s>>>(part, grid, out_c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sens(cudaStream_t s, const Grid& g, int nc, const double* C, const double* x64,
+                        const double* f, const double* rho, double penal, double dE, double* ce,
+                        double* dc, double* part, double* out_c) {
+  return g.dim == 2 ? sens_impl<2>(s, g, nc, C, x64, f, rho, penal, dE, ce, dc, part, out_c)
+                    : sens_impl<3>(s, g, nc, C, x64, f, rho, penal, dE, ce, dc, part, out_c);
+}
+
 // ---------------------------------------------------------------------------
-// Host launchers.
+// Launchers: moduli, diagonal, layouts.
 
 cudaError_t launch_young(cudaStream_t s, const double* rho, float* E32, double* E64, long long ne,
                          double E0, double Emin, double penal) {
@@ -223,7 +437,7 @@ static cudaError_t diag_impl(cudaStream_t s, const Grid& g, const double* K0, co
   a.mask = mask;
   a.inv32 = inv32;
   a.inv64 = inv64;
-  constexpr int nd = TileGeom<DIM>::ND;
+  constexpr int nd = DIM * (DIM == 2 ? 4 : 8);
   for (int i = 0; i < nd; i++) a.kd[i] = K0[i * nd + i];
   diag_kernel<DIM><<<grid_for(g.nn), 256, 0, s>>>(a);
   return cudaGetLastError();
@@ -233,73 +447,6 @@ cudaError_t launch_diag(cudaStream_t s, const Grid& g, const double* K0, const d
                         const uint8_t* mask, float* inv32, double* inv64) {
   return g.dim == 2 ? diag_impl<2>(s, g, K0, E64, mask, inv32, inv64)
                     : diag_impl<3>(s, g, K0, E64, mask, inv32, inv64);
-}
-
-template <int DIM, typename T>
-static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* K0, const void* E,
-                               const uint8_t* mask, const void* u, void* y, int ncopies) {
-  using G = TileGeom<DIM>;
-  MvArgs<DIM, T> a;
-  a.g = g;
-  a.tm = tile_map<DIM>(g);
-  a.E = (const T*)E;
-  a.mask = mask;
-  a.u = (const T*)u;
-  a.y = (T*)y;
-  a.stride = g.nn * DIM;
-  fill_k<DIM, T>(a.k, K0);
-  const size_t smem = (size_t)(G::HN * DIM + G::EN) * sizeof(T);
-  dim3 grid(a.tm.ntiles, ncopies);
-  matvec_kernel<DIM, T><<<grid, kThreads, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* K0, bool f64, const void* E,
-                          const uint8_t* mask, const void* u, void* y, int ncopies) {
-  if (g.dim == 2)
-    return f64 ? matvec_impl<2, double>(s, g, K0, E, mask, u, y, ncopies)
-               : matvec_impl<2, float>(s, g, K0, E, mask, u, y, ncopies);
-  return f64 ? matvec_impl<3, double>(s, g, K0, E, mask, u, y, ncopies)
-             : matvec_impl<3, float>(s, g, K0, E, mask, u, y, ncopies);
-}
-
-cudaError_t launch_pcg2(cudaStream_t s, const PcgLaunch& L, bool f64, int nsm, int* grid_out);
-cudaError_t launch_pcg3(cudaStream_t s, const PcgLaunch& L, bool f64, int nsm, int* grid_out);
-
-cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch& L, bool f64, int nsm, int* grid_out) {
-  return L.g.dim == 2 ? launch_pcg2(s, L, f64, nsm, grid_out) : launch_pcg3(s, L, f64, nsm, grid_out);
-}
-
-template <int DIM>
-static cudaError_t sens_impl(cudaStream_t s, const Grid& g, int nc, const double* K0, const double* x64,
-                             const double* f, const double* rho, double penal, double dE, double* ce,
-                             double* dc, double* part, double* out_c) {
-  SensArgs<DIM> a;
-  a.g = g;
-  a.nc = nc;
-  a.nv = nc * DIM;
-  a.x64 = x64;
-  a.f = f;
-  a.rho = rho;
-  a.penal = penal;
-  a.dE = dE;
-  a.ce = ce;
-  a.dc = dc;
-  a.part = part;
-  fill_k<DIM, double>(a.kD, K0);
-  const int grid = grid_for(g.ne > g.nn * nc * DIM ? g.ne : g.nn * nc * DIM);
-  sens_kernel<DIM><<<grid, kThreads, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  final_sum_kernel<<<1, 256, 0, s>>>(part, grid, out_c);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sens(cudaStream_t s, const Grid& g, int nc, const double* K0, const double* x64,
-                        const double* f, const double* rho, double penal, double dE, double* ce,
-                        double* dc, double* part, double* out_c) {
-  return g.dim == 2 ? sens_impl<2>(s, g, nc, K0, x64, f, rho, penal, dE, ce, dc, part, out_c)
-                    : sens_impl<3>(s, g, nc, K0, x64, f, rho, penal, dE, ce, dc, part, out_c);
 }
 
 cudaError_t launch_to_internal(cudaStream_t s, const double* src, double* dst, long long nn, int dim,
@@ -313,4 +460,12 @@ cudaError_t launch_to_abi(cudaStream_t s, const double* src, double* dst, long l
   return cudaGetLastError();
 }
 
+}  // namespace tp
+
+namespace tp {
+cudaError_t launch_cg_segment2(cudaStream_t s, const Solver& S, bool f64, int nsm, int* grid_out);
+cudaError_t launch_cg_segment3(cudaStream_t s, const Solver& S, bool f64, int nsm, int* grid_out);
+cudaError_t launch_cg_segment(cudaStream_t s, const Solver& S, bool f64, int nsm, int* grid_out) {
+  return S.g.dim == 2 ? launch_cg_segment2(s, S, f64, nsm, grid_out) : launch_cg_segment3(s, S, f64, nsm, grid_out);
+}
 }  // namespace tp

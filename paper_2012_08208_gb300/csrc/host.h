@@ -14,24 +14,34 @@ constexpr int kMaxTaps = 512;
 // Element stiffness (host, FP64) and filter stencil.
 void element_k0(int dim, double nu, double* K);
 int filter_taps(int dim, double rmin, int max_taps, int* off, double* wts);
+// K0 = G^T C G with generalised strains G (5 rows in 2D, 18 in 3D); returns the row count.
+int element_strain_C(int dim, const double* K0, double* C, double* recon_err);
 
-// Per-solve status written by the persistent CG kernel.
-struct PcgStatus {
-  int iters;
-  int updates;
-  int flags;          // ERR_* bits
-  int state[kMaxCases];  // 0 = not converged, 1 = converged, 2 = breakdown, 3 = stagnated
-  double rr_true[kMaxCases];  // final true ||f - K u||^2 per case
+// CG state kept in device memory between the persistent CG segments and the
+// FP64 true-residual updates.
+struct CgState {
+  int it;        // CG iterations so far
+  int pbuf;      // which of the two direction buffers holds the current p
+  int need;      // segment ended because an update is due
+  int flags;     // ERR_* bits
+  int updates;   // FP64 true-residual evaluations
+  int state[kMaxCases];  // 0 = active, 1 = converged, 2 = breakdown, 3 = stagnated
+  int stall[kMaxCases];
+  double rz[kMaxCases];       // r.z of the current residual
+  double rr_ref[kMaxCases];   // true ||r||^2 at the last update
+  double beta[kMaxCases];     // next direction update coefficient
+  double rr_true[kMaxCases];  // last true ||f - K u||^2
 };
 
-struct PcgLaunch {
+struct Solver {
   Grid g;
   int nc;
-  const void* E;        // operator moduli in the CG precision
-  const double* E64;    // FP64 moduli for the true residual
-  const uint8_t* mask;  // per-node fixed bits
-  const void* invdiag;  // per DOF, CG precision
-  const double* f;      // internal layout [node][case][comp]
+  int zlen;              // 3D streaming tile depth (planes per tile)
+  const void* E;         // operator moduli in the CG precision
+  const double* E64;     // FP64 moduli for the true residual
+  const uint8_t* mask;   // per-node fixed bits
+  const void* invdiag;   // per DOF, CG precision
+  const double* f;       // internal layout [node][case][comp]
   double* x64;
   void* xl;
   void* r;
@@ -39,13 +49,14 @@ struct PcgLaunch {
   void* p0;
   void* p1;
   void* q;
-  double* part;
+  double* part;          // partial sums; its tail (after 16 * max tiles) holds tol2ff
+  double* tol2ff_dev;    // device copy of tol^2 ||f_c||^2
   GridBar* bar;
-  PcgStatus* st;
+  CgState* cs;
   double tol2ff[kMaxCases];
   double drop2;
   int max_it;
-  const double* K0;  // host FP64 K0 (copied into the kernel parameters)
+  const double* C;       // generalised-strain matrix (host, FP64), 5x5 or 18x18
 };
 
 // Launchers (return cudaError_t of the launch).
@@ -53,10 +64,15 @@ cudaError_t launch_young(cudaStream_t s, const double* rho, float* E32, double* 
                          double E0, double Emin, double penal);
 cudaError_t launch_diag(cudaStream_t s, const Grid& g, const double* K0, const double* E64,
                         const uint8_t* mask, float* inv32, double* inv64);
-cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* K0, bool f64, const void* E,
-                          const uint8_t* mask, const void* u, void* y, int ncopies);
-cudaError_t launch_pcg(cudaStream_t s, const PcgLaunch& L, bool f64, int nsm, int* grid_out);
-cudaError_t launch_sens(cudaStream_t s, const Grid& g, int nc, const double* K0, const double* x64,
+cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f64, const void* E,
+                          const uint8_t* mask, const void* u, void* y, int ncopies, int zlen);
+// FP64 update: x64 += x_l, x_l = 0; r = f - K64 x64; z = D^-1 r; CgState update.
+// `init` starts a solve (beta = 0, counters reset).  Returns the number of
+// kernels launched through *nlaunch.
+cudaError_t launch_true_residual(cudaStream_t s, const Solver& S, bool f64, bool init, int* nlaunch);
+// One persistent CG segment (cooperative launch).
+cudaError_t launch_cg_segment(cudaStream_t s, const Solver& S, bool f64, int nsm, int* grid_out);
+cudaError_t launch_sens(cudaStream_t s, const Grid& g, int nc, const double* C, const double* x64,
                         const double* f, const double* rho, double penal, double dE, double* ce,
                         double* dc, double* part, double* out_c);
 cudaError_t launch_to_internal(cudaStream_t s, const double* src, double* dst, long long nn, int dim,

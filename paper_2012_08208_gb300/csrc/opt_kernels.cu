@@ -7,7 +7,7 @@
 //     Lagrange multiplier (Eq. "update", Section 3.2.1), one cooperative launch.
 #include <cmath>
 
-#include "tile.cuh"
+#include "pcg_common.cuh"
 
 namespace tp {
 

@@ -1,33 +1,31 @@
-// Persistent Jacobi-preconditioned CG kernel (one cooperative launch per solve).
+// One segment of the persistent Jacobi-preconditioned CG (cooperative launch).
+//
+// All load cases advance in lock-step.  Per iteration two grid barriers:
+//   phase A  p = z + beta p_old (formed while the tile operator loads its
+//            input), q = K p, partial p.q                        -> barrier
+//   phase B  x_l += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r
+//                                                                 -> barrier
+// The segment returns when a case's recurrence residual has dropped by
+// `drop` since the last FP64 update or has reached the tolerance (an update is
+// due), or at max_it.  The host then runs the FP64 true-residual update
+// (fem_kernels.cu), which replaces r by f - K64 x64 and sets the next beta;
+// the search direction is kept (reliable update).
 #pragma once
-#include "tile.cuh"
+#include "pcg_common.cuh"
 
 namespace tp {
 
-// ---------------------------------------------------------------------------
-// Persistent Jacobi-PCG over all load cases.
-//
-// Per iteration two grid barriers:
-//   phase A  p = z + beta p_old (formed while loading the halo tile), q = K p,
-//            partial p.q                                         -> barrier
-//   phase B  x_l += alpha p, r -= alpha q, z = D^-1 r, partial r.z and r.r
-//                                                                   -> barrier
-// Reliable update (FP64): when a case's recurrence residual has dropped by
-// `drop` since the last update, or has reached the tolerance, x64 += x_l and
-// r = f - K64 x64 is recomputed in FP64 (its norm is the true residual that
-// decides convergence); the search direction is kept.
+constexpr int SLOT_A = 0;   // NCM partials: p.q
+constexpr int SLOT_B = 8;   // 2 NCM partials: r.z, r.r
 
 template <int DIM, typename T>
-struct PcgArgs {
+struct SegArgs {
   Grid g;
-  TileMap<DIM> tm;
+  TileMapG tm;
   int nc, nv;
   const T* E;
-  const double* E64;
   const uint8_t* mask;
   const T* invd;
-  const double* f;
-  double* x64;
   T* xl;
   T* r;
   T* z;
@@ -36,184 +34,88 @@ struct PcgArgs {
   T* q;
   double* part;
   GridBar* bar;
-  PcgStatus* st;
+  CgState* cs;
   double tol2ff[kMaxCases];
   double drop2;
   int max_it;
-  KMat<DIM, T> kT;
-  KMat<DIM, double> kD;
+  CMat<DIM, T> C;
 };
 
-// partial-sum slots in `part` (each slot holds gridDim.x doubles)
-constexpr int SLOT_RES = 0;   // 16: rr_true[8], rz[8]
-constexpr int SLOT_A = 16;    // 8: pq[8]
-constexpr int SLOT_B = 24;    // 16: rz[8], rr[8]
-constexpr int kPartSlots = 40;
-constexpr int kStallUpdates = 6;  // updates without progress before a case stops
+constexpr size_t kSegHeader = 32 * 16 * sizeof(double) + 32 * sizeof(double);
 
 template <int DIM, typename T, int NCM>
-__global__ void __launch_bounds__(kThreads) pcg_kernel(const __grid_constant__ PcgArgs<DIM, T> a) {
-  using G = TileGeom<DIM>;
+__global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
+    cg_segment_kernel(const __grid_constant__ SegArgs<DIM, T> a) {
+  using Op = TileOp<DIM, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sRed = reinterpret_cast<double*>(smem_raw);  // 32 * 16 doubles
+  double* sRed = reinterpret_cast<double*>(smem_raw);                    // 32 x 16
   T* sCoef = reinterpret_cast<T*>(smem_raw + 32 * 16 * sizeof(double));  // beta[8] | alpha[8]
   int* sAct = reinterpret_cast<int*>(smem_raw + 32 * 16 * sizeof(double) + 16 * sizeof(double));
-  unsigned char* sTile = smem_raw + 32 * 16 * sizeof(double) + 32 * sizeof(double);
-  const int nc = a.nc, nv = a.nv;
+  unsigned char* sTile = smem_raw + kSegHeader;
+  const int nc = a.nc, nv = a.nv, nb = gridDim.x;
   const long long nvals = a.g.nn * nv;
-  const int nb = gridDim.x;
-  unsigned gen = 0;
-  bool ok = true;
 
-  // Per-case scalars; every thread holds identical copies (computed from the
-  // same deterministic grid totals), indexed with compile-time indices only.
+  int it = a.cs->it, pbuf = a.cs->pbuf;
   int state[NCM];
-  double rz[NCM], rr_ref[NCM], beta[NCM], alpha[NCM], rr_true[NCM];
-  int stall[NCM];
+  double rz[NCM], rr_ref[NCM], beta[NCM], alpha[NCM];
 #pragma unroll
   for (int c = 0; c < NCM; c++) {
-    state[c] = c < nc ? 0 : 1;
-    rz[c] = rr_ref[c] = beta[c] = alpha[c] = rr_true[c] = 0.0;
-    stall[c] = 0;
+    state[c] = c < nc ? a.cs->state[c] : 1;
+    rz[c] = a.cs->rz[c];
+    rr_ref[c] = a.cs->rr_ref[c];
+    beta[c] = a.cs->beta[c];
+    alpha[c] = 0.0;
   }
-  auto publish = [&]() {  // block-uniform coefficients to shared memory
+  unsigned gen = 0;
+  bool ok = true, need = false;
+  int flags = 0;
+  auto publish = [&]() {
     __syncthreads();
     if (threadIdx.x < NCM) {
       sCoef[threadIdx.x] = (T)pick(beta, threadIdx.x);
-      sCoef[NCM + threadIdx.x] = (T)pick(alpha, threadIdx.x);
+      sCoef[kMaxCases + threadIdx.x] = (T)pick(alpha, threadIdx.x);
       sAct[threadIdx.x] = pick(state, threadIdx.x) == 0;
     }
     __syncthreads();
   };
 
-  // r = f - K64 x64 (FP64), z = D^-1 r; totals: rr_true, rz.
-  auto residual_phase = [&](double (&rrt)[NCM], double (&rzo)[NCM]) -> bool {
-    double acc[2 * NCM];
-#pragma unroll
-    for (int i = 0; i < 2 * NCM; i++) acc[i] = 0.0;
-    double* sX = reinterpret_cast<double*>(sTile);
-    double* sE = sX + G::HN * nv;
-    for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
-      int x0, y0, z0;
-      tile_origin<DIM>(a.tm, t, x0, y0, z0);
-      load_E<DIM, double>(a.g, x0, y0, z0, a.E64, sE);
-      load_halo<DIM, double>(a.g, x0, y0, z0, nv, sX, [&](long long node, int v, bool) -> double {
-        const int comp = v % DIM;
-        return ((a.mask[node] >> comp) & 1) ? 0.0 : __ldcg(a.x64 + node * nv + v);
-      });
-      __syncthreads();
-      for (int ln = threadIdx.x; ln < G::TN; ln += blockDim.x) {
-        int tx, ty, tz;
-        long long node;
-        if (!own_node<DIM>(a.g, ln, x0, y0, z0, tx, ty, tz, node)) continue;
-        const uint8_t mk = a.mask[node];
-        for (int cs = 0; cs < nc; cs++) {
-          double kx[DIM];
-          node_apply<DIM, double>(sX, sE, nv, cs, tx, ty, tz, a.kD, kx);
-          double srr = 0.0, srz = 0.0;
-#pragma unroll
-          for (int r = 0; r < DIM; r++) {
-            const long long idx = node * nv + cs * DIM + r;
-            const double r64 = ((mk >> r) & 1) ? 0.0 : __ldg(a.f + idx) - kx[r];
-            const T rt = (T)r64;
-            const T zt = rt * __ldg(a.invd + node * DIM + r);
-            a.r[idx] = rt;
-            a.z[idx] = zt;
-            srr += r64 * r64;
-            srz += (double)rt * (double)zt;
-          }
-          addto<2 * NCM>(acc, cs, srr);
-          addto<2 * NCM>(acc, NCM + cs, srz);
-        }
-      }
-      __syncthreads();
-    }
-    block_sum<2 * NCM>(acc, sRed);
-    if (threadIdx.x == 0)
-      for (int i = 0; i < 2 * NCM; i++) a.part[(size_t)(SLOT_RES + i) * nb + blockIdx.x] = acc[i];
-    if (!grid_sync(a.bar, gen)) return false;
-    double tot[2 * NCM];
-    grid_total<2 * NCM>(a.part + (size_t)SLOT_RES * nb, tot, sRed);
-#pragma unroll
-    for (int c = 0; c < NCM; c++) {
-      rrt[c] = tot[c];
-      rzo[c] = tot[NCM + c];
-    }
-    return true;
-  };
-
-  // x64 += x_l, x_l = 0
-  auto merge_phase = [&]() -> bool {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvals;
-         i += (long long)nb * blockDim.x) {
-      const T v = a.xl[i];
-      a.x64[i] = __ldcg(a.x64 + i) + (double)v;
-      a.xl[i] = T(0);
-    }
-    return grid_sync(a.bar, gen);
-  };
-
-  int it = 0, updates = 0, flags = 0;
-  bool fresh = true;  // x_l merged and r is the true residual
-  ok = residual_phase(rr_true, rz);
-  if (ok) {
-#pragma unroll
-    for (int c = 0; c < NCM; c++) {
-      rr_ref[c] = rr_true[c];
-      if (c < nc && rr_true[c] <= a.tol2ff[c]) state[c] = 1;
-    }
-  }
-
-  while (ok && it < a.max_it) {
+  while (it < a.max_it) {
     bool any = false;
 #pragma unroll
     for (int c = 0; c < NCM; c++) any |= state[c] == 0;
     if (!any) break;
     publish();
 
-    // ---- phase A: p = z + beta p_old, q = K p, partial p.q
-    const T* Pold = (it & 1) ? a.p1 : a.p0;
-    T* Pnew = (it & 1) ? a.p0 : a.p1;
+    // ---- phase A
+    const T* Pold = pbuf ? a.p1 : a.p0;
+    T* Pnew = pbuf ? a.p0 : a.p1;
     double accA[NCM];
 #pragma unroll
     for (int i = 0; i < NCM; i++) accA[i] = 0.0;
-    {
-      T* sP = reinterpret_cast<T*>(sTile);
-      T* sE = sP + G::HN * nv;
-      for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
-        int x0, y0, z0;
-        tile_origin<DIM>(a.tm, t, x0, y0, z0);
-        load_E<DIM, T>(a.g, x0, y0, z0, a.E, sE);
-        load_halo<DIM, T>(a.g, x0, y0, z0, nv, sP, [&](long long node, int v, bool own) -> T {
-          const long long idx = node * nv + v;
-          const T b = sCoef[v / DIM];
-          T val = __ldcg(a.z + idx);
-          if (b != T(0)) val = fma(b, __ldcg(Pold + idx), val);
-          if (own) Pnew[idx] = val;
-          return val;
-        });
-        __syncthreads();
-        for (int ln = threadIdx.x; ln < G::TN; ln += blockDim.x) {
-          int tx, ty, tz;
-          long long node;
-          if (!own_node<DIM>(a.g, ln, x0, y0, z0, tx, ty, tz, node)) continue;
-          const uint8_t mk = a.mask[node];
-          const int hself = (((DIM == 3 ? tz + 1 : 0) * G::HY + ty + 1) * G::HX + tx + 1) * nv;
-          for (int cs = 0; cs < nc; cs++) {
-            if (!sAct[cs]) continue;
-            T kq[DIM];
-            node_apply<DIM, T>(sP, sE, nv, cs, tx, ty, tz, a.kT, kq);
-            double spq = 0.0;
+    for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
+      for (int cs = 0; cs < nc; cs++) {
+        if (!sAct[cs]) continue;
+        const T b = sCoef[cs];
+        double spq = 0.0;
+        Op::apply(
+            a.g, a.tm, t, a.E, a.C, sTile,
+            [&](long long node, int comp, bool own) -> T {
+              const long long idx = node * nv + cs * DIM + comp;
+              T v = __ldcg(a.z + idx);
+              if (b != T(0)) v = fma(b, __ldcg(Pold + idx), v);
+              if (own) Pnew[idx] = v;
+              return v;
+            },
+            [&](long long node, const T(&yv)[DIM], const T(&us)[DIM]) {
+              const uint8_t mk = a.mask[node];
 #pragma unroll
-            for (int r = 0; r < DIM; r++) {
-              const T qv = ((mk >> r) & 1) ? T(0) : kq[r];
-              a.q[node * nv + cs * DIM + r] = qv;
-              spq += (double)sP[hself + cs * DIM + r] * (double)qv;
-            }
-            addto<NCM>(accA, cs, spq);
-          }
-        }
-        __syncthreads();
+              for (int r = 0; r < DIM; r++) {
+                const T qv = ((mk >> r) & 1) ? T(0) : yv[r];
+                a.q[node * nv + cs * DIM + r] = qv;
+                spq += (double)us[r] * (double)qv;
+              }
+            });
+        addto<NCM>(accA, cs, spq);
       }
     }
     block_sum<NCM>(accA, sRed);
@@ -237,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const __grid_constant__ P
     }
     publish();
 
-    // ---- phase B: x_l += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r
+    // ---- phase B
     double accB[2 * NCM];
 #pragma unroll
     for (int i = 0; i < 2 * NCM; i++) accB[i] = 0.0;
@@ -246,7 +148,7 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const __grid_constant__ P
       const long long node = i / nv;
       const int v = (int)(i - node * nv);
       const int cs = v / DIM, comp = v - cs * DIM;
-      const T al = sCoef[NCM + cs];
+      const T al = sCoef[kMaxCases + cs];
       T rv = __ldcg(a.r + i);
       T zv;
       if (al != T(0)) {
@@ -277,97 +179,62 @@ __global__ void __launch_bounds__(kThreads) pcg_kernel(const __grid_constant__ P
       }
     }
     it++;
-    fresh = false;
-
-    bool need = false;
+    pbuf ^= 1;
 #pragma unroll
     for (int c = 0; c < NCM; c++)
       if (state[c] == 0 && (rr[c] <= a.tol2ff[c] || rr[c] <= a.drop2 * rr_ref[c])) need = true;
-    if (need) {
-      if (!(ok = merge_phase())) break;
-      if (!(ok = residual_phase(rr_true, rzn))) break;
-      updates++;
-      fresh = true;
-#pragma unroll
-      for (int c = 0; c < NCM; c++) {
-        if (state[c] != 0) continue;
-        // stagnation: the true residual no longer halves between updates
-        stall[c] = rr_true[c] > 0.25 * rr_ref[c] ? stall[c] + 1 : 0;
-        rr_ref[c] = rr_true[c];
-        if (rr_true[c] <= a.tol2ff[c]) state[c] = 1;
-        else if (stall[c] >= kStallUpdates) state[c] = 3;
-      }
-    }
+    if (need) break;  // rz keeps the value the finalize step divides by
 #pragma unroll
     for (int c = 0; c < NCM; c++) {
       beta[c] = (state[c] == 0 && rz[c] != 0.0) ? rzn[c] / rz[c] : 0.0;
       rz[c] = rzn[c];
     }
   }
-  if (ok && !fresh) {
-    ok = merge_phase();
-    if (ok) {
-      double dummy[NCM];
-      ok = residual_phase(rr_true, dummy);
-      updates++;
-    }
-    if (ok) {
-#pragma unroll
-      for (int c = 0; c < NCM; c++)
-        if (state[c] == 0 && rr_true[c] <= a.tol2ff[c]) state[c] = 1;
-    }
-  }
   if (!ok) flags |= ERR_TIMEOUT;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.st->iters = it;
-    a.st->updates = updates;
-    a.st->flags = flags;
+    a.cs->it = it;
+    a.cs->pbuf = pbuf;
+    a.cs->need = need ? 1 : 0;
+    a.cs->flags |= flags;
+#pragma unroll
     for (int c = 0; c < NCM; c++) {
-      a.st->state[c] = state[c];
-      a.st->rr_true[c] = rr_true[c];
-    }
-    for (int c = NCM; c < kMaxCases; c++) {
-      a.st->state[c] = 1;
-      a.st->rr_true[c] = 0.0;
+      if (c < nc) a.cs->state[c] = state[c];
+      a.cs->rz[c] = rz[c];
+      a.cs->beta[c] = beta[c];
     }
   }
 }
 
 template <int DIM, typename T, int NCM>
-static cudaError_t pcg_impl(cudaStream_t s, const PcgLaunch& L, int nsm, int* grid_out) {
-  using G = TileGeom<DIM>;
-  PcgArgs<DIM, T> a;
-  a.g = L.g;
-  a.tm = tile_map<DIM>(L.g);
-  a.nc = L.nc;
-  a.nv = L.nc * DIM;
-  a.E = (const T*)L.E;
-  a.E64 = L.E64;
-  a.mask = L.mask;
-  a.invd = (const T*)L.invdiag;
-  a.f = L.f;
-  a.x64 = L.x64;
-  a.xl = (T*)L.xl;
-  a.r = (T*)L.r;
-  a.z = (T*)L.z;
-  a.p0 = (T*)L.p0;
-  a.p1 = (T*)L.p1;
-  a.q = (T*)L.q;
-  a.part = L.part;
-  a.bar = L.bar;
-  a.st = L.st;
-  for (int c = 0; c < kMaxCases; c++) a.tol2ff[c] = L.tol2ff[c];
-  a.drop2 = L.drop2;
-  a.max_it = L.max_it;
-  fill_k<DIM, T>(a.kT, L.K0);
-  fill_k<DIM, double>(a.kD, L.K0);
-  const size_t tile_bytes = (size_t)(G::HN * a.nv + G::EN) * sizeof(double);
-  const size_t smem = 32 * 16 * sizeof(double) + 32 * sizeof(double) + tile_bytes;
-  auto kern = pcg_kernel<DIM, T, NCM>;
+static cudaError_t segment_impl(cudaStream_t s, const Solver& S, int nsm, int* grid_out) {
+  using Op = TileOp<DIM, T>;
+  SegArgs<DIM, T> a;
+  a.g = S.g;
+  a.tm = Op::map(S.g, S.zlen);
+  a.nc = S.nc;
+  a.nv = S.nc * DIM;
+  a.E = (const T*)S.E;
+  a.mask = S.mask;
+  a.invd = (const T*)S.invdiag;
+  a.xl = (T*)S.xl;
+  a.r = (T*)S.r;
+  a.z = (T*)S.z;
+  a.p0 = (T*)S.p0;
+  a.p1 = (T*)S.p1;
+  a.q = (T*)S.q;
+  a.part = S.part;
+  a.bar = S.bar;
+  a.cs = S.cs;
+  for (int c = 0; c < kMaxCases; c++) a.tol2ff[c] = S.tol2ff[c];
+  a.drop2 = S.drop2;
+  a.max_it = S.max_it;
+  fill_c<DIM, T>(a.C, S.C);
+  const size_t smem = kSegHeader + Op::smem_bytes();
+  auto kern = cg_segment_kernel<DIM, T, NCM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Op::THREADS, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = per_sm * nsm;
@@ -375,14 +242,14 @@ static cudaError_t pcg_impl(cudaStream_t s, const PcgLaunch& L, int nsm, int* gr
   if (grid < 1) grid = 1;
   *grid_out = grid;
   void* args[] = {(void*)&a};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(Op::THREADS), args, smem, s);
 }
 
 template <int DIM, typename T>
-static cudaError_t pcg_nc(cudaStream_t s, const PcgLaunch& L, int nsm, int* grid_out) {
-  if (L.nc == 1) return pcg_impl<DIM, T, 1>(s, L, nsm, grid_out);
-  if (L.nc <= 4) return pcg_impl<DIM, T, 4>(s, L, nsm, grid_out);
-  return pcg_impl<DIM, T, 8>(s, L, nsm, grid_out);
+static cudaError_t segment_nc(cudaStream_t s, const Solver& S, int nsm, int* grid_out) {
+  if (S.nc == 1) return segment_impl<DIM, T, 1>(s, S, nsm, grid_out);
+  if (S.nc <= 4) return segment_impl<DIM, T, 4>(s, S, nsm, grid_out);
+  return segment_impl<DIM, T, 8>(s, S, nsm, grid_out);
 }
 
 }  // namespace tp
