@@ -53,7 +53,6 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
   int* sAct = reinterpret_cast<int*>(smem_raw + 32 * 16 * sizeof(double) + 16 * sizeof(double));
   unsigned char* sTile = smem_raw + kSegHeader;
   const int nc = a.nc, nv = a.nv, nb = gridDim.x;
-  const long long nvals = a.g.nn * nv;
 
   int it = a.cs->it, pbuf = a.cs->pbuf;
   int state[NCM];
@@ -89,14 +88,15 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     // ---- phase A
     const T* Pold = pbuf ? a.p1 : a.p0;
     T* Pnew = pbuf ? a.p0 : a.p1;
-    double accA[NCM];
+    // per-thread partial sums in the CG precision; FP64 from the block level on
+    T accAt[NCM];
 #pragma unroll
-    for (int i = 0; i < NCM; i++) accA[i] = 0.0;
+    for (int i = 0; i < NCM; i++) accAt[i] = T(0);
     for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
       for (int cs = 0; cs < nc; cs++) {
         if (!sAct[cs]) continue;
         const T b = sCoef[cs];
-        double spq = 0.0;
+        T spq = T(0);
         Op::apply(
             a.g, a.tm, t, a.E, a.C, sTile,
             [&](long long node, int comp, bool own) -> T {
@@ -112,12 +112,17 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
               for (int r = 0; r < DIM; r++) {
                 const T qv = ((mk >> r) & 1) ? T(0) : yv[r];
                 a.q[node * nv + cs * DIM + r] = qv;
-                spq += (double)us[r] * (double)qv;
+                spq = fma(us[r], qv, spq);
               }
             });
-        addto<NCM>(accA, cs, spq);
+#pragma unroll
+        for (int c2 = 0; c2 < NCM; c2++)
+          if (c2 == cs) accAt[c2] += spq;
       }
     }
+    double accA[NCM];
+#pragma unroll
+    for (int i = 0; i < NCM; i++) accA[i] = (double)accAt[i];
     block_sum<NCM>(accA, sRed);
     if (threadIdx.x == 0)
       for (int i = 0; i < NCM; i++) a.part[(size_t)(SLOT_A + i) * nb + blockIdx.x] = accA[i];
@@ -139,31 +144,43 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     }
     publish();
 
-    // ---- phase B
+    // ---- phase B (one node per thread, all cases and components of the node)
+    T accBt[2 * NCM];
+#pragma unroll
+    for (int i = 0; i < 2 * NCM; i++) accBt[i] = T(0);
+    const long long nn = a.g.nn;
+    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
+         node += (long long)nb * blockDim.x) {
+      T inv[DIM];
+#pragma unroll
+      for (int r = 0; r < DIM; r++) inv[r] = __ldg(a.invd + node * DIM + r);
+#pragma unroll
+      for (int cs = 0; cs < NCM; cs++) {
+        if (cs >= nc) break;
+        const T al = sCoef[kMaxCases + cs];
+#pragma unroll
+        for (int r = 0; r < DIM; r++) {
+          const long long i = node * nv + cs * DIM + r;
+          T rv = __ldcg(a.r + i);
+          T zv;
+          if (al != T(0)) {
+            const T pv = __ldcg(Pnew + i), qv = __ldcg(a.q + i);
+            a.xl[i] = fma(al, pv, a.xl[i]);
+            rv = fma(-al, qv, rv);
+            a.r[i] = rv;
+            zv = rv * inv[r];
+            a.z[i] = zv;
+          } else {
+            zv = __ldcg(a.z + i);
+          }
+          accBt[cs] = fma(rv, zv, accBt[cs]);
+          accBt[NCM + cs] = fma(rv, rv, accBt[NCM + cs]);
+        }
+      }
+    }
     double accB[2 * NCM];
 #pragma unroll
-    for (int i = 0; i < 2 * NCM; i++) accB[i] = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nvals;
-         i += (long long)nb * blockDim.x) {
-      const long long node = i / nv;
-      const int v = (int)(i - node * nv);
-      const int cs = v / DIM, comp = v - cs * DIM;
-      const T al = sCoef[kMaxCases + cs];
-      T rv = __ldcg(a.r + i);
-      T zv;
-      if (al != T(0)) {
-        const T pv = __ldcg(Pnew + i), qv = __ldcg(a.q + i);
-        a.xl[i] = fma(al, pv, a.xl[i]);
-        rv = fma(-al, qv, rv);
-        a.r[i] = rv;
-        zv = rv * __ldg(a.invd + node * DIM + comp);
-        a.z[i] = zv;
-      } else {
-        zv = __ldcg(a.z + i);
-      }
-      addto<2 * NCM>(accB, cs, (double)rv * (double)zv);
-      addto<2 * NCM>(accB, NCM + cs, (double)rv * (double)rv);
-    }
+    for (int i = 0; i < 2 * NCM; i++) accB[i] = (double)accBt[i];
     block_sum<2 * NCM>(accB, sRed);
     if (threadIdx.x == 0)
       for (int i = 0; i < 2 * NCM; i++) a.part[(size_t)(SLOT_B + i) * nb + blockIdx.x] = accB[i];
