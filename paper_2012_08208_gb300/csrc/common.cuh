@@ -27,39 +27,143 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
-// barrier word must be zeroed before the launch; `gen` is the CTA-local
-// generation counter starting at 0.  The wait is bounded: on expiry the CTA
-// records ERR_TIMEOUT and returns false, and every CTA returns false once the
-// error word is set, so no CTA can wait forever.
+// barrier word must be zeroed before the launch; `gen` is the CTA-local count
+// of barriers passed, starting at 0.  Each CTA adds 1 to a monotone arrival
+// counter with release semantics and waits (acquire) until the counter reaches
+// gridDim.x * (gen + 1).  The wait is bounded: on expiry the CTA records
+// ERR_TIMEOUT and returns false, and every CTA returns false once the error word
+// is set, so no CTA can wait forever.
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned& gen) {
   __syncthreads();
+  gen++;
   if (threadIdx.x == 0) {
-    const unsigned nb = gridDim.x;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&b->count, 1u);
-    if (arrived == nb - 1) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (ld_acquire_u32(&b->gen) == gen) {
-        if (clock64() - t0 > kSpinCycles) {
-          atomicOr(&b->err, ERR_TIMEOUT);
-          break;
-        }
-        if (ld_volatile_i32(&b->err) & ERR_TIMEOUT) break;
+    const unsigned target = gen * gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&b->count), "r"(1u) : "memory");
+    const long long t0 = clock64();
+    while (ld_acquire_u32(&b->count) < target) {
+      if (clock64() - t0 > kSpinCycles) {
+        atomicOr(&b->err, ERR_TIMEOUT);
+        break;
       }
+      if (ld_volatile_i32(&b->err) & ERR_TIMEOUT) break;
     }
-    __threadfence();
   }
   __syncthreads();
-  gen++;
   return (ld_volatile_i32(&b->err) & ERR_TIMEOUT) == 0;
 }
 
-// Deterministic reduction of NV doubles over the CTA; result valid in all threads.
-// `sm` must hold 32 * NV doubles.
+// Double-float accumulator (hi + lo, ~48-bit mantissa) built from FP32
+// operations only: on GB300 an FP64 add costs 64 FP32 issue slots, so
+// reductions of FP32 data accumulate in pairs of floats (TwoSum, Knuth).
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+  const float s = a.hi + b.hi;
+  const float v = s - a.hi;
+  float e = (a.hi - (s - v)) + (b.hi - v);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return dfl{hi, e - (hi - s)};
+}
+
+// CTA partial of NV per-thread FP32 values: FP32 warp trees, then one thread
+// per value combines the per-warp sums in double-float and stores the pair in
+// slot[i * gridDim.x + blockIdx.x].  `sm` holds 32 * NV floats.
+template <int NV>
+__device__ __forceinline__ void block_partial_f(float (&v)[NV], float2* slot, unsigned char* sm) {
+  float* sw = reinterpret_cast<float*>(sm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; i++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; i++) sw[warp * NV + i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    dfl s{0.f, 0.f};
+    for (int w = 0; w < nw; w++) s = dfl_add(s, dfl{sw[w * NV + threadIdx.x], 0.f});
+    slot[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = make_float2(s.hi, s.lo);
+  }
+}
+
+// Grid total of NV per-CTA double-float partials part[i * gridDim.x + cta]
+// (stored as float2): warp w sums values w, w + nw, ... over all CTAs in
+// double-float, in a fixed order, so every CTA obtains the identical total.
+template <int NV>
+__device__ __forceinline__ void grid_total_f(const float2* part, double (&out)[NV], unsigned char* sm) {
+  double* sd = reinterpret_cast<double*>(sm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = gridDim.x;
+  for (int i = warp; i < NV; i += nw) {
+    dfl s{0.f, 0.f};
+    for (int b = lane; b < nb; b += 32) {
+      const float2 p = __ldcg(part + (size_t)i * nb + b);
+      s = dfl_add(s, dfl{p.x, p.y});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const dfl t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+      s = dfl_add(s, t);
+    }
+    if (lane == 0) sd[i] = (double)s.hi + (double)s.lo;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; i++) out[i] = sd[i];
+  __syncthreads();
+}
+
+// FP64 counterparts (the plain FP64 solver): FP64 warp trees; the per-warp and
+// per-CTA sums are combined by one warp lane-parallel instead of by every thread.
+template <int NV>
+__device__ __forceinline__ void block_partial_d(double (&v)[NV], double* slot, unsigned char* sm) {
+  double* sw = reinterpret_cast<double*>(sm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; i++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; i++) sw[warp * NV + i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nw; w++) s += sw[w * NV + threadIdx.x];
+    slot[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void grid_total_d(const double* part, double (&out)[NV], unsigned char* sm) {
+  double* sd = reinterpret_cast<double*>(sm);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = gridDim.x;
+  for (int i = warp; i < NV; i += nw) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += __ldcg(part + (size_t)i * nb + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sd[i] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; i++) out[i] = sd[i];
+  __syncthreads();
+}
+
+// Deterministic reduction of NV doubles over the CTA; result valid in all
+// threads.  FP64 warp trees; the per-warp sums are combined by NV threads and
+// broadcast.  `sm` must hold 32 * NV doubles.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -75,12 +179,14 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
     for (int i = 0; i < NV; i++) sm[warp * NV + i] = v[i];
   }
   __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; i++) {
+  if (threadIdx.x < NV) {
     double s = 0.0;
-    for (int w = 0; w < nw; w++) s += sm[w * NV + i];
-    v[i] = s;
+    for (int w = 0; w < nw; w++) s += sm[w * NV + threadIdx.x];
+    sm[threadIdx.x] = s;  // only this thread reads warp 0's slot threadIdx.x
   }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; i++) v[i] = sm[i];
   __syncthreads();
 }
 

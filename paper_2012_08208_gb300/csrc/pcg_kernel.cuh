@@ -43,12 +43,24 @@ struct SegArgs {
 
 constexpr size_t kSegHeader = 32 * 16 * sizeof(double) + 32 * sizeof(double);
 
+// CTA partial / grid total in the precision policy of the CG type: double-float
+// accumulation for FP32 data, FP64 for FP64 data.  Slots hold 8 bytes per value.
+template <int NV, typename T>
+__device__ __forceinline__ void cta_partial(T (&v)[NV], double* slot, unsigned char* sm) {
+  if constexpr (std::is_same<T, float>::value) block_partial_f<NV>(v, reinterpret_cast<float2*>(slot), sm);
+  else block_partial_d<NV>(v, slot, sm);
+}
+template <int NV>
+__device__ __forceinline__ void cta_total_any(const double* slot, double (&out)[NV], unsigned char* sm, bool f32) {
+  if (f32) grid_total_f<NV>(reinterpret_cast<const float2*>(slot), out, sm);
+  else grid_total_d<NV>(slot, out, sm);
+}
+
 template <int DIM, typename T, int NCM>
 __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     cg_segment_kernel(const __grid_constant__ SegArgs<DIM, T> a) {
   using Op = TileOp<DIM, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sRed = reinterpret_cast<double*>(smem_raw);                    // 32 x 16
   T* sCoef = reinterpret_cast<T*>(smem_raw + 32 * 16 * sizeof(double));  // beta[8] | alpha[8]
   int* sAct = reinterpret_cast<int*>(smem_raw + 32 * 16 * sizeof(double) + 16 * sizeof(double));
   unsigned char* sTile = smem_raw + kSegHeader;
@@ -120,16 +132,11 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
           if (c2 == cs) accAt[c2] += spq;
       }
     }
-    double accA[NCM];
-#pragma unroll
-    for (int i = 0; i < NCM; i++) accA[i] = (double)accAt[i];
-    block_sum<NCM>(accA, sRed);
-    if (threadIdx.x == 0)
-      for (int i = 0; i < NCM; i++) a.part[(size_t)(SLOT_A + i) * nb + blockIdx.x] = accA[i];
+    cta_partial<NCM>(accAt, a.part + (size_t)SLOT_A * nb, smem_raw);
     if (!(ok = grid_sync(a.bar, gen))) break;
     {
       double pq[NCM];
-      grid_total<NCM>(a.part + (size_t)SLOT_A * nb, pq, sRed);
+      cta_total_any<NCM>(a.part + (size_t)SLOT_A * nb, pq, smem_raw, std::is_same<T, float>::value);
 #pragma unroll
       for (int c = 0; c < NCM; c++) {
         alpha[c] = 0.0;
@@ -178,17 +185,12 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
         }
       }
     }
-    double accB[2 * NCM];
-#pragma unroll
-    for (int i = 0; i < 2 * NCM; i++) accB[i] = (double)accBt[i];
-    block_sum<2 * NCM>(accB, sRed);
-    if (threadIdx.x == 0)
-      for (int i = 0; i < 2 * NCM; i++) a.part[(size_t)(SLOT_B + i) * nb + blockIdx.x] = accB[i];
+    cta_partial<2 * NCM>(accBt, a.part + (size_t)SLOT_B * nb, smem_raw);
     if (!(ok = grid_sync(a.bar, gen))) break;
     double rzn[NCM], rr[NCM];
     {
       double tot[2 * NCM];
-      grid_total<2 * NCM>(a.part + (size_t)SLOT_B * nb, tot, sRed);
+      cta_total_any<2 * NCM>(a.part + (size_t)SLOT_B * nb, tot, smem_raw, std::is_same<T, float>::value);
 #pragma unroll
       for (int c = 0; c < NCM; c++) {
         rzn[c] = tot[c];
