@@ -33,7 +33,10 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile
 // gridDim.x * (gen + 1).  The wait is bounded: on expiry the CTA records
 // ERR_TIMEOUT and returns false, and every CTA returns false once the error word
 // is set, so no CTA can wait forever.
+// The returned flag is decided by thread 0 and shared through shared memory, so
+// it is uniform across the CTA (all threads take the same branch afterwards).
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned& gen) {
+  __shared__ int s_ok;
   __syncthreads();
   gen++;
   if (threadIdx.x == 0) {
@@ -47,9 +50,10 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned& gen) {
       }
       if (ld_volatile_i32(&b->err) & ERR_TIMEOUT) break;
     }
+    s_ok = (ld_volatile_i32(&b->err) & ERR_TIMEOUT) == 0;
   }
   __syncthreads();
-  return (ld_volatile_i32(&b->err) & ERR_TIMEOUT) == 0;
+  return s_ok != 0;
 }
 
 // Double-float accumulator (hi + lo, ~48-bit mantissa) built from FP32

@@ -41,19 +41,56 @@ struct SegArgs {
   CMat<DIM, T> C;
 };
 
-constexpr size_t kSegHeader = 32 * 16 * sizeof(double) + 32 * sizeof(double);
+// Shared-memory layout of the segment kernel: reduction scratch, then the
+// per-case control block (owned by thread 0; FP64 scalar work stays off the
+// other threads), then the tile operator's buffers.
+struct SegCtl {
+  double rz[kMaxCases], rr_ref[kMaxCases], beta[kMaxCases], alpha[kMaxCases];
+  double tot[2 * kMaxCases];
+  float coef_f[2 * kMaxCases];   // beta | alpha in FP32
+  double coef_d[2 * kMaxCases];  // beta | alpha in FP64
+  int state[kMaxCases];
+  int act[kMaxCases];
+  int it, pbuf, need, go, flags;
+};
+constexpr size_t kRedBytes = 32 * 16 * sizeof(double);
+constexpr size_t kSegHeader = kRedBytes + ((sizeof(SegCtl) + 255) / 256) * 256;
 
 // CTA partial / grid total in the precision policy of the CG type: double-float
 // accumulation for FP32 data, FP64 for FP64 data.  Slots hold 8 bytes per value.
+// The total lands in ctl->tot (read by thread 0 after a barrier).
 template <int NV, typename T>
 __device__ __forceinline__ void cta_partial(T (&v)[NV], double* slot, unsigned char* sm) {
   if constexpr (std::is_same<T, float>::value) block_partial_f<NV>(v, reinterpret_cast<float2*>(slot), sm);
   else block_partial_d<NV>(v, slot, sm);
 }
-template <int NV>
-__device__ __forceinline__ void cta_total_any(const double* slot, double (&out)[NV], unsigned char* sm, bool f32) {
-  if (f32) grid_total_f<NV>(reinterpret_cast<const float2*>(slot), out, sm);
-  else grid_total_d<NV>(slot, out, sm);
+template <int NV, typename T>
+__device__ __forceinline__ void cta_total(const double* slot, SegCtl* ctl) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = gridDim.x;
+  for (int i = warp; i < NV; i += nw) {
+    if constexpr (std::is_same<T, float>::value) {
+      const float2* part = reinterpret_cast<const float2*>(slot);
+      dfl s{0.f, 0.f};
+      for (int b = lane; b < nb; b += 32) {
+        const float2 p = __ldcg(part + (size_t)i * nb + b);
+        s = dfl_add(s, dfl{p.x, p.y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const dfl t{__shfl_xor_sync(0xffffffffu, s.hi, o), __shfl_xor_sync(0xffffffffu, s.lo, o)};
+        s = dfl_add(s, t);
+      }
+      if (lane == 0) ctl->tot[i] = (double)s.hi + (double)s.lo;
+    } else {
+      double s = 0.0;
+      for (int b = lane; b < nb; b += 32) s += __ldcg(slot + (size_t)i * nb + b);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) ctl->tot[i] = s;
+    }
+  }
+  __syncthreads();
 }
 
 template <int DIM, typename T, int NCM>
@@ -61,53 +98,58 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     cg_segment_kernel(const __grid_constant__ SegArgs<DIM, T> a) {
   using Op = TileOp<DIM, T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sCoef = reinterpret_cast<T*>(smem_raw + 32 * 16 * sizeof(double));  // beta[8] | alpha[8]
-  int* sAct = reinterpret_cast<int*>(smem_raw + 32 * 16 * sizeof(double) + 16 * sizeof(double));
+  SegCtl* ctl = reinterpret_cast<SegCtl*>(smem_raw + kRedBytes);
   unsigned char* sTile = smem_raw + kSegHeader;
   const int nc = a.nc, nv = a.nv, nb = gridDim.x;
-
-  int it = a.cs->it, pbuf = a.cs->pbuf;
-  int state[NCM];
-  double rz[NCM], rr_ref[NCM], beta[NCM], alpha[NCM];
-#pragma unroll
-  for (int c = 0; c < NCM; c++) {
-    state[c] = c < nc ? a.cs->state[c] : 1;
-    rz[c] = a.cs->rz[c];
-    rr_ref[c] = a.cs->rr_ref[c];
-    beta[c] = a.cs->beta[c];
-    alpha[c] = 0.0;
-  }
-  unsigned gen = 0;
-  bool ok = true, need = false;
-  int flags = 0;
-  auto publish = [&]() {
-    __syncthreads();
-    if (threadIdx.x < NCM) {
-      sCoef[threadIdx.x] = (T)pick(beta, threadIdx.x);
-      sCoef[kMaxCases + threadIdx.x] = (T)pick(alpha, threadIdx.x);
-      sAct[threadIdx.x] = pick(state, threadIdx.x) == 0;
-    }
-    __syncthreads();
+  const bool t0 = threadIdx.x == 0;
+  constexpr bool F32 = std::is_same<T, float>::value;
+  auto coef = [&](int i) -> T {
+    if constexpr (F32) return ctl->coef_f[i];
+    else return ctl->coef_d[i];
   };
-
-  while (it < a.max_it) {
+  // thread 0 publishes beta / alpha / activity for the next phase
+  auto publish = [&]() {
+    for (int c = 0; c < kMaxCases; c++) {
+      ctl->coef_f[c] = (float)ctl->beta[c];
+      ctl->coef_f[kMaxCases + c] = (float)ctl->alpha[c];
+      ctl->coef_d[c] = ctl->beta[c];
+      ctl->coef_d[kMaxCases + c] = ctl->alpha[c];
+      ctl->act[c] = ctl->state[c] == 0;
+    }
+  };
+  if (t0) {
+    ctl->it = a.cs->it;
+    ctl->pbuf = a.cs->pbuf;
+    ctl->need = 0;
+    ctl->flags = 0;
+    for (int c = 0; c < kMaxCases; c++) {
+      ctl->state[c] = c < nc ? a.cs->state[c] : 1;
+      ctl->rz[c] = a.cs->rz[c];
+      ctl->rr_ref[c] = a.cs->rr_ref[c];
+      ctl->beta[c] = a.cs->beta[c];
+      ctl->alpha[c] = 0.0;
+    }
     bool any = false;
-#pragma unroll
-    for (int c = 0; c < NCM; c++) any |= state[c] == 0;
-    if (!any) break;
+    for (int c = 0; c < nc; c++) any |= ctl->state[c] == 0;
+    ctl->go = any && ctl->it < a.max_it;
     publish();
+  }
+  __syncthreads();
+  unsigned gen = 0;
+  bool ok = true;
 
-    // ---- phase A
+  while (ctl->go) {
+    // ---- phase A: p = z + beta p_old, q = K p, partial p.q
+    const int pbuf = ctl->pbuf;
     const T* Pold = pbuf ? a.p1 : a.p0;
     T* Pnew = pbuf ? a.p0 : a.p1;
-    // per-thread partial sums in the CG precision; FP64 from the block level on
     T accAt[NCM];
 #pragma unroll
     for (int i = 0; i < NCM; i++) accAt[i] = T(0);
     for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
       for (int cs = 0; cs < nc; cs++) {
-        if (!sAct[cs]) continue;
-        const T b = sCoef[cs];
+        if (!ctl->act[cs]) continue;
+        const T b = coef(cs);
         T spq = T(0);
         Op::apply(
             a.g, a.tm, t, a.E, a.C, sTile,
@@ -134,22 +176,22 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     }
     cta_partial<NCM>(accAt, a.part + (size_t)SLOT_A * nb, smem_raw);
     if (!(ok = grid_sync(a.bar, gen))) break;
-    {
-      double pq[NCM];
-      cta_total_any<NCM>(a.part + (size_t)SLOT_A * nb, pq, smem_raw, std::is_same<T, float>::value);
-#pragma unroll
-      for (int c = 0; c < NCM; c++) {
-        alpha[c] = 0.0;
-        if (state[c] != 0) continue;
-        if (!(pq[c] > 0.0) || !isfinite(pq[c]) || !isfinite(rz[c])) {
-          state[c] = 2;
-          flags |= ERR_BREAKDOWN;
+    cta_total<NCM, T>(a.part + (size_t)SLOT_A * nb, ctl);
+    if (t0) {
+      for (int c = 0; c < kMaxCases; c++) {
+        ctl->alpha[c] = 0.0;
+        if (c >= NCM || ctl->state[c] != 0) continue;
+        const double pq = ctl->tot[c];
+        if (!(pq > 0.0) || !isfinite(pq) || !isfinite(ctl->rz[c])) {
+          ctl->state[c] = 2;
+          ctl->flags |= ERR_BREAKDOWN;
           continue;
         }
-        alpha[c] = rz[c] / pq[c];
+        ctl->alpha[c] = ctl->rz[c] / pq;
       }
+      publish();
     }
-    publish();
+    __syncthreads();
 
     // ---- phase B (one node per thread, all cases and components of the node)
     T accBt[2 * NCM];
@@ -164,7 +206,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
 #pragma unroll
       for (int cs = 0; cs < NCM; cs++) {
         if (cs >= nc) break;
-        const T al = sCoef[kMaxCases + cs];
+        const T al = coef(kMaxCases + cs);
 #pragma unroll
         for (int r = 0; r < DIM; r++) {
           const long long i = node * nv + cs * DIM + r;
@@ -187,39 +229,39 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     }
     cta_partial<2 * NCM>(accBt, a.part + (size_t)SLOT_B * nb, smem_raw);
     if (!(ok = grid_sync(a.bar, gen))) break;
-    double rzn[NCM], rr[NCM];
-    {
-      double tot[2 * NCM];
-      cta_total_any<2 * NCM>(a.part + (size_t)SLOT_B * nb, tot, smem_raw, std::is_same<T, float>::value);
-#pragma unroll
-      for (int c = 0; c < NCM; c++) {
-        rzn[c] = tot[c];
-        rr[c] = tot[NCM + c];
+    cta_total<2 * NCM, T>(a.part + (size_t)SLOT_B * nb, ctl);
+    if (t0) {
+      ctl->it += 1;
+      ctl->pbuf ^= 1;
+      bool need = false;
+      for (int c = 0; c < NCM && c < nc; c++) {
+        const double rr = ctl->tot[NCM + c];
+        if (ctl->state[c] == 0 && (rr <= a.tol2ff[c] || rr <= a.drop2 * ctl->rr_ref[c])) need = true;
       }
+      if (!need) {  // otherwise rz keeps the value the update step divides by
+        for (int c = 0; c < NCM && c < nc; c++) {
+          const double rzn = ctl->tot[c];
+          ctl->beta[c] = (ctl->state[c] == 0 && ctl->rz[c] != 0.0) ? rzn / ctl->rz[c] : 0.0;
+          ctl->rz[c] = rzn;
+        }
+      }
+      ctl->need = need;
+      bool any = false;
+      for (int c = 0; c < nc; c++) any |= ctl->state[c] == 0;
+      ctl->go = !need && any && ctl->it < a.max_it;
+      publish();
     }
-    it++;
-    pbuf ^= 1;
-#pragma unroll
-    for (int c = 0; c < NCM; c++)
-      if (state[c] == 0 && (rr[c] <= a.tol2ff[c] || rr[c] <= a.drop2 * rr_ref[c])) need = true;
-    if (need) break;  // rz keeps the value the finalize step divides by
-#pragma unroll
-    for (int c = 0; c < NCM; c++) {
-      beta[c] = (state[c] == 0 && rz[c] != 0.0) ? rzn[c] / rz[c] : 0.0;
-      rz[c] = rzn[c];
-    }
+    __syncthreads();
   }
-  if (!ok) flags |= ERR_TIMEOUT;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.cs->it = it;
-    a.cs->pbuf = pbuf;
-    a.cs->need = need ? 1 : 0;
-    a.cs->flags |= flags;
-#pragma unroll
-    for (int c = 0; c < NCM; c++) {
-      if (c < nc) a.cs->state[c] = state[c];
-      a.cs->rz[c] = rz[c];
-      a.cs->beta[c] = beta[c];
+  if (blockIdx.x == 0 && t0) {
+    a.cs->it = ctl->it;
+    a.cs->pbuf = ctl->pbuf;
+    a.cs->need = ctl->need;
+    a.cs->flags |= ctl->flags | (ok ? 0 : ERR_TIMEOUT);
+    for (int c = 0; c < NCM && c < kMaxCases; c++) {
+      if (c < nc) a.cs->state[c] = ctl->state[c];
+      a.cs->rz[c] = ctl->rz[c];
+      a.cs->beta[c] = ctl->beta[c];
     }
   }
 }
