@@ -120,12 +120,12 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* u = a.u + blockIdx.y * a.stride;
   T* y = a.y + blockIdx.y * a.stride;
-  TileOp<DIM, T>::apply(
-      a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw,
+  TileOp<DIM, T>::template apply<1>(
+      a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1,
       [&](long long node, int comp, bool) -> T {
         return ((a.mask[node] >> comp) & 1) ? T(0) : u[node * DIM + comp];
       },
-      [&](long long node, const T(&yv)[DIM], const T(&)[DIM]) {
+      [&](long long node, int, const T(&yv)[DIM], const T(&)[DIM]) {
         const uint8_t mk = a.mask[node];
 #pragma unroll
         for (int r = 0; r < DIM; r++) y[node * DIM + r] = ((mk >> r) & 1) ? u[node * DIM + r] : yv[r];
@@ -198,30 +198,28 @@ __global__ void __launch_bounds__(TileOp<DIM, double>::THREADS)
   double acc[16];
 #pragma unroll
   for (int i = 0; i < 16; i++) acc[i] = 0.0;
-  for (int cs = 0; cs < a.nc; cs++) {
-    double srr = 0.0, srz = 0.0;
-    TileOp<DIM, double>::apply(
-        a.g, a.tm, blockIdx.x, a.E64, a.C, smem_raw,
-        [&](long long node, int comp, bool) -> double {
-          return ((a.mask[node] >> comp) & 1) ? 0.0 : a.x64[node * a.nv + cs * DIM + comp];
-        },
-        [&](long long node, const double(&yv)[DIM], const double(&)[DIM]) {
-          const uint8_t mk = a.mask[node];
+  TileOp<DIM, double>::template apply<kMaxCases>(
+      a.g, a.tm, blockIdx.x, a.E64, a.C, smem_raw, a.nc,
+      [&](long long node, int v, bool) -> double {
+        return ((a.mask[node] >> (v % DIM)) & 1) ? 0.0 : a.x64[node * a.nv + v];
+      },
+      [&](long long node, int cs, const double(&yv)[DIM], const double(&)[DIM]) {
+        const uint8_t mk = a.mask[node];
+        double srr = 0.0, srz = 0.0;
 #pragma unroll
-          for (int r = 0; r < DIM; r++) {
-            const long long idx = node * a.nv + cs * DIM + r;
-            const double r64 = ((mk >> r) & 1) ? 0.0 : a.f[idx] - yv[r];
-            const T rt = (T)r64;
-            const T zt = rt * a.invd[node * DIM + r];
-            a.r[idx] = rt;
-            a.z[idx] = zt;
-            srr += r64 * r64;
-            srz += (double)rt * (double)zt;
-          }
-        });
-    addto<16>(acc, cs, srr);
-    addto<16>(acc, 8 + cs, srz);
-  }
+        for (int r = 0; r < DIM; r++) {
+          const long long idx = node * a.nv + cs * DIM + r;
+          const double r64 = ((mk >> r) & 1) ? 0.0 : a.f[idx] - yv[r];
+          const T rt = (T)r64;
+          const T zt = rt * a.invd[node * DIM + r];
+          a.r[idx] = rt;
+          a.z[idx] = zt;
+          srr += r64 * r64;
+          srz += (double)rt * (double)zt;
+        }
+        addto<16>(acc, cs, srr);
+        addto<16>(acc, 8 + cs, srz);
+      });
   block_sum<16>(acc, sRed);
   if (threadIdx.x == 0)
     for (int i = 0; i < 16; i++) a.part[(size_t)i * gridDim.x + blockIdx.x] = acc[i];
@@ -298,7 +296,7 @@ static cudaError_t residual_impl(cudaStream_t s, const Solver& S, bool init, int
   a.z = (T*)S.z;
   a.part = S.part;
   fill_c<DIM, double>(a.C, S.C);
-  const size_t smem = Op::smem_bytes();
+  const size_t smem = Op::smem_bytes(S.nc);
   auto kern = residual_kernel<DIM, T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -147,32 +147,29 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
 #pragma unroll
     for (int i = 0; i < NCM; i++) accAt[i] = T(0);
     for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
-      for (int cs = 0; cs < nc; cs++) {
-        if (!ctl->act[cs]) continue;
-        const T b = coef(cs);
-        T spq = T(0);
-        Op::apply(
-            a.g, a.tm, t, a.E, a.C, sTile,
-            [&](long long node, int comp, bool own) -> T {
-              const long long idx = node * nv + cs * DIM + comp;
-              T v = __ldcg(a.z + idx);
-              if (b != T(0)) v = fma(b, __ldcg(Pold + idx), v);
-              if (own) Pnew[idx] = v;
-              return v;
-            },
-            [&](long long node, const T(&yv)[DIM], const T(&us)[DIM]) {
-              const uint8_t mk = a.mask[node];
+      Op::template apply<NCM>(
+          a.g, a.tm, t, a.E, a.C, sTile, nc,
+          [&](long long node, int v, bool own) -> T {
+            const long long idx = node * nv + v;
+            const T b = coef(v / DIM);
+            T val = __ldcg(a.z + idx);
+            if (b != T(0)) val = fma(b, __ldcg(Pold + idx), val);
+            if (own) Pnew[idx] = val;
+            return val;
+          },
+          [&](long long node, int cs, const T(&yv)[DIM], const T(&us)[DIM]) {
+            const uint8_t mk = a.mask[node];
+            T spq = T(0);
 #pragma unroll
-              for (int r = 0; r < DIM; r++) {
-                const T qv = ((mk >> r) & 1) ? T(0) : yv[r];
-                a.q[node * nv + cs * DIM + r] = qv;
-                spq = fma(us[r], qv, spq);
-              }
-            });
+            for (int r = 0; r < DIM; r++) {
+              const T qv = ((mk >> r) & 1) ? T(0) : yv[r];
+              a.q[node * nv + cs * DIM + r] = qv;
+              spq = fma(us[r], qv, spq);
+            }
 #pragma unroll
-        for (int c2 = 0; c2 < NCM; c2++)
-          if (c2 == cs) accAt[c2] += spq;
-      }
+            for (int c2 = 0; c2 < NCM; c2++)
+              if (c2 == cs) accAt[c2] += spq;
+          });
     }
     cta_partial<NCM>(accAt, a.part + (size_t)SLOT_A * nb, smem_raw);
     if (!(ok = grid_sync(a.bar, gen))) break;
@@ -290,7 +287,7 @@ static cudaError_t segment_impl(cudaStream_t s, const Solver& S, int nsm, int* g
   a.drop2 = S.drop2;
   a.max_it = S.max_it;
   fill_c<DIM, T>(a.C, S.C);
-  const size_t smem = kSegHeader + Op::smem_bytes();
+  const size_t smem = kSegHeader + Op::smem_bytes(S.nc);
   auto kern = cg_segment_kernel<DIM, T, NCM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -1,15 +1,16 @@
 // Tile operators: apply y = sum_e E_e K0 u_e over one tile of output nodes.
 //
-// Both operators read their input through a functor load(node, comp, own)
-// (masking, or forming p = z + beta p_old on the fly, is the caller's business)
-// and hand every output node to emit(node, y[DIM], u_self[DIM]).  Each output
+// Both operators read their input through a functor load(node, v, own), v =
+// case * DIM + component (masking, or forming p = z + beta p_old on the fly, is
+// the caller's business) and hand every output node to
+// emit(node, case, y[DIM], u_self[DIM]).  Each output
 // node is owned by exactly one tile; elements on tile borders are recomputed by
 // the neighbouring tile, so there are no atomics and the summation order of
 // every node is fixed (bitwise deterministic results).
 //
-//   TileOp<2,T>: 32 x 8 node tile, one node per thread (256 threads).  Each node
-//     evaluates the strains of its four elements from a shared-memory halo tile
-//     and sums its own corner forces.
+//   TileOp<2,T>: 32 x 16 node tile, two nodes per thread (256 threads), all load
+//     cases in one pass.  Each node evaluates the strains of its four elements
+//     from a shared-memory halo tile and sums its own corner forces.
 //   TileOp<3,T>: 32 x 8 node columns x zlen planes, 320 threads, streamed along z.
 //     Per element layer the 33 x 9 elements touching the columns compute all
 //     eight corner forces once (element-centric); each node then sums the lower
@@ -36,7 +37,8 @@ struct TileOp;
 template <typename T>
 struct TileOp<2, T> {
   static constexpr int THREADS = 256;
-  static constexpr int TX = 32, TY = 8, HX = TX + 2, HY = TY + 2, EX = TX + 1, EY = TY + 1;
+  static constexpr int TX = 32, TY = 16, HX = TX + 2, HY = TY + 2, EX = TX + 1, EY = TY + 1;
+  static constexpr int NPT = TX * TY / THREADS;  // output nodes per thread
 
   static __host__ TileMapG map(const Grid& g, int /*zlen*/) {
     TileMapG m;
@@ -47,66 +49,78 @@ struct TileOp<2, T> {
     m.zlen = 1;
     return m;
   }
-  static __host__ __device__ constexpr size_t smem_bytes() {
-    return (size_t)(HX * HY * 2 + EX * EY) * sizeof(T);
+  // shared memory for up to NCM load cases
+  static __host__ __device__ constexpr size_t smem_bytes(int ncm = 1) {
+    return (size_t)(HX * HY * 2 * ncm + EX * EY) * sizeof(T);
   }
 
-  template <class Load, class Emit>
+  // All `nc` cases of the tile in one pass: load(node, v, own) supplies value v
+  // (v = case * 2 + comp) of a node; emit(node, case, y[2], u_self[2]).
+  template <int NCM, class Load, class Emit>
   __device__ static void apply(const Grid& g, const TileMapG& m, int t, const T* __restrict__ E,
-                               const CMat<2, T>& C, unsigned char* smem, Load load, Emit emit) {
-    T* sU = reinterpret_cast<T*>(smem);  // [HY][HX][2]
-    T* sE = sU + HX * HY * 2;            // [EY][EX]
+                               const CMat<2, T>& C, unsigned char* smem, int nc, Load load, Emit emit) {
+    const int nv = 2 * nc;
+    T* sU = reinterpret_cast<T*>(smem);  // [HY][HX][nv]
+    T* sE = sU + HX * HY * nv;           // [EY][EX]
     const int x0 = (t % m.tiles_x) * TX, y0 = (t / m.tiles_x) * TY;
     for (int i = threadIdx.x; i < EX * EY; i += blockDim.x) {
       const int ex = x0 - 1 + i % EX, ey = y0 - 1 + i / EX;
       sE[i] = (ex >= 0 && ex < g.ex && ey >= 0 && ey < g.ey) ? __ldg(E + ex + (long long)g.ex * ey) : T(0);
     }
-    for (int i = threadIdx.x; i < HX * HY * 2; i += blockDim.x) {
-      const int hn = i >> 1, comp = i & 1;
+    const int total = HX * HY * nv;
+#pragma unroll 4
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int hn = i / nv, v = i - hn * nv;
       const int hx = hn % HX, hy = hn / HX;
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-      T v = T(0);
+      T val = T(0);
       if (gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
         const bool own = hx >= 1 && hx <= TX && hy >= 1 && hy <= TY;
-        v = load(gx + (long long)g.nx * gy, comp, own);
+        val = load(gx + (long long)g.nx * gy, v, own);
       }
-      sU[i] = v;
+      sU[i] = val;
     }
     __syncthreads();
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int gx = x0 + tx, gy = y0 + ty;
-    if (threadIdx.x < TX * TY && gx < g.nx && gy < g.ny) {
-      T yx = T(0), yy = T(0);
-      // element in which this node is corner c: tile coords (tx+1-cx, ty+1-cy)
-      auto elem = [&](auto cc) {
-        constexpr int c = decltype(cc)::value;
-        constexpr int cx = (c == 1 || c == 2) ? 1 : 0, cy = c >= 2 ? 1 : 0;
-        const int ex = tx + 1 - cx, ey = ty + 1 - cy;
-        const T Ee = sE[ey * EX + ex];
-        T ux[4], uy[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const int kx = (k == 1 || k == 2) ? 1 : 0, ky = k >= 2 ? 1 : 0;
-          const T* p = sU + ((ey + ky) * HX + ex + kx) * 2;
-          ux[k] = p[0];
-          uy[k] = p[1];
-        }
-        T gg[5], s[5];
-        q4_strain(ux, uy, gg);
-        q4_stress(gg, Ee, C, s);
-        T fx, fy;
-        q4_corner_force<c>(s, fx, fy);
-        yx += fx;
-        yy += fy;
-      };
-      elem(std::integral_constant<int, 0>());
-      elem(std::integral_constant<int, 1>());
-      elem(std::integral_constant<int, 2>());
-      elem(std::integral_constant<int, 3>());
-      const T* ps = sU + ((ty + 1) * HX + tx + 1) * 2;
-      T y[2] = {yx, yy};
-      T us[2] = {ps[0], ps[1]};
-      emit(gx + (long long)g.nx * gy, y, us);
+    for (int k = 0; k < NPT; k++) {
+      const int ln = threadIdx.x + k * THREADS;
+      const int tx = ln % TX, ty = ln / TX;
+      const int gx = x0 + tx, gy = y0 + ty;
+      if (gx >= g.nx || gy >= g.ny) continue;
+      const long long node = gx + (long long)g.nx * gy;
+      for (int cs = 0; cs < nc; cs++) {
+        T yx = T(0), yy = T(0);
+        // element in which this node is corner c: tile coords (tx+1-cx, ty+1-cy)
+        auto elem = [&](auto cc) {
+          constexpr int c = decltype(cc)::value;
+          constexpr int cx = (c == 1 || c == 2) ? 1 : 0, cy = c >= 2 ? 1 : 0;
+          const int ex = tx + 1 - cx, ey = ty + 1 - cy;
+          const T Ee = sE[ey * EX + ex];
+          T ux[4], uy[4];
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int qx = (q == 1 || q == 2) ? 1 : 0, qy = q >= 2 ? 1 : 0;
+            const T* p = sU + ((ey + qy) * HX + ex + qx) * nv + 2 * cs;
+            ux[q] = p[0];
+            uy[q] = p[1];
+          }
+          T gg[5], sg[5];
+          q4_strain(ux, uy, gg);
+          q4_stress(gg, Ee, C, sg);
+          T fx, fy;
+          q4_corner_force<c>(sg, fx, fy);
+          yx += fx;
+          yy += fy;
+        };
+        elem(std::integral_constant<int, 0>());
+        elem(std::integral_constant<int, 1>());
+        elem(std::integral_constant<int, 2>());
+        elem(std::integral_constant<int, 3>());
+        const T* ps = sU + ((ty + 1) * HX + tx + 1) * nv + 2 * cs;
+        T y[2] = {yx, yy};
+        T us[2] = {ps[0], ps[1]};
+        emit(node, cs, y, us);
+      }
     }
     __syncthreads();
   }
@@ -135,9 +149,22 @@ struct TileOp<3, T> {
     return (size_t)(3 * PLANE + 3 * 4 * NEL) * sizeof(V4<T>);
   }
 
-  template <class Load, class Emit>
+  static __host__ __device__ constexpr size_t smem_bytes(int) { return smem_bytes(); }
+
+  // All `nc` cases, one streaming pass per case: load(node, v, own) with
+  // v = case * 3 + comp; emit(node, case, y[3], u_self[3]).
+  template <int NCM, class Load, class Emit>
   __device__ static void apply(const Grid& g, const TileMapG& m, int t, const T* __restrict__ E,
-                               const CMat<3, T>& C, unsigned char* smem, Load load, Emit emit) {
+                               const CMat<3, T>& C, unsigned char* smem, int nc, Load load, Emit emit) {
+    for (int cs = 0; cs < nc; cs++)
+      apply1(
+          g, m, t, E, C, smem, [&](long long node, int comp, bool own) -> T { return load(node, cs * 3 + comp, own); },
+          [&](long long node, const T(&y)[3], const T(&us)[3]) { emit(node, cs, y, us); });
+  }
+
+  template <class Load, class Emit>
+  __device__ static void apply1(const Grid& g, const TileMapG& m, int t, const T* __restrict__ E,
+                                const CMat<3, T>& C, unsigned char* smem, Load load, Emit emit) {
     V4<T>* ring = reinterpret_cast<V4<T>*>(smem);  // [3][HY][HX]
     V4<T>* flo = ring + 3 * PLANE;                 // [4][NEL]   lower corners, current layer
     V4<T>* fhi = flo + 4 * NEL;                    // [2][4][NEL] upper corners, by layer parity
