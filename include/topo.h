@@ -166,6 +166,15 @@ tp_status tp_matvec(tp_problem* p, const void* u, void* y, int precision, int nc
 /* Launch accounting: number of kernels this library enqueued since creation. */
 long long tp_launch_count(const tp_problem* p);
 
+/* Phase tracing of the persistent CG (not in the paper; a profiling aid).
+ * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at four
+ * points of each iteration -- start, after the operator phase, after the vector
+ * phase, after the closing grid barrier -- into a ring of 64 iterations.
+ * tp_get_trace copies the ring (64 x 4 int64, row = iteration mod 64) to `out`
+ * (host).  Tracing adds one store per point and stays off by default. */
+tp_status tp_set_trace(tp_problem* p, int enable);
+tp_status tp_get_trace(tp_problem* p, long long* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,6 +40,7 @@ struct tp_problem {
   CgState* cgs = nullptr;
   double* tol2 = nullptr;
   OcStatus* ost = nullptr;
+  long long* trace = nullptr;  // CG phase timestamps (when enabled)
   double* scal = nullptr;
   double* dc = nullptr;
   double* dcf = nullptr;
@@ -85,7 +86,8 @@ cudaError_t dalloc(T** ptr, size_t count) {
 void free_all(tp_problem* p) {
   void* ptrs[] = {p->rho, p->rho_new, p->E32, p->E64, p->mask, p->passive, p->f, p->x64,
                   p->inv32, p->inv64, p->w[0], p->w[1], p->w[2], p->w[3], p->w[4], p->w[5],
-                  p->part, p->bar, p->cgs, p->tol2, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi};
+                  p->part, p->bar, p->cgs, p->tol2, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi,
+                  p->trace};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -226,6 +228,27 @@ const char* tp_last_error(const tp_problem* p) { return p ? p->err.c_str() : "nu
 
 long long tp_launch_count(const tp_problem* p) { return p ? p->launches : 0; }
 
+tp_status tp_set_trace(tp_problem* p, int enable) {
+  if (!p) return TP_ERR_ARG;
+  if (enable && !p->trace) {
+    TPCK(cudaMalloc((void**)&p->trace, 64 * 4 * sizeof(long long)), "alloc trace");
+    TPCK(cudaMemsetAsync(p->trace, 0, 64 * 4 * sizeof(long long), p->stream), "memset");
+  } else if (!enable && p->trace) {
+    cudaStreamSynchronize(p->stream);
+    cudaFree(p->trace);
+    p->trace = nullptr;
+  }
+  return TP_OK;
+}
+
+tp_status tp_get_trace(tp_problem* p, long long* out) {
+  if (!p || !out) return TP_ERR_ARG;
+  if (!p->trace) return fail(p, TP_ERR_STATE, "tracing is not enabled");
+  TPCK(cudaMemcpyAsync(out, p->trace, 64 * 4 * sizeof(long long), cudaMemcpyDeviceToHost, p->stream), "copy");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  return TP_OK;
+}
+
 tp_status tp_set_fixed(tp_problem* p, const uint8_t* fixed) {
   if (!p || !fixed) return fail(p, TP_ERR_ARG, "null argument");
   std::vector<uint8_t> m(p->nn, 0);
@@ -342,6 +365,7 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
   S.drop2 = f64 ? 0.0 : drop * drop;
   S.max_it = opts->max_it;
   S.C = p->C.data();
+  S.trace = p->trace;
   TPCK(cudaMemcpyAsync(p->tol2, S.tol2ff, sizeof(S.tol2ff), cudaMemcpyHostToDevice, p->stream), "copy");
   TPCK(cudaEventRecord(p->ev0, p->stream), "event");
   int nl = 0;

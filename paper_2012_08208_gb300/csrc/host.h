@@ -49,7 +49,7 @@ struct Solver {
   void* p0;
   void* p1;
   void* q;
-  double* part;          // partial sums; its tail (after 16 * max tiles) holds tol2ff
+  double* part;          // per-CTA / per-tile partial sums
   double* tol2ff_dev;    // device copy of tol^2 ||f_c||^2
   GridBar* bar;
   CgState* cs;
@@ -57,6 +57,7 @@ struct Solver {
   double drop2;
   int max_it;
   const double* C;       // generalised-strain matrix (host, FP64), 5x5 or 18x18
+  long long* trace;      // optional per-iteration phase timestamps (device), or null
 };
 
 // Launchers (return cudaError_t of the launch).

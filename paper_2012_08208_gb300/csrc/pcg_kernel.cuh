@@ -38,8 +38,16 @@ struct SegArgs {
   double tol2ff[kMaxCases];
   double drop2;
   int max_it;
+  long long* trace;  // optional: per-iteration timestamps of CTA 0 (kTraceIters x 4)
   CMat<DIM, T> C;
 };
+
+constexpr int kTraceIters = 64;
+__device__ __forceinline__ long long globaltimer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Shared-memory layout of the segment kernel: reduction scratch, then the
 // per-case control block (owned by thread 0; FP64 scalar work stays off the
@@ -139,6 +147,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
   bool ok = true;
 
   while (ctl->go) {
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 0] = globaltimer();
     // ---- phase A: p = z + beta p_old, q = K p, partial p.q
     const int pbuf = ctl->pbuf;
     const T* Pold = pbuf ? a.p1 : a.p0;
@@ -190,42 +199,49 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     }
     __syncthreads();
 
-    // ---- phase B (one node per thread, all cases and components of the node)
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 1] = globaltimer();
+
+    // ---- phase B.  Nodes are visited with the thread mapping of phase A's
+    // output, so every value read here (r, x_l, q, p of the node) was last
+    // written by this same thread (or by an earlier kernel): L1-cached loads
+    // are coherent, and each cache line is fetched from L2 once.
     T accBt[2 * NCM];
 #pragma unroll
     for (int i = 0; i < 2 * NCM; i++) accBt[i] = T(0);
-    const long long nn = a.g.nn;
-    for (long long node = blockIdx.x * (long long)blockDim.x + threadIdx.x; node < nn;
-         node += (long long)nb * blockDim.x) {
-      T inv[DIM];
+    for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
+      Op::for_each_own(a.g, a.tm, t, [&](long long node) {
+        T inv[DIM];
 #pragma unroll
-      for (int r = 0; r < DIM; r++) inv[r] = __ldg(a.invd + node * DIM + r);
+        for (int r = 0; r < DIM; r++) inv[r] = __ldg(a.invd + node * DIM + r);
 #pragma unroll
-      for (int cs = 0; cs < NCM; cs++) {
-        if (cs >= nc) break;
-        const T al = coef(kMaxCases + cs);
+        for (int cs = 0; cs < NCM; cs++) {
+          if (cs >= nc) break;
+          const T al = coef(kMaxCases + cs);
 #pragma unroll
-        for (int r = 0; r < DIM; r++) {
-          const long long i = node * nv + cs * DIM + r;
-          T rv = __ldcg(a.r + i);
-          T zv;
-          if (al != T(0)) {
-            const T pv = __ldcg(Pnew + i), qv = __ldcg(a.q + i);
-            a.xl[i] = fma(al, pv, a.xl[i]);
-            rv = fma(-al, qv, rv);
-            a.r[i] = rv;
-            zv = rv * inv[r];
-            a.z[i] = zv;
-          } else {
-            zv = __ldcg(a.z + i);
+          for (int r = 0; r < DIM; r++) {
+            const long long i = node * nv + cs * DIM + r;
+            T rv = a.r[i];
+            T zv;
+            if (al != T(0)) {
+              const T pv = Pnew[i], qv = a.q[i];
+              a.xl[i] = fma(al, pv, a.xl[i]);
+              rv = fma(-al, qv, rv);
+              a.r[i] = rv;
+              zv = rv * inv[r];
+              a.z[i] = zv;
+            } else {
+              zv = a.z[i];
+            }
+            accBt[cs] = fma(rv, zv, accBt[cs]);
+            accBt[NCM + cs] = fma(rv, rv, accBt[NCM + cs]);
           }
-          accBt[cs] = fma(rv, zv, accBt[cs]);
-          accBt[NCM + cs] = fma(rv, rv, accBt[NCM + cs]);
         }
-      }
+      });
     }
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 2] = globaltimer();
     cta_partial<2 * NCM>(accBt, a.part + (size_t)SLOT_B * nb, smem_raw);
     if (!(ok = grid_sync(a.bar, gen))) break;
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 3] = globaltimer();
     cta_total<2 * NCM, T>(a.part + (size_t)SLOT_B * nb, ctl);
     if (t0) {
       ctl->it += 1;
@@ -286,6 +302,7 @@ static cudaError_t segment_impl(cudaStream_t s, const Solver& S, int nsm, int* g
   for (int c = 0; c < kMaxCases; c++) a.tol2ff[c] = S.tol2ff[c];
   a.drop2 = S.drop2;
   a.max_it = S.max_it;
+  a.trace = S.trace;
   fill_c<DIM, T>(a.C, S.C);
   const size_t smem = kSegHeader + Op::smem_bytes(S.nc);
   auto kern = cg_segment_kernel<DIM, T, NCM>;

@@ -54,6 +54,19 @@ struct TileOp<2, T> {
     return (size_t)(HX * HY * 2 * ncm + EX * EY) * sizeof(T);
   }
 
+  // Calls fn(node) for every output node of tile t, with the thread / node
+  // assignment of apply (the thread that emitted a node visits it).
+  template <class Fn>
+  __device__ static void for_each_own(const Grid& g, const TileMapG& m, int t, Fn fn) {
+    const int x0 = (t % m.tiles_x) * TX, y0 = (t / m.tiles_x) * TY;
+#pragma unroll
+    for (int k = 0; k < NPT; k++) {
+      const int ln = threadIdx.x + k * THREADS;
+      const int gx = x0 + ln % TX, gy = y0 + ln / TX;
+      if (gx < g.nx && gy < g.ny) fn(gx + (long long)g.nx * gy);
+    }
+  }
+
   // All `nc` cases of the tile in one pass: load(node, v, own) supplies value v
   // (v = case * 2 + comp) of a node; emit(node, case, y[2], u_self[2]).
   template <int NCM, class Load, class Emit>
@@ -68,7 +81,7 @@ struct TileOp<2, T> {
       sE[i] = (ex >= 0 && ex < g.ex && ey >= 0 && ey < g.ey) ? __ldg(E + ex + (long long)g.ex * ey) : T(0);
     }
     const int total = HX * HY * nv;
-#pragma unroll 4
+#pragma unroll 8
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
       const int hn = i / nv, v = i - hn * nv;
       const int hx = hn % HX, hy = hn / HX;
@@ -150,6 +163,20 @@ struct TileOp<3, T> {
   }
 
   static __host__ __device__ constexpr size_t smem_bytes(int) { return smem_bytes(); }
+
+  // Calls fn(node) for every output node of tile t, with the thread / node
+  // assignment of the node phase of apply1.
+  template <class Fn>
+  __device__ static void for_each_own(const Grid& g, const TileMapG& m, int t, Fn fn) {
+    const int x0 = (t % m.tiles_x) * TX;
+    const int y0 = ((t / m.tiles_x) % m.tiles_y) * TY;
+    const int z0 = (t / (m.tiles_x * m.tiles_y)) * m.zlen;
+    const int z1 = min(z0 + m.zlen, g.nz);
+    if (threadIdx.x >= TX * TY) return;
+    const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX;
+    if (gx >= g.nx || gy >= g.ny) return;
+    for (int kz = z0; kz < z1; kz++) fn(gx + (long long)g.nx * (gy + (long long)g.ny * kz));
+  }
 
   // All `nc` cases, one streaming pass per case: load(node, v, own) with
   // v = case * 3 + comp; emit(node, case, y[3], u_self[3]).

@@ -71,6 +71,8 @@ def _load():
         "tp_get": (C.c_int, [P, C.c_int, P, C.c_int]),
         "tp_set": (C.c_int, [P, C.c_int, P, C.c_int]),
         "tp_matvec": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
+        "tp_set_trace": (C.c_int, [P, C.c_int]),
+        "tp_get_trace": (C.c_int, [P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -84,7 +86,7 @@ lib = _load()
 # Every name the header declares (checked by the CPU test suite).
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
-            "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec"]
+            "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace"]
 
 
 class TopoError(RuntimeError):
@@ -171,6 +173,14 @@ class Problem:
 
     def launch_count(self):
         return int(lib.tp_launch_count(self.h))
+
+    def set_trace(self, enable=True):
+        self._check(lib.tp_set_trace(self.h, 1 if enable else 0))
+
+    def get_trace(self):
+        out = np.zeros((64, 4), dtype=np.int64)
+        self._check(lib.tp_get_trace(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def set_fixed(self, fixed):
         a = np.ascontiguousarray(fixed, dtype=np.uint8)
