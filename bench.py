@@ -120,8 +120,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     w = W.cantilever2d()
-    opts = topo.solve_opts(tol=w.tol, max_it=200000, precision=topo.TP_PREC_MIXED,
-                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=1e-2)
+    opts = topo.solve_opts(tol=w.tol, max_it=100000, precision=topo.TP_PREC_MIXED,
+                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=1e-1)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -133,7 +133,7 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         p = topo.Problem.from_workload(w, stream=stream.cuda_stream)
         for _ in range(args.warmup):
-            p.simp_step(opts)
+            p.simp_step(opts, check=False)
             flush.add_(1.0)
         barrier()
         clocks = ClockSampler(local)
@@ -145,7 +145,7 @@ def run_ours(args):
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
             ev[k][0].record(stream)
-            infos.append(p.simp_step(opts))
+            infos.append(p.simp_step(opts, check=False))
             ev[k][1].record(stream)
             flush.add_(1.0)  # L2 flush between timed steps (outside the events)
         barrier()
@@ -162,7 +162,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             p.set_density(rho_h)
-            p.simp_step(opts)
+            p.simp_step(opts, check=False)
             p.get(topo.TP_RHO, out=out_h)
             rho_h.copy_(out_h)
         barrier()
@@ -212,6 +212,8 @@ def run_ours(args):
                      "cg_iters_per_step": float(np.mean([i.solve.iters for i in infos])),
                      "updates_per_step": float(np.mean([i.solve.updates for i in infos])),
                      "solve_ms_per_step": round(avg_ms, 3),
+                     "converged_steps": int(sum(i.solve.converged for i in infos)),
+                     "max_true_rel_res": float(max(max(i.solve.rel_res[c] for c in range(w.n_cases)) for i in infos)),
                      "note": "working set of this workload is L2-resident within a step"},
         "clocks": clk,
         "cpu_baseline": cpu,
