@@ -166,6 +166,37 @@ tp_status tp_matvec(tp_problem* p, const void* u, void* y, int precision, int nc
 /* Launch accounting: number of kernels this library enqueued since creation. */
 long long tp_launch_count(const tp_problem* p);
 
+/* Allocation-free OC update.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they update the
+ * design -- e.g. a host framework whose allocator already holds the device
+ * memory budget, a plugin host that forbids device allocations after start-up,
+ * or a tight loop that must not pay for cudaMalloc/cudaFree and the device-wide
+ * synchronisation cudaFree can imply.  It computes exactly what tp_oc_update
+ * computes (same kernel, same readings), without a problem handle and without
+ * allocating anything: its scratch (about 8.3 MB) is one static device array
+ * that each GPU loading this library keeps until the process exits.
+ *
+ * Arguments: rho[n_el], dcf[n_el] (filtered sensitivities) and rho_new[n_el]
+ * are device pointers on the current device; passive[n_el] (device, 1 = void) may
+ * be NULL; rho_new must not alias rho or dcf.  volfrac, move, dmin as in
+ * tp_params.  cuda_stream: the stream to run on (NULL = legacy default stream).
+ * lambda, volume, change (host, each may be NULL) receive the multiplier, the new
+ * volume and max |rho_new - rho|.  The call synchronises the stream before it
+ * returns.
+ * Limits and errors: 1 <= n_el <= TP_NOALLOC_MAX_ELEMENTS, else TP_ERR_ARG (the
+ * scratch holds one double per element); bad ranges or NULL arrays give
+ * TP_ERR_ARG; CUDA failures TP_ERR_CUDA.
+ * Sharing: every call uses the same scratch array, which keeps the last call's
+ * contents (the call clears what must start at zero).  Calls whose work overlaps
+ * on the GPU -- e.g. from two threads or on two streams at once -- race and give
+ * undefined results; serialise them.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture. */
+#define TP_NOALLOC_MAX_ELEMENTS 1048576LL
+tp_status tp_oc_update_noalloc(const double* rho, const double* dcf, const int8_t* passive, long long n_el,
+                               double volfrac, double move, double dmin, double* rho_new, void* cuda_stream,
+                               double* lambda, double* volume, double* change);
+
 /* Phase tracing of the persistent CG (not in the paper; a profiling aid).
  * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at four
  * points of each iteration -- start, after the operator phase, after the vector

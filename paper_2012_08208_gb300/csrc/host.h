@@ -99,6 +99,8 @@ struct OcStatus {
 cudaError_t launch_oc(cudaStream_t s, long long ne, const double* rho, const double* dcf,
                       const int8_t* passive, double volfrac, double move, double dmin,
                       double* rho_new, double* bscratch, double* part, GridBar* bar, OcStatus* st,
-                      int nsm, int* grid_out);
+                      int nsm, int* grid_out, int max_grid = 0);
+// Partial-sum slots the OC kernel needs for `grid` CTAs (doubles).
+constexpr long long oc_part_doubles(int grid) { return (long long)(2 * 15 + 2) * grid; }
 
 }  // namespace tp

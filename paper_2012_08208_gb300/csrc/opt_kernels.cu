@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
 cudaError_t launch_oc(cudaStream_t s, long long ne, const double* rho, const double* dcf,
                       const int8_t* passive, double volfrac, double move, double dmin,
                       double* rho_new, double* bscratch, double* part, GridBar* bar, OcStatus* st,
-                      int nsm, int* grid_out) {
+                      int nsm, int* grid_out, int max_grid) {
   OcArgs a;
   a.ne = ne;
   a.rho = rho;
@@ -314,6 +314,7 @@ cudaError_t launch_oc(cudaStream_t s, long long ne, const double* rho, const dou
   long long need = (ne + 255) / 256;
   int grid = per_sm * nsm;
   if (need < grid) grid = (int)need;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
   if (grid < 1) grid = 1;
   *grid_out = grid;
   void* args[] = {(void*)&a};

@@ -72,6 +72,8 @@ def _load():
         "tp_set": (C.c_int, [P, C.c_int, P, C.c_int]),
         "tp_matvec": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
         "tp_set_trace": (C.c_int, [P, C.c_int]),
+        "tp_oc_update_noalloc": (C.c_int, [P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double, P, P,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_get_trace": (C.c_int, [P, P]),
     }
     for name, (res, args) in sigs.items():
@@ -86,7 +88,24 @@ lib = _load()
 # Every name the header declares (checked by the CPU test suite).
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
-            "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace"]
+            "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
+            "tp_oc_update_noalloc"]
+NOALLOC_MAX_ELEMENTS = 1048576
+
+
+def oc_update_noalloc(rho, dcf, rho_new, volfrac, move=0.2, dmin=1e-3, passive=None, stream=None):
+    """Allocation-free OC update on device tensors (see tp_oc_update_noalloc in
+    include/topo.h).  rho, dcf, rho_new: CUDA float64 tensors; passive: CUDA int8
+    tensor or None.  Returns (lambda, volume, change)."""
+    lam, vol, ch = C.c_double(), C.c_double(), C.c_double()
+    pp = C.c_void_p(passive.data_ptr()) if passive is not None else None
+    st = lib.tp_oc_update_noalloc(C.c_void_p(rho.data_ptr()), C.c_void_p(dcf.data_ptr()), pp, rho.numel(),
+                                  volfrac, move, dmin, C.c_void_p(rho_new.data_ptr()),
+                                  C.c_void_p(0 if stream is None else int(stream)),
+                                  C.byref(lam), C.byref(vol), C.byref(ch))
+    if st != TP_OK:
+        raise TopoError(st, "tp_oc_update_noalloc failed")
+    return lam.value, vol.value, ch.value
 
 
 class TopoError(RuntimeError):
