@@ -155,15 +155,16 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     T accAt[NCM];
 #pragma unroll
     for (int i = 0; i < NCM; i++) accAt[i] = T(0);
+    // The loader only loads (a store between loads would keep the compiler from
+    // batching them); p of the tile's own nodes is written at emit time.
     for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
       Op::template apply<NCM>(
           a.g, a.tm, t, a.E, a.C, sTile, nc,
-          [&](long long node, int v, bool own) -> T {
+          [&](long long node, int v, bool) -> T {
             const long long idx = node * nv + v;
             const T b = coef(v / DIM);
             T val = __ldcg(a.z + idx);
             if (b != T(0)) val = fma(b, __ldcg(Pold + idx), val);
-            if (own) Pnew[idx] = val;
             return val;
           },
           [&](long long node, int cs, const T(&yv)[DIM], const T(&us)[DIM]) {
@@ -172,7 +173,9 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
 #pragma unroll
             for (int r = 0; r < DIM; r++) {
               const T qv = ((mk >> r) & 1) ? T(0) : yv[r];
-              a.q[node * nv + cs * DIM + r] = qv;
+              const long long idx = node * nv + cs * DIM + r;
+              a.q[idx] = qv;
+              Pnew[idx] = us[r];
               spq = fma(us[r], qv, spq);
             }
 #pragma unroll
@@ -210,30 +213,40 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     for (int i = 0; i < 2 * NCM; i++) accBt[i] = T(0);
     for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
       Op::for_each_own(a.g, a.tm, t, [&](long long node) {
-        T inv[DIM];
+        // all loads of the node first, then arithmetic, then stores
+        constexpr int NVM = NCM * DIM;
+        T rv[NVM], pv[NVM], qv[NVM], xv[NVM], inv[DIM];
+        const long long base = node * nv;
 #pragma unroll
         for (int r = 0; r < DIM; r++) inv[r] = __ldg(a.invd + node * DIM + r);
 #pragma unroll
-        for (int cs = 0; cs < NCM; cs++) {
-          if (cs >= nc) break;
-          const T al = coef(kMaxCases + cs);
+        for (int v = 0; v < NVM; v++) {
+          if (v < nv) {
+            rv[v] = a.r[base + v];
+            pv[v] = Pnew[base + v];
+            qv[v] = a.q[base + v];
+            xv[v] = a.xl[base + v];
+          }
+        }
 #pragma unroll
-          for (int r = 0; r < DIM; r++) {
-            const long long i = node * nv + cs * DIM + r;
-            T rv = a.r[i];
-            T zv;
-            if (al != T(0)) {
-              const T pv = Pnew[i], qv = a.q[i];
-              a.xl[i] = fma(al, pv, a.xl[i]);
-              rv = fma(-al, qv, rv);
-              a.r[i] = rv;
-              zv = rv * inv[r];
-              a.z[i] = zv;
-            } else {
-              zv = a.z[i];
-            }
-            accBt[cs] = fma(rv, zv, accBt[cs]);
-            accBt[NCM + cs] = fma(rv, rv, accBt[NCM + cs]);
+        for (int v = 0; v < NVM; v++) {
+          if (v >= nv) break;
+          const int cs = v / DIM, r = v - cs * DIM;
+          const T al = coef(kMaxCases + cs);
+          const T rn = fma(-al, qv[v], rv[v]);
+          const T zn = rn * inv[r];
+          xv[v] = fma(al, pv[v], xv[v]);
+          rv[v] = rn;
+          pv[v] = zn;  // reuse as z
+          accBt[cs] = fma(rn, zn, accBt[cs]);
+          accBt[NCM + cs] = fma(rn, rn, accBt[NCM + cs]);
+        }
+#pragma unroll
+        for (int v = 0; v < NVM; v++) {
+          if (v < nv) {
+            a.xl[base + v] = xv[v];
+            a.r[base + v] = rv[v];
+            a.z[base + v] = pv[v];
           }
         }
       });
