@@ -65,20 +65,21 @@ __global__ void diag_kernel(const __grid_constant__ DiagArgs<DIM> a) {
 #pragma unroll
     for (int r = 0; r < DIM; r++) {
       const double v = ((mk >> r) & 1) ? 1.0 : 1.0 / d[r];
-      a.inv64[n * DIM + r] = v;
-      a.inv32[n * DIM + r] = (float)v;
+      a.inv64[r * g.nn + n] = v;
+      a.inv32[r * g.nn + n] = (float)v;
     }
   }
 }
 
+// ABI layout [case][node * dim + comp]  <->  internal planar layout
+// [(case * dim + comp) * n_nodes + node].
 __global__ void to_internal_kernel(const double* __restrict__ src, double* dst, long long nn, int dim,
                                    int nc, const uint8_t* mask, int zero_fixed) {
   const long long total = nn * dim * nc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long node = i / (dim * nc);
-    const int v = (int)(i - node * dim * nc);
-    const int c = v / dim, comp = v - c * dim;
+    const long long v = i / nn, node = i - v * nn;
+    const int c = (int)(v / dim), comp = (int)(v - (long long)c * dim);
     double val = src[(long long)c * nn * dim + node * dim + comp];
     if (zero_fixed && ((mask[node] >> comp) & 1)) val = 0.0;
     dst[i] = val;
@@ -93,7 +94,7 @@ __global__ void to_abi_kernel(const double* __restrict__ src, double* dst, long 
     const long long rem = i - (long long)c * nn * dim;
     const long long node = rem / dim;
     const int comp = (int)(rem - node * dim);
-    dst[i] = src[(node * nc + c) * dim + comp];
+    dst[i] = src[((long long)c * dim + comp) * nn + node];
   }
 }
 
@@ -201,17 +202,17 @@ __global__ void __launch_bounds__(TileOp<DIM, double>::THREADS)
   TileOp<DIM, double>::template apply<kMaxCases>(
       a.g, a.tm, blockIdx.x, a.E64, a.C, smem_raw, a.nc,
       [&](long long node, int v, bool) -> double {
-        return ((a.mask[node] >> (v % DIM)) & 1) ? 0.0 : a.x64[node * a.nv + v];
+        return ((a.mask[node] >> (v % DIM)) & 1) ? 0.0 : a.x64[(long long)v * a.g.nn + node];
       },
       [&](long long node, int cs, const double(&yv)[DIM], const double(&)[DIM]) {
         const uint8_t mk = a.mask[node];
         double srr = 0.0, srz = 0.0;
 #pragma unroll
         for (int r = 0; r < DIM; r++) {
-          const long long idx = node * a.nv + cs * DIM + r;
+          const long long idx = (long long)(cs * DIM + r) * a.g.nn + node;
           const double r64 = ((mk >> r) & 1) ? 0.0 : a.f[idx] - yv[r];
           const T rt = (T)r64;
-          const T zt = rt * a.invd[node * DIM + r];
+          const T zt = rt * a.invd[(long long)r * a.g.nn + node];
           a.r[idx] = rt;
           a.z[idx] = zt;
           srr += r64 * r64;
@@ -346,8 +347,8 @@ __global__ void __launch_bounds__(256) sens_kernel(const __grid_constant__ SensA
 #pragma unroll
         for (int m = 0; m < 4; m++) {
           const long long node = (ex + cofs(m, 0)) + (long long)g.nx * (ey + cofs(m, 1));
-          ux[m] = a.x64[node * a.nv + cs * 2];
-          uy[m] = a.x64[node * a.nv + cs * 2 + 1];
+          ux[m] = a.x64[(long long)(cs * 2) * g.nn + node];
+          uy[m] = a.x64[(long long)(cs * 2 + 1) * g.nn + node];
         }
         ce += q4_energy(ux, uy, a.C);
       } else {
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(256) sens_kernel(const __grid_constant__ SensA
           const long long node = (ex + cofs(m, 0)) +
                                  (long long)g.nx * ((ey + cofs(m, 1)) + (long long)g.ny * (ez + cofs(m, 2)));
 #pragma unroll
-          for (int s = 0; s < 3; s++) u[m][s] = a.x64[node * a.nv + cs * 3 + s];
+          for (int s = 0; s < 3; s++) u[m][s] = a.x64[(long long)(cs * 3 + s) * g.nn + node];
         }
         ce += h8_energy(u, a.C);
       }

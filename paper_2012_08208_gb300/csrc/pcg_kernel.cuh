@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
   SegCtl* ctl = reinterpret_cast<SegCtl*>(smem_raw + kRedBytes);
   unsigned char* sTile = smem_raw + kSegHeader;
   const int nc = a.nc, nv = a.nv, nb = gridDim.x;
+  const long long nn = a.g.nn;
   const bool t0 = threadIdx.x == 0;
   constexpr bool F32 = std::is_same<T, float>::value;
   auto coef = [&](int i) -> T {
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
       Op::template apply<NCM>(
           a.g, a.tm, t, a.E, a.C, sTile, nc,
           [&](long long node, int v, bool) -> T {
-            const long long idx = node * nv + v;
+            const long long idx = (long long)v * nn + node;
             const T b = coef(v / DIM);
             T val = __ldcg(a.z + idx);
             if (b != T(0)) val = fma(b, __ldcg(Pold + idx), val);
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
 #pragma unroll
             for (int r = 0; r < DIM; r++) {
               const T qv = ((mk >> r) & 1) ? T(0) : yv[r];
-              const long long idx = node * nv + cs * DIM + r;
+              const long long idx = (long long)(cs * DIM + r) * nn + node;
               a.q[idx] = qv;
               Pnew[idx] = us[r];
               spq = fma(us[r], qv, spq);
@@ -216,16 +217,16 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
         // all loads of the node first, then arithmetic, then stores
         constexpr int NVM = NCM * DIM;
         T rv[NVM], pv[NVM], qv[NVM], xv[NVM], inv[DIM];
-        const long long base = node * nv;
 #pragma unroll
-        for (int r = 0; r < DIM; r++) inv[r] = __ldg(a.invd + node * DIM + r);
+        for (int r = 0; r < DIM; r++) inv[r] = __ldg(a.invd + (long long)r * nn + node);
 #pragma unroll
         for (int v = 0; v < NVM; v++) {
           if (v < nv) {
-            rv[v] = a.r[base + v];
-            pv[v] = Pnew[base + v];
-            qv[v] = a.q[base + v];
-            xv[v] = a.xl[base + v];
+            const long long i = (long long)v * nn + node;
+            rv[v] = a.r[i];
+            pv[v] = Pnew[i];
+            qv[v] = a.q[i];
+            xv[v] = a.xl[i];
           }
         }
 #pragma unroll
@@ -244,9 +245,10 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
 #pragma unroll
         for (int v = 0; v < NVM; v++) {
           if (v < nv) {
-            a.xl[base + v] = xv[v];
-            a.r[base + v] = rv[v];
-            a.z[base + v] = pv[v];
+            const long long i = (long long)v * nn + node;
+            a.xl[i] = xv[v];
+            a.r[i] = rv[v];
+            a.z[i] = pv[v];
           }
         }
       });

@@ -73,17 +73,18 @@ struct TileOp<2, T> {
   __device__ static void apply(const Grid& g, const TileMapG& m, int t, const T* __restrict__ E,
                                const CMat<2, T>& C, unsigned char* smem, int nc, Load load, Emit emit) {
     const int nv = 2 * nc;
-    T* sU = reinterpret_cast<T*>(smem);  // [HY][HX][nv]
+    T* sU = reinterpret_cast<T*>(smem);  // [nv][HY][HX]
     T* sE = sU + HX * HY * nv;           // [EY][EX]
     const int x0 = (t % m.tiles_x) * TX, y0 = (t / m.tiles_x) * TY;
     for (int i = threadIdx.x; i < EX * EY; i += blockDim.x) {
       const int ex = x0 - 1 + i % EX, ey = y0 - 1 + i / EX;
       sE[i] = (ex >= 0 && ex < g.ex && ey >= 0 && ey < g.ey) ? __ldg(E + ex + (long long)g.ex * ey) : T(0);
     }
+    // planar halo [v][HY][HX]: consecutive threads load consecutive nodes of a row
     const int total = HX * HY * nv;
 #pragma unroll 8
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
-      const int hn = i / nv, v = i - hn * nv;
+      const int v = i / (HX * HY), hn = i - v * (HX * HY);
       const int hx = hn % HX, hy = hn / HX;
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
       T val = T(0);
@@ -113,9 +114,9 @@ struct TileOp<2, T> {
 #pragma unroll
           for (int q = 0; q < 4; q++) {
             const int qx = (q == 1 || q == 2) ? 1 : 0, qy = q >= 2 ? 1 : 0;
-            const T* p = sU + ((ey + qy) * HX + ex + qx) * nv + 2 * cs;
+            const T* p = sU + (2 * cs) * (HX * HY) + (ey + qy) * HX + ex + qx;
             ux[q] = p[0];
-            uy[q] = p[1];
+            uy[q] = p[HX * HY];
           }
           T gg[5], sg[5];
           q4_strain(ux, uy, gg);
@@ -129,9 +130,9 @@ struct TileOp<2, T> {
         elem(std::integral_constant<int, 1>());
         elem(std::integral_constant<int, 2>());
         elem(std::integral_constant<int, 3>());
-        const T* ps = sU + ((ty + 1) * HX + tx + 1) * nv + 2 * cs;
+        const T* ps = sU + (2 * cs) * (HX * HY) + (ty + 1) * HX + tx + 1;
         T y[2] = {yx, yy};
-        T us[2] = {ps[0], ps[1]};
+        T us[2] = {ps[0], ps[HX * HY]};
         emit(node, cs, y, us);
       }
     }
@@ -205,7 +206,7 @@ struct TileOp<3, T> {
     auto load_plane = [&](int kz) {
       T* dst = reinterpret_cast<T*>(ring + slot(kz) * PLANE);
       for (int i = tid; i < PLANE * 3; i += blockDim.x) {
-        const int hn = i / 3, comp = i - 3 * hn;
+        const int comp = i / PLANE, hn = i - comp * PLANE;
         const int hx = hn % HX, hy = hn / HX;
         const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
         T v = T(0);
