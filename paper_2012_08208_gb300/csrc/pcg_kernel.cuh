@@ -74,15 +74,24 @@ __device__ __forceinline__ void cta_partial(T (&v)[NV], double* slot, unsigned c
 }
 template <int NV, typename T>
 __device__ __forceinline__ void cta_total(const double* slot, SegCtl* ctl) {
+  // one warp per value; each lane loads its share of the per-CTA partials in
+  // batches of 8 independent loads, then accumulates in a fixed order
+  constexpr int kB = 8;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int nb = gridDim.x;
   for (int i = warp; i < NV; i += nw) {
     if constexpr (std::is_same<T, float>::value) {
-      const float2* part = reinterpret_cast<const float2*>(slot);
+      const float2* part = reinterpret_cast<const float2*>(slot) + (size_t)i * nb;
       dfl s{0.f, 0.f};
-      for (int b = lane; b < nb; b += 32) {
-        const float2 p = __ldcg(part + (size_t)i * nb + b);
-        s = dfl_add(s, dfl{p.x, p.y});
+      for (int b0 = 0; b0 < nb; b0 += 32 * kB) {
+        float2 buf[kB];
+#pragma unroll
+        for (int j = 0; j < kB; j++) {
+          const int b = b0 + j * 32 + lane;
+          buf[j] = b < nb ? __ldcg(part + b) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < kB; j++) s = dfl_add(s, dfl{buf[j].x, buf[j].y});
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -91,8 +100,18 @@ __device__ __forceinline__ void cta_total(const double* slot, SegCtl* ctl) {
       }
       if (lane == 0) ctl->tot[i] = (double)s.hi + (double)s.lo;
     } else {
+      const double* part = slot + (size_t)i * nb;
       double s = 0.0;
-      for (int b = lane; b < nb; b += 32) s += __ldcg(slot + (size_t)i * nb + b);
+      for (int b0 = 0; b0 < nb; b0 += 32 * kB) {
+        double buf[kB];
+#pragma unroll
+        for (int j = 0; j < kB; j++) {
+          const int b = b0 + j * 32 + lane;
+          buf[j] = b < nb ? __ldcg(part + b) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < kB; j++) s += buf[j];
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) ctl->tot[i] = s;
