@@ -198,11 +198,13 @@ tp_status tp_oc_update_noalloc(const double* rho, const double* dcf, const int8_
                                double* lambda, double* volume, double* change);
 
 /* Phase tracing of the persistent CG (not in the paper; a profiling aid).
- * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at four
- * points of each iteration -- start, after the operator phase, after the vector
- * phase, after the closing grid barrier -- into a ring of 64 iterations.
- * tp_get_trace copies the ring (64 x 4 int64, row = iteration mod 64) to `out`
- * (host).  Tracing adds one store per point and stays off by default. */
+ * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at eight
+ * points of each iteration into a ring of 32 iterations: 0 start, 1 operator
+ * done, 2 CTA partial written, 3 first grid barrier passed, 4 scalars of the
+ * first phase published, 5 vector update done, 6 second grid barrier passed,
+ * 7 totals of the second phase read.  tp_get_trace copies the ring (32 x 8
+ * int64, row = iteration mod 32) to `out` (host).  Tracing adds one store per
+ * point and stays off by default. */
 tp_status tp_set_trace(tp_problem* p, int enable);
 tp_status tp_get_trace(tp_problem* p, long long* out);
 

@@ -231,8 +231,8 @@ long long tp_launch_count(const tp_problem* p) { return p ? p->launches : 0; }
 tp_status tp_set_trace(tp_problem* p, int enable) {
   if (!p) return TP_ERR_ARG;
   if (enable && !p->trace) {
-    TPCK(cudaMalloc((void**)&p->trace, 64 * 4 * sizeof(long long)), "alloc trace");
-    TPCK(cudaMemsetAsync(p->trace, 0, 64 * 4 * sizeof(long long), p->stream), "memset");
+    TPCK(cudaMalloc((void**)&p->trace, 32 * 8 * sizeof(long long)), "alloc trace");
+    TPCK(cudaMemsetAsync(p->trace, 0, 32 * 8 * sizeof(long long), p->stream), "memset");
   } else if (!enable && p->trace) {
     cudaStreamSynchronize(p->stream);
     cudaFree(p->trace);
@@ -244,7 +244,7 @@ tp_status tp_set_trace(tp_problem* p, int enable) {
 tp_status tp_get_trace(tp_problem* p, long long* out) {
   if (!p || !out) return TP_ERR_ARG;
   if (!p->trace) return fail(p, TP_ERR_STATE, "tracing is not enabled");
-  TPCK(cudaMemcpyAsync(out, p->trace, 64 * 4 * sizeof(long long), cudaMemcpyDeviceToHost, p->stream), "copy");
+  TPCK(cudaMemcpyAsync(out, p->trace, 32 * 8 * sizeof(long long), cudaMemcpyDeviceToHost, p->stream), "copy");
   TPCK(cudaStreamSynchronize(p->stream), "sync");
   return TP_OK;
 }

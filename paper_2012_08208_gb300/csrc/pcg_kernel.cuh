@@ -42,7 +42,8 @@ struct SegArgs {
   CMat<DIM, T> C;
 };
 
-constexpr int kTraceIters = 64;
+constexpr int kTraceIters = 32;
+constexpr int kTracePts = 8;
 __device__ __forceinline__ long long globaltimer() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
   bool ok = true;
 
   while (ctl->go) {
-    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 0] = globaltimer();
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 0] = globaltimer();
     // ---- phase A: p = z + beta p_old, q = K p, partial p.q
     const int pbuf = ctl->pbuf;
     const T* Pold = pbuf ? a.p1 : a.p0;
@@ -203,8 +204,11 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
               if (c2 == cs) accAt[c2] += spq;
           });
     }
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 1] = globaltimer();
     cta_partial<NCM>(accAt, a.part + (size_t)SLOT_A * nb, smem_raw);
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 2] = globaltimer();
     if (!(ok = grid_sync(a.bar, gen))) break;
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 3] = globaltimer();
     cta_total<NCM, T>(a.part + (size_t)SLOT_A * nb, ctl);
     if (t0) {
       for (int c = 0; c < kMaxCases; c++) {
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     }
     __syncthreads();
 
-    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 1] = globaltimer();
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 4] = globaltimer();
 
     // ---- phase B.  Nodes are visited with the thread mapping of phase A's
     // output, so every value read here (r, x_l, q, p of the node) was last
@@ -272,11 +276,12 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
         }
       });
     }
-    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 2] = globaltimer();
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 5] = globaltimer();
     cta_partial<2 * NCM>(accBt, a.part + (size_t)SLOT_B * nb, smem_raw);
     if (!(ok = grid_sync(a.bar, gen))) break;
-    if (a.trace && blockIdx.x == 0 && t0) a.trace[4 * (ctl->it % kTraceIters) + 3] = globaltimer();
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 6] = globaltimer();
     cta_total<2 * NCM, T>(a.part + (size_t)SLOT_B * nb, ctl);
+    if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 7] = globaltimer();
     if (t0) {
       ctl->it += 1;
       ctl->pbuf ^= 1;

@@ -197,7 +197,7 @@ class Problem:
         self._check(lib.tp_set_trace(self.h, 1 if enable else 0))
 
     def get_trace(self):
-        out = np.zeros((64, 4), dtype=np.int64)
+        out = np.zeros((32, 8), dtype=np.int64)
         self._check(lib.tp_get_trace(self.h, out.ctypes.data_as(C.c_void_p)))
         return out
 
