@@ -166,6 +166,61 @@ tp_status tp_matvec(tp_problem* p, const void* u, void* y, int precision, int nc
 /* Launch accounting: number of kernels this library enqueued since creation. */
 long long tp_launch_count(const tp_problem* p);
 
+/* ---------------------------------------------------------------------------
+ * Batches of independent 2D problems (one persistent launch for all solves).
+ *
+ * A batch holds n independent 2D Q4 problems (one load case each, same nu),
+ * each with its own grid, volfrac, rmin, penal, move and dmin (Section 4
+ * problem statement per instance).  tp_batch_step performs one SIMP iteration
+ * of every instance:
+ *   - one persistent cooperative CG launch solves all instances (FP32
+ *     operator and vectors, FP64 reductions and true-residual updates inside
+ *     the launch, previous displacement as warm start);
+ *   - then sensitivities, the sensitivity filter and the per-instance OC
+ *     bisection follow, all as batched kernels.
+ * The step's kernels are captured once in a CUDA graph and replayed while the
+ * options stay the same.  Densities start at each instance's volfrac.
+ * Instances are independent: none of these calls exchanges data between them.
+ * Errors as for single problems; tp_batch_last_error describes the last one. */
+typedef struct tp_batch tp_batch;
+typedef struct tp_batch_info {
+  int max_iters;        /* CG iterations of the slowest instance */
+  int updates;          /* FP64 true-residual evaluations (max over instances) */
+  int converged;        /* 1 if every instance met tol */
+  int graph;            /* 1 if the step ran as a replayed CUDA graph */
+  int tile_rows;        /* node rows per tile (tiles are 32 nodes wide) */
+  int ctas;             /* CTAs of the persistent launch */
+  double max_rel_res;   /* largest final true relative residual */
+  double ms;            /* device time of the step */
+} tp_batch_info;
+
+/* params[n]: dim 2, n_cases 1, equal nu.  Allocates all device state. */
+tp_status tp_batch_create(int n, const tp_params* params, void* cuda_stream, tp_batch** out);
+void tp_batch_destroy(tp_batch* b);
+const char* tp_batch_last_error(const tp_batch* b);
+/* Instance i: fixed[2 * nodes_i], loads f[2 * nodes_i] (host, ABI DOF layout),
+ * densities rho[n_el_i] (host, in (0, 1]). */
+tp_status tp_batch_set_fixed(tp_batch* b, int i, const uint8_t* fixed);
+tp_status tp_batch_set_loads(tp_batch* b, int i, const double* f);
+tp_status tp_batch_set_density(tp_batch* b, int i, const double* rho);
+/* Tile shape of the CG launch: tile_rows in {4, 8, 16}, ctas_per_sm in 1..8. */
+tp_status tp_batch_set_tiles(tp_batch* b, int tile_rows, int ctas_per_sm);
+/* Autotuner: times a short CG for every tile_rows x ctas_per_sm in
+ * {4, 8, 16} x {1, 2, 4} and keeps the fastest.  The choice is cached in the JSON
+ * file `cache_path` (may be NULL) under a key naming the size class (instance
+ * count, total nodes to 2 significant digits, SM count); a cached key skips the
+ * sweep.  Outputs (may be NULL): the chosen shape. */
+tp_status tp_batch_autotune(tp_batch* b, const char* cache_path, int* tile_rows, int* ctas_per_sm);
+/* One SIMP iteration of every instance.  opts->precision must be
+ * TP_PREC_MIXED; warm_start is always the previous displacement.  compliance
+ * (host, n doubles, may be NULL) receives each instance's c = f^T u. */
+tp_status tp_batch_step(tp_batch* b, const tp_solve_opts* opts, tp_batch_info* info, double* compliance);
+/* Copy TP_RHO, TP_DC, TP_DCF (n_el_i) or TP_U (2 * nodes_i) of instance i to host
+ * `dst` (may be NULL); scalars (host, 6 doubles, may be NULL) receives compliance,
+ * lambda, volume, change, CG iterations and final true relative residual. */
+tp_status tp_batch_get(tp_batch* b, int i, int what, double* dst, double* scalars);
+long long tp_batch_launch_count(const tp_batch* b);
+
 /* Allocation-free OC update.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory when they update the
  * design -- e.g. a host framework whose allocator already holds the device

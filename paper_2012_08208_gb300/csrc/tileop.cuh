@@ -34,10 +34,10 @@ template <int DIM, typename T>
 struct TileOp;
 
 // ---------------------------------------------------------------------------
-template <typename T>
-struct TileOp<2, T> {
+template <typename T, int TY_ = 16>
+struct Q4Tile {
   static constexpr int THREADS = 256;
-  static constexpr int TX = 32, TY = 16, HX = TX + 2, HY = TY + 2, EX = TX + 1, EY = TY + 1;
+  static constexpr int TX = 32, TY = TY_, HX = TX + 2, HY = TY + 2, EX = TX + 1, EY = TY + 1;
   static constexpr int NPT = TX * TY / THREADS;  // output nodes per thread
 
   static __host__ TileMapG map(const Grid& g, int /*zlen*/) {
@@ -60,8 +60,9 @@ struct TileOp<2, T> {
   __device__ static void for_each_own(const Grid& g, const TileMapG& m, int t, Fn fn) {
     const int x0 = (t % m.tiles_x) * TX, y0 = (t / m.tiles_x) * TY;
 #pragma unroll
-    for (int k = 0; k < NPT; k++) {
+    for (int k = 0; k < (NPT > 0 ? NPT : 1); k++) {
       const int ln = threadIdx.x + k * THREADS;
+      if (ln >= TX * TY) break;
       const int gx = x0 + ln % TX, gy = y0 + ln / TX;
       if (gx < g.nx && gy < g.ny) fn(gx + (long long)g.nx * gy);
     }
@@ -96,8 +97,9 @@ struct TileOp<2, T> {
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NPT; k++) {
+    for (int k = 0; k < (NPT > 0 ? NPT : 1); k++) {
       const int ln = threadIdx.x + k * THREADS;
+      if (ln >= TX * TY) break;
       const int tx = ln % TX, ty = ln / TX;
       const int gx = x0 + tx, gy = y0 + ty;
       if (gx >= g.nx || gy >= g.ny) continue;
@@ -139,6 +141,9 @@ struct TileOp<2, T> {
     __syncthreads();
   }
 };
+
+template <typename T>
+struct TileOp<2, T> : Q4Tile<T, 16> {};
 
 // ---------------------------------------------------------------------------
 template <typename T>

@@ -42,6 +42,11 @@ class tp_solve_info(C.Structure):
                 ("rel_res", C.c_double * 8), ("ms", C.c_double)]
 
 
+class tp_batch_info(C.Structure):
+    _fields_ = [("max_iters", C.c_int), ("updates", C.c_int), ("converged", C.c_int), ("graph", C.c_int),
+                ("tile_rows", C.c_int), ("ctas", C.c_int), ("max_rel_res", C.c_double), ("ms", C.c_double)]
+
+
 class tp_step_info(C.Structure):
     _fields_ = [("solve", tp_solve_info), ("compliance", C.c_double), ("lambda_", C.c_double),
                 ("volume", C.c_double), ("change", C.c_double)]
@@ -72,6 +77,17 @@ def _load():
         "tp_set": (C.c_int, [P, C.c_int, P, C.c_int]),
         "tp_matvec": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
         "tp_set_trace": (C.c_int, [P, C.c_int]),
+        "tp_batch_create": (C.c_int, [C.c_int, C.POINTER(tp_params), P, C.POINTER(P)]),
+        "tp_batch_destroy": (None, [P]),
+        "tp_batch_last_error": (C.c_char_p, [P]),
+        "tp_batch_set_fixed": (C.c_int, [P, C.c_int, P]),
+        "tp_batch_set_loads": (C.c_int, [P, C.c_int, P]),
+        "tp_batch_set_density": (C.c_int, [P, C.c_int, P]),
+        "tp_batch_set_tiles": (C.c_int, [P, C.c_int, C.c_int]),
+        "tp_batch_autotune": (C.c_int, [P, C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "tp_batch_step": (C.c_int, [P, C.POINTER(tp_solve_opts), C.POINTER(tp_batch_info), P]),
+        "tp_batch_get": (C.c_int, [P, C.c_int, C.c_int, P, P]),
+        "tp_batch_launch_count": (C.c_longlong, [P]),
         "tp_oc_update_noalloc": (C.c_int, [P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double, P, P,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_get_trace": (C.c_int, [P, P]),
@@ -89,7 +105,9 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
-            "tp_oc_update_noalloc"]
+            "tp_oc_update_noalloc", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
+            "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count"]
 NOALLOC_MAX_ELEMENTS = 1048576
 
 
@@ -276,3 +294,70 @@ class Problem:
         assert dev == dev2
         self._check(lib.tp_matvec(self.h, ptr_u, ptr_y, precision, ncopies, dev))
         return out
+
+
+class Batch:
+    """Owns a tp_batch handle (independent 2D problems solved together)."""
+
+    def __init__(self, workloads_list, stream=None):
+        n = len(workloads_list)
+        arr = (tp_params * n)(*[make_params(w.dim, w.nelx, w.nely, w.nelz, w.E0, w.Emin, w.nu, w.penal,
+                                             w.volfrac, w.rmin, w.move, w.dmin, w.n_cases)
+                                 for w in workloads_list])
+        h = C.c_void_p()
+        st = lib.tp_batch_create(n, arr, C.c_void_p(0 if stream is None else int(stream)), C.byref(h))
+        if st != TP_OK:
+            raise TopoError(st, "tp_batch_create rejected the parameters")
+        self.h = h
+        self.n = n
+        self.w = list(workloads_list)
+        for i, w in enumerate(self.w):
+            self._check(lib.tp_batch_set_fixed(h, i, np.ascontiguousarray(w.fixed, np.uint8).ctypes.data_as(C.c_void_p)))
+            self._check(lib.tp_batch_set_loads(h, i, np.ascontiguousarray(w.loads[0], np.float64).ctypes.data_as(C.c_void_p)))
+
+    def _check(self, st):
+        if st != TP_OK:
+            raise TopoError(st, lib.tp_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.tp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_density(self, i, rho):
+        a = np.ascontiguousarray(rho, np.float64)
+        self._check(lib.tp_batch_set_density(self.h, i, a.ctypes.data_as(C.c_void_p)))
+
+    def set_tiles(self, tile_rows, ctas_per_sm):
+        self._check(lib.tp_batch_set_tiles(self.h, tile_rows, ctas_per_sm))
+
+    def autotune(self, cache_path=None):
+        ty, cps = C.c_int(), C.c_int()
+        self._check(lib.tp_batch_autotune(self.h, None if cache_path is None else cache_path.encode(),
+                                          C.byref(ty), C.byref(cps)))
+        return ty.value, cps.value
+
+    def step(self, opts, check=True):
+        info = tp_batch_info()
+        comp = np.zeros(self.n)
+        st = lib.tp_batch_step(self.h, C.byref(opts), C.byref(info), comp.ctypes.data_as(C.c_void_p))
+        if check:
+            self._check(st)
+        return info, comp
+
+    def get(self, i, what):
+        w = self.w[i]
+        size = 2 * w.n_nodes if what == TP_U else w.n_el
+        out = np.empty(size)
+        sc = np.empty(6)
+        self._check(lib.tp_batch_get(self.h, i, what, out.ctypes.data_as(C.c_void_p), sc.ctypes.data_as(C.c_void_p)))
+        return out, sc
+
+    def launch_count(self):
+        return int(lib.tp_batch_launch_count(self.h))
