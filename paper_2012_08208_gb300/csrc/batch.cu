@@ -247,7 +247,10 @@ __global__ void __launch_bounds__(256) batch_cg_kernel(const __grid_constant__ B
     cta_partial1(srz, a.part + (size_t)BSLOT_RZT * nb, sred);
   };
   // after a residual phase and its barrier: totals and the instance's update (thread 0)
-  auto after_residual = [&](bool init) {
+  // `own` = the update was requested by this instance; only then does a true
+  // residual that failed to halve count towards stagnation (updates requested
+  // by other instances can come after only a few iterations).
+  auto after_residual = [&](bool init, bool own) {
     const double rr = inst_total(a.part + (size_t)BSLOT_RT * nb, I.cta0, I.ncta, &sbuf);
     const double rzt = inst_total(a.part + (size_t)BSLOT_RZT * nb, I.cta0, I.ncta, &sbuf);
     if (t0) {
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(256) batch_cg_kernel(const __grid_constant__ B
         beta = 0.0;
         state = rr <= I.tol2ff ? 1 : 0;
       } else if (state == 0) {
-        stall = rr > 0.25 * rr_ref ? stall + 1 : 0;
+        if (own) stall = rr > 0.25 * rr_ref ? stall + 1 : 0;
         rr_ref = rr;
         beta = rz != 0.0 ? rzt / rz : 0.0;
         rz = rzt;
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(256) batch_cg_kernel(const __grid_constant__ B
 
   residual();
   ok = grid_sync(a.bar, gen);
-  if (ok) after_residual(true);
+  if (ok) after_residual(true, false);
   bool fresh = true;
   flag_add(1, 0, s_state == 0);
   if (ok) ok = grid_sync(a.bar, gen);
@@ -371,6 +374,7 @@ __global__ void __launch_bounds__(256) batch_cg_kernel(const __grid_constant__ B
     fresh = false;
     bool need = false;
     if (t0) need = state == 0 && (rr <= I.tol2ff || rr <= a.drop2 * rr_ref);
+    const bool own_need = need;
     flag_add(0, it & 1, need);
     if (!(ok = grid_sync(a.bar, gen))) break;
     const bool any_need = flag_read(0, it & 1);
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(256) batch_cg_kernel(const __grid_constant__ B
       if (!(ok = grid_sync(a.bar, gen))) break;
       residual();
       if (!(ok = grid_sync(a.bar, gen))) break;
-      after_residual(false);
+      after_residual(false, own_need);
       updates++;
       fresh = true;
     } else {
@@ -400,7 +404,7 @@ __global__ void __launch_bounds__(256) batch_cg_kernel(const __grid_constant__ B
     if (ok) ok = grid_sync(a.bar, gen);
     if (ok) {
       const int st_keep = t0 ? state : 0;
-      after_residual(false);
+      after_residual(false, false);
       if (t0 && st_keep == 0 && state == 3) state = 0;  // one final evaluation is not stagnation
       updates++;
     }
