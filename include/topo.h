@@ -74,13 +74,18 @@ enum { TP_RHO = 0, TP_U = 1, TP_DC = 2, TP_DCF = 3, TP_CE = 4, TP_RHO_PHYS = 5 }
  * and the solution accumulated in FP64 with reliable updates: whenever the FP32
  * recurrence residual has dropped by `update_drop` (e.g. 1e-2) since the last
  * update, the FP64 true residual f - K u replaces it.  warm_start: TP_WARM_*.
- * TP_WARM_USER uses the displacement set by tp_set(TP_U, ...). */
+ * TP_WARM_USER uses the displacement set by tp_set(TP_U, ...) or by the learned
+ * warm start (tp_warm_start_nn, topo_nn.h); if its true relative residual
+ * exceeds warm_max_rel in any case, the solve falls back to u = 0 and reports
+ * warm_fallback. */
 typedef struct tp_solve_opts {
   double tol;
   int max_it;
   int precision;
   int warm_start;
   double update_drop;
+  double warm_max_rel;  /* TP_WARM_USER: largest accepted starting true relative
+                           residual (0 means 1, i.e. no worse than u = 0) */
 } tp_solve_opts;
 
 typedef struct tp_solve_info {
@@ -90,6 +95,8 @@ typedef struct tp_solve_info {
   int status;           /* tp_status of the solve */
   double rel_res[8];    /* final true relative residual per case */
   double ms;            /* device time of the solve */
+  double rel_res_init[8];  /* true relative residual of the starting guess per case */
+  int warm_fallback;    /* 1 if a TP_WARM_USER start was dropped for u = 0 */
 } tp_solve_info;
 
 typedef struct tp_step_info {

@@ -105,32 +105,38 @@ def init_params(seed=0, c_in=5, c_out=3, widths=(16, 32, 64, 64)):
     return params
 
 
-def forward(params, x, keep=False):
-    """x: [C_in][D][H][W] with D, H, W divisible by 8.  Returns y (and the cache)."""
+def forward(params, x, keep=False, quant=None):
+    """x: [C_in][D][H][W] with D, H, W divisible by 8.  Returns y (and the cache).
+
+    `quant` (optional) is applied to every stored activation -- each ReLU
+    output, pooling output and upsample-plus-skip sum, not the head's output --
+    to model a network that stores its activations at reduced precision
+    (e.g. quant=to_bf16)."""
     cache = []
+    q = (lambda a: a) if quant is None else quant
 
     def conv(i, a, act=True):
         w, b = params[i]
         z = conv3d(a, w, b)
-        y = relu(z) if act else z
+        y = q(relu(z)) if act else z
         cache.append(("conv", i, a, y, act))
         return y
 
     a = conv(0, x)
     s0 = conv(1, a)
-    a = pool2(s0)
+    a = q(pool2(s0))
     a = conv(2, a)
     s1 = conv(3, a)
-    a = pool2(s1)
+    a = q(pool2(s1))
     a = conv(4, a)
     s2 = conv(5, a)
-    a = pool2(s2)
+    a = q(pool2(s2))
     a = conv(6, a)
-    a = up2(a) + s2
+    a = q(up2(a) + s2)
     a = conv(7, a)
-    a = up2(a) + s1
+    a = q(up2(a) + s1)
     a = conv(8, a)
-    a = up2(a) + s0
+    a = q(up2(a) + s0)
     a = conv(9, a)
     y = conv(10, a, act=False)
     return (y, cache) if keep else y

@@ -9,53 +9,9 @@
 
 #include "../../include/topo.h"
 #include "host.h"
+#include "problem.h"
 
 using namespace tp;
-
-struct tp_problem {
-  tp_params prm;
-  cudaStream_t stream = nullptr;
-  int dev = 0, nsm = 0;
-  Grid g;
-  long long nn = 0, ne = 0, ndof = 0;
-  int nc = 1, dim = 2, nv = 2;
-  std::vector<double> K0;
-  std::vector<double> C;  // generalised-strain matrix (K0 = G^T C G)
-  int zlen = 8;           // 3D streaming tile depth
-  FilterLaunch* flt = nullptr;
-
-  double* rho = nullptr;
-  double* rho_new = nullptr;
-  float* E32 = nullptr;
-  double* E64 = nullptr;
-  uint8_t* mask = nullptr;
-  int8_t* passive = nullptr;
-  double* f = nullptr;
-  double* x64 = nullptr;
-  float* inv32 = nullptr;
-  double* inv64 = nullptr;
-  void* w[6] = {};  // xl, r, z, p0, p1, q (sized for double)
-  double* part = nullptr;
-  GridBar* bar = nullptr;
-  CgState* cgs = nullptr;
-  double* tol2 = nullptr;
-  OcStatus* ost = nullptr;
-  long long* trace = nullptr;  // CG phase timestamps (when enabled)
-  double* scal = nullptr;
-  double* dc = nullptr;
-  double* dcf = nullptr;
-  double* ce = nullptr;
-  double* bscr = nullptr;
-  double* abi = nullptr;
-
-  bool has_fixed = false, has_loads = false, has_density = false, has_u = false;
-  bool has_dc = false, has_dcf = false, E_dirty = true, has_passive = false;
-  double ff[kMaxCases] = {};
-  std::string err;
-  long long launches = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  int last_grid = 0;
-};
 
 namespace {
 
@@ -87,7 +43,7 @@ void free_all(tp_problem* p) {
   void* ptrs[] = {p->rho, p->rho_new, p->E32, p->E64, p->mask, p->passive, p->f, p->x64,
                   p->inv32, p->inv64, p->w[0], p->w[1], p->w[2], p->w[3], p->w[4], p->w[5],
                   p->part, p->bar, p->cgs, p->tol2, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi,
-                  p->trace};
+                  p->trace, p->nn_feat, p->nn_out, p->nn_scal};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -117,6 +73,8 @@ cudaMemcpyKind kind_of(int on_device, bool to_device) {
 }
 
 }  // namespace
+
+tp_status tp_problem_ensure_E(tp_problem* p) { return ensure_E(p); }
 
 extern "C" {
 
@@ -284,6 +242,10 @@ tp_status tp_set_loads(tp_problem* p, const double* f) {
     }
     if (!(s > 0.0)) return fail(p, TP_ERR_ARG, "a load case has no load on free DOFs");
     p->ff[c] = s;
+    double mx = 0.0;
+    for (long long i = 0; i < p->ndof; i++)
+      if (!((m[i / p->dim] >> (i % p->dim)) & 1)) mx = std::max(mx, std::fabs(f[(size_t)c * p->ndof + i]));
+    p->fmax[c] = mx;
   }
   TPCK(cudaMemcpyAsync(p->abi, f, n * sizeof(double), cudaMemcpyHostToDevice, p->stream), "copy loads");
   TPCK(launch_to_internal(p->stream, p->abi, p->f, p->nn, p->dim, p->nc, p->mask, 1), "layout kernel");
@@ -372,6 +334,22 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
   TPCK(launch_true_residual(p->stream, S, f64, true, &nl), "residual kernel");
   p->launches += nl;
   CgState st;
+  TPCK(cudaMemcpyAsync(&st, p->cgs, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "copy state");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  double rel0[kMaxCases] = {};
+  for (int c = 0; c < p->nc; c++) rel0[c] = std::sqrt(st.rr_true[c] / p->ff[c]);
+  int fallback = 0;
+  if (opts->warm_start == TP_WARM_USER) {
+    // A user (or learned) start whose true residual exceeds warm_max_rel times
+    // that of the zero start is dropped: the solve restarts from u = 0.
+    const double lim = opts->warm_max_rel > 0.0 ? opts->warm_max_rel : 1.0;
+    for (int c = 0; c < p->nc; c++) fallback |= !(st.rr_true[c] <= lim * lim * p->ff[c]);
+    if (fallback) {
+      TPCK(cudaMemsetAsync(p->x64, 0, nvals * sizeof(double), p->stream), "memset");
+      TPCK(launch_true_residual(p->stream, S, f64, true, &nl), "residual kernel");
+      p->launches += nl;
+    }
+  }
   for (int guard = 0; guard < 1000000; guard++) {
     TPCK(cudaMemcpyAsync(&st, p->cgs, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "copy state");
     TPCK(cudaStreamSynchronize(p->stream), "sync");
@@ -407,6 +385,8 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
     info->status = rs;
     for (int c = 0; c < p->nc; c++) info->rel_res[c] = std::sqrt(st.rr_true[c] / p->ff[c]);
     info->ms = ms;
+    for (int c = 0; c < p->nc; c++) info->rel_res_init[c] = rel0[c];
+    info->warm_fallback = fallback;
   }
   if (rs == TP_ERR_TIMEOUT) return fail(p, rs, "a device-side wait timed out in the CG kernel");
   if (rs == TP_ERR_BREAKDOWN) return fail(p, rs, "CG breakdown (p^T K p <= 0 or not finite)");

@@ -1246,7 +1246,7 @@ void cache_store(const char* path, const std::string& key, int ty, int cps, doub
 
 // Time `iters` CG iterations (no FP64 update triggers) on the current state.
 tp_status time_cg(tp_batch* b, int iters, double* us_per_iter) {
-  tp_solve_opts o;
+  tp_solve_opts o{};
   o.tol = 1e-300;
   o.max_it = iters;
   o.precision = TP_PREC_MIXED;

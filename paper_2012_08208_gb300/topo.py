@@ -34,12 +34,13 @@ class tp_params(C.Structure):
 
 class tp_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_it", C.c_int), ("precision", C.c_int),
-                ("warm_start", C.c_int), ("update_drop", C.c_double)]
+                ("warm_start", C.c_int), ("update_drop", C.c_double), ("warm_max_rel", C.c_double)]
 
 
 class tp_solve_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("updates", C.c_int), ("converged", C.c_int), ("status", C.c_int),
-                ("rel_res", C.c_double * 8), ("ms", C.c_double)]
+                ("rel_res", C.c_double * 8), ("ms", C.c_double), ("rel_res_init", C.c_double * 8),
+                ("warm_fallback", C.c_int)]
 
 
 class tp_batch_info(C.Structure):
@@ -91,6 +92,24 @@ def _load():
         "tp_oc_update_noalloc": (C.c_int, [P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double, P, P,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_get_trace": (C.c_int, [P, P]),
+        "tpnn_create": (C.c_int, [C.c_int, C.c_int, P, P, C.POINTER(P)]),
+        "tpnn_destroy": (None, [P]),
+        "tpnn_last_error": (C.c_char_p, [P]),
+        "tpnn_param_count": (C.c_longlong, [P]),
+        "tpnn_info": (C.c_int, [P, P, P, P]),
+        "tpnn_set_params": (C.c_int, [P, P]),
+        "tpnn_get_params": (C.c_int, [P, P]),
+        "tpnn_get_grads": (C.c_int, [P, P]),
+        "tpnn_forward": (C.c_int, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P]),
+        "tpnn_backward": (C.c_int, [P, P]),
+        "tpnn_zero_grad": (C.c_int, [P]),
+        "tpnn_adam": (C.c_int, [P, C.c_float, C.c_float, C.c_float, C.c_float]),
+        "tpnn_mse": (C.c_int, [P, P, P, C.c_longlong, P, C.POINTER(C.c_double)]),
+        "tpnn_train_step": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                                      C.POINTER(C.c_double)]),
+        "tpnn_features": (C.c_int, [P, P]),
+        "tpnn_targets": (C.c_int, [P, P]),
+        "tp_warm_start_nn": (C.c_int, [P, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -107,7 +126,12 @@ EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_laun
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
             "tp_oc_update_noalloc", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
-            "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count"]
+            "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
+            "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
+            "tpnn_set_params", "tpnn_get_params", "tpnn_get_grads", "tpnn_forward", "tpnn_backward",
+            "tpnn_zero_grad", "tpnn_adam", "tpnn_mse", "tpnn_train_step", "tpnn_features", "tpnn_targets",
+            "tp_warm_start_nn"]
+TPNN_FEATURES = 8
 NOALLOC_MAX_ELEMENTS = 1048576
 
 
@@ -154,8 +178,9 @@ def make_params(dim, nelx, nely, nelz=0, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0, v
     return tp_params(dim, nelx, nely, nelz, E0, Emin, nu, penal, volfrac, rmin, move, dmin, n_cases)
 
 
-def solve_opts(tol=1e-8, max_it=20000, precision=TP_PREC_MIXED, warm_start=TP_WARM_ZERO, update_drop=1e-2):
-    return tp_solve_opts(tol, max_it, precision, warm_start, update_drop)
+def solve_opts(tol=1e-8, max_it=20000, precision=TP_PREC_MIXED, warm_start=TP_WARM_ZERO, update_drop=1e-2,
+               warm_max_rel=0.0):
+    return tp_solve_opts(tol, max_it, precision, warm_start, update_drop, warm_max_rel)
 
 
 class Problem:
@@ -283,6 +308,26 @@ class Problem:
         ptr, dev = _ptr(src)
         self._check(lib.tp_set(self.h, what, ptr, dev))
 
+    def features(self, out):
+        """Network input of every load case into `out` (CUDA bfloat16 tensor
+        [n_cases, 8, nelz, nely, nelx])."""
+        self._check(lib.tpnn_features(self.h, _dev_ptr(out, 2, self.n_cases * TPNN_FEATURES * self.n_el)))
+        return out
+
+    def targets(self, out):
+        """Normalised element means of the current displacement into `out` (CUDA
+        bfloat16 tensor [n_cases, 3, nelz, nely, nelx])."""
+        self._check(lib.tpnn_targets(self.h, _dev_ptr(out, 2, self.n_cases * 3 * self.n_el)))
+        return out
+
+    def warm_start_nn(self, net):
+        """Store alpha * u^ from the network as the start of the next solve with
+        warm_start=TP_WARM_USER.  Returns (alpha per case, device ms)."""
+        alpha = np.zeros(self.n_cases)
+        ms = C.c_double()
+        self._check(lib.tp_warm_start_nn(self.h, net.h, alpha.ctypes.data_as(C.c_void_p), C.byref(ms)))
+        return alpha, ms.value
+
     def matvec(self, u, precision=TP_PREC_F64, ncopies=1, out=None):
         if isinstance(u, np.ndarray):
             dt = np.float64 if precision == TP_PREC_F64 else np.float32
@@ -361,3 +406,125 @@ class Batch:
 
     def launch_count(self):
         return int(lib.tp_batch_launch_count(self.h))
+
+
+def _dev_ptr(t, itemsize, numel):
+    """Device pointer of a contiguous CUDA tensor with the expected size."""
+    ptr, dev = _ptr(t)
+    if not dev:
+        raise ValueError("a CUDA tensor is required")
+    if t.numel() != numel or t.element_size() != itemsize:
+        raise ValueError(f"expected {numel} elements of {itemsize} bytes, got {t.numel()} of {t.element_size()}")
+    return ptr
+
+
+def layer_shapes(c_in=TPNN_FEATURES, c_out=3, widths=(16, 32, 64, 64)):
+    """(c_out, c_in) of the 11 convolutions in network order."""
+    c0, c1, c2, c3 = widths
+    return [(c0, c_in), (c0, c0), (c1, c0), (c1, c1), (c2, c1), (c2, c2), (c3, c2), (c1, c3), (c0, c1),
+            (c0, c0), (c_out, c0)]
+
+
+def pack_params(params):
+    """[(w[co][ci][27], b[co])] -> the packed FP32 vector of the C-ABI."""
+    return np.concatenate([np.concatenate([np.asarray(w, np.float32).ravel(), np.asarray(b, np.float32).ravel()])
+                           for w, b in params]).astype(np.float32)
+
+
+def unpack_params(flat, shapes):
+    out, o = [], 0
+    for co, ci in shapes:
+        nw = co * ci * 27
+        out.append((np.asarray(flat[o:o + nw], np.float64).reshape(co, ci, 27),
+                    np.asarray(flat[o + nw:o + nw + co], np.float64)))
+        o += nw + co
+    assert o == len(flat)
+    return out
+
+
+class Net:
+    """Owns a tpnn handle: the warm-start U-Net with hand-written BF16/FP32
+    kernels.  Tensor arguments are CUDA tensors (bfloat16 inputs/targets,
+    float32 outputs/gradients) on the network's stream."""
+
+    def __init__(self, c_in=TPNN_FEATURES, widths=(16, 32, 64, 64), stream=None):
+        h = C.c_void_p()
+        wd = (C.c_int * 4)(*widths)
+        st = lib.tpnn_create(c_in, 3, wd, C.c_void_p(0 if stream is None else int(stream)), C.byref(h))
+        if st != TP_OK:
+            raise TopoError(st, "tpnn_create rejected the configuration")
+        self.h = h
+        self.c_in = c_in
+        self.widths = tuple(widths)
+        self.shapes = layer_shapes(c_in, 3, widths)
+        self.n_params = int(lib.tpnn_param_count(h))
+
+    def _check(self, st):
+        if st != TP_OK:
+            raise TopoError(st, lib.tpnn_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.tpnn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        flat = params if isinstance(params, np.ndarray) else pack_params(params)
+        flat = np.ascontiguousarray(flat, np.float32)
+        assert flat.size == self.n_params
+        self._check(lib.tpnn_set_params(self.h, flat.ctypes.data_as(C.c_void_p)))
+
+    def get_params(self):
+        out = np.empty(self.n_params, np.float32)
+        self._check(lib.tpnn_get_params(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def get_grads(self):
+        out = np.empty(self.n_params, np.float32)
+        self._check(lib.tpnn_get_grads(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def forward(self, x, y):
+        n, c, D, H, W = x.shape
+        assert c == self.c_in
+        self._check(lib.tpnn_forward(self.h, _dev_ptr(x, 2, x.numel()), n, D, H, W,
+                                     _dev_ptr(y, 4, n * 3 * D * H * W)))
+        return y
+
+    def backward(self, gy):
+        self._check(lib.tpnn_backward(self.h, _dev_ptr(gy, 4, gy.numel())))
+
+    def zero_grad(self):
+        self._check(lib.tpnn_zero_grad(self.h))
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(lib.tpnn_adam(self.h, lr, beta1, beta2, eps))
+
+    def mse(self, y, t, gy):
+        loss = C.c_double()
+        self._check(lib.tpnn_mse(self.h, _dev_ptr(y, 4, y.numel()), _dev_ptr(t, 2, y.numel()), y.numel(),
+                                 _dev_ptr(gy, 4, y.numel()), C.byref(loss)))
+        return loss.value
+
+    def train_step(self, x, t, lr):
+        n, c, D, H, W = x.shape
+        loss = C.c_double()
+        self._check(lib.tpnn_train_step(self.h, _dev_ptr(x, 2, x.numel()), _dev_ptr(t, 2, n * 3 * D * H * W),
+                                        n, D, H, W, lr, C.byref(loss)))
+        return loss.value
+
+    def save(self, path):
+        np.savez(path, params=self.get_params(), widths=np.array(self.widths), c_in=self.c_in)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        d = np.load(path)
+        net = cls(int(d["c_in"]), tuple(int(v) for v in d["widths"]), stream)
+        net.set_params(d["params"])
+        return net

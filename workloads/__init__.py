@@ -207,6 +207,43 @@ def small3d(nelx: int, nely: int, nelz: int, n_cases: int = 1, rmin: float = 1.5
                    rmin=rmin, fixed=fixed, loads=f, n_iter=10, tol=1e-12, precision="f64")
 
 
+def warmstart3d(nelx: int, nely: int, nelz: int, seed: int) -> Problem:
+    """Seeded 3D cantilever variant for the warm-start network's training
+    trajectories (x = 0 face clamped).  Draw order: volfrac ~ U(0.08, 0.3),
+    rmin ~ U(1.2, 2.5), load kind (0 full line load along z on the bottom edge
+    of the x = nelx face, as in the 3D cantilever; 1 a line segment of that edge;
+    2 a point load on it), the segment or point position, then 0 to 2 passive
+    boxes (void), each with corner and extent uniform over the inner domain.
+    Loads act in -y with unit intensity (line loads lumped as in cantilever3d)."""
+    rng = np.random.default_rng(seed)
+    vf = float(rng.uniform(0.08, 0.3))
+    rmin = float(rng.uniform(1.2, 2.5))
+    kind = int(rng.integers(0, 3))
+    fixed, f = _empty(3, nelx, nely, nelz, 1)
+    _fix_face_x0(fixed, 3, nelx, nely, nelz)
+    if kind == 0:
+        k0, k1 = 0, nelz
+    elif kind == 1:
+        a, b = sorted(int(v) for v in rng.integers(0, nelz + 1, size=2))
+        k0, k1 = a, max(b, a + 1)
+    else:
+        k0 = k1 = int(rng.integers(0, nelz + 1))
+    for k in range(k0, k1 + 1):
+        n = nelx + (nelx + 1) * (0 + (nely + 1) * k)
+        f[0, 3 * n + 1] = -1.0 if k0 == k1 else (-0.5 if k in (k0, k1) else -1.0)
+    passive = np.zeros(nelx * nely * nelz, dtype=np.int8)
+    ek, ej, ei = np.meshgrid(np.arange(nelz), np.arange(nely), np.arange(nelx), indexing="ij")
+    for _ in range(int(rng.integers(0, 3))):
+        lo = rng.uniform([0.2, 0.1, 0.1], [0.7, 0.6, 0.6]) * np.array([nelx, nely, nelz])
+        ext = rng.uniform(0.1, 0.3, size=3) * np.array([nelx, nely, nelz])
+        box = ((ei + 0.5 >= lo[0]) & (ei + 0.5 <= lo[0] + ext[0]) & (ej + 0.5 >= lo[1]) &
+               (ej + 0.5 <= lo[1] + ext[1]) & (ek + 0.5 >= lo[2]) & (ek + 0.5 <= lo[2] + ext[2]))
+        passive[box.ravel()] = 1
+    return Problem(f"warmstart3d_{nelx}x{nely}x{nelz}_s{seed}", 3, nelx, nely, nelz, volfrac=vf, rmin=rmin,
+                   fixed=fixed, loads=f, passive=passive if passive.any() else None, n_iter=30, tol=1e-6,
+                   precision="mixed", extra={"load_kind": kind, "k0": k0, "k1": k1})
+
+
 def random_density(n_el: int, seed: int = 1, lo: float = 1e-3, hi: float = 1.0) -> np.ndarray:
     """rho ~ U(lo, hi), seeded."""
     return np.random.default_rng(seed).uniform(lo, hi, size=n_el)
