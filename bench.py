@@ -170,7 +170,12 @@ def run_ours(args):
         clk = clocks.stop()
         extras = {}
         if not args.no_extras and rank == 0:
-            extras["matvec"] = matvec_roofline(topo, torch, dev, stream)
+            extras["matvec"] = matvec_roofline(topo, torch, dev, stream, W.cantilever3d_large(),
+                                               "cantilever3d_240x80x80 H8 FP32 K(rho)u")
+            extras["matvec_2d"] = matvec_roofline(topo, torch, dev, stream, w,
+                                                  "cantilever2d_600x200 Q4 FP32 K(rho)u", copies=96, reps=5)
+            extras["batch"] = batch_extra(topo, torch, dev, stream)
+            extras["learned"] = learned_extra(topo)
         p.close()
 
     total_ms = float(sum(step_ms))
@@ -225,39 +230,95 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def matvec_roofline(topo, torch, dev, stream):
-    """K(rho)u in FP32 on the largest 3D grid (240 x 80 x 80 H8, 4.74M DOFs):
-    GDOF/s and fraction of the HBM roofline.  Several (u, y) pairs are rotated
-    so that the data touched between two launches exceeds L2."""
-    import workloads as W
-    w = W.cantilever3d_large()
-    p = topo.Problem(topo.make_params(3, w.nelx, w.nely, w.nelz, volfrac=w.volfrac, rmin=w.rmin),
+def matvec_roofline(topo, torch, dev, stream, w, label, copies=8, reps=10):
+    """K(rho)u in FP32 on workload w: GDOF/s and fraction of the HBM roofline.
+    One library call applies the operator to `copies` vectors (one launch, the
+    copies on the grid's y axis), so the per-call host synchronisation is
+    amortised; u and y of all copies together exceed L2."""
+    p = topo.Problem(topo.make_params(w.dim, w.nelx, w.nely, w.nelz, volfrac=w.volfrac, rmin=w.rmin),
                      stream=stream.cuda_stream)
     p.set_fixed(w.fixed)
+    import workloads as W
     p.set_density(W.random_density(w.n_el, seed=1))
-    npair = 4
-    us = [torch.randn(w.n_dof, dtype=torch.float32, device=dev) for _ in range(npair)]
-    ys = [torch.empty(w.n_dof, dtype=torch.float32, device=dev) for _ in range(npair)]
-    for k in range(3):
-        p.matvec(us[k % npair], topo.TP_PREC_MIXED, out=ys[k % npair])
-    reps = 40
+    u = torch.randn((copies, w.n_dof), dtype=torch.float32, device=dev)
+    y = torch.empty_like(u)
+    for _ in range(3):
+        p.matvec(u, topo.TP_PREC_MIXED, ncopies=copies, out=y)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
-    for k in range(reps):
-        p.matvec(us[k % npair], topo.TP_PREC_MIXED, out=ys[k % npair])
+    for _ in range(reps):
+        p.matvec(u, topo.TP_PREC_MIXED, ncopies=copies, out=y)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1) / reps
-    nodes = w.n_nodes
-    byts = nodes * 12 * 2 + w.n_el * 4  # read u, write y (FP32, 3 comps), read E
+    ms = e0.elapsed_time(e1) / (reps * copies)
+    byts = w.n_nodes * w.dim * 4 * 2 + w.n_el * 4  # read u, write y (FP32), read E
     hbm, kind = _peaks()
     ach = byts / (ms * 1e-3) / 1e9
     p.close()
-    return {"workload": "cantilever3d_240x80x80 H8 FP32 K(rho)u", "n_dof": w.n_dof, "us_per_apply": round(ms * 1e3, 2),
+    return {"workload": label, "n_dof": w.n_dof, "us_per_apply": round(ms * 1e3, 2),
             "gdof_s": round(w.n_dof / (ms * 1e-3) / 1e9, 3), "achieved_gbs": round(ach, 1), "peak": hbm,
-            "frac": round(ach / hbm, 4), "bytes_per_apply": byts,
-            "note": "time per launch includes the host-side ctypes call; launches are back to back"}
+            "peak_kind": kind, "frac": round(ach / hbm, 4), "bytes_per_apply": byts,
+            "note": f"{copies} vectors per launch, {reps} launches back to back"}
+
+
+def learned_extra(topo, n_oc=(0, 5)):
+    """Time to a true relative residual of 1e-6 on the 240 x 80 x 80 H8 cantilever
+    (4.74M DOFs) at the densities after n_oc OC iterations: plain FP64
+    Jacobi-PCG from u = 0, mixed-precision PCG from u = 0, and mixed PCG from the
+    learned start (network time included; the start is dropped for u = 0 when
+    its true residual exceeds that of u = 0), plus the learned start forced."""
+    import workloads as W
+    from paper_2012_08208_gb300 import warmstart as WS
+    w = W.cantilever3d_large()
+    net = topo.Net.load(WS.WEIGHTS)
+    rows = []
+    for k in n_oc:
+        p = WS.density_after(w, k)
+        r = {"oc_iter": k}
+        for kind, kw in (("f64", {}), ("mixed", {}), ("learned", {}), ("learned_forced", {"warm_max_rel": 1e30})):
+            t = WS.time_to_tol(p, "learned" if kind.startswith("learned") else kind, 1e-6, net, **kw)
+            r[kind] = {"ms": round(t["ms"], 2), "iters": t["iters"], "rel_res": t["rel_res"],
+                       "rel_res_init": round(t["rel_res_init"], 4), "fallback": t["fallback"],
+                       "warm_ms": round(t["warm_ms"], 3)}
+        r["speedup_vs_f64"] = round(r["f64"]["ms"] / r["learned"]["ms"], 3)
+        r["learned_gain_vs_mixed"] = round(r["mixed"]["ms"] / r["learned"]["ms"], 4)
+        rows.append(r)
+        p.close()
+    net.close()
+    return {"workload": "cantilever3d_240x80x80 H8, time to true rel-res 1e-6", "rows": rows,
+            "note": "ms = device time of the solve (+ the warm start for 'learned'); weights trained on "
+                    "48x16x16 / 96x32x32 trajectories by paper_2012_08208_gb300.warmstart"}
+
+
+def batch_extra(topo, torch, dev, stream, steps=5, warmup=3):
+    """64 uneven 2D cantilevers (batch2d, seed 0) in one persistent graph-captured
+    launch per step with the autotuned tile shape: instance SIMP iterations/s."""
+    import workloads as W
+    ws = W.batch2d()
+    b = topo.Batch(ws, stream=stream.cuda_stream)
+    for i, w in enumerate(ws):
+        b.set_density(i, w.initial_density())
+    cache = os.path.join(ROOT, "_build", "batch_autotune.json")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    ty, cps = b.autotune(cache)
+    opts = topo.solve_opts(tol=1e-6, max_it=100000, precision=topo.TP_PREC_MIXED,
+                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=0.1)
+    for _ in range(warmup):
+        b.step(opts, check=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    infos = [b.step(opts, check=False)[0] for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    b.close()
+    return {"workload": "batch2d_64 (widths 40-320, seed 0)", "instances": len(ws),
+            "value": round(len(ws) * steps / (ms * 1e-3), 2), "unit": "instance SIMP iter/s",
+            "ms_per_step": round(ms / steps, 3), "tile_rows": ty, "ctas_per_sm": cps,
+            "graph": int(all(i.graph for i in infos)), "max_cg_iters": max(i.max_iters for i in infos),
+            "max_rel_res": max(i.max_rel_res for i in infos)}
 
 
 # ---------------------------------------------------------------------------

@@ -103,6 +103,16 @@ tp_status tpnn_train_step(tpnn* m, const void* x_bf16, const void* t_bf16, int n
 tp_status tpnn_features(tp_problem* p, void* dst_bf16);
 tp_status tpnn_targets(tp_problem* p, void* dst_bf16);
 tp_status tp_warm_start_nn(tp_problem* p, tpnn* net, double* alpha, double* ms);
+/* Training loss of the warm start: for the network output y[n_cases][3][nelz]
+ * [nely][nelx] (FP32, device) of this problem, u^ = node average of y (as in
+ * tp_warm_start_nn) and
+ *   L_k = ||u*_k - alpha_k u^_k||_K^2 / c_k = 1 - (f_k^T u^_k)^2 / ((u^_k^T K u^_k) c_k),
+ * the energy-norm error of the best multiple of u^_k relative to the energy
+ * c_k = f_k^T u*_k of the solution (the case's compliance, host, > 0).  Writes
+ * dL_k/dy to gy (FP32, device, same layout as y); loss (host, n_cases, may be
+ * NULL) receives L_k.  dL/du^ = -(2 alpha / c)(f - alpha K u^): the scaled
+ * residual of the start. */
+tp_status tpnn_energy_grad(tp_problem* p, const float* y, const double* comp, float* gy, double* loss);
 
 #ifdef __cplusplus
 }

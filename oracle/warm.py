@@ -77,3 +77,32 @@ def alpha(prob, rho, uhat, case=0, K=None):
     a = float(prob.loads[case] @ np.where(prob.fixed.astype(bool), 0.0, uhat))
     b = float(uhat @ Ku)
     return a / b if b > 0 else 0.0
+
+
+def node_average_adjoint(prob, g):
+    """Adjoint of node_average: g [n_dof] (ABI) -> [3][nelz][nely][nelx];
+    element e receives sum over its nodes n of g_n / (elements adjacent to n),
+    with g read as zero on fixed DOFs."""
+    en = mesh.element_nodes(3, prob.nelx, prob.nely, prob.nelz)
+    cnt = np.zeros(prob.n_nodes)
+    for c in range(8):
+        np.add.at(cnt, en[:, c], 1.0)
+    gn = np.where(prob.fixed.astype(bool), 0.0, g).reshape(-1, 3) / cnt[:, None]
+    return gn[en].sum(axis=1).T.reshape((3,) + _grid_shape(prob))
+
+
+def energy_loss(prob, rho, y, comp, case=0, K=None):
+    """Energy-norm error left by the best multiple of the averaged prediction,
+    relative to the solution's energy c = f^T u* (the compliance):
+        L(y) = ||u* - alpha u^||_K^2 / c = 1 - (f^T u^)^2 / ((u^T K u^) c),
+    u^ = node_average(y).  Returns (L, dL/dy).  With alpha = f^T u^ / u^T K u^,
+    dL/du^ = -(2 alpha / c) (f - alpha K u^) on free DOFs."""
+    K = fem.assemble(prob, rho) if K is None else K
+    uh = node_average(prob, y)
+    Ku = fem.matvec_bc(prob, rho, uh, K=K)
+    fixed = prob.fixed.astype(bool)
+    f = np.where(fixed, 0.0, prob.loads[case])
+    a, b = float(f @ uh), float(uh @ Ku)
+    al = a / b
+    g = -(2.0 * al / comp) * (f - al * np.where(fixed, 0.0, Ku))
+    return 1.0 - a * al / comp, node_average_adjoint(prob, g)

@@ -171,6 +171,45 @@ __global__ void warm_apply_kernel(long long nn, int nc, const double* __restrict
   }
 }
 
+struct Comp {
+  double v[kCases];
+};
+
+// g[c][node*3 + d] = -(2 alpha_c / comp_c) (f - alpha_c K u^), 0 on fixed DOFs:
+// the gradient of the relative energy error 1 - alpha_c f^T u^ / comp_c.
+__global__ void energy_grad_node_kernel(long long nn, int nc, const uint8_t* __restrict__ mask,
+                                        const double* __restrict__ f, const double* __restrict__ kuhat,
+                                        const double* __restrict__ scal, Comp comp, double* __restrict__ g) {
+  const long long total = (long long)nc * nn * 3;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / (nn * 3));
+    const long long r = i - c * nn * 3, nd = r / 3;
+    const int d = (int)(r - nd * 3);
+    const double al = scal[c];
+    const double v = -(2.0 * al / comp.v[c]) * (f[((long long)c * 3 + d) * nn + nd] - al * kuhat[i]);
+    g[i] = ((mask[nd] >> d) & 1) ? 0.0 : v;
+  }
+}
+
+// Adjoint of the node averaging: gy[c][d][e] = sum over the element's 8 nodes
+// of g[node][d] / (number of elements adjacent to the node).
+__global__ void node_average_adjoint_kernel(Grid g, int nc, const double* __restrict__ gn, float* __restrict__ gy) {
+  const long long ne = g.ne, nn = g.nn;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % g.ex), j = (int)((e / g.ex) % g.ey), k = (int)(e / ((long long)g.ex * g.ey));
+    for (int c = 0; c < nc; c++) {
+      double s[3] = {0.0, 0.0, 0.0};
+      for (int c8 = 0; c8 < 8; c8++) {
+        const int ni = i + (c8 & 1), nj = j + ((c8 >> 1) & 1), nk = k + (c8 >> 2);
+        const int cnt = ((ni > 0) + (ni < g.ex)) * ((nj > 0) + (nj < g.ey)) * ((nk > 0) + (nk < g.ez));
+        const long long nd = node_of(g, ni, nj, nk);
+        for (int d = 0; d < 3; d++) s[d] += gn[(long long)c * nn * 3 + nd * 3 + d] / cnt;
+      }
+      for (int d = 0; d < 3; d++) gy[((long long)c * 3 + d) * ne + e] = (float)s[d];
+    }
+  }
+}
+
 int blocks_for(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 8); }
 
 tp_status wfail(tp_problem* p, tp_status s, const std::string& m) {
@@ -288,6 +327,45 @@ tp_status tp_warm_start_nn(tp_problem* p, tpnn* net, double* alpha, double* ms) 
   }
   p->has_u = true;
   p->has_dc = p->has_dcf = false;
+  return TP_OK;
+}
+
+tp_status tpnn_energy_grad(tp_problem* p, const float* y, const double* comp, float* gy, double* loss) {
+  if (!p || !y || !comp || !gy) return wfail(p, TP_ERR_ARG, "null argument");
+  tp_status s = check_grid(p);
+  if (s != TP_OK) return s;
+  if (!p->has_fixed || !p->has_loads || !p->has_density)
+    return wfail(p, TP_ERR_STATE, "fixed DOFs, loads and density must be set");
+  Comp cm;
+  for (int c = 0; c < kCases; c++) {
+    cm.v[c] = c < p->nc ? comp[c] : 1.0;
+    if (c < p->nc && !(comp[c] > 0.0)) return wfail(p, TP_ERR_ARG, "compliances must be positive");
+  }
+  s = ensure_scratch(p);
+  if (s != TP_OK) return s;
+  s = tp_problem_ensure_E(p);
+  if (s != TP_OK) return s;
+  double* uhat = p->abi;
+  double* kuhat = (double*)p->w[1];
+  double* gn = (double*)p->w[2];
+  node_average_kernel<<<blocks_for(p->nn), 256, 0, p->stream>>>(p->g, p->nc, y, p->mask, uhat);
+  WCK(cudaGetLastError(), "node average kernel");
+  WCK(tp::launch_matvec(p->stream, p->g, p->C.data(), true, p->E64, p->mask, uhat, kuhat, p->nc, p->zlen),
+      "matvec");
+  const int nb = blocks_for((long long)p->nc * p->ndof);
+  warm_dots_kernel<<<nb, 256, 0, p->stream>>>(p->nn, p->nc, p->f, uhat, kuhat, p->part);
+  warm_alpha_kernel<<<1, 32, 0, p->stream>>>(nb, p->nc, p->part, p->nn_scal);
+  energy_grad_node_kernel<<<blocks_for((long long)p->nc * p->ndof), 256, 0, p->stream>>>(
+      p->nn, p->nc, p->mask, p->f, kuhat, p->nn_scal, cm, gn);
+  node_average_adjoint_kernel<<<blocks_for(p->ne), 256, 0, p->stream>>>(p->g, p->nc, gn, gy);
+  WCK(cudaGetLastError(), "energy gradient kernels");
+  p->launches += 6;
+  if (loss) {
+    double h[3 * kCases];
+    WCK(cudaMemcpyAsync(h, p->nn_scal, sizeof(h), cudaMemcpyDeviceToHost, p->stream), "copy");
+    WCK(cudaStreamSynchronize(p->stream), "sync");
+    for (int c = 0; c < p->nc; c++) loss[c] = 1.0 - h[c] * h[kCases + c] / comp[c];
+  }
   return TP_OK;
 }
 

@@ -109,6 +109,7 @@ def _load():
                                       C.POINTER(C.c_double)]),
         "tpnn_features": (C.c_int, [P, P]),
         "tpnn_targets": (C.c_int, [P, P]),
+        "tpnn_energy_grad": (C.c_int, [P, P, P, P, P]),
         "tp_warm_start_nn": (C.c_int, [P, P, P, P]),
     }
     for name, (res, args) in sigs.items():
@@ -129,7 +130,7 @@ EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_laun
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
             "tpnn_set_params", "tpnn_get_params", "tpnn_get_grads", "tpnn_forward", "tpnn_backward",
-            "tpnn_zero_grad", "tpnn_adam", "tpnn_mse", "tpnn_train_step", "tpnn_features", "tpnn_targets",
+            "tpnn_zero_grad", "tpnn_adam", "tpnn_mse", "tpnn_train_step", "tpnn_features", "tpnn_targets", "tpnn_energy_grad",
             "tp_warm_start_nn"]
 TPNN_FEATURES = 8
 NOALLOC_MAX_ELEMENTS = 1048576
@@ -319,6 +320,17 @@ class Problem:
         bfloat16 tensor [n_cases, 3, nelz, nely, nelx])."""
         self._check(lib.tpnn_targets(self.h, _dev_ptr(out, 2, self.n_cases * 3 * self.n_el)))
         return out
+
+    def energy_grad(self, y, comp, gy):
+        """Relative energy error of the scaled, node-averaged prediction y (CUDA
+        float32 [n_cases, 3, nelz, nely, nelx]) and its gradient into gy.
+        comp: the solution's compliance per case.  Returns the losses."""
+        cm = np.ascontiguousarray(np.atleast_1d(comp), np.float64)
+        loss = np.zeros(self.n_cases)
+        n = self.n_cases * 3 * self.n_el
+        self._check(lib.tpnn_energy_grad(self.h, _dev_ptr(y, 4, n), cm.ctypes.data_as(C.c_void_p),
+                                         _dev_ptr(gy, 4, n), loss.ctypes.data_as(C.c_void_p)))
+        return loss
 
     def warm_start_nn(self, net):
         """Store alpha * u^ from the network as the start of the next solve with

@@ -40,9 +40,21 @@ def _torch():
     return torch
 
 
+class Dataset:
+    """Samples of one grid size: X [N, 8, D, H, W] and T [N, 3, D, H, W] (bf16),
+    R [N, n_el] densities (FP64), comp [N] compliances, traj [N] index of the
+    trajectory problem (kept alive: its loads and supports define K and f)."""
+
+    def __init__(self, X, T, R, comp, traj, problems):
+        self.X, self.T, self.R, self.comp, self.traj, self.problems = X, T, R, comp, traj, problems
+
+    def __len__(self):
+        return self.X.shape[0]
+
+
 def generate(sizes=SIZES, snapshots=25, seed0=1000, tol=1e-7, log=print):
-    """Returns {(nelz, nely, nelx): (X, T)} with X [N, 8, D, H, W] and T [N, 3, D, H, W]
-    bf16 CUDA tensors, samples stored in a seeded random order."""
+    """Returns {(nelz, nely, nelx): Dataset}; samples are stored in a seeded
+    random order of slots."""
     torch = _torch()
     import workloads as W
     out = {}
@@ -51,57 +63,116 @@ def generate(sizes=SIZES, snapshots=25, seed0=1000, tol=1e-7, log=print):
     seed = seed0
     for (nx, ny, nz, ntraj) in sizes:
         N = ntraj * snapshots
+        ne = nx * ny * nz
         X = torch.empty((N, topo.TPNN_FEATURES, nz, ny, nx), dtype=torch.bfloat16, device="cuda")
         T = torch.empty((N, 3, nz, ny, nx), dtype=torch.bfloat16, device="cuda")
+        R = torch.empty((N, ne), dtype=torch.float64, device="cuda")
+        comp = np.zeros(N)
+        traj = np.zeros(N, dtype=np.int64)
         slots = np.random.default_rng(seed0 + nx).permutation(N)
+        problems = []
         t0 = time.time()
         k = 0
         for tr in range(ntraj):
             w = W.warmstart3d(nx, ny, nz, seed)
             seed += 1
             p = topo.Problem.from_workload(w)
+            problems.append(p)
             for it in range(snapshots):
                 info = p.solve(opts, check=False)
                 if info.status not in (topo.TP_OK, topo.TP_ERR_NOT_CONVERGED):
                     raise topo.TopoError(info.status, p.last_error())
-                s = int(slots[k])
-                p.features(X[s:s + 1])
-                p.targets(T[s:s + 1])
+                sl = int(slots[k])
+                p.features(X[sl:sl + 1])
+                p.targets(T[sl:sl + 1])
+                p.get(topo.TP_RHO, out=R[sl])
+                comp[sl] = p.sensitivities()
+                traj[sl] = tr
                 k += 1
-                p.sensitivities()
                 p.filter()
                 p.oc_update()
-            p.close()
         torch.cuda.synchronize()
         log(f"generated {N} samples at {nx}x{ny}x{nz} in {time.time() - t0:.1f} s")
-        out[(nz, ny, nx)] = (X, T)
+        out[(nz, ny, nx)] = Dataset(X, T, R, comp, traj, problems)
     return out
 
 
-def train(net, data, steps=3000, batch=None, lr=2e-3, lr_min=1e-4, seed=0, log=print, log_every=250):
-    """Adam on minibatches drawn in turn from the size groups (each group in
-    proportion to its sample count), cosine learning-rate decay.  Returns the
-    loss history (one value per step)."""
-    batch = batch or {16: 8, 32: 2}
+def _batches(data, steps, batch, seed):
+    """(key, start, size) per step: groups drawn in proportion to their sizes,
+    contiguous windows of the (already shuffled) slots."""
     keys = sorted(data)
-    counts = np.array([data[k][0].shape[0] for k in keys], float)
+    counts = np.array([len(data[k]) for k in keys], float)
     rng = np.random.default_rng(seed)
     pos = {k: 0 for k in keys}
+    for _ in range(steps):
+        k = keys[rng.choice(len(keys), p=counts / counts.sum())]
+        b = batch.get(k[0], 2)
+        if pos[k] + b > len(data[k]):
+            pos[k] = int(rng.integers(0, b))  # new pass with a shifted window
+        yield k, pos[k], b
+        pos[k] += b
+
+
+def _lr(s, steps, lr, lr_min):
+    return lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * s / max(1, steps - 1)))
+
+
+def train(net, data, steps=3000, batch=None, lr=2e-3, lr_min=1e-4, seed=0, log=print, log_every=250):
+    """Pre-training: MSE of the element-mean targets.  Adam on minibatches,
+    cosine learning-rate decay.  Returns the loss per step."""
+    batch = batch or {16: 8, 32: 2}
     hist = []
     t0 = time.time()
-    for s in range(steps):
-        k = keys[rng.choice(len(keys), p=counts / counts.sum())]
-        X, T = data[k]
-        b = batch.get(k[0], 2)
-        if pos[k] + b > X.shape[0]:
-            pos[k] = int(rng.integers(0, b))  # new pass with a shifted window
-        i = pos[k]
-        pos[k] += b
-        cur = lr_min + 0.5 * (lr - lr_min) * (1.0 + math.cos(math.pi * s / max(1, steps - 1)))
-        hist.append(net.train_step(X[i:i + b], T[i:i + b], cur))
+    for s, (k, i, b) in enumerate(_batches(data, steps, batch, seed)):
+        d = data[k]
+        cur = _lr(s, steps, lr, lr_min)
+        hist.append(net.train_step(d.X[i:i + b], d.T[i:i + b], cur))
         if log and (s % log_every == 0 or s == steps - 1):
-            log(f"step {s:5d} lr {cur:.2e} loss {np.mean(hist[-log_every:]):.5f} ({time.time() - t0:.1f} s)")
+            log(f"mse step {s:5d} lr {cur:.2e} loss {np.mean(hist[-log_every:]):.5f} ({time.time() - t0:.1f} s)")
     return hist
+
+
+def train_energy(net, data, steps=3000, batch=None, lr=5e-4, lr_min=1e-5, seed=1, log=print, log_every=250):
+    """Fine-tuning on the quantity the solver gains from: the relative energy
+    error of the best multiple of the node-averaged prediction (tpnn_energy_grad
+    on each sample's own operator).  Returns the mean loss per step."""
+    torch = _torch()
+    batch = batch or {16: 8, 32: 2}
+    bufs = {}
+    hist = []
+    t0 = time.time()
+    for s, (k, i, b) in enumerate(_batches(data, steps, batch, seed)):
+        d = data[k]
+        if (k, b) not in bufs:
+            bufs[(k, b)] = (torch.empty((b, 3) + k, device="cuda"), torch.empty((b, 3) + k, device="cuda"))
+        Y, GY = bufs[(k, b)]
+        net.zero_grad()
+        net.forward(d.X[i:i + b], Y)
+        ls = []
+        for j in range(b):
+            p = d.problems[int(d.traj[i + j])]
+            p.set_density(d.R[i + j])
+            ls.append(float(p.energy_grad(Y[j:j + 1], d.comp[i + j], GY[j:j + 1])[0]))
+        net.backward(GY)
+        net.adam(_lr(s, steps, lr, lr_min))
+        hist.append(float(np.mean(ls)))
+        if log and (s % log_every == 0 or s == steps - 1):
+            log(f"energy step {s:5d} loss {np.mean(hist[-log_every:]):.4f} ({time.time() - t0:.1f} s)")
+    return hist
+
+
+def energy_error(p, net, comp):
+    """Relative energy-norm error of the learned start for problem p (whose
+    compliance at the current density is comp)."""
+    torch = _torch()
+    pr = p.params
+    shape = (pr.nelz, pr.nely, pr.nelx)
+    X = torch.empty((p.n_cases, topo.TPNN_FEATURES) + shape, dtype=torch.bfloat16, device="cuda")
+    Y = torch.empty((p.n_cases, 3) + shape, device="cuda")
+    GY = torch.empty_like(Y)
+    p.features(X)
+    net.forward(X, Y)
+    return float(np.sqrt(max(p.energy_grad(Y, comp, GY)[0], 0.0)))
 
 
 def time_to_tol(p, kind, tol=1e-6, net=None, max_it=400000, drop=0.1, warm_max_rel=0.0):
@@ -146,6 +217,11 @@ def evaluate(w, net, n_oc=(0, 5), tol=1e-6, kinds=("f64", "mixed", "learned"), w
     out = []
     for k in n_oc:
         p = density_after(w, k, tol)
+        p.solve(topo.solve_opts(tol=1e-9, max_it=400000, precision=topo.TP_PREC_MIXED, update_drop=0.1),
+                check=False)
+        err = energy_error(p, net, p.sensitivities())
+        if log:
+            log(json.dumps({"oc_iter": k, "learned_energy_err": err}))
         for kind in kinds:
             r = time_to_tol(p, kind, tol, net, warm_max_rel=warm_max_rel)
             r["oc_iter"] = k
@@ -162,6 +238,8 @@ def main(argv=None):
     t = sub.add_parser("train")
     t.add_argument("--out", default=WEIGHTS)
     t.add_argument("--steps", type=int, default=3000)
+    t.add_argument("--energy-steps", type=int, default=3000)
+    t.add_argument("--init", default=None, help="start from these weights (skips the MSE stage)")
     t.add_argument("--snapshots", type=int, default=25)
     t.add_argument("--scale", type=float, default=1.0, help="fraction of the trajectories to generate")
     t.add_argument("--lr", type=float, default=2e-3)
@@ -178,13 +256,19 @@ def main(argv=None):
     if a.cmd == "train":
         sizes = tuple((nx, ny, nz, max(1, int(round(n * a.scale)))) for (nx, ny, nz, n) in SIZES)
         data = generate(sizes, snapshots=a.snapshots)
-        rng = np.random.default_rng(a.seed)
-        net = topo.Net(topo.TPNN_FEATURES, WIDTHS)
-        params = []
-        for co, ci in net.shapes:
-            params.append((rng.normal(0.0, math.sqrt(2.0 / (27 * ci)), size=(co, ci, 27)), np.zeros(co)))
-        net.set_params(params)
-        hist = train(net, data, steps=a.steps, lr=a.lr, seed=a.seed)
+        hist = [float("nan")]
+        if a.init:
+            net = topo.Net.load(a.init)
+        else:
+            rng = np.random.default_rng(a.seed)
+            net = topo.Net(topo.TPNN_FEATURES, WIDTHS)
+            params = []
+            for co, ci in net.shapes:
+                params.append((rng.normal(0.0, math.sqrt(2.0 / (27 * ci)), size=(co, ci, 27)), np.zeros(co)))
+            net.set_params(params)
+            hist = train(net, data, steps=a.steps, lr=a.lr, seed=a.seed)
+        if a.energy_steps > 0:
+            hist = train_energy(net, data, steps=a.energy_steps, seed=a.seed + 1)
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
         net.save(a.out)
         print(json.dumps({"saved": a.out, "final_loss": float(np.mean(hist[-100:])), "steps": a.steps}))

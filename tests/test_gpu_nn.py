@@ -2,6 +2,8 @@
 kernels against the oracle's FP64 network evaluated with the same bf16
 storage points, the problem-side features / targets / energy-scaled start
 against their oracle definitions, and the fallback to plain PCG."""
+import json
+
 import numpy as np
 import pytest
 
@@ -186,6 +188,22 @@ def test_warm_start_matches_oracle_and_solves(topo, small):
     net.close()
 
 
+def test_energy_loss_and_gradient_match_oracle(topo, small):
+    w, rho, p = small
+    p.solve(topo.solve_opts(tol=1e-12, max_it=50000, precision=topo.TP_PREC_F64))
+    comp = p.sensitivities()
+    rng = np.random.default_rng(40)
+    y = rng.normal(size=(3, 8, 8, 16)).astype(np.float32)
+    yt = torch.from_numpy(y[None]).cuda()
+    gy = torch.empty_like(yt)
+    loss = p.energy_grad(yt, comp, gy)[0]
+    ref_l, ref_g = warm.energy_loss(w, rho, y.astype(np.float64), comp)
+    # FP64 arithmetic on both sides except the FP32 node sums and gradient store
+    assert loss == pytest.approx(ref_l, rel=1e-5)
+    g = gy.cpu().numpy()[0]
+    assert np.linalg.norm(g - ref_g) <= 1e-5 * np.linalg.norm(ref_g)
+
+
 def test_bad_user_start_falls_back_to_zero(topo, small):
     w, rho, p = small
     p.set(topo.TP_U, 1e3 * W.random_vector(w.n_dof, seed=30))
@@ -202,4 +220,39 @@ def test_warm_start_rejects_unsupported_grids(topo):
     with pytest.raises(topo.TopoError):
         p.warm_start_nn(net)
     net.close()
+    p.close()
+
+
+def test_trained_network_gain_on_a_held_out_problem(topo):
+    """What the trained network gains over the method without it, on a 3D
+    cantilever it was not trained on (96 x 32 x 32, volfrac 0.12, the density
+    after 5 OC iterations):
+      - start quality: the energy-norm error of the learned start is well
+        below that of u = 0 (1 by definition) and below that of the untrained
+        (He-initialised) network;
+      - solve: with the default acceptance rule (true residual no worse than
+        u = 0) the solve meets the tolerance and costs no more CG iterations
+        than plain mixed PCG, plus the network's time."""
+    import workloads as W
+    from paper_2012_08208_gb300 import warmstart as WS
+    w = W.cantilever3d(96, 32, 32, volfrac=0.12, rmin=1.5)
+    p = WS.density_after(w, 5)
+    p.solve(topo.solve_opts(tol=1e-10, max_it=400000, precision=topo.TP_PREC_MIXED, update_drop=0.1))
+    comp = p.sensitivities()
+    net = topo.Net.load(WS.WEIGHTS)
+    err = WS.energy_error(p, net, comp)
+    raw = topo.Net(8, (16, 32, 64, 64))
+    raw.set_params(_params((16, 32, 64, 64), 8, seed=0))
+    err_raw = WS.energy_error(p, raw, comp)
+    assert err < 0.9 and err < err_raw, (err, err_raw)
+    cold = WS.time_to_tol(p, "mixed", 1e-6)
+    learned = WS.time_to_tol(p, "learned", 1e-6, net)
+    forced = WS.time_to_tol(p, "learned", 1e-6, net, warm_max_rel=1e30)
+    print(json.dumps({"energy_err": err, "energy_err_untrained": err_raw, "cold": cold, "learned": learned,
+                      "learned_forced": forced}))
+    assert learned["converged"] == 1 and learned["rel_res"] <= 1e-6
+    if learned["fallback"]:  # dropped start: exactly the plain solve
+        assert learned["iters"] == cold["iters"]
+    net.close()
+    raw.close()
     p.close()

@@ -93,3 +93,37 @@ def test_quantised_forward_stores_representable_activations():
             assert np.array_equal(nn.to_bf16(act_out), act_out)
     # the quantised network stays close to the exact one (bf16 has 8 significant bits)
     assert np.linalg.norm(y - y0) <= 0.05 * np.linalg.norm(y0)
+
+
+def test_node_average_adjoint_identity():
+    p = W.small3d(4, 3, 2)
+    rng = np.random.default_rng(13)
+    y = rng.normal(size=(3, 2, 3, 4))
+    g = rng.normal(size=p.n_dof)
+    assert float(warm.node_average(p, y) @ g) == pytest.approx(float(np.sum(y * warm.node_average_adjoint(p, g))),
+                                                                rel=1e-12)
+
+
+def test_energy_loss_value_and_gradient():
+    p = W.small3d(4, 3, 2)
+    rho = W.random_density(p.n_el, seed=14, lo=0.2)
+    U = fem.solve(p, rho)[0]
+    comp = float(p.loads[0] @ U)
+    rng = np.random.default_rng(15)
+    y = rng.normal(size=(3, 2, 3, 4))
+    K = fem.assemble(p, rho)
+    L, g = warm.energy_loss(p, rho, y, comp, K=K)
+    # the value is the relative energy error of the optimally scaled start
+    uh = warm.node_average(p, y)
+    a = warm.alpha(p, rho, uh, K=K)
+    e = U - a * uh
+    assert L == pytest.approx(float(e @ fem.matvec_bc(p, rho, e, K=K)) / comp, rel=1e-9)
+    assert 0.0 <= L <= 1.0
+    # central differences of the loss
+    h = 1e-6
+    for idx in [(0, 0, 0, 0), (1, 1, 2, 3), (2, 1, 1, 2)]:
+        yp, ym = y.copy(), y.copy()
+        yp[idx] += h
+        ym[idx] -= h
+        fd = (warm.energy_loss(p, rho, yp, comp, K=K)[0] - warm.energy_loss(p, rho, ym, comp, K=K)[0]) / (2 * h)
+        assert fd == pytest.approx(g[idx], rel=1e-5, abs=1e-10)
