@@ -386,6 +386,29 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_only(args):
+    """One extra measurement on its own (profiling entry point)."""
+    import torch
+
+    import workloads as W
+    from paper_2012_08208_gb300 import topo
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        if args.only == "matvec3d":
+            out = matvec_roofline(topo, torch, dev, stream, W.cantilever3d_large(),
+                                  "cantilever3d_240x80x80 H8 FP32 K(rho)u", copies=args.copies, reps=args.reps)
+        elif args.only == "matvec2d":
+            out = matvec_roofline(topo, torch, dev, stream, W.cantilever2d(),
+                                  "cantilever2d_600x200 Q4 FP32 K(rho)u", copies=args.copies, reps=args.reps)
+        elif args.only == "batch":
+            out = batch_extra(topo, torch, dev, stream)
+        else:
+            out = learned_extra(topo)
+    print(json.dumps({args.only: out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -395,8 +418,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned"], default=None,
+                    help="run one extra measurement alone (for profiling)")
+    ap.add_argument("--copies", type=int, default=8)
+    ap.add_argument("--reps", type=int, default=10)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.only:
+        run_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

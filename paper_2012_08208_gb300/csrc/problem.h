@@ -21,7 +21,7 @@ struct tp_problem {
   int nc = 1, dim = 2, nv = 2;
   std::vector<double> K0;
   std::vector<double> C;  // generalised-strain matrix (K0 = G^T C G)
-  int zlen = 8;           // 3D streaming tile depth
+  int zlen = 16;          // 3D streaming tile depth (planes per tile, balanced)
   FilterLaunch* flt = nullptr;
 
   double* rho = nullptr;

@@ -11,11 +11,9 @@
 //   TileOp<2,T>: 32 x 16 node tile, two nodes per thread (256 threads), all load
 //     cases in one pass.  Each node evaluates the strains of its four elements
 //     from a shared-memory halo tile and sums its own corner forces.
-//   TileOp<3,T>: 32 x 8 node columns x zlen planes, 320 threads, streamed along z.
-//     Per element layer the 33 x 9 elements touching the columns compute all
-//     eight corner forces once (element-centric); each node then sums the lower
-//     corners of layer k and the upper corners of layer k-1 in a fixed order.
-//     Node planes live in a three-plane ring in shared memory.
+//   TileOp<3,T>: 32 x 8 element columns streamed along z (256 threads), each
+//     thread computing its element's eight corner forces once per layer; node
+//     sums by registers (z), warp shuffles (x) and a shared exchange (y).
 #pragma once
 #include "strain.cuh"
 
@@ -146,40 +144,64 @@ template <typename T>
 struct TileOp<2, T> : Q4Tile<T, 16> {};
 
 // ---------------------------------------------------------------------------
+// H8: element columns streamed along z.
+//
+// A tile is 32 x 8 element columns (one thread each: lane = x, warp = y),
+// elements ex = x0 - 1 + lane, ey = y0 - 1 + warp, and owns the 31 x 7 node
+// columns x0 <= x < x0 + 31, y0 <= y < y0 + 7 (thread (lane, warp) owns node
+// (ex, ey) when lane >= 1 and warp >= 1) over the planes z0 <= z < z1.  Per
+// element layer kz (between node planes kz and kz + 1) each thread
+//   - reads the four new corners (plane kz + 1) from a double-buffered shared
+//     plane; the four old corners are kept in registers from the previous layer;
+//   - issues the global loads of plane kz + 2 before its element arithmetic and
+//     stores them into the free plane buffer afterwards;
+//   - computes its element's eight corner forces (strain form);
+//   - sums, for its own node of plane kz, the lower corners of layer kz and the
+//     upper corners of layer kz - 1 (kept in registers): its own column's by
+//     addition, the x-neighbour's by a warp shuffle, the y-neighbours' through
+//     one double-buffered shared exchange.
+// One __syncthreads per layer.  The summation order of every node is fixed.
 template <typename T>
 struct TileOp<3, T> {
-  static constexpr int THREADS = 320;
-  static constexpr int TX = 32, TY = 8, HX = TX + 2, HY = TY + 2, EX = TX + 1, EY = TY + 1;
-  static constexpr int NEL = EX * EY;  // 297 elements per layer
-  static constexpr int PLANE = HX * HY;
+  static constexpr int THREADS = 256;
+  static constexpr int LX = 32, LY = 8;          // element columns per tile
+  static constexpr int OX = LX - 1, OY = LY - 1;  // owned node columns per tile
+  static constexpr int PX = LX + 1, PY = LY + 1;  // nodes per staged plane
+  static constexpr int PLANE = PX * PY;           // 297
 
   static __host__ TileMapG map(const Grid& g, int zlen) {
     TileMapG m;
     if (zlen < 1) zlen = 1;
     if (zlen > g.nz) zlen = g.nz;
-    m.tiles_x = (g.nx + TX - 1) / TX;
-    m.tiles_y = (g.ny + TY - 1) / TY;
-    m.tiles_z = (g.nz + zlen - 1) / zlen;
+    const int nzt = (g.nz + zlen - 1) / zlen;  // balance the z chunks
+    m.zlen = (g.nz + nzt - 1) / nzt;
+    m.tiles_x = (g.nx + OX - 1) / OX;
+    m.tiles_y = (g.ny + OY - 1) / OY;
+    m.tiles_z = (g.nz + m.zlen - 1) / m.zlen;
     m.ntiles = m.tiles_x * m.tiles_y * m.tiles_z;
-    m.zlen = zlen;
     return m;
   }
   static __host__ __device__ constexpr size_t smem_bytes() {
-    return (size_t)(3 * PLANE + 3 * 4 * NEL) * sizeof(V4<T>);
+    return (size_t)(2 * PLANE + 2 * THREADS) * sizeof(V4<T>);
   }
-
   static __host__ __device__ constexpr size_t smem_bytes(int) { return smem_bytes(); }
 
+  __device__ static void origin(const Grid& g, const TileMapG& m, int t, int& x0, int& y0, int& z0, int& z1) {
+    x0 = (t % m.tiles_x) * OX;
+    y0 = ((t / m.tiles_x) % m.tiles_y) * OY;
+    z0 = (t / (m.tiles_x * m.tiles_y)) * m.zlen;
+    z1 = min(z0 + m.zlen, g.nz);
+  }
+
   // Calls fn(node) for every output node of tile t, with the thread / node
-  // assignment of the node phase of apply1.
+  // assignment of apply1's output.
   template <class Fn>
   __device__ static void for_each_own(const Grid& g, const TileMapG& m, int t, Fn fn) {
-    const int x0 = (t % m.tiles_x) * TX;
-    const int y0 = ((t / m.tiles_x) % m.tiles_y) * TY;
-    const int z0 = (t / (m.tiles_x * m.tiles_y)) * m.zlen;
-    const int z1 = min(z0 + m.zlen, g.nz);
-    if (threadIdx.x >= TX * TY) return;
-    const int gx = x0 + threadIdx.x % TX, gy = y0 + threadIdx.x / TX;
+    int x0, y0, z0, z1;
+    origin(g, m, t, x0, y0, z0, z1);
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    if (lane == 0 || row == 0) return;
+    const int gx = x0 - 1 + lane, gy = y0 - 1 + row;
     if (gx >= g.nx || gy >= g.ny) return;
     for (int kz = z0; kz < z1; kz++) fn(gx + (long long)g.nx * (gy + (long long)g.ny * kz));
   }
@@ -198,87 +220,115 @@ struct TileOp<3, T> {
   template <class Load, class Emit>
   __device__ static void apply1(const Grid& g, const TileMapG& m, int t, const T* __restrict__ E,
                                 const CMat<3, T>& C, unsigned char* smem, Load load, Emit emit) {
-    V4<T>* ring = reinterpret_cast<V4<T>*>(smem);  // [3][HY][HX]
-    V4<T>* flo = ring + 3 * PLANE;                 // [4][NEL]   lower corners, current layer
-    V4<T>* fhi = flo + 4 * NEL;                    // [2][4][NEL] upper corners, by layer parity
-    const int x0 = (t % m.tiles_x) * TX;
-    const int y0 = ((t / m.tiles_x) % m.tiles_y) * TY;
-    const int z0 = (t / (m.tiles_x * m.tiles_y)) * m.zlen;
-    const int z1 = min(z0 + m.zlen, g.nz);  // owned planes [z0, z1)
-    const int tid = threadIdx.x;
+    V4<T>* P = reinterpret_cast<V4<T>*>(smem);  // [2][PY][PX] staged node planes
+    V4<T>* X = P + 2 * PLANE;                   // [2][LY][LX] y-exchange of corner sums
+    int x0, y0, z0, z1;
+    origin(g, m, t, x0, y0, z0, z1);
+    const int tid = threadIdx.x, lane = tid & 31, row = tid >> 5;
+    const int ex = x0 - 1 + lane, ey = y0 - 1 + row;
+    const bool col_ok = ex >= 0 && ex < g.ex && ey >= 0 && ey < g.ey;
+    const bool owner = lane >= 1 && row >= 1 && ex < g.nx && ey < g.ny;
+    const long long nplane = (long long)g.nx * g.ny;
+    // Staging: every thread loads its own column's node (plane slot (row, lane));
+    // threads 0..40 also load one of the 41 nodes of the last plane row and
+    // column (never owned by the tile).
+    const bool main_ok = ex >= 0 && ex < g.nx && ey >= 0 && ey < g.ny;
+    const long long main_off = main_ok ? ex + (long long)g.nx * ey : 0;
+    const int xs_slot = tid < PX ? (PY - 1) * PX + tid : (tid - PX) * PX + PX - 1;
+    const int xs_x = tid < PX ? x0 - 1 + tid : x0 + LX - 1;
+    const int xs_y = tid < PX ? y0 + LY - 1 : y0 - 1 + (tid - PX);
+    const bool has_xs = tid < PX + LY;
+    const bool xs_ok = has_xs && xs_x >= 0 && xs_x < g.nx && xs_y >= 0 && xs_y < g.ny;
+    const long long xs_off = xs_ok ? xs_x + (long long)g.nx * xs_y : 0;
 
-    auto slot = [](int kz) { return ((kz % 3) + 3) % 3; };
-    auto load_plane = [&](int kz) {
-      T* dst = reinterpret_cast<T*>(ring + slot(kz) * PLANE);
-      for (int i = tid; i < PLANE * 3; i += blockDim.x) {
-        const int comp = i / PLANE, hn = i - comp * PLANE;
-        const int hx = hn % HX, hy = hn / HX;
-        const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-        T v = T(0);
-        if (kz >= 0 && kz < g.nz && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny) {
-          const bool own = hx >= 1 && hx <= TX && hy >= 1 && hy <= TY && kz >= z0 && kz < z1;
-          v = load(gx + (long long)g.nx * (gy + (long long)g.ny * kz), comp, own);
-        }
-        dst[hn * 4 + comp] = v;
+    auto prefetch = [&](int kz, T (&v)[6]) {
+      const bool zin = kz >= 0 && kz < g.nz;
+      const bool own = owner && kz >= z0 && kz < z1;
+#pragma unroll
+      for (int r = 0; r < 3; r++) v[r] = (zin && main_ok) ? load(main_off + nplane * kz, r, own) : T(0);
+#pragma unroll
+      for (int r = 0; r < 3; r++) v[3 + r] = (zin && xs_ok) ? load(xs_off + nplane * kz, r, false) : T(0);
+    };
+    auto stage = [&](V4<T>* dst, const T (&v)[6]) {
+      dst[row * PX + lane] = V4<T>{v[0], v[1], v[2], T(0)};
+      if (has_xs) dst[xs_slot] = V4<T>{v[3], v[4], v[5], T(0)};
+    };
+    auto corners = [&](const V4<T>* pl, T (&u)[4][3]) {
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const V4<T> v = pl[(row + cofs(c, 1)) * PX + lane + cofs(c, 0)];
+        u[c][0] = v.x;
+        u[c][1] = v.y;
+        u[c][2] = v.z;
       }
     };
+    auto modulus = [&](int kz) -> T {
+      return (col_ok && kz >= 0 && kz < g.ez) ? __ldg(E + ex + (long long)g.ex * (ey + (long long)g.ey * kz)) : T(-1);
+    };
 
-    load_plane(z0 - 1);
-    for (int kz = z0 - 1; kz < z1; kz++) {  // element layer kz spans node planes kz, kz+1
-      load_plane(kz + 1);
-      __syncthreads();
-      if (tid < NEL) {
-        const int ex_t = tid % EX, ey_t = tid / EX;
-        const int gex = x0 - 1 + ex_t, gey = y0 - 1 + ey_t;
-        V4<T> out[8];
-        const bool valid = gex >= 0 && gex < g.ex && gey >= 0 && gey < g.ey && kz >= 0 && kz < g.ez;
-        if (valid) {
-          const T Ee = __ldg(E + gex + (long long)g.ex * (gey + (long long)g.ey * kz));
-          T u[8][3];
+    {
+      T v[6];
+      prefetch(z0 - 1, v);
+      stage(P + ((z0 - 1) & 1) * PLANE, v);
+      prefetch(z0, v);
+      stage(P + (z0 & 1) * PLANE, v);
+    }
+    __syncthreads();
+    T uo[4][3], fu[4][3];
+    corners(P + ((z0 - 1) & 1) * PLANE, uo);
+    __syncthreads();  // the first layer restages this buffer
 #pragma unroll
-          for (int c = 0; c < 8; c++) {
-            const int cx = cofs(c, 0), cy = cofs(c, 1), cz = cofs(c, 2);
-            const V4<T> v = ring[slot(kz + cz) * PLANE + (ey_t + cy) * HX + ex_t + cx];
-            u[c][0] = v.x;
-            u[c][1] = v.y;
-            u[c][2] = v.z;
+    for (int c = 0; c < 4; c++) fu[c][0] = fu[c][1] = fu[c][2] = T(0);
+    T Ee = modulus(z0 - 1);  // < 0: no element in this column at this layer
+
+    for (int kz = z0 - 1; kz < z1; kz++) {
+      T un[4][3];
+      corners(P + ((kz + 1) & 1) * PLANE, un);
+      T pf[6];
+      const bool more = kz + 2 <= z1;  // plane kz + 2 is needed by the next layer
+      if (more) prefetch(kz + 2, pf);
+      const T Enext = modulus(kz + 1);
+      T f[8][3];
+      if (Ee >= T(0)) {
+        T u[8][3];
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+#pragma unroll
+          for (int r = 0; r < 3; r++) {
+            u[c][r] = uo[c][r];
+            u[c + 4][r] = un[c][r];
           }
-          T f[8][3];
-          h8_element_forces(u, Ee, C, f);
+        h8_element_forces(u, Ee, C, f);
+      } else {
 #pragma unroll
-          for (int c = 0; c < 8; c++) out[c] = V4<T>{f[c][0], f[c][1], f[c][2], T(0)};
-        } else {
-#pragma unroll
-          for (int c = 0; c < 8; c++) out[c] = V4<T>{T(0), T(0), T(0), T(0)};
-        }
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-          flo[c * NEL + tid] = out[c];
-          fhi[((kz & 1) * 4 + c) * NEL + tid] = out[4 + c];
-        }
+        for (int c = 0; c < 8; c++) f[c][0] = f[c][1] = f[c][2] = T(0);
       }
+      // corner sums for plane kz: s_c = lower corner c of layer kz + upper corner c of layer kz - 1
+      T a[3], b[3];
+#pragma unroll
+      for (int r = 0; r < 3; r++) {
+        const T s0 = f[0][r] + fu[0][r], s1 = f[1][r] + fu[1][r];
+        const T s2 = f[2][r] + fu[2][r], s3 = f[3][r] + fu[3][r];
+        a[r] = s0 + __shfl_up_sync(0xffffffffu, s1, 1);  // node (ex, ey): elements ex and ex - 1
+        b[r] = s3 + __shfl_up_sync(0xffffffffu, s2, 1);  // node (ex, ey + 1) from this row
+      }
+      X[(kz & 1) * THREADS + tid] = V4<T>{b[0], b[1], b[2], T(0)};
+      if (more) stage(P + (kz & 1) * PLANE, pf);
       __syncthreads();
-      if (kz >= z0 && tid < TX * TY) {
-        const int tx = tid % TX, ty = tid / TX;
-        const int gx = x0 + tx, gy = y0 + ty;
-        if (gx < g.nx && gy < g.ny) {
-          T y[3] = {T(0), T(0), T(0)};
-          const int prev = (kz - 1) & 1;
-#pragma unroll
-          for (int c = 0; c < 4; c++) {  // node is corner c (lower) of layer kz, corner c+4 of layer kz-1
-            const int ex_t = tx + 1 - cofs(c, 0), ey_t = ty + 1 - cofs(c, 1);
-            const int e = ey_t * EX + ex_t;
-            const V4<T> a = flo[c * NEL + e];
-            const V4<T> b = fhi[(prev * 4 + c) * NEL + e];
-            y[0] += a.x + b.x;
-            y[1] += a.y + b.y;
-            y[2] += a.z + b.z;
-          }
-          const V4<T> s = ring[slot(kz) * PLANE + (ty + 1) * HX + tx + 1];
-          T us[3] = {s.x, s.y, s.z};
-          emit(gx + (long long)g.nx * (gy + (long long)g.ny * kz), y, us);
-        }
+      if (kz >= z0 && owner) {
+        const V4<T> w = X[(kz & 1) * THREADS + tid - 32];
+        T y[3] = {a[0] + w.x, a[1] + w.y, a[2] + w.z};
+        T us[3] = {uo[0][0], uo[0][1], uo[0][2]};
+        emit(main_off + nplane * kz, y, us);
       }
+#pragma unroll
+      for (int c = 0; c < 4; c++)
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+          uo[c][r] = un[c][r];
+          fu[c][r] = f[c + 4][r];
+        }
+      Ee = Enext;
     }
     __syncthreads();
   }
