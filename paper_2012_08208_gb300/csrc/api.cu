@@ -74,6 +74,29 @@ cudaMemcpyKind kind_of(int on_device, bool to_device) {
 
 }  // namespace
 
+// Depth (node planes) of the 3D streaming tiles.  Each tile of 31 x 7 node
+// columns streams zlen + 1 element layers after a two-plane prologue; the
+// persistent CG runs `resident` CTAs that take the tiles in rounds.  Pick the
+// balanced depth with the least rounds * (zlen + 3).
+static int pick_zlen(const Grid& g, int resident) {
+  const int tx = (g.nx + 30) / 31, ty = (g.ny + 6) / 7;
+  int best = 16;
+  long long best_cost = -1;
+  for (int zl = 1; zl <= g.nz; zl++) {
+    const int chunks = (g.nz + zl - 1) / zl;
+    const int zb = (g.nz + chunks - 1) / chunks;
+    if (zb != zl) continue;  // only balanced depths
+    const long long ntiles = (long long)tx * ty * chunks;
+    const long long rounds = (ntiles + resident - 1) / resident;
+    const long long cost = rounds * (zl + 3);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = zl;
+    }
+  }
+  return best;
+}
+
 tp_status tp_problem_ensure_E(tp_problem* p) { return ensure_E(p); }
 
 extern "C" {
@@ -131,6 +154,7 @@ tp_status tp_create_problem(const tp_params* params, void* cuda_stream, tp_probl
 
   cudaError_t e = cudaGetDevice(&p->dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
+  if (e == cudaSuccess && q.dim == 3) p->zlen = pick_zlen(p->g, 2 * p->nsm);
   const size_t nvals = (size_t)p->nn * p->nv;
   const size_t maxgrid = (size_t)p->nsm * kMaxGridPerSm;
   if (e == cudaSuccess) e = dalloc(&p->rho, p->ne);

@@ -25,6 +25,10 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
+// Hint: bring the line holding p into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  The
 // barrier word must be zeroed before the launch; `gen` is the CTA-local count

@@ -237,6 +237,26 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     for (int i = 0; i < 2 * NCM; i++) accBt[i] = T(0);
     for (int t = blockIdx.x; t < a.tm.ntiles; t += nb) {
       Op::for_each_own(a.g, a.tm, t, [&](long long node) {
+        if constexpr (DIM == 3) {
+          // Each thread walks its node column plane by plane, and the stores of
+          // one plane keep the next plane's loads from being issued early: ask
+          // L2 for the column four planes ahead (no registers held).
+          const long long ahead = node + 4LL * a.g.nx * a.g.ny;
+          if (ahead < nn) {
+#pragma unroll
+            for (int v = 0; v < NCM * DIM; v++) {
+              if (v < nv) {
+                const long long i = (long long)v * nn + ahead;
+                prefetch_l2(a.r + i);
+                prefetch_l2(Pnew + i);
+                prefetch_l2(a.q + i);
+                prefetch_l2(a.xl + i);
+              }
+            }
+#pragma unroll
+            for (int r = 0; r < DIM; r++) prefetch_l2(a.invd + (long long)r * nn + ahead);
+          }
+        }
         // all loads of the node first, then arithmetic, then stores
         constexpr int NVM = NCM * DIM;
         T rv[NVM], pv[NVM], qv[NVM], xv[NVM], inv[DIM];
