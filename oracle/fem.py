@@ -68,11 +68,15 @@ def matvec_elementwise(prob, rho, u):
     return np.bincount(edofs.ravel(), weights=fe.ravel(), minlength=prob.n_dof)
 
 
-def matvec_rows(prob, rho, u, dofs):
+def matvec_rows(prob, rho, u, dofs, absolute=False):
     """Rows `dofs` of the boundary-conditioned operator, evaluated one by one from
     the element sum (for sampled checks at sizes the assembled matrix cannot
-    reach).  Returns y[dofs] exactly as matvec_bc would."""
+    reach).  Returns y[dofs] exactly as matvec_bc would.  With absolute=True
+    the same rows of |K| |u| (the scale of the rounding error of the sum)."""
     K0 = k0_for(prob)
+    if absolute:
+        K0 = np.abs(K0)
+        u = np.abs(u)
     dim = prob.dim
     nx, ny, nz = prob.nelx, prob.nely, prob.nelz
     fixed = prob.fixed.astype(bool)
