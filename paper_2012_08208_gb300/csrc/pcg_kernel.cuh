@@ -136,15 +136,16 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     if constexpr (F32) return ctl->coef_f[i];
     else return ctl->coef_d[i];
   };
-  // thread 0 publishes beta / alpha / activity for the next phase
+  // publishes beta / alpha / activity of case c for the next phase
+  auto publish_case = [&](int c) {
+    ctl->coef_f[c] = (float)ctl->beta[c];
+    ctl->coef_f[kMaxCases + c] = (float)ctl->alpha[c];
+    ctl->coef_d[c] = ctl->beta[c];
+    ctl->coef_d[kMaxCases + c] = ctl->alpha[c];
+    ctl->act[c] = ctl->state[c] == 0;
+  };
   auto publish = [&]() {
-    for (int c = 0; c < kMaxCases; c++) {
-      ctl->coef_f[c] = (float)ctl->beta[c];
-      ctl->coef_f[kMaxCases + c] = (float)ctl->alpha[c];
-      ctl->coef_d[c] = ctl->beta[c];
-      ctl->coef_d[kMaxCases + c] = ctl->alpha[c];
-      ctl->act[c] = ctl->state[c] == 0;
-    }
+    for (int c = 0; c < kMaxCases; c++) publish_case(c);
   };
   if (t0) {
     ctl->it = a.cs->it;
@@ -210,19 +211,22 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     if (!(ok = grid_sync(a.bar, gen))) break;
     if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 3] = globaltimer();
     cta_total<NCM, T>(a.part + (size_t)SLOT_A * nb, ctl);
-    if (t0) {
-      for (int c = 0; c < kMaxCases; c++) {
-        ctl->alpha[c] = 0.0;
-        if (c >= NCM || ctl->state[c] != 0) continue;
+    if (threadIdx.x < kMaxCases) {  // one lane per case
+      const int c = threadIdx.x;
+      double al = 0.0;
+      bool brk = false;
+      if (c < NCM && ctl->state[c] == 0) {
         const double pq = ctl->tot[c];
         if (!(pq > 0.0) || !isfinite(pq) || !isfinite(ctl->rz[c])) {
           ctl->state[c] = 2;
-          ctl->flags |= ERR_BREAKDOWN;
-          continue;
+          brk = true;
+        } else {
+          al = ctl->rz[c] / pq;
         }
-        ctl->alpha[c] = ctl->rz[c] / pq;
       }
-      publish();
+      ctl->alpha[c] = al;
+      publish_case(c);
+      if (__any_sync(0xffu, brk) && c == 0) ctl->flags |= ERR_BREAKDOWN;
     }
     __syncthreads();
 
@@ -302,26 +306,27 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 6] = globaltimer();
     cta_total<2 * NCM, T>(a.part + (size_t)SLOT_B * nb, ctl);
     if (a.trace && blockIdx.x == 0 && t0) a.trace[kTracePts * (ctl->it % kTraceIters) + 7] = globaltimer();
-    if (t0) {
-      ctl->it += 1;
-      ctl->pbuf ^= 1;
-      bool need = false;
-      for (int c = 0; c < NCM && c < nc; c++) {
-        const double rr = ctl->tot[NCM + c];
-        if (ctl->state[c] == 0 && (rr <= a.tol2ff[c] || rr <= a.drop2 * ctl->rr_ref[c])) need = true;
+    if (threadIdx.x < kMaxCases) {  // one lane per case
+      const int c = threadIdx.x;
+      const bool on = c < NCM && c < nc && ctl->state[c] == 0;
+      const double rr = on ? ctl->tot[NCM + c] : 0.0;
+      const bool due = on && (rr <= a.tol2ff[c] || rr <= a.drop2 * ctl->rr_ref[c]);
+      const bool need = __any_sync(0xffu, due);
+      if (!need && c < NCM && c < nc) {  // otherwise rz keeps the value the update step divides by
+        const double rzn = ctl->tot[c];
+        ctl->beta[c] = (on && ctl->rz[c] != 0.0) ? rzn / ctl->rz[c] : 0.0;
+        ctl->rz[c] = rzn;
       }
-      if (!need) {  // otherwise rz keeps the value the update step divides by
-        for (int c = 0; c < NCM && c < nc; c++) {
-          const double rzn = ctl->tot[c];
-          ctl->beta[c] = (ctl->state[c] == 0 && ctl->rz[c] != 0.0) ? rzn / ctl->rz[c] : 0.0;
-          ctl->rz[c] = rzn;
-        }
+      const bool any = __any_sync(0xffu, c < nc && ctl->state[c] == 0);
+      const int it = ctl->it + 1;
+      publish_case(c);
+      __syncwarp(0xffu);
+      if (c == 0) {
+        ctl->it = it;
+        ctl->pbuf ^= 1;
+        ctl->need = need;
+        ctl->go = !need && any && it < a.max_it;
       }
-      ctl->need = need;
-      bool any = false;
-      for (int c = 0; c < nc; c++) any |= ctl->state[c] == 0;
-      ctl->go = !need && any && ctl->it < a.max_it;
-      publish();
     }
     __syncthreads();
   }
