@@ -57,14 +57,15 @@ typedef struct tp_params {
 
 enum { TP_PREC_F64 = 0, TP_PREC_MIXED = 1 };
 enum { TP_WARM_ZERO = 0, TP_WARM_PREVIOUS = 1, TP_WARM_USER = 2 };
-enum { TP_FILTER_SENSITIVITY = 0 };
+enum { TP_FILTER_SENSITIVITY = 0, TP_FILTER_DENSITY = 1 };
 /* Quantities for tp_get / tp_set (all FP64):
  *   TP_RHO   design densities rho[n_el]
  *   TP_U     displacements u[n_cases][n_dof] (the solution, or the warm start)
  *   TP_DC    raw sensitivities dc[n_el] (after tp_sensitivities)
  *   TP_DCF   filtered sensitivities dc~[n_el] (after tp_filter)
  *   TP_CE    element energies sum_k u_e^T K0 u_e [n_el] (after tp_sensitivities)
- *   TP_RHO_PHYS  physical densities used for stiffness [n_el] */
+ *   TP_RHO_PHYS  physical densities used for stiffness [n_el] (rho, or rho~ in
+ *                the density-filter mode) */
 enum { TP_RHO = 0, TP_U = 1, TP_DC = 2, TP_DCF = 3, TP_CE = 4, TP_RHO_PHYS = 5 };
 
 /* Solver options.  tol: target TRUE relative residual ||f - K u||_2 / ||f||_2
@@ -142,9 +143,18 @@ tp_status tp_sensitivities(tp_problem* p, double* compliance);
 /* Mesh-independency filter (Section 3.2.2, Eq. "filter", "filter_cond"; Eq.
  * "filter_mat"): W_ab = max(0, rmin - |x_a - x_b|) over element midpoints, rows
  * truncated at the mesh boundary.
- * mode TP_FILTER_SENSITIVITY: dc~_a = sum_b W_ab rho_b dc_b / (rho_a sum_b W_ab).
- * Any other mode returns TP_ERR_ARG. */
+ * mode TP_FILTER_SENSITIVITY (the paper's): dc~_a = sum_b W_ab rho_b dc_b /
+ *   (rho_a sum_b W_ab).
+ * mode TP_FILTER_DENSITY: the stiffness uses the filtered densities
+ *   rho~ = W rho / rowsum (tp_set_filter_mode); dc then holds d c / d rho~
+ *   and this call applies the chain rule dc~ = W^T (dc / rowsum).  The OC
+ *   update keeps its volume constraint on rho.
+ * `mode` must equal the problem's filter mode (else TP_ERR_STATE). */
 tp_status tp_filter(tp_problem* p, int mode);
+/* Filter mode of the problem (default TP_FILTER_SENSITIVITY); also the mode
+ * tp_simp_step uses.  TP_FILTER_DENSITY makes tp_solve / tp_sensitivities use
+ * rho~ = W rho / rowsum (TP_RHO_PHYS). */
+tp_status tp_set_filter_mode(tp_problem* p, int mode);
 
 /* OC update with bisection on lambda (Section 3.2, Eq. "update", Section 3.2.1):
  * rho_new = max(dmin, max(rho - m, min(1, min(rho + m, rho sqrt(-dc~ / lambda))))),

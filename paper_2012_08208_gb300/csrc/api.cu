@@ -43,7 +43,7 @@ void free_all(tp_problem* p) {
   void* ptrs[] = {p->rho, p->rho_new, p->E32, p->E64, p->mask, p->passive, p->f, p->x64,
                   p->inv32, p->inv64, p->w[0], p->w[1], p->w[2], p->w[3], p->w[4], p->w[5],
                   p->part, p->bar, p->cgs, p->tol2, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi,
-                  p->trace, p->nn_feat, p->nn_out, p->nn_scal};
+                  p->trace, p->nn_feat, p->nn_out, p->nn_scal, p->rho_phys, p->rowsum};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -57,9 +57,16 @@ bool finite_all(const double* a, size_t n) {
   return true;
 }
 
+// Densities that set the stiffness: rho, or its density filter in mode 1.
+const double* phys(const tp_problem* p) { return p->filter_mode == TP_FILTER_DENSITY ? p->rho_phys : p->rho; }
+
 tp_status ensure_E(tp_problem* p) {
   if (!p->E_dirty) return TP_OK;
-  TPCK(launch_young(p->stream, p->rho, p->E32, p->E64, p->ne, p->prm.E0, p->prm.Emin, p->prm.penal),
+  if (p->filter_mode == TP_FILTER_DENSITY) {
+    TPCK(launch_filter(p->stream, *p->flt, 1, p->rho, nullptr, p->rho_phys), "density filter kernel");
+    p->launches++;
+  }
+  TPCK(launch_young(p->stream, phys(p), p->E32, p->E64, p->ne, p->prm.E0, p->prm.Emin, p->prm.penal),
        "young kernel");
   TPCK(launch_diag(p->stream, p->g, p->K0.data(), p->E64, p->mask, p->inv32, p->inv64), "diag kernel");
   p->launches += 2;
@@ -423,7 +430,7 @@ tp_status tp_sensitivities(tp_problem* p, double* compliance) {
   if (!p) return TP_ERR_ARG;
   if (!p->has_u) return fail(p, TP_ERR_STATE, "tp_solve must precede tp_sensitivities");
   const double dE = p->prm.E0 - p->prm.Emin;
-  TPCK(launch_sens(p->stream, p->g, p->nc, p->C.data(), p->x64, p->f, p->rho, p->prm.penal, dE, p->ce,
+  TPCK(launch_sens(p->stream, p->g, p->nc, p->C.data(), p->x64, p->f, phys(p), p->prm.penal, dE, p->ce,
                    p->dc, p->part, p->scal),
        "sensitivity kernel");
   p->launches += 2;
@@ -436,11 +443,34 @@ tp_status tp_sensitivities(tp_problem* p, double* compliance) {
   return TP_OK;
 }
 
+tp_status tp_set_filter_mode(tp_problem* p, int mode) {
+  if (!p) return TP_ERR_ARG;
+  if (mode != TP_FILTER_SENSITIVITY && mode != TP_FILTER_DENSITY) return fail(p, TP_ERR_ARG, "unknown filter mode");
+  if (mode == TP_FILTER_DENSITY && !p->rho_phys) {
+    TPCK(dalloc(&p->rho_phys, p->ne), "alloc");
+    TPCK(dalloc(&p->rowsum, p->ne), "alloc");
+    TPCK(launch_filter(p->stream, *p->flt, 3, nullptr, nullptr, p->rowsum), "row-sum kernel");
+    p->launches++;
+  }
+  if (mode != p->filter_mode) {
+    p->filter_mode = mode;
+    p->E_dirty = true;
+    p->has_dc = p->has_dcf = false;
+  }
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  return TP_OK;
+}
+
 tp_status tp_filter(tp_problem* p, int mode) {
   if (!p) return TP_ERR_ARG;
-  if (mode != TP_FILTER_SENSITIVITY) return fail(p, TP_ERR_ARG, "only the sensitivity filter (mode 0) is available");
+  if (mode != TP_FILTER_SENSITIVITY && mode != TP_FILTER_DENSITY) return fail(p, TP_ERR_ARG, "unknown filter mode");
+  if (mode != p->filter_mode)
+    return fail(p, TP_ERR_STATE, "tp_filter mode differs from the problem's filter mode (tp_set_filter_mode)");
   if (!p->has_dc || !p->has_density) return fail(p, TP_ERR_STATE, "tp_sensitivities must precede tp_filter");
-  TPCK(launch_filter(p->stream, *p->flt, 0, p->rho, p->dc, p->dcf), "filter kernel");
+  if (mode == TP_FILTER_SENSITIVITY)
+    TPCK(launch_filter(p->stream, *p->flt, 0, p->rho, p->dc, p->dcf), "filter kernel");
+  else
+    TPCK(launch_filter(p->stream, *p->flt, 2, p->rowsum, p->dc, p->dcf), "filter chain kernel");
   p->launches++;
   p->has_dcf = true;
   return TP_OK;
@@ -479,7 +509,7 @@ tp_status tp_simp_step(tp_problem* p, const tp_solve_opts* opts, tp_step_info* i
     return s;
   }
   tp_status s2 = tp_sensitivities(p, &loc.compliance);
-  if (s2 == TP_OK) s2 = tp_filter(p, TP_FILTER_SENSITIVITY);
+  if (s2 == TP_OK) s2 = tp_filter(p, p->filter_mode);
   if (s2 == TP_OK) s2 = tp_oc_update(p, &loc.lambda, &loc.volume, &loc.change);
   if (info) *info = loc;
   if (s2 != TP_OK) return s2;
@@ -491,10 +521,16 @@ tp_status tp_get(tp_problem* p, int what, void* dst, int on_device) {
   const cudaMemcpyKind k = kind_of(on_device, false);
   switch (what) {
     case TP_RHO:
-    case TP_RHO_PHYS:
       if (!p->has_density) return fail(p, TP_ERR_STATE, "density not set");
       TPCK(cudaMemcpyAsync(dst, p->rho, p->ne * sizeof(double), k, p->stream), "copy");
       break;
+    case TP_RHO_PHYS: {
+      if (!p->has_density) return fail(p, TP_ERR_STATE, "density not set");
+      tp_status st = ensure_E(p);
+      if (st != TP_OK) return st;
+      TPCK(cudaMemcpyAsync(dst, phys(p), p->ne * sizeof(double), k, p->stream), "copy");
+      break;
+    }
     case TP_U:
       if (!p->has_u) return fail(p, TP_ERR_STATE, "no displacement yet");
       TPCK(launch_to_abi(p->stream, p->x64, p->abi, p->nn, p->dim, p->nc), "layout kernel");

@@ -37,6 +37,9 @@ struct FilterArgs {
 
 // mode 0 (sensitivity filter): out_a = sum_b W_ab rho_b dc_b / (rho_a sum_b W_ab)
 // mode 1 (density filter):     out_a = sum_b W_ab rho_b / sum_b W_ab
+// mode 2 (its chain rule):     out_a = sum_b W_ab dc_b / rowsum_b  (W symmetric;
+//                              `rho` carries rowsum)
+// mode 3 (row sums):           out_a = sum_b W_ab
 // Elements outside the mesh carry no weight (rows truncated at the boundary).
 template <int DIM>
 __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ FilterArgs a) {
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Fil
     double v = 0.0;
     if (gx >= 0 && gx < g.ex && gy >= 0 && gy < g.ey && gz >= 0 && gz < g.ez) {
       const long long e = gx + (long long)g.ex * (gy + (long long)g.ey * gz);
-      v = a.mode == 0 ? a.rho[e] * a.dc[e] : a.rho[e];
+      v = a.mode == 0 ? a.rho[e] * a.dc[e] : (a.mode == 1 ? a.rho[e] : (a.mode == 2 ? a.dc[e] / a.rho[e] : 0.0));
     }
     sG[i] = v;
   }
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Fil
       den += a.w[k];
     }
     const long long e = gx + (long long)g.ex * (gy + (long long)g.ey * gz);
-    a.out[e] = a.mode == 0 ? num / (a.rho[e] * den) : num / den;
+    a.out[e] = a.mode == 0 ? num / (a.rho[e] * den) : (a.mode == 1 ? num / den : (a.mode == 2 ? num : den));
   }
 }
 

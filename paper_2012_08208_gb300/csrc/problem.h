@@ -55,6 +55,9 @@ struct tp_problem {
   long long launches = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int last_grid = 0;
+  int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
+  double* rho_phys = nullptr;    // density-filtered densities (filter mode 1)
+  double* rowsum = nullptr;      // sum_b W_ab per element (filter mode 1)
   double fmax[kMaxCases] = {};   // max |f| per load case (warm-start feature scale)
   // learned warm start scratch (allocated on first use)
   void* nn_feat = nullptr;       // bf16 [n_cases][8][nelz][nely][nelx]

@@ -22,6 +22,7 @@ STATUS_NAMES = ["TP_OK", "TP_ERR_ARG", "TP_ERR_CUDA", "TP_ERR_OOM", "TP_ERR_NOT_
 TP_PREC_F64, TP_PREC_MIXED = 0, 1
 TP_WARM_ZERO, TP_WARM_PREVIOUS, TP_WARM_USER = 0, 1, 2
 TP_FILTER_SENSITIVITY = 0
+TP_FILTER_DENSITY = 1
 TP_RHO, TP_U, TP_DC, TP_DCF, TP_CE, TP_RHO_PHYS = range(6)
 
 
@@ -72,6 +73,7 @@ def _load():
         "tp_solve": (C.c_int, [P, C.POINTER(tp_solve_opts), C.POINTER(tp_solve_info)]),
         "tp_sensitivities": (C.c_int, [P, C.POINTER(C.c_double)]),
         "tp_filter": (C.c_int, [P, C.c_int]),
+        "tp_set_filter_mode": (C.c_int, [P, C.c_int]),
         "tp_oc_update": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_simp_step": (C.c_int, [P, C.POINTER(tp_solve_opts), C.POINTER(tp_step_info)]),
         "tp_get": (C.c_int, [P, C.c_int, P, C.c_int]),
@@ -125,7 +127,7 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
-            "tp_oc_update_noalloc", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_oc_update_noalloc", "tp_set_filter_mode", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
@@ -278,8 +280,12 @@ class Problem:
         self._check(lib.tp_sensitivities(self.h, C.byref(c)))
         return c.value
 
-    def filter(self, mode=TP_FILTER_SENSITIVITY):
-        self._check(lib.tp_filter(self.h, mode))
+    def filter(self, mode=None):
+        self._check(lib.tp_filter(self.h, getattr(self, "filter_mode", TP_FILTER_SENSITIVITY) if mode is None else mode))
+
+    def set_filter_mode(self, mode):
+        self._check(lib.tp_set_filter_mode(self.h, mode))
+        self.filter_mode = mode
 
     def oc_update(self):
         lam, vol, ch = C.c_double(), C.c_double(), C.c_double()

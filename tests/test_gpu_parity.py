@@ -198,3 +198,32 @@ def test_error_paths_keep_handle_usable(topo):
     info = p.solve(topo.solve_opts(tol=1e-10, max_it=10000, precision=topo.TP_PREC_F64))
     assert info.converged == 1
     p.close()
+
+
+@pytest.mark.parametrize("prob", [W.mbb2d(), W.small3d(12, 6, 5, rmin=1.8, volfrac=0.3)], ids=lambda p: p.name)
+def test_density_filter_mode_iterations(topo, prob):
+    """Density-filter variant (the physical densities are W rho / rowsum, the
+    sensitivities go back through the chain rule): every iteration against the
+    oracle's filter_mode=1 iteration on the GPU's own design densities."""
+    Wm = filt.weights_for(prob)
+    p = topo.Problem.from_workload(prob)
+    p.set_filter_mode(topo.TP_FILTER_DENSITY)
+    rho = prob.initial_density()
+    opts = topo.solve_opts(tol=1e-11, max_it=50000, precision=topo.TP_PREC_F64, warm_start=topo.TP_WARM_PREVIOUS)
+    for it in range(4):
+        phys = p.get(topo.TP_RHO_PHYS)
+        assert np.allclose(phys, filt.density_filter(Wm, rho), rtol=1e-13, atol=0)
+        info = p.simp_step(opts)
+        ref = simp.iteration(prob, rho, W=Wm, filter_mode=1)
+        assert abs(info.compliance - ref["c"]) <= 1e-8 * ref["c"]
+        rho_gpu = p.get(topo.TP_RHO)
+        lam_exact = oc.exact_lambda(rho, ref["dcf"], prob.volfrac)
+        assert info.lambda_ == pytest.approx(lam_exact, rel=1e-8)
+        assert np.max(np.abs(rho_gpu - ref["rho_new"])) <= 1e-6
+        rho = rho_gpu
+    # the mode is checked: a sensitivity-filter call on a density-filter problem is refused
+    p.solve(opts)
+    p.sensitivities()
+    with pytest.raises(topo.TopoError):
+        p.filter(topo.TP_FILTER_SENSITIVITY)
+    p.close()

@@ -125,3 +125,23 @@ def test_bisection_paper_rule_ties_move_upper_bound():
     new, lam, vol, change, it = oc.bisect(rho, dcf, 0.5)
     assert vol == pytest.approx(5.0, rel=1e-8)
     assert lam == pytest.approx(1.0, rel=1e-8)
+
+
+def test_density_filter_chain_rule_is_the_adjoint_and_the_gradient():
+    """d/d rho of phi(W rho / rowsum) is W^T (g / rowsum): the adjoint identity
+    <density_filter(x), y> = <x, chain(y)> and central finite differences of a
+    smooth function of the filtered densities."""
+    prob = W.small2d(9, 7, rmin=2.2)
+    Wd = filt.weights_for(prob)
+    rng = np.random.default_rng(17)
+    x, y = rng.uniform(0.1, 1, prob.n_el), rng.normal(size=prob.n_el)
+    assert float(filt.density_filter(Wd, x) @ y) == pytest.approx(float(x @ filt.density_filter_chain(Wd, y)), rel=1e-12)
+    phi = lambda r: float(np.sum(np.sin(filt.density_filter(Wd, r)) ** 2))
+    g = np.sin(2 * filt.density_filter(Wd, x))  # d phi / d rho~
+    grad = filt.density_filter_chain(Wd, g)
+    h = 1e-6
+    for e in (0, 17, prob.n_el - 1):
+        xp, xm = x.copy(), x.copy()
+        xp[e] += h
+        xm[e] -= h
+        assert (phi(xp) - phi(xm)) / (2 * h) == pytest.approx(grad[e], rel=1e-6)
