@@ -416,7 +416,7 @@ def run_only(args):
             w = W.cantilever2d() if args.only == "cg2d" else W.cantilever3d_large()
             p = topo.Problem.from_workload(w, stream=stream.cuda_stream)
             info = p.solve(topo.solve_opts(tol=1e-8, max_it=args.reps, precision=topo.TP_PREC_MIXED,
-                                           update_drop=0.1), check=False)
+                                           update_drop=0.1, precond=args.precond), check=False)
             out = {"workload": w.name, "n_dof": w.n_dof, "n_cases": w.n_cases, "iters": info.iters,
                    "updates": info.updates, "ms": round(info.ms, 3)}
             p.close()
@@ -437,6 +437,7 @@ def main():
     ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned", "cg2d", "cg3d"], default=None,
                     help="run one extra measurement alone (for profiling)")
     ap.add_argument("--copies", type=int, default=8)
+    ap.add_argument("--precond", type=int, default=0, help="0 Jacobi-PCG, 1 multigrid-PCG (--only cg2d / cg3d)")
     ap.add_argument("--reps", type=int, default=10)
     args = ap.parse_args()
     if args.only:

@@ -57,6 +57,14 @@ typedef struct tp_params {
 
 enum { TP_PREC_F64 = 0, TP_PREC_MIXED = 1 };
 enum { TP_WARM_ZERO = 0, TP_WARM_PREVIOUS = 1, TP_WARM_USER = 2 };
+/* Preconditioner of tp_solve.  TP_PRECOND_JACOBI: the persistent Jacobi-PCG
+ * described above.  TP_PRECOND_MG: CG in FP64 preconditioned by one geometric
+ * multigrid V-cycle in FP32 per iteration (nested structured grids coarsened
+ * 2:1 while the element counts are even, then by their smallest common odd
+ * factor; Galerkin coarse operators; damped-Jacobi smoothing; exact solve on a
+ * coarsest grid of at most 256 DOFs).  Needs element counts that reach such a
+ * coarsest grid (else TP_ERR_ARG); `precision` and `update_drop` are ignored. */
+enum { TP_PRECOND_JACOBI = 0, TP_PRECOND_MG = 1 };
 enum { TP_FILTER_SENSITIVITY = 0, TP_FILTER_DENSITY = 1 };
 /* Quantities for tp_get / tp_set (all FP64):
  *   TP_RHO   design densities rho[n_el]
@@ -87,6 +95,7 @@ typedef struct tp_solve_opts {
   double update_drop;
   double warm_max_rel;  /* TP_WARM_USER: largest accepted starting true relative
                            residual (0 means 1, i.e. no worse than u = 0) */
+  int precond;          /* TP_PRECOND_JACOBI (default) or TP_PRECOND_MG */
 } tp_solve_opts;
 
 typedef struct tp_solve_info {

@@ -46,6 +46,9 @@ void free_all(tp_problem* p) {
                   p->trace, p->nn_feat, p->nn_out, p->nn_scal, p->rho_phys, p->rowsum};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  delete p->mg;
+  p->mg = nullptr;
+  if (p->mg_sc) cudaFree(p->mg_sc);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   delete p->flt;
@@ -71,6 +74,7 @@ tp_status ensure_E(tp_problem* p) {
   TPCK(launch_diag(p->stream, p->g, p->K0.data(), p->E64, p->mask, p->inv32, p->inv64), "diag kernel");
   p->launches += 2;
   p->E_dirty = false;
+  p->E_version++;
   return TP_OK;
 }
 
@@ -105,6 +109,196 @@ static int pick_zlen(const Grid& g, int resident) {
 }
 
 tp_status tp_problem_ensure_E(tp_problem* p) { return ensure_E(p); }
+
+// CG in FP64 preconditioned by one FP32 multigrid V-cycle per iteration
+// (TP_PRECOND_MG).  Vectors in the ABI layout; the solution ends in x64.
+static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info) {
+  tp_status st = ensure_E(p);
+  if (st != TP_OK) return st;
+  if (!p->mg) {
+    p->mg = new MgHierarchy();
+    cudaError_t e = p->mg->plan(p->g, p->mask, p->nc);
+    if (e != cudaSuccess) {
+      delete p->mg;
+      p->mg = nullptr;
+      cudaGetLastError();
+      if (e == cudaErrorInvalidValue)
+        return fail(p, TP_ERR_ARG, "no multigrid hierarchy for this grid (element counts without small common factors)");
+      return cuda_fail(p, e, "multigrid allocation");
+    }
+  }
+  if (!p->mg_sc) TPCK(dalloc(&p->mg_sc, 64), "alloc");
+  MgHierarchy& M = *p->mg;
+  const cudaStream_t s = p->stream;
+  const long long n = p->ndof;
+  const int nc = p->nc;
+  double* x = (double*)p->w[0];
+  double* r = (double*)p->w[1];
+  double* z = (double*)p->w[2];
+  double* pp = (double*)p->w[3];
+  double* q = (double*)p->w[4];
+  double* fA = (double*)p->w[5];
+  double* sc = p->mg_sc;
+  int nl = 0;
+  TPCK(cudaEventRecord(p->ev0, s), "event");
+  if (M.version != p->E_version) {
+    TPCK(M.build(s, p->K0.data(), p->E32, &nl), "multigrid setup");
+    M.version = p->E_version;
+  }
+  TPCK(launch_to_abi(s, p->f, fA, p->nn, p->dim, nc), "layout kernel");
+  if (opts->warm_start == TP_WARM_ZERO || (opts->warm_start == TP_WARM_PREVIOUS && !p->has_u))
+    TPCK(cudaMemsetAsync(x, 0, (size_t)nc * n * sizeof(double), s), "memset");
+  else
+    TPCK(launch_to_abi(s, p->x64, x, p->nn, p->dim, nc), "layout kernel");
+  nl += 2;
+  auto matvec = [&](const double* u, double* y) -> cudaError_t {  // FP64 operator
+    nl++;
+    return launch_matvec(s, p->g, p->C.data(), true, p->E64, p->mask, u, y, nc, p->zlen);
+  };
+  // Inner operator: the FP32 strain-form operator on FP32 copies (the outer
+  // restarts recompute the true residual with the FP64 operator).
+  float* u32 = M.lv[0].t;
+  float* y32 = M.lv[0].x[1];
+  auto matvec32 = [&](const double* u, double* y) -> cudaError_t {
+    cudaError_t e = to_f32(s, (long long)nc * n, u, u32);
+    if (e == cudaSuccess) e = launch_matvec(s, p->g, p->C.data(), false, p->E32, p->mask, u32, y32, nc, p->zlen);
+    if (e == cudaSuccess) e = to_f64(s, (long long)nc * n, y32, y);
+    nl += 3;
+    return e;
+  };
+  auto true_rr = [&](double* rr_out) -> tp_status {  // r = f - K x, rr per case (synchronises)
+    TPCK(matvec(x, q), "matvec");
+    TPCK(pcg_residual(s, n, nc, fA, q, p->mask, p->dim, r), "residual kernel");
+    int nb = 0;
+    TPCK(pcg_dot2(s, n, nc, r, r, r, r, p->part, &nb), "dot kernel");
+    TPCK(pcg_scalars(s, nb, nc, p->part, 2, sc), "scalar kernel");
+    nl += 3;
+    double h[64];
+    TPCK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
+    TPCK(cudaStreamSynchronize(s), "sync");
+    for (int c = 0; c < nc; c++) rr_out[c] = h[32 + c];
+    return TP_OK;
+  };
+  auto precondition = [&]() -> tp_status {  // z = V(r)
+    TPCK(to_f32(s, (long long)nc * n, r, M.lv[0].b), "convert");
+    TPCK(M.vcycle(s, 0, &nl), "v-cycle");
+    TPCK(to_f64(s, (long long)nc * n, M.lv[0].x[0], z), "convert");
+    nl += 2;
+    return TP_OK;
+  };
+  double rr[kMaxCases] = {}, rel0[kMaxCases] = {};
+  st = true_rr(rr);
+  if (st != TP_OK) return st;
+  int fallback = 0;
+  for (int c = 0; c < nc; c++) rel0[c] = std::sqrt(rr[c] / p->ff[c]);
+  if (opts->warm_start == TP_WARM_USER) {
+    const double lim = opts->warm_max_rel > 0.0 ? opts->warm_max_rel : 1.0;
+    for (int c = 0; c < nc; c++) fallback |= !(rr[c] <= lim * lim * p->ff[c]);
+    if (fallback) {
+      TPCK(cudaMemsetAsync(x, 0, (size_t)nc * n * sizeof(double), s), "memset");
+      st = true_rr(rr);
+      if (st != TP_OK) return st;
+    }
+  }
+  auto done = [&](const double* v, double margin) {
+    for (int c = 0; c < nc; c++)
+      if (!(v[c] <= margin * margin * opts->tol * opts->tol * p->ff[c])) return false;
+    return true;
+  };
+  int it = 0, restarts = 0;
+  bool conv = done(rr, 1.0), brk = false;
+  // FP32 inner operator unless FP64 was asked for, or until a restart cycle
+  // gains less than 10x (the FP32 operator's error limits the refinement when
+  // eps32 * cond(K) is not small)
+  bool use64 = opts->precision == TP_PREC_F64;
+  while (!conv && it < opts->max_it && !brk) {
+    // (re)start from the current residual
+    st = precondition();
+    if (st != TP_OK) return st;
+    int nb = 0;
+    TPCK(pcg_dot2(s, n, nc, r, z, r, r, p->part, &nb), "dot kernel");
+    TPCK(pcg_scalars(s, nb, nc, p->part, 2, sc), "scalar kernel");
+    TPCK(cudaMemcpyAsync(pp, z, (size_t)nc * n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    nl += 2;
+    double rr_start[kMaxCases], best = 0.0;
+    for (int c = 0; c < nc; c++) rr_start[c] = rr[c];
+    int best_it = it;
+    while (it < opts->max_it) {
+      if (use64) TPCK(matvec(pp, q), "matvec");
+      else TPCK(matvec32(pp, q), "matvec");
+      TPCK(pcg_dot2(s, n, nc, pp, q, nullptr, nullptr, p->part, &nb), "dot kernel");
+      TPCK(pcg_scalars(s, nb, nc, p->part, 0, sc), "scalar kernel");
+      TPCK(pcg_update_xr(s, n, nc, sc, x, pp, r, q), "update kernel");
+      nl += 3;
+      st = precondition();
+      if (st != TP_OK) return st;
+      TPCK(pcg_dot2(s, n, nc, r, z, r, r, p->part, &nb), "dot kernel");
+      TPCK(pcg_scalars(s, nb, nc, p->part, 1, sc), "scalar kernel");
+      nl += 2;
+      it++;
+      double h[64];
+      TPCK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
+      TPCK(cudaStreamSynchronize(s), "sync");
+      double rec[kMaxCases];
+      for (int c = 0; c < nc; c++) {
+        rec[c] = h[32 + c];
+        if (!std::isfinite(rec[c]) || !(h[24 + c] > 0.0)) brk = true;
+      }
+      // stop at the tolerance, or when the FP32 operator's error may dominate
+      // the recurrence (1e-5 of the restart residual): then restart with the
+      // FP64 true residual
+      bool inner = !use64;
+      double worst = 0.0;
+      for (int c = 0; c < nc; c++) {
+        inner &= rec[c] <= 1e-10 * rr_start[c];
+        worst = std::max(worst, rec[c] / p->ff[c]);
+      }
+      // stagnation: no halving of the worst recurrence residual in 50 iterations
+      if (best == 0.0 || worst < 0.25 * best) {
+        best = worst;
+        best_it = it;
+      }
+      const bool stalled = it - best_it >= 50;
+      if (brk || done(rec, 0.5) || inner || stalled) break;
+      TPCK(pcg_update_p(s, n, nc, sc, pp, z), "update kernel");
+      nl++;
+    }
+    double before = 0.0, after = 0.0;
+    for (int c = 0; c < nc; c++) before = std::max(before, rr[c] / p->ff[c]);
+    st = true_rr(rr);
+    if (st != TP_OK) return st;
+    for (int c = 0; c < nc; c++) after = std::max(after, rr[c] / p->ff[c]);
+    conv = done(rr, 1.0);
+    if (!conv && !(after < 1e-2 * before)) use64 = true;
+    if (!conv && ++restarts > 12) break;
+  }
+  TPCK(launch_to_internal(s, x, p->x64, p->nn, p->dim, nc, p->mask, 1), "layout kernel");
+  nl++;
+  TPCK(cudaEventRecord(p->ev1, s), "event");
+  TPCK(cudaEventSynchronize(p->ev1), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+  p->launches += nl;
+  p->has_u = true;
+  p->has_dc = p->has_dcf = false;
+  tp_status rs = conv ? TP_OK : (brk ? TP_ERR_BREAKDOWN : TP_ERR_NOT_CONVERGED);
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->iters = it;
+    info->updates = restarts + 1;
+    info->converged = conv ? 1 : 0;
+    info->status = rs;
+    for (int c = 0; c < nc; c++) {
+      info->rel_res[c] = std::sqrt(rr[c] / p->ff[c]);
+      info->rel_res_init[c] = rel0[c];
+    }
+    info->warm_fallback = fallback;
+    info->ms = ms;
+  }
+  if (rs == TP_ERR_BREAKDOWN) return fail(p, rs, "multigrid PCG breakdown (p^T K p <= 0 or not finite)");
+  if (rs == TP_ERR_NOT_CONVERGED) return fail(p, rs, "multigrid PCG stopped before the tolerance");
+  return TP_OK;
+}
 
 extern "C" {
 
@@ -322,6 +516,9 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
     return fail(p, TP_ERR_ARG, "unknown warm_start");
   if (opts->warm_start == TP_WARM_USER && !p->has_u)
     return fail(p, TP_ERR_STATE, "TP_WARM_USER needs tp_set(TP_U, ...) first");
+  if (opts->precond != TP_PRECOND_JACOBI && opts->precond != TP_PRECOND_MG)
+    return fail(p, TP_ERR_ARG, "unknown preconditioner");
+  if (opts->precond == TP_PRECOND_MG) return mg_solve(p, opts, info);
   double drop = opts->update_drop;
   if (opts->precision == TP_PREC_MIXED) {
     if (drop == 0.0) drop = 1e-2;

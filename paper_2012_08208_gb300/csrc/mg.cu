@@ -1,0 +1,836 @@
+// Geometric multigrid preconditioner for the CG solve (not in the paper, which
+// factorises K directly): nested structured grids, Galerkin coarse operators
+// held as per-element matrices, damped-Jacobi smoothing, and an exact solve
+// on the coarsest grid.
+//
+// Level 0 is the problem's grid with element matrices E_e K0.  A coarse
+// element of level l + 1 covers f^dim elements of level l (f = 2 while every
+// element count is even, then the smallest odd factor common to all counts);
+// with the multilinear interpolation P of the coarse element's corner values
+// onto the fine nodes inside it, the coarse element matrix is the Galerkin sum
+//   K_E = sum_{children c} P_c^T (M K_c M) P_c,
+// M zeroing the fine fixed DOFs.  A coarse DOF is fixed when the fine DOF at the
+// same place is; its rows and columns are zeroed and the operator is the
+// identity there.  Restriction is P^T.  All vectors are [case][node * dim + comp]
+// (the ABI layout), FP32 inside the V-cycle.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mg.h"
+
+namespace tp {
+namespace {
+
+template <int DIM>
+struct MgC {
+  static constexpr int NC = DIM == 2 ? 4 : 8;  // element corners
+  static constexpr int ND = NC * DIM;          // element DOFs
+};
+
+__constant__ float c_K0[24 * 24];  // level-0 element matrix (unit modulus), row-major
+
+__device__ __forceinline__ long long node_index(const Grid& g, int i, int j, int k) {
+  return i + (long long)g.nx * (j + (long long)g.ny * k);
+}
+
+// Element matrix entry (row a, column b) of element e on a level.
+template <int DIM>
+__device__ __forceinline__ float kentry(const float* K, const float* E, long long e, int a, int b) {
+  constexpr int ND = MgC<DIM>::ND;
+  return K ? K[e * ND * ND + a * ND + b] : E[e] * c_K0[a * ND + b];
+}
+
+// y = A u on one level (node-centric, fixed DOFs read as 0 and mapped by the
+// identity), optionally fused into a damped-Jacobi sweep:
+//   mode 0: y = A u
+//   mode 1: y = u + omega D^-1 (b - A u)     (smoothing sweep)
+//   mode 2: y = b - A u                       (residual)
+// One thread per node and case (blockIdx.y = case).
+template <int DIM>
+__global__ void apply_kernel(Grid g, const float* __restrict__ K, const float* __restrict__ E,
+                             const uint8_t* __restrict__ mask, const float* __restrict__ invd,
+                             const float* __restrict__ u, const float* __restrict__ b, float* __restrict__ y,
+                             int mode, float omega) {
+  constexpr int NC = MgC<DIM>::NC;
+  const long long ndof = g.nn * DIM;
+  const float* uc = u + blockIdx.y * ndof;
+  const float* bc = b ? b + blockIdx.y * ndof : nullptr;
+  float* yc = y + blockIdx.y * ndof;
+  const int nn = (int)g.nn, nxy = g.nx * g.ny;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
+    const uint8_t mk = mask[nd];
+    float acc[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; r++) acc[r] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {  // this node is corner c of element (i - cx, j - cy, k - cz)
+      const int ei = i - cofs(c, 0), ej = j - cofs(c, 1), ek = k - (DIM == 3 ? cofs(c, 2) : 0);
+      if (ei < 0 || ej < 0 || ek < 0 || ei >= g.ex || ej >= g.ey || ek >= g.ez) continue;
+      const long long e = ei + (long long)g.ex * (ej + (long long)g.ey * ek);
+      constexpr int ND = MgC<DIM>::ND;
+      const float* Ke = K ? K + e * ND * ND : c_K0;  // level 0: E_e K0
+      float part[DIM];
+#pragma unroll
+      for (int r = 0; r < DIM; r++) part[r] = 0.f;
+#pragma unroll
+      for (int cc = 0; cc < NC; cc++) {
+        const long long n2 = node_index(g, ei + cofs(cc, 0), ej + cofs(cc, 1), ek + (DIM == 3 ? cofs(cc, 2) : 0));
+        const uint8_t m2 = mask[n2];
+#pragma unroll
+        for (int s = 0; s < DIM; s++) {
+          if ((m2 >> s) & 1) continue;
+          const float v = uc[n2 * DIM + s];
+#pragma unroll
+          for (int r = 0; r < DIM; r++) part[r] = fmaf(Ke[(c * DIM + r) * ND + cc * DIM + s], v, part[r]);
+        }
+      }
+      const float sc = K ? 1.f : E[e];
+#pragma unroll
+      for (int r = 0; r < DIM; r++) acc[r] = fmaf(sc, part[r], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < DIM; r++) {
+      const long long idx = nd * DIM + r;
+      const bool fx = (mk >> r) & 1;
+      const float au = fx ? uc[idx] : acc[r];
+      float out;
+      if (mode == 0) out = au;
+      else if (mode == 1) out = fx ? 0.f : uc[idx] + omega * invd[idx] * (bc[idx] - au);
+      else out = fx ? 0.f : bc[idx] - au;
+      yc[idx] = out;
+    }
+  }
+}
+
+// Assembled form of a level: per node, the DIM x DIM coupling block to each of
+// its 3^DIM neighbours, S[((nbr * DIM + r) * DIM + s) * n_nodes + node]
+// (structure of arrays: one coalesced load per entry), with the rows and
+// columns of fixed DOFs zeroed.  nbr = (dx+1) + 3 (dy+1) [+ 9 (dz+1)].
+template <int DIM>
+__global__ void stencil_kernel(Grid g, const float* __restrict__ K, const float* __restrict__ E,
+                               const uint8_t* __restrict__ mask, float* __restrict__ S) {
+  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NB = DIM == 2 ? 9 : 27;
+  const int nn = (int)g.nn, nxy = g.nx * g.ny;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
+    const uint8_t mk = mask[nd];
+    for (int q = 0; q < NB * DIM * DIM; q++) S[(long long)q * nn + nd] = 0.f;
+    for (int c = 0; c < NC; c++) {
+      const int ei = i - cofs(c, 0), ej = j - cofs(c, 1), ek = k - (DIM == 3 ? cofs(c, 2) : 0);
+      if (ei < 0 || ej < 0 || ek < 0 || ei >= g.ex || ej >= g.ey || ek >= g.ez) continue;
+      const long long e = ei + (long long)g.ex * (ej + (long long)g.ey * ek);
+      const float* Ke = K ? K + e * ND * ND : c_K0;
+      const float sc = K ? 1.f : E[e];
+      for (int cc = 0; cc < NC; cc++) {
+        const int dx = cofs(cc, 0) - cofs(c, 0), dy = cofs(cc, 1) - cofs(c, 1);
+        const int dz = DIM == 3 ? cofs(cc, 2) - cofs(c, 2) : 0;
+        const int nbr = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+        const uint8_t m2 = mask[node_index(g, ei + cofs(cc, 0), ej + cofs(cc, 1), ek + (DIM == 3 ? cofs(cc, 2) : 0))];
+        for (int r = 0; r < DIM; r++) {
+          if ((mk >> r) & 1) continue;
+          for (int s2 = 0; s2 < DIM; s2++) {
+            if ((m2 >> s2) & 1) continue;
+            S[((long long)(nbr * DIM + r) * DIM + s2) * nn + nd] += sc * Ke[(c * DIM + r) * ND + cc * DIM + s2];
+          }
+        }
+      }
+    }
+  }
+}
+
+// apply_kernel on the assembled form (same modes).
+template <int DIM>
+__global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
+                                     const float* __restrict__ invd, const float* __restrict__ u,
+                                     const float* __restrict__ b, float* __restrict__ y, int mode, float omega) {
+  const int nn = (int)g.nn, nxy = g.nx * g.ny;
+  const long long ndof = (long long)nn * DIM;
+  const float* uc = u + blockIdx.y * ndof;
+  const float* bc = b ? b + blockIdx.y * ndof : nullptr;
+  float* yc = y + blockIdx.y * ndof;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
+    float acc[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; r++) acc[r] = 0.f;
+#pragma unroll
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
+      if (k + dz < 0 || k + dz >= g.nz) continue;
+#pragma unroll
+      for (int dy = -1; dy <= 1; dy++) {
+        if (j + dy < 0 || j + dy >= g.ny) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+          if (i + dx < 0 || i + dx >= g.nx) continue;
+          const int nbr = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+          const int n2 = nd + dx + g.nx * dy + nxy * dz;
+#pragma unroll
+          for (int s2 = 0; s2 < DIM; s2++) {
+            const float v = uc[(long long)n2 * DIM + s2];
+#pragma unroll
+            for (int r = 0; r < DIM; r++) acc[r] = fmaf(S[((long long)(nbr * DIM + r) * DIM + s2) * nn + nd], v, acc[r]);
+          }
+        }
+      }
+    }
+    const uint8_t mk = mask[nd];
+#pragma unroll
+    for (int r = 0; r < DIM; r++) {
+      const long long idx = (long long)nd * DIM + r;
+      const bool fx = (mk >> r) & 1;
+      const float au = fx ? uc[idx] : acc[r];
+      float out;
+      if (mode == 0) out = au;
+      else if (mode == 1) out = fx ? 0.f : uc[idx] + omega * invd[idx] * (bc[idx] - au);
+      else out = fx ? 0.f : bc[idx] - au;
+      yc[idx] = out;
+    }
+  }
+}
+
+// Inverse l1 row sums from the assembled form (see diag_kernel).
+template <int DIM>
+__global__ void diag_stencil_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
+                                    float* __restrict__ invd) {
+  constexpr int NB = DIM == 2 ? 9 : 27;
+  const int nn = (int)g.nn;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const uint8_t mk = mask[nd];
+#pragma unroll
+    for (int r = 0; r < DIM; r++) {
+      float d = 0.f;
+      for (int q = 0; q < NB; q++)
+#pragma unroll
+        for (int s2 = 0; s2 < DIM; s2++) d += fabsf(S[((long long)(q * DIM + r) * DIM + s2) * nn + nd]);
+      invd[(long long)nd * DIM + r] = ((mk >> r) & 1) || !(d > 0.f) ? 1.f : 1.f / d;
+    }
+  }
+}
+
+// First sweep from x = 0: y = omega D^-1 b.
+__global__ void jacobi0_kernel(long long n, int ncopies, const float* __restrict__ invd, const float* __restrict__ b,
+                               float* __restrict__ y, float omega) {
+  const int nn = (int)n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    const float w = omega * invd[i];
+    for (int c = 0; c < ncopies; c++) y[(long long)c * nn + i] = w * b[(long long)c * nn + i];
+  }
+}
+
+// Inverse l1 row sums of a level, 1 / sum_j |A_ij| (1 on fixed DOFs): the
+// l1-Jacobi smoother x += D_l1^-1 (b - A x) contracts in the A-norm for any
+// SPD A, without a damping parameter to tune.
+template <int DIM>
+__global__ void diag_kernel(Grid g, const float* __restrict__ K, const float* __restrict__ E,
+                            const uint8_t* __restrict__ mask, float* __restrict__ invd) {
+  constexpr int NC = MgC<DIM>::NC;
+  const int nn = (int)g.nn, nxy = g.nx * g.ny;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
+    float d[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; r++) d[r] = 0.f;
+#pragma unroll
+    for (int c = 0; c < NC; c++) {
+      const int ei = i - cofs(c, 0), ej = j - cofs(c, 1), ek = k - (DIM == 3 ? cofs(c, 2) : 0);
+      if (ei < 0 || ej < 0 || ek < 0 || ei >= g.ex || ej >= g.ey || ek >= g.ez) continue;
+      const long long e = ei + (long long)g.ex * (ej + (long long)g.ey * ek);
+      constexpr int ND = MgC<DIM>::ND;
+#pragma unroll
+      for (int r = 0; r < DIM; r++)
+        for (int b = 0; b < ND; b++) {
+          const int n2c = b / DIM, s2 = b % DIM;
+          const long long n2 = node_index(g, ei + cofs(n2c, 0), ej + cofs(n2c, 1), ek + (DIM == 3 ? cofs(n2c, 2) : 0));
+          if ((mask[n2] >> s2) & 1) continue;  // fixed columns do not couple
+          d[r] += fabsf(kentry<DIM>(K, E, e, c * DIM + r, b));
+        }
+    }
+    const uint8_t mk = mask[nd];
+#pragma unroll
+    for (int r = 0; r < DIM; r++) invd[nd * DIM + r] = ((mk >> r) & 1) || !(d[r] > 0.f) ? 1.f : 1.f / d[r];
+  }
+}
+
+// Coarse mask: a coarse node takes the fixed bits of the fine node at its place.
+__global__ void coarse_mask_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, uint8_t* __restrict__ mc) {
+  const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = nd / nxy, rem = nd - k * nxy, j = rem / gc.nx, i = rem - j * gc.nx;
+    mc[nd] = mf[node_index(gf, f * i, f * j, f * k)];
+  }
+}
+
+// 1D multilinear weight of coarse corner offset `o` (0 or 1) at fine position t in [0, f].
+__device__ __forceinline__ float w1(int o, int t, int f) { return o ? (float)t / f : 1.f - (float)t / f; }
+
+// Galerkin coarse element matrices: one CTA per coarse element, one thread per
+// entry (row a = (C, r), column b = (C', r')), children staged one at a time.
+template <int DIM>
+__global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Kf, const float* __restrict__ Ef,
+                                const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc, float* __restrict__ Kc) {
+  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND;
+  __shared__ float sK[ND * ND];
+  __shared__ uint8_t sM[NC];
+  const long long ec = blockIdx.x;
+  const int I = (int)(ec % gc.ex), J = (int)((ec / gc.ex) % gc.ey), Kz = (int)(ec / ((long long)gc.ex * gc.ey));
+  const int a = threadIdx.x / ND, b = threadIdx.x % ND;  // blockDim.x == ND * ND
+  const int Ca = a / DIM, ra = a % DIM, Cb = b / DIM, rb = b % DIM;
+  float acc = 0.f;
+  const int nch = DIM == 2 ? f * f : f * f * f;
+  for (int ch = 0; ch < nch; ch++) {
+    const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+    const int fi = f * I + cx, fj = f * J + cy, fk = DIM == 3 ? f * Kz + cz : 0;
+    const long long e = fi + (long long)gf.ex * (fj + (long long)gf.ey * fk);
+    __syncthreads();
+    sK[threadIdx.x] = kentry<DIM>(Kf, Ef, e, a, b);
+    if (threadIdx.x < NC) {
+      const int c = threadIdx.x;
+      sM[c] = mf[node_index(gf, fi + cofs(c, 0), fj + cofs(c, 1), fk + (DIM == 3 ? cofs(c, 2) : 0))];
+    }
+    __syncthreads();
+    for (int n1 = 0; n1 < NC; n1++) {
+      if ((sM[n1] >> ra) & 1) continue;
+      const int t1x = cx + cofs(n1, 0), t1y = cy + cofs(n1, 1), t1z = cz + (DIM == 3 ? cofs(n1, 2) : 0);
+      float pa = w1(cofs(Ca, 0), t1x, f) * w1(cofs(Ca, 1), t1y, f);
+      if (DIM == 3) pa *= w1(cofs(Ca, 2), t1z, f);
+      if (pa == 0.f) continue;
+      for (int n2 = 0; n2 < NC; n2++) {
+        if ((sM[n2] >> rb) & 1) continue;
+        const int t2x = cx + cofs(n2, 0), t2y = cy + cofs(n2, 1), t2z = cz + (DIM == 3 ? cofs(n2, 2) : 0);
+        float pb = w1(cofs(Cb, 0), t2x, f) * w1(cofs(Cb, 1), t2y, f);
+        if (DIM == 3) pb *= w1(cofs(Cb, 2), t2z, f);
+        acc = fmaf(pa * pb, sK[(n1 * DIM + ra) * ND + n2 * DIM + rb], acc);
+      }
+    }
+  }
+  // zero rows and columns of fixed coarse DOFs
+  const uint8_t ma = mc[node_index(gc, I + cofs(Ca, 0), J + cofs(Ca, 1), Kz + (DIM == 3 ? cofs(Ca, 2) : 0))];
+  const uint8_t mb = mc[node_index(gc, I + cofs(Cb, 0), J + cofs(Cb, 1), Kz + (DIM == 3 ? cofs(Cb, 2) : 0))];
+  if (((ma >> ra) & 1) || ((mb >> rb) & 1)) acc = 0.f;
+  Kc[ec * ND * ND + threadIdx.x] = acc;
+}
+
+// b_c = P^T r_f for f = 2 (3^dim fine neighbours): one thread per coarse node.
+template <int DIM>
+__global__ void restrict2_kernel(Grid gf, Grid gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
+                                 const float* __restrict__ rf, float* __restrict__ bc) {
+  const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
+  const float* r = rf + blockIdx.y * ndf;
+  float* out = bc + blockIdx.y * ndc;
+  const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int Kz = nd / nxy, rem = nd - Kz * nxy, J = rem / gc.nx, I = rem - J * gc.nx;
+    float acc[DIM];
+#pragma unroll
+    for (int s2 = 0; s2 < DIM; s2++) acc[s2] = 0.f;
+#pragma unroll
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
+      const int fk = 2 * Kz + dz;
+      if (fk < 0 || fk >= gf.nz) continue;
+#pragma unroll
+      for (int dy = -1; dy <= 1; dy++) {
+        const int fj = 2 * J + dy;
+        if (fj < 0 || fj >= gf.ny) continue;
+#pragma unroll
+        for (int dx = -1; dx <= 1; dx++) {
+          const int fi = 2 * I + dx;
+          if (fi < 0 || fi >= gf.nx) continue;
+          const float wgt = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f);
+          const long long n2 = node_index(gf, fi, fj, fk);
+          const uint8_t m2 = mf[n2];
+#pragma unroll
+          for (int s2 = 0; s2 < DIM; s2++)
+            if (!((m2 >> s2) & 1)) acc[s2] = fmaf(wgt, r[n2 * DIM + s2], acc[s2]);
+        }
+      }
+    }
+    const uint8_t mk = mc[nd];
+#pragma unroll
+    for (int s2 = 0; s2 < DIM; s2++) out[(long long)nd * DIM + s2] = ((mk >> s2) & 1) ? 0.f : acc[s2];
+  }
+}
+
+// b_c = P^T r_f (fine fixed DOFs read as 0, coarse fixed DOFs set to 0).  One
+// warp per coarse node: the lanes split the (2f - 1)^dim fine neighbours and
+// the sum is reduced in a fixed order.
+template <int DIM>
+__global__ void restrict_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
+                                const float* __restrict__ rf, float* __restrict__ bc) {
+  const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
+  const float* r = rf + blockIdx.y * ndf;
+  float* out = bc + blockIdx.y * ndc;
+  const int lane = threadIdx.x & 31;
+  const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
+  const int w = 2 * f - 1, nz = DIM == 3 ? w : 1, tot = w * w * nz;
+  for (int nd = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; nd < nn; nd += (gridDim.x * blockDim.x) >> 5) {
+    const int Kz = nd / nxy, rem = nd - Kz * nxy, J = rem / gc.nx, I = rem - J * gc.nx;
+    float acc[DIM];
+#pragma unroll
+    for (int s2 = 0; s2 < DIM; s2++) acc[s2] = 0.f;
+    for (int q = lane; q < tot; q += 32) {
+      const int dx = q % w - (f - 1), dy = (q / w) % w - (f - 1), dz = DIM == 3 ? q / (w * w) - (f - 1) : 0;
+      const int fi = f * I + dx, fj = f * J + dy, fk = f * Kz + dz;
+      if (fi < 0 || fi >= gf.nx || fj < 0 || fj >= gf.ny || fk < 0 || fk >= gf.nz) continue;
+      float wgt = (1.f - fabsf((float)dx) / f) * (1.f - fabsf((float)dy) / f);
+      if (DIM == 3) wgt *= 1.f - fabsf((float)dz) / f;
+      const long long n2 = node_index(gf, fi, fj, fk);
+      const uint8_t m2 = mf[n2];
+#pragma unroll
+      for (int s2 = 0; s2 < DIM; s2++)
+        if (!((m2 >> s2) & 1)) acc[s2] = fmaf(wgt, r[n2 * DIM + s2], acc[s2]);
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < DIM; s2++)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[s2] += __shfl_xor_sync(0xffffffffu, acc[s2], o);
+    if (lane == 0) {
+      const uint8_t mk = mc[nd];
+#pragma unroll
+      for (int s2 = 0; s2 < DIM; s2++) out[(long long)nd * DIM + s2] = ((mk >> s2) & 1) ? 0.f : acc[s2];
+    }
+  }
+}
+
+// x_f += P x_c on free fine DOFs.
+template <int DIM>
+__global__ void prolong_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, const float* __restrict__ xc,
+                               float* __restrict__ xf) {
+  constexpr int NC = MgC<DIM>::NC;
+  const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
+  const float* x = xc + blockIdx.y * ndc;
+  float* out = xf + blockIdx.y * ndf;
+  const int nn = (int)gf.nn, nxy = gf.nx * gf.ny;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = nd / nxy, rem = nd - k * nxy, j = rem / gf.nx, i = rem - j * gf.nx;
+    const int I = min(i / f, gc.ex - 1), J = min(j / f, gc.ey - 1), Kz = DIM == 3 ? min(k / f, gc.ez - 1) : 0;
+    const int tx = i - f * I, ty = j - f * J, tz = k - f * Kz;
+    float acc[DIM];
+#pragma unroll
+    for (int s = 0; s < DIM; s++) acc[s] = 0.f;
+#pragma unroll
+    for (int C = 0; C < NC; C++) {
+      float wgt = w1(cofs(C, 0), tx, f) * w1(cofs(C, 1), ty, f);
+      if (DIM == 3) wgt *= w1(cofs(C, 2), tz, f);
+      if (wgt == 0.f) continue;
+      const long long n2 = node_index(gc, I + cofs(C, 0), J + cofs(C, 1), Kz + (DIM == 3 ? cofs(C, 2) : 0));
+#pragma unroll
+      for (int s = 0; s < DIM; s++) acc[s] = fmaf(wgt, x[n2 * DIM + s], acc[s]);
+    }
+    const uint8_t mk = mf[nd];
+#pragma unroll
+    for (int s = 0; s < DIM; s++)
+      if (!((mk >> s) & 1)) out[nd * DIM + s] += acc[s];
+  }
+}
+
+// Coarsest solve: x = A^-1 b with the dense inverse; one warp per row
+// (blockIdx.y = case).
+__global__ void dense_solve_kernel(int n, const float* __restrict__ Ainv, const float* __restrict__ b, float* __restrict__ x) {
+  const float* bc = b + (long long)blockIdx.y * n;
+  float* xc = x + (long long)blockIdx.y * n;
+  const int lane = threadIdx.x & 31;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    float s = 0.f;
+    for (int j = lane; j < n; j += 32) s = fmaf(Ainv[(long long)i * n + j], bc[j], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) xc[i] = s;
+  }
+}
+
+int blocks(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
+
+// Smallest factor f >= 2 dividing every element count (2 first), or 0.
+int common_factor(const Grid& g) {
+  for (int f : {2, 3, 5, 7}) {
+    if (g.ex % f || g.ey % f || (g.dim == 3 && g.ez % f)) continue;
+    if (g.ex / f < 1 || g.ey / f < 1 || (g.dim == 3 && g.ez / f < 1)) continue;
+    return f;
+  }
+  return 0;
+}
+
+Grid coarsen(const Grid& g, int f) {
+  Grid c = g;
+  c.ex = g.ex / f;
+  c.ey = g.ey / f;
+  c.ez = g.dim == 3 ? g.ez / f : 1;
+  c.nx = c.ex + 1;
+  c.ny = c.ey + 1;
+  c.nz = g.dim == 3 ? c.ez + 1 : 1;
+  c.nn = (long long)c.nx * c.ny * c.nz;
+  c.ne = (long long)c.ex * c.ey * c.ez;
+  return c;
+}
+
+// In-place inverse of an SPD matrix (Cholesky, FP64, row-major n x n).
+bool spd_inverse(std::vector<double>& A, int n) {
+  std::vector<double> L(A);
+  for (int j = 0; j < n; j++) {
+    double d = L[(size_t)j * n + j];
+    for (int k = 0; k < j; k++) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; i++) {
+      double s = L[(size_t)i * n + j];
+      for (int k = 0; k < j; k++) s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = s / ljj;
+    }
+  }
+  // columns of A^-1: solve L L^T x = e_c
+  std::vector<double> y(n);
+  for (int c = 0; c < n; c++) {
+    for (int i = 0; i < n; i++) {
+      double s = i == c ? 1.0 : 0.0;
+      for (int k = 0; k < i; k++) s -= L[(size_t)i * n + k] * y[k];
+      y[i] = s / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; i--) {
+      double s = y[i];
+      for (int k = i + 1; k < n; k++) s -= L[(size_t)k * n + i] * A[(size_t)k * n + c];
+      A[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+void MgHierarchy::release() {
+  for (auto& l : lv) {
+    void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+  }
+  lv.clear();
+  if (cinv) cudaFree(cinv);
+  cinv = nullptr;
+  built = false;
+}
+
+cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int max_coarse_dofs) {
+  release();
+  nc = nc_;
+  MgLevel l0;
+  l0.g = g0;
+  l0.f = 1;
+  l0.mask = const_cast<uint8_t*>(mask0);
+  l0.mask_own = false;
+  lv.push_back(l0);
+  while ((int)lv.size() < 12 && lv.back().g.nn * g0.dim > max_coarse_dofs) {
+    const int f = common_factor(lv.back().g);
+    if (!f) break;
+    MgLevel l;
+    l.g = coarsen(lv.back().g, f);
+    l.f = f;
+    lv.push_back(l);
+  }
+  if (lv.back().g.nn * g0.dim > 4096 || lv.size() < 2) return cudaErrorInvalidValue;
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < lv.size() && e == cudaSuccess; i++) {
+    MgLevel& l = lv[i];
+    const long long ndof = l.g.nn * g0.dim, nd = g0.dim == 2 ? 8 : 24;
+    if (i > 0) {
+      e = cudaMalloc((void**)&l.K, l.g.ne * nd * nd * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc((void**)&l.mask, l.g.nn);
+      l.mask_own = true;
+    }
+    if (e == cudaSuccess && (g0.dim == 2 || i > 0)) {
+      const long long nb = g0.dim == 2 ? 9 * 4 : 27 * 9;
+      e = cudaMalloc((void**)&l.S, l.g.nn * nb * sizeof(float));
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&l.invd, ndof * sizeof(float));
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMalloc((void**)&l.x[k], nc * ndof * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&l.b, nc * ndof * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&l.t, nc * ndof * sizeof(float));
+  }
+  cn = (int)(lv.back().g.nn * g0.dim);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&cinv, (size_t)cn * cn * sizeof(float));
+  return e;
+}
+
+cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E32, int* nlaunch) {
+  const int dim = lv[0].g.dim, nd = dim == 2 ? 8 : 24;
+  std::vector<float> k0f(nd * nd);
+  for (int i = 0; i < nd * nd; i++) k0f[i] = (float)K0[i];
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_K0, k0f.data(), nd * nd * sizeof(float), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  E0 = E32;
+  int nl = 0;
+  for (size_t i = 0; i < lv.size(); i++) {
+    MgLevel& l = lv[i];
+    if (i > 0) {
+      const MgLevel& fl = lv[i - 1];
+      coarse_mask_kernel<<<blocks(l.g.nn), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, l.mask);
+      if (dim == 2)
+        galerkin_kernel<2><<<(unsigned)l.g.ne, 64, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, fl.mask, l.mask, l.K);
+      else
+        galerkin_kernel<3><<<(unsigned)l.g.ne, 576, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, fl.mask, l.mask, l.K);
+      nl += 2;
+    }
+    if (l.S) {
+      if (dim == 2) {
+        stencil_kernel<2><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.K, i == 0 ? E32 : nullptr, l.mask, l.S);
+        diag_stencil_kernel<2><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.S, l.mask, l.invd);
+      } else {
+        stencil_kernel<3><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.K, i == 0 ? E32 : nullptr, l.mask, l.S);
+        diag_stencil_kernel<3><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.S, l.mask, l.invd);
+      }
+      nl += 2;
+    } else {
+      if (dim == 2) diag_kernel<2><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.K, i == 0 ? E32 : nullptr, l.mask, l.invd);
+      else diag_kernel<3><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.K, i == 0 ? E32 : nullptr, l.mask, l.invd);
+      nl++;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // coarsest: assemble on the host in FP64 and invert (a few hundred DOFs)
+  const MgLevel& c = lv.back();
+  std::vector<float> Kc((size_t)c.g.ne * nd * nd);
+  std::vector<uint8_t> mc(c.g.nn);
+  e = cudaMemcpyAsync(Kc.data(), c.K, Kc.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(mc.data(), c.mask, mc.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  const int n = cn, nce = dim == 2 ? 4 : 8;
+  std::vector<double> A((size_t)n * n, 0.0);
+  for (long long el = 0; el < c.g.ne; el++) {
+    const int I = (int)(el % c.g.ex), J = (int)((el / c.g.ex) % c.g.ey), Kz = (int)(el / ((long long)c.g.ex * c.g.ey));
+    long long nodes[8];
+    for (int q = 0; q < nce; q++)
+      nodes[q] = (I + cofs(q, 0)) + (long long)c.g.nx * ((J + cofs(q, 1)) + (long long)c.g.ny * (Kz + (dim == 3 ? cofs(q, 2) : 0)));
+    for (int a = 0; a < nd; a++)
+      for (int b = 0; b < nd; b++)
+        A[(size_t)(nodes[a / dim] * dim + a % dim) * n + nodes[b / dim] * dim + b % dim] += Kc[(size_t)el * nd * nd + a * nd + b];
+  }
+  for (int i = 0; i < n; i++)
+    if ((mc[i / dim] >> (i % dim)) & 1) {
+      for (int j = 0; j < n; j++) A[(size_t)i * n + j] = A[(size_t)j * n + i] = 0.0;
+      A[(size_t)i * n + i] = 1.0;
+    }
+  // symmetrise the FP32 sums
+  for (int i = 0; i < n; i++)
+    for (int j = i + 1; j < n; j++) {
+      const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = v;
+    }
+  if (!spd_inverse(A, n)) return cudaErrorInvalidValue;
+  std::vector<float> Af((size_t)n * n);
+  for (size_t i = 0; i < Af.size(); i++) Af[i] = (float)A[i];
+  e = cudaMemcpyAsync(cinv, Af.data(), Af.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  built = e == cudaSuccess;
+  if (nlaunch) *nlaunch += nl;
+  return e;
+}
+
+template <int DIM>
+static cudaError_t apply_level(cudaStream_t s, const MgLevel& l, const float* E0, int nc, const float* u, const float* b,
+                               float* y, int mode, float omega) {
+  dim3 grid(blocks(l.g.nn), nc);
+  if (l.S) apply_stencil_kernel<DIM><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, b, y, mode, omega);
+  else apply_kernel<DIM><<<grid, 256, 0, s>>>(l.g, l.K, l.K ? nullptr : E0, l.mask, l.invd, u, b, y, mode, omega);
+  return cudaGetLastError();
+}
+
+// One V-cycle on level li: x = V(b) with x starting at zero.  The result is
+// left in lv[li].x[0].
+cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch) {
+  MgLevel& l = lv[li];
+  const int dim = l.g.dim;
+  const long long ndof = l.g.nn * dim;
+  if (li == (int)lv.size() - 1) {
+    dense_solve_kernel<<<dim3((cn + 7) / 8, nc), 256, 0, s>>>(cn, cinv, l.b, l.x[0]);
+    (*nlaunch)++;
+    return cudaGetLastError();
+  }
+  auto apply = [&](const float* u, const float* b, float* y, int mode) {
+    return dim == 2 ? apply_level<2>(s, l, E0, nc, u, b, y, mode, omega)
+                    : apply_level<3>(s, l, E0, nc, u, b, y, mode, omega);
+  };
+  // pre-smoothing from zero
+  jacobi0_kernel<<<blocks(ndof), 256, 0, s>>>(ndof, nc, l.invd, l.b, l.x[0], omega);
+  (*nlaunch)++;
+  int cur = 0;
+  for (int k = 1; k < nu; k++) {
+    cudaError_t e = apply(l.x[cur], l.b, l.x[cur ^ 1], 1);
+    if (e != cudaSuccess) return e;
+    cur ^= 1;
+    (*nlaunch)++;
+  }
+  cudaError_t e = apply(l.x[cur], l.b, l.t, 2);  // residual
+  if (e != cudaSuccess) return e;
+  (*nlaunch)++;
+  MgLevel& c = lv[li + 1];
+  if (c.f == 2) {
+    dim3 gr(blocks(c.g.nn), nc);
+    if (dim == 2) restrict2_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b);
+    else restrict2_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b);
+  } else {
+    dim3 gr(blocks(c.g.nn * 32), nc);
+    if (dim == 2) restrict_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.mask, l.t, c.b);
+    else restrict_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.mask, l.t, c.b);
+  }
+  (*nlaunch)++;
+  e = vcycle(s, li + 1, nlaunch);
+  if (e != cudaSuccess) return e;
+  dim3 gp(blocks(l.g.nn), nc);
+  if (dim == 2) prolong_kernel<2><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.x[0], l.x[cur]);
+  else prolong_kernel<3><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.x[0], l.x[cur]);
+  (*nlaunch)++;
+  for (int k = 0; k < nu; k++) {  // post-smoothing (as many sweeps: symmetric)
+    e = apply(l.x[cur], l.b, l.x[cur ^ 1], 1);
+    if (e != cudaSuccess) return e;
+    cur ^= 1;
+    (*nlaunch)++;
+  }
+  if (cur != 0) {
+    e = cudaMemcpyAsync(l.x[0], l.x[1], nc * ndof * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tp
+
+// ---------------------------------------------------------------------------
+// FP64 outer-PCG vector kernels.
+namespace tp {
+namespace {
+
+// Per-case partial dot products: block (b, c) sums chunk b of case c;
+// part[(c * nb + b) * 2 + k] for the two products k.
+__global__ void dot2_kernel(long long n, const double* __restrict__ a1, const double* __restrict__ b1,
+                            const double* __restrict__ a2, const double* __restrict__ b2, double* __restrict__ part) {
+  __shared__ double sred[32 * 2];
+  const int c = blockIdx.y, nb = gridDim.x;
+  const long long base = (long long)c * n;
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)nb * blockDim.x) {
+    acc[0] = fma(a1[base + i], b1[base + i], acc[0]);
+    if (a2) acc[1] = fma(a2[base + i], b2[base + i], acc[1]);
+  }
+  block_sum<2>(acc, sred);
+  if (threadIdx.x < 2) part[((long long)c * nb + blockIdx.x) * 2 + threadIdx.x] = acc[threadIdx.x];
+}
+
+// Sums the partials (one warp per (case, product), fixed order) and forms the
+// PCG scalars of each case.
+__global__ void scalars_kernel(int nb, int nc, const double* __restrict__ part, int what, double* sc) {
+  __shared__ double tot[16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int pr = warp; pr < 2 * nc; pr += blockDim.x >> 5) {
+    const int c = pr >> 1, k = pr & 1;
+    double sum = 0.0;
+    for (int b = lane; b < nb; b += 32) sum += part[((long long)c * nb + b) * 2 + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) tot[pr] = sum;
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c >= 8) return;
+  if (c >= nc) {
+    sc[c] = sc[8 + c] = 0.0;
+    return;
+  }
+  const double s1 = tot[2 * c], s2 = tot[2 * c + 1];
+  if (what == 0) {  // alpha = rz / pq
+    sc[24 + c] = s1;
+    sc[c] = (s1 > 0.0 && isfinite(s1)) ? sc[16 + c] / s1 : 0.0;
+  } else if (what == 1) {  // beta = rz_new / rz
+    sc[8 + c] = sc[16 + c] != 0.0 ? s1 / sc[16 + c] : 0.0;
+    sc[16 + c] = s1;
+    sc[32 + c] = s2;
+  } else {  // start
+    sc[16 + c] = s1;
+    sc[32 + c] = s2;
+    sc[8 + c] = 0.0;
+  }
+}
+
+// One block row per case (blockIdx.y); 32-bit indices within a case.
+__global__ void update_xr_kernel(long long n, const double* __restrict__ sc, double* x, const double* __restrict__ p,
+                                 double* r, const double* __restrict__ q) {
+  const int c = blockIdx.y, nn = (int)n;
+  const double a = sc[c];
+  const long long base = (long long)c * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    x[base + i] = fma(a, p[base + i], x[base + i]);
+    r[base + i] = fma(-a, q[base + i], r[base + i]);
+  }
+}
+
+__global__ void update_p_kernel(long long n, const double* __restrict__ sc, double* p, const double* __restrict__ z) {
+  const int c = blockIdx.y, nn = (int)n;
+  const double b = sc[8 + c];
+  const long long base = (long long)c * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+    p[base + i] = fma(b, p[base + i], z[base + i]);
+}
+
+__global__ void residual_abi_kernel(long long n, const double* __restrict__ f, const double* __restrict__ Ax,
+                                    const uint8_t* __restrict__ mask, int dim, double* r) {
+  const int c = blockIdx.y, nn = (int)n;
+  const long long base = (long long)c * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    const int node = i / dim, comp = i - node * dim;
+    r[base + i] = ((mask[node] >> comp) & 1) ? 0.0 : f[base + i] - Ax[base + i];
+  }
+}
+
+__global__ void f32_kernel(long long n, const double* __restrict__ a, float* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f64_kernel(long long n, const float* __restrict__ a, double* b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+int vblocks(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 8); }
+
+}  // namespace
+
+cudaError_t pcg_dot2(cudaStream_t s, long long n, int nc, const double* a1, const double* b1, const double* a2,
+                     const double* b2, double* part, int* nblocks) {
+  const int nb = (int)std::min<long long>(std::max<long long>((n + 1023) / 1024, 1), 2 * 152 / nc + 1);
+  dot2_kernel<<<dim3(nb, nc), 256, 0, s>>>(n, a1, b1, a2, b2, part);
+  *nblocks = nb;
+  return cudaGetLastError();
+}
+cudaError_t pcg_scalars(cudaStream_t s, int nblocks, int nc, const double* part, int what, double* sc) {
+  scalars_kernel<<<1, 512, 0, s>>>(nblocks, nc, part, what, sc);
+  return cudaGetLastError();
+}
+cudaError_t pcg_update_xr(cudaStream_t s, long long n, int nc, const double* sc, double* x, const double* p, double* r,
+                          const double* q) {
+  update_xr_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, sc, x, p, r, q);
+  return cudaGetLastError();
+}
+cudaError_t pcg_update_p(cudaStream_t s, long long n, int nc, const double* sc, double* p, const double* z) {
+  update_p_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, sc, p, z);
+  return cudaGetLastError();
+}
+cudaError_t pcg_residual(cudaStream_t s, long long n, int nc, const double* f, const double* Ax, const uint8_t* mask,
+                         int dim, double* r) {
+  residual_abi_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, f, Ax, mask, dim, r);
+  return cudaGetLastError();
+}
+cudaError_t to_f32(cudaStream_t s, long long n, const double* a, float* b) {
+  f32_kernel<<<vblocks(n), 256, 0, s>>>(n, a, b);
+  return cudaGetLastError();
+}
+cudaError_t to_f64(cudaStream_t s, long long n, const float* a, double* b) {
+  f64_kernel<<<vblocks(n), 256, 0, s>>>(n, a, b);
+  return cudaGetLastError();
+}
+
+}  // namespace tp

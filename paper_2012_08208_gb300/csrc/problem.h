@@ -5,6 +5,7 @@
 
 #include "../../include/topo.h"
 #include "host.h"
+#include "mg.h"
 
 struct tp_problem {
   using FilterLaunch = tp::FilterLaunch;
@@ -55,6 +56,9 @@ struct tp_problem {
   long long launches = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int last_grid = 0;
+  tp::MgHierarchy* mg = nullptr; // multigrid preconditioner (built on first use)
+  long long E_version = 0;       // bumped whenever the moduli are recomputed
+  double* mg_sc = nullptr;       // device scalars of the multigrid PCG
   int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
   double* rho_phys = nullptr;    // density-filtered densities (filter mode 1)
   double* rowsum = nullptr;      // sum_b W_ab per element (filter mode 1)

@@ -23,6 +23,8 @@ TP_PREC_F64, TP_PREC_MIXED = 0, 1
 TP_WARM_ZERO, TP_WARM_PREVIOUS, TP_WARM_USER = 0, 1, 2
 TP_FILTER_SENSITIVITY = 0
 TP_FILTER_DENSITY = 1
+TP_PRECOND_JACOBI = 0
+TP_PRECOND_MG = 1
 TP_RHO, TP_U, TP_DC, TP_DCF, TP_CE, TP_RHO_PHYS = range(6)
 
 
@@ -35,7 +37,8 @@ class tp_params(C.Structure):
 
 class tp_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_it", C.c_int), ("precision", C.c_int),
-                ("warm_start", C.c_int), ("update_drop", C.c_double), ("warm_max_rel", C.c_double)]
+                ("warm_start", C.c_int), ("update_drop", C.c_double), ("warm_max_rel", C.c_double),
+                ("precond", C.c_int)]
 
 
 class tp_solve_info(C.Structure):
@@ -182,8 +185,8 @@ def make_params(dim, nelx, nely, nelz=0, E0=1.0, Emin=1e-9, nu=0.3, penal=3.0, v
 
 
 def solve_opts(tol=1e-8, max_it=20000, precision=TP_PREC_MIXED, warm_start=TP_WARM_ZERO, update_drop=1e-2,
-               warm_max_rel=0.0):
-    return tp_solve_opts(tol, max_it, precision, warm_start, update_drop, warm_max_rel)
+               warm_max_rel=0.0, precond=0):
+    return tp_solve_opts(tol, max_it, precision, warm_start, update_drop, warm_max_rel, precond)
 
 
 class Problem:

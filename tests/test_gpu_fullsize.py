@@ -33,12 +33,13 @@ def topo():
     return t
 
 
-def test_cantilever2d_full_step(topo):
+@pytest.mark.parametrize("precond", [0, 1], ids=["jacobi", "multigrid"])
+def test_cantilever2d_full_step(topo, precond):
     w = W.cantilever2d()
     rho0 = w.initial_density()
     p = topo.Problem.from_workload(w)
     opts = topo.solve_opts(tol=w.tol, max_it=100000, precision=topo.TP_PREC_MIXED,
-                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=0.1)
+                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=0.1, precond=precond)
     info = p.simp_step(opts)
     assert info.solve.converged == 1 and max(info.solve.rel_res[c] for c in range(3)) <= 1e-8
     rho1 = p.get(topo.TP_RHO)

@@ -227,3 +227,58 @@ def test_density_filter_mode_iterations(topo, prob):
     with pytest.raises(topo.TopoError):
         p.filter(topo.TP_FILTER_SENSITIVITY)
     p.close()
+
+
+MG_GRIDS = [W.small2d(40, 12, n_cases=3, passive_disk=(12, 6, 3)), W.small2d(60, 20), W.small3d(16, 8, 6),
+            W.small3d(20, 10, 10, n_cases=2)]
+
+
+@pytest.mark.parametrize("prob", MG_GRIDS, ids=lambda p: p.name + f"_nc{p.n_cases}")
+def test_multigrid_solve_matches_direct_solve(topo, prob):
+    """Multigrid-preconditioned CG (FP64 outer, FP32 V-cycle) against the
+    oracle's LU solve on a random density: true residual <= tol, compliance
+    rel <= 1e-8, displacements rel <= 1e-6."""
+    rho = W.random_density(prob.n_el, seed=51, lo=0.05)
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    info = p.solve(topo.solve_opts(tol=1e-11, max_it=5000, precond=topo.TP_PRECOND_MG))
+    assert info.converged == 1 and max(info.rel_res[c] for c in range(prob.n_cases)) <= 1e-11
+    assert info.iters < 200
+    U = fem.solve(prob, rho)
+    u = p.get(topo.TP_U).reshape(prob.n_cases, -1)
+    for c in range(prob.n_cases):
+        assert float(prob.loads[c] @ u[c]) == pytest.approx(float(prob.loads[c] @ U[c]), rel=1e-8)
+        assert np.linalg.norm(u[c] - U[c]) <= 1e-6 * np.linalg.norm(U[c])
+    p.close()
+
+
+def test_multigrid_simp_iterations_mbb(topo):
+    """Config 1 SIMP iterations with the multigrid solver, each against the
+    oracle on the GPU's own density (compliance <= 1e-8, rho <= 1e-6, lambda
+    <= 1e-9 of the exact root)."""
+    prob = W.mbb2d()
+    Wm = filt.weights_for(prob)
+    p = topo.Problem.from_workload(prob)
+    rho = prob.initial_density()
+    opts = topo.solve_opts(tol=1e-10, max_it=5000, warm_start=topo.TP_WARM_PREVIOUS, precond=topo.TP_PRECOND_MG)
+    for it in range(8):
+        info = p.simp_step(opts)
+        assert info.solve.iters < 100
+        ref = simp.iteration(prob, rho, W=Wm)
+        assert abs(info.compliance - ref["c"]) <= 1e-8 * ref["c"]
+        rho_gpu = p.get(topo.TP_RHO)
+        assert info.lambda_ == pytest.approx(oc.exact_lambda(rho, ref["dcf"], prob.volfrac), rel=1e-9)
+        assert np.max(np.abs(rho_gpu - ref["rho_new"])) <= 1e-6
+        rho = rho_gpu
+    p.close()
+
+
+def test_multigrid_needs_a_hierarchy(topo):
+    prob = W.small2d(37, 11)  # prime element counts: no coarse grid
+    p = topo.Problem.from_workload(prob)
+    with pytest.raises(topo.TopoError) as e:
+        p.solve(topo.solve_opts(tol=1e-8, precond=topo.TP_PRECOND_MG))
+    assert e.value.status == topo.TP_ERR_ARG
+    info = p.solve(topo.solve_opts(tol=1e-8, max_it=20000))  # the handle stays usable
+    assert info.converged == 1
+    p.close()
