@@ -119,7 +119,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     w = W.cantilever2d()
     opts = topo.solve_opts(tol=w.tol, max_it=100000, precision=topo.TP_PREC_MIXED,
-                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=1e-1)
+                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=1e-1, precond=args.solver)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -134,6 +134,8 @@ def run_ours(args):
             p.simp_step(opts, check=False)
             flush.add_(1.0)
         barrier()
+        if args.solver == 1:
+            p.set_profile(True)  # event pairs around the finest-level multigrid launches
         clocks = ClockSampler(local)
         clocks.start()
         launches0 = p.launch_count()
@@ -149,6 +151,9 @@ def run_ours(args):
         barrier()
         t_wall = time.perf_counter() - t_wall0
         launches = p.launch_count() - launches0
+        prof = p.get_profile() if args.solver == 1 else None
+        if args.solver == 1:
+            p.set_profile(False)
         step_ms = [a.elapsed_time(b) for a, b in ev]
         # end-to-end through the public API with host buffers: H2D of the step's
         # design from pinned memory, the step, D2H of the updated design.
@@ -187,10 +192,24 @@ def run_ours(args):
     # dominant kernel: the persistent CG launch (one per step); its duration is
     # the library's CUDA-event pair around the cooperative launch on `stream`
     solve_ms = [i.solve.ms for i in infos]
-    byts = [algorithmic_bytes_pcg(i.solve, w.n_dof, w.n_el, w.n_cases) for i in infos]
-    avg_bytes = float(np.mean(byts))
     avg_ms = float(np.mean(solve_ms))
-    achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
+    if args.solver == 1:
+        # dominant kernel: the finest-level operator launches of the multigrid
+        # V-cycles (l1-Jacobi sweeps and residuals), timed live by event pairs
+        n_l, ms_l, bytes_l, levels = prof
+        achieved = bytes_l / (ms_l / max(n_l, 1) * 1e-3) / 1e9
+        roof_kernel = "apply_stencil_kernel<2> (finest multigrid level, assembled 2x2 blocks, 3 cases)"
+        roof_extra = {"launches_timed": n_l, "us_per_launch": round(1e3 * ms_l / max(n_l, 1), 3),
+                      "bytes_per_launch": bytes_l, "levels": levels,
+                      "traffic_note": "see profiles/apply_stencil_cantilever2d_600x200_full.md"}
+    else:
+        byts = [algorithmic_bytes_pcg(i.solve, w.n_dof, w.n_el, w.n_cases) for i in infos]
+        avg_bytes = float(np.mean(byts))
+        achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
+        roof_kernel = "pcg_kernel<2,float,4> (persistent CG, 3 cases)"
+        roof_extra = {"traffic_note": "L2-resident working set: ncu of a 68-iteration launch reads 10.3 MB and "
+                                      "writes 1.5 MB of DRAM, with 32 MB of L2 reads per iteration against 42 MB "
+                                      "algorithmic (profiles/cg_segment_cantilever2d_600x200_full.md)"}
     value = ws * args.steps / (total_ms * 1e-3)
     cpu = None
     if not args.no_cpu:
@@ -203,23 +222,21 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "grid": "600x200 Q4", "n_dof": w.n_dof, "n_cases": w.n_cases,
                    "tol": w.tol, "precision": "FP32 operator + FP64 reductions/reliable updates",
                    "warm_start": "previous iteration's displacement", "l2": "flushed between timed steps",
+                   "solver": "multigrid-preconditioned CG (FP32 V-cycle, FP64 CG)" if args.solver == 1
+                   else "Jacobi-PCG (persistent, FP32 + FP64 reliable updates)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(ws * e2e_steps / t_e2e, 4), "unit": "SIMP iter/s",
                 "h2d_bytes_per_step": w.n_el * 8, "d2h_bytes_per_step": w.n_el * 8},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "pcg_kernel<2,float,4> (persistent CG, 3 cases)", "bound": "hbm",
-                     "achieved": round(achieved, 2), "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None,
-                     "traffic_note": "L2-resident working set: ncu of a 68-iteration launch reads 10.3 MB and "
-                                     "writes 1.5 MB of DRAM, with 32 MB of L2 reads per iteration against 42 MB "
-                                     "algorithmic (profiles/cg_segment_cantilever2d_600x200_full.md); DRAM bytes "
-                                     "do not scale with the launch length, so no per-launch figure is given",
-                     "cg_iters_per_step": float(np.mean([i.solve.iters for i in infos])),
-                     "updates_per_step": float(np.mean([i.solve.updates for i in infos])),
-                     "solve_ms_per_step": round(avg_ms, 3),
-                     "converged_steps": int(sum(i.solve.converged for i in infos)),
-                     "max_true_rel_res": float(max(max(i.solve.rel_res[c] for c in range(w.n_cases)) for i in infos)),
-                     "note": "working set of this workload is L2-resident within a step"},
+        "roofline": dict({"kernel": roof_kernel, "bound": "hbm",
+                          "achieved": round(achieved, 2), "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                          "frac": round(achieved / hbm, 4), "traffic": None,
+                          "solver_iters_per_step": float(np.mean([i.solve.iters for i in infos])),
+                          "restarts_per_step": float(np.mean([i.solve.updates for i in infos])),
+                          "solve_ms_per_step": round(avg_ms, 3),
+                          "converged_steps": int(sum(i.solve.converged for i in infos)),
+                          "max_true_rel_res": float(max(max(i.solve.rel_res[c] for c in range(w.n_cases))
+                                                        for i in infos))}, **roof_extra),
         "clocks": clk,
         "cpu_baseline": cpu,
         "wall_s_timed": round(t_wall, 3),
@@ -276,12 +293,15 @@ def learned_extra(topo, n_oc=(0, 5)):
     for k in n_oc:
         p = WS.density_after(w, k)
         r = {"oc_iter": k}
-        for kind, kw in (("f64", {}), ("mixed", {}), ("learned", {}), ("learned_forced", {"warm_max_rel": 1e30})):
+        for kind, kw in (("f64", {}), ("mixed", {}), ("learned", {}), ("learned_forced", {"warm_max_rel": 1e30}),
+                         ("mg", {}), ("mg_learned", {})):
             t = WS.time_to_tol(p, "learned" if kind.startswith("learned") else kind, 1e-6, net, **kw)
             r[kind] = {"ms": round(t["ms"], 2), "iters": t["iters"], "rel_res": t["rel_res"],
                        "rel_res_init": round(t["rel_res_init"], 4), "fallback": t["fallback"],
                        "warm_ms": round(t["warm_ms"], 3)}
         r["speedup_vs_f64"] = round(r["f64"]["ms"] / r["learned"]["ms"], 3)
+        r["mg_speedup_vs_f64"] = round(r["f64"]["ms"] / r["mg"]["ms"], 3)
+        r["learned_gain_vs_mg"] = round(r["mg"]["ms"] / r["mg_learned"]["ms"], 4)
         r["learned_gain_vs_mixed"] = round(r["mixed"]["ms"] / r["learned"]["ms"], 4)
         rows.append(r)
         p.close()
@@ -438,6 +458,7 @@ def main():
                     help="run one extra measurement alone (for profiling)")
     ap.add_argument("--copies", type=int, default=8)
     ap.add_argument("--precond", type=int, default=0, help="0 Jacobi-PCG, 1 multigrid-PCG (--only cg2d / cg3d)")
+    ap.add_argument("--solver", type=int, default=1, help="solver of the timed SIMP step: 0 Jacobi-PCG, 1 multigrid-PCG")
     ap.add_argument("--reps", type=int, default=10)
     args = ap.parse_args()
     if args.only:

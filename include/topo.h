@@ -289,6 +289,16 @@ tp_status tp_oc_update_noalloc(const double* rho, const double* dcf, const int8_
 tp_status tp_set_trace(tp_problem* p, int enable);
 tp_status tp_get_trace(tp_problem* p, long long* out);
 
+/* Launch timing of the multigrid solver's finest-level operator (profiling
+ * aid).  When enabled, every finest-level smoothing / residual launch of
+ * TP_PRECOND_MG solves is bracketed by a CUDA event pair on the problem's
+ * stream; tp_get_profile writes out[4] (host): the number of timed launches,
+ * their total device time in ms, the algorithmic bytes of one launch (the
+ * finest level's operator data, plus per case u read, b read and y written, and
+ * one scale per DOF) and the number of levels.  Enabling resets the totals. */
+tp_status tp_set_profile(tp_problem* p, int enable);
+tp_status tp_get_profile(tp_problem* p, double* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -128,6 +128,11 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     }
   }
   if (!p->mg_sc) TPCK(dalloc(&p->mg_sc, 64), "alloc");
+  if (p->profile && p->mg->ev.empty()) {
+    p->mg->ev.resize(8192);
+    for (auto& ev : p->mg->ev) TPCK(cudaEventCreate(&ev), "event");
+  }
+  p->mg->timing = p->profile;
   MgHierarchy& M = *p->mg;
   const cudaStream_t s = p->stream;
   const long long n = p->ndof;
@@ -239,6 +244,7 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
       double h[64];
       TPCK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
       TPCK(cudaStreamSynchronize(s), "sync");
+      if (M.timing && M.ev_used + 64 > (int)M.ev.size()) M.collect_timing();
       double rec[kMaxCases];
       for (int c = 0; c < nc; c++) {
         rec[c] = h[32 + c];
@@ -276,6 +282,7 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   nl++;
   TPCK(cudaEventRecord(p->ev1, s), "event");
   TPCK(cudaEventSynchronize(p->ev1), "sync");
+  if (M.timing) M.collect_timing();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, p->ev0, p->ev1);
   p->launches += nl;
@@ -420,6 +427,28 @@ tp_status tp_set_trace(tp_problem* p, int enable) {
     cudaStreamSynchronize(p->stream);
     cudaFree(p->trace);
     p->trace = nullptr;
+  }
+  return TP_OK;
+}
+
+tp_status tp_set_profile(tp_problem* p, int enable) {
+  if (!p) return TP_ERR_ARG;
+  p->profile = enable != 0;
+  if (p->mg) {
+    p->mg->timed_launches = 0;
+    p->mg->timed_ms = 0.0;
+  }
+  return TP_OK;
+}
+
+tp_status tp_get_profile(tp_problem* p, double* out) {
+  if (!p || !out) return TP_ERR_ARG;
+  out[0] = out[1] = out[2] = out[3] = 0.0;
+  if (p->mg) {
+    out[0] = (double)p->mg->timed_launches;
+    out[1] = p->mg->timed_ms;
+    out[2] = p->mg->fine_bytes();
+    out[3] = (double)p->mg->lv.size();
   }
   return TP_OK;
 }

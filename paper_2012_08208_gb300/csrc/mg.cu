@@ -502,7 +502,31 @@ bool spd_inverse(std::vector<double>& A, int n) {
 
 // ---------------------------------------------------------------------------
 
+double MgHierarchy::fine_bytes() const {
+  const MgLevel& l = lv[0];
+  const int dim = l.g.dim;
+  // operator data read once per launch (assembled blocks, or one modulus per
+  // element), then per case: u read, b read, y written; the l1 scale per DOF
+  const double op = l.S ? (double)l.g.nn * (dim == 2 ? 36 : 243) * 4.0 : (double)l.g.ne * 4.0;
+  return op + (double)l.g.nn * dim * 4.0 * (1 + 3 * nc);
+}
+
+void MgHierarchy::collect_timing() {
+  for (int k = 0; k + 1 < ev_used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess) {
+      timed_ms += ms;
+      timed_launches++;
+    }
+  }
+  ev_used = 0;
+  cudaGetLastError();
+}
+
 void MgHierarchy::release() {
+  for (auto& e : ev) cudaEventDestroy(e);
+  ev.clear();
+  ev_used = 0;
   for (auto& l : lv) {
     void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t};
     for (void* q : ptrs)
@@ -652,8 +676,15 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch) {
     return cudaGetLastError();
   }
   auto apply = [&](const float* u, const float* b, float* y, int mode) {
-    return dim == 2 ? apply_level<2>(s, l, E0, nc, u, b, y, mode, omega)
-                    : apply_level<3>(s, l, E0, nc, u, b, y, mode, omega);
+    const bool tm = timing && li == 0 && ev_used + 2 <= (int)ev.size();
+    if (tm) cudaEventRecord(ev[ev_used], s);
+    cudaError_t e = dim == 2 ? apply_level<2>(s, l, E0, nc, u, b, y, mode, omega)
+                             : apply_level<3>(s, l, E0, nc, u, b, y, mode, omega);
+    if (tm) {
+      cudaEventRecord(ev[ev_used + 1], s);
+      ev_used += 2;
+    }
+    return e;
   };
   // pre-smoothing from zero
   jacobi0_kernel<<<blocks(ndof), 256, 0, s>>>(ndof, nc, l.invd, l.b, l.x[0], omega);

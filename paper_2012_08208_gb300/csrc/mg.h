@@ -32,6 +32,14 @@ struct MgHierarchy {
   int nu = 2;               // sweeps before and after the coarse correction
   bool built = false;
   long long version = -1;   // moduli version the operators were built for
+  // optional timing of the finest level's operator launches (event pairs)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  int ev_used = 0;
+  long long timed_launches = 0;
+  double timed_ms = 0.0;
+  double fine_bytes() const;  // algorithmic bytes of one finest-level sweep launch
+  void collect_timing();      // after the stream has synchronised
 
   // Level plan for grid g0: 2:1 while possible, then the smallest common odd
   // factor, until the coarsest has <= max_coarse_dofs DOFs.  Allocates all

@@ -59,6 +59,7 @@ struct tp_problem {
   tp::MgHierarchy* mg = nullptr; // multigrid preconditioner (built on first use)
   long long E_version = 0;       // bumped whenever the moduli are recomputed
   double* mg_sc = nullptr;       // device scalars of the multigrid PCG
+  bool profile = false;          // time the multigrid finest-level launches
   int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
   double* rho_phys = nullptr;    // density-filtered densities (filter mode 1)
   double* rowsum = nullptr;      // sum_b W_ab per element (filter mode 1)

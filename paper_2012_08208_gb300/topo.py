@@ -97,6 +97,8 @@ def _load():
         "tp_oc_update_noalloc": (C.c_int, [P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double, P, P,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_get_trace": (C.c_int, [P, P]),
+        "tp_set_profile": (C.c_int, [P, C.c_int]),
+        "tp_get_profile": (C.c_int, [P, P]),
         "tpnn_create": (C.c_int, [C.c_int, C.c_int, P, P, C.POINTER(P)]),
         "tpnn_destroy": (None, [P]),
         "tpnn_last_error": (C.c_char_p, [P]),
@@ -130,7 +132,7 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
-            "tp_oc_update_noalloc", "tp_set_filter_mode", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_oc_update_noalloc", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
@@ -249,6 +251,16 @@ class Problem:
         out = np.zeros((32, 8), dtype=np.int64)
         self._check(lib.tp_get_trace(self.h, out.ctypes.data_as(C.c_void_p)))
         return out
+
+    def set_profile(self, enable=True):
+        self._check(lib.tp_set_profile(self.h, 1 if enable else 0))
+
+    def get_profile(self):
+        """(timed finest-level multigrid launches, their total ms, algorithmic
+        bytes per launch, levels)."""
+        out = np.zeros(4)
+        self._check(lib.tp_get_profile(self.h, out.ctypes.data_as(C.c_void_p)))
+        return int(out[0]), float(out[1]), float(out[2]), int(out[3])
 
     def set_fixed(self, fixed):
         a = np.ascontiguousarray(fixed, dtype=np.uint8)

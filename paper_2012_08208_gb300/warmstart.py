@@ -177,9 +177,10 @@ def energy_error(p, net, comp):
 
 def time_to_tol(p, kind, tol=1e-6, net=None, max_it=400000, drop=0.1, warm_max_rel=0.0):
     """Solve the problem's current state equation from scratch to `tol`:
-    kind 'f64' (plain FP64 PCG, u = 0), 'mixed' (u = 0) or 'learned' (mixed
+    kind 'f64' (plain FP64 PCG, u = 0), 'mixed' (u = 0), 'learned' (mixed
     PCG from the network's start, dropped for u = 0 when its true relative
-    residual exceeds warm_max_rel, 0 meaning 1).  Returns a dict of the device
+    residual exceeds warm_max_rel, 0 meaning 1), 'mg' (multigrid-preconditioned
+    CG from u = 0) or 'mg_learned' (the same from the network's start).  Returns a dict of the device
     time (ms, network included), CG iterations, initial and final true
     residuals."""
     ws_ms = 0.0
@@ -194,6 +195,14 @@ def time_to_tol(p, kind, tol=1e-6, net=None, max_it=400000, drop=0.1, warm_max_r
         alpha = float(a[0])
         o = topo.solve_opts(tol=tol, max_it=max_it, precision=topo.TP_PREC_MIXED, warm_start=topo.TP_WARM_USER,
                             update_drop=drop, warm_max_rel=warm_max_rel)
+    elif kind == "mg":
+        o = topo.solve_opts(tol=tol, max_it=max_it, precision=topo.TP_PREC_MIXED, warm_start=topo.TP_WARM_ZERO,
+                            precond=topo.TP_PRECOND_MG)
+    elif kind == "mg_learned":
+        a, ws_ms = p.warm_start_nn(net)
+        alpha = float(a[0])
+        o = topo.solve_opts(tol=tol, max_it=max_it, precision=topo.TP_PREC_MIXED, warm_start=topo.TP_WARM_USER,
+                            warm_max_rel=warm_max_rel, precond=topo.TP_PRECOND_MG)
     else:
         raise ValueError(kind)
     info = p.solve(o, check=False)
