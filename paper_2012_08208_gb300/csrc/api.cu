@@ -110,6 +110,12 @@ static int pick_zlen(const Grid& g, int resident) {
 
 tp_status tp_problem_ensure_E(tp_problem* p) { return ensure_E(p); }
 
+// Finest multigrid level: the problem's FP32 strain-form operator on all cases.
+static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, float* y) {
+  tp_problem* p = (tp_problem*)ctx;
+  return launch_matvec(s, p->g, p->C.data(), false, p->E32, p->mask, u, y, p->nc, p->zlen);
+}
+
 // CG in FP64 preconditioned by one FP32 multigrid V-cycle per iteration
 // (TP_PRECOND_MG).  Vectors in the ABI layout; the solution ends in x64.
 static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info) {
@@ -133,6 +139,8 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     for (auto& ev : p->mg->ev) TPCK(cudaEventCreate(&ev), "event");
   }
   p->mg->timing = p->profile;
+  p->mg->fine_op_fn = mg_fine_op;
+  p->mg->fine_ctx = p;
   MgHierarchy& M = *p->mg;
   const cudaStream_t s = p->stream;
   const long long n = p->ndof;

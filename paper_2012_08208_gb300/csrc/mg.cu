@@ -117,26 +117,37 @@ __global__ void stencil_kernel(Grid g, const float* __restrict__ K, const float*
   for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
     const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
     const uint8_t mk = mask[nd];
-    for (int q = 0; q < NB * DIM * DIM; q++) S[(long long)q * nn + nd] = 0.f;
-    for (int c = 0; c < NC; c++) {
-      const int ei = i - cofs(c, 0), ej = j - cofs(c, 1), ek = k - (DIM == 3 ? cofs(c, 2) : 0);
-      if (ei < 0 || ej < 0 || ek < 0 || ei >= g.ex || ej >= g.ey || ek >= g.ez) continue;
-      const long long e = ei + (long long)g.ex * (ej + (long long)g.ey * ek);
-      const float* Ke = K ? K + e * ND * ND : c_K0;
-      const float sc = K ? 1.f : E[e];
-      for (int cc = 0; cc < NC; cc++) {
-        const int dx = cofs(cc, 0) - cofs(c, 0), dy = cofs(cc, 1) - cofs(c, 1);
-        const int dz = DIM == 3 ? cofs(cc, 2) - cofs(c, 2) : 0;
-        const int nbr = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
-        const uint8_t m2 = mask[node_index(g, ei + cofs(cc, 0), ej + cofs(cc, 1), ek + (DIM == 3 ? cofs(cc, 2) : 0))];
-        for (int r = 0; r < DIM; r++) {
-          if ((mk >> r) & 1) continue;
-          for (int s2 = 0; s2 < DIM; s2++) {
-            if ((m2 >> s2) & 1) continue;
-            S[((long long)(nbr * DIM + r) * DIM + s2) * nn + nd] += sc * Ke[(c * DIM + r) * ND + cc * DIM + s2];
-          }
+    for (int nbr = 0; nbr < NB; nbr++) {  // one DIM x DIM block at a time, summed in registers
+      const int dx = nbr % 3 - 1, dy = (nbr / 3) % 3 - 1, dz = DIM == 3 ? nbr / 9 - 1 : 0;
+      float acc[DIM * DIM];
+#pragma unroll
+      for (int q = 0; q < DIM * DIM; q++) acc[q] = 0.f;
+      const int i2 = i + dx, j2 = j + dy, k2 = k + dz;
+      if (i2 >= 0 && i2 < g.nx && j2 >= 0 && j2 < g.ny && k2 >= 0 && k2 < g.nz) {
+        const uint8_t m2 = mask[node_index(g, i2, j2, k2)];
+        for (int c = 0; c < NC; c++) {  // elements holding this node as corner c ...
+          const int ei = i - cofs(c, 0), ej = j - cofs(c, 1), ek = k - (DIM == 3 ? cofs(c, 2) : 0);
+          if (ei < 0 || ej < 0 || ek < 0 || ei >= g.ex || ej >= g.ey || ek >= g.ez) continue;
+          // ... and the neighbour as corner cc
+          const int ox = cofs(c, 0) + dx, oy = cofs(c, 1) + dy, oz = (DIM == 3 ? cofs(c, 2) : 0) + dz;
+          if (ox < 0 || ox > 1 || oy < 0 || oy > 1 || oz < 0 || oz > 1) continue;
+          const int cc = h8_corner(ox, oy, DIM == 3 ? oz : 0);
+          const long long e = ei + (long long)g.ex * (ej + (long long)g.ey * ek);
+          const float* Ke = K ? K + e * ND * ND : c_K0;
+          const float sc = K ? 1.f : E[e];
+#pragma unroll
+          for (int r = 0; r < DIM; r++)
+#pragma unroll
+            for (int s2 = 0; s2 < DIM; s2++) acc[r * DIM + s2] = fmaf(sc, Ke[(c * DIM + r) * ND + cc * DIM + s2], acc[r * DIM + s2]);
         }
+#pragma unroll
+        for (int r = 0; r < DIM; r++)
+#pragma unroll
+          for (int s2 = 0; s2 < DIM; s2++)
+            if (((mk >> r) & 1) || ((m2 >> s2) & 1)) acc[r * DIM + s2] = 0.f;
       }
+#pragma unroll
+      for (int q = 0; q < DIM * DIM; q++) S[((long long)nbr * DIM * DIM + q) * nn + nd] = acc[q];
     }
   }
 }
@@ -267,17 +278,24 @@ __global__ void coarse_mask_kernel(Grid gf, Grid gc, int f, const uint8_t* __res
 __device__ __forceinline__ float w1(int o, int t, int f) { return o ? (float)t / f : 1.f - (float)t / f; }
 
 // Galerkin coarse element matrices: one CTA per coarse element, one thread per
-// entry (row a = (C, r), column b = (C', r')), children staged one at a time.
+// entry.  For each child c (fine DOFs masked), with Phi_c[n][C] the weight of
+// coarse corner C at the child's node n, in two separable stages:
+//   T = K_c (Phi_c x I),   K_E += (Phi_c x I)^T T.
 template <int DIM>
 __global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Kf, const float* __restrict__ Ef,
-                                const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc, float* __restrict__ Kc) {
+                                const float* __restrict__ K0g, const uint8_t* __restrict__ mf,
+                                const uint8_t* __restrict__ mc, float* __restrict__ Kc) {
   constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND;
   __shared__ float sK[ND * ND];
+  __shared__ float sT[ND * ND];
+  __shared__ float sK0[ND * ND];  // level-0 children: K0 staged once (divergent constant reads serialise)
+  __shared__ float sPhi[NC * NC];
   __shared__ uint8_t sM[NC];
+  const int t = threadIdx.x;  // blockDim.x == ND * ND
+  if (!Kf) sK0[t] = K0g[t];
   const long long ec = blockIdx.x;
   const int I = (int)(ec % gc.ex), J = (int)((ec / gc.ex) % gc.ey), Kz = (int)(ec / ((long long)gc.ex * gc.ey));
-  const int a = threadIdx.x / ND, b = threadIdx.x % ND;  // blockDim.x == ND * ND
-  const int Ca = a / DIM, ra = a % DIM, Cb = b / DIM, rb = b % DIM;
+  const int a = t / ND, b = t % ND;
   float acc = 0.f;
   const int nch = DIM == 2 ? f * f : f * f * f;
   for (int ch = 0; ch < nch; ch++) {
@@ -285,32 +303,55 @@ __global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict
     const int fi = f * I + cx, fj = f * J + cy, fk = DIM == 3 ? f * Kz + cz : 0;
     const long long e = fi + (long long)gf.ex * (fj + (long long)gf.ey * fk);
     __syncthreads();
-    sK[threadIdx.x] = kentry<DIM>(Kf, Ef, e, a, b);
-    if (threadIdx.x < NC) {
-      const int c = threadIdx.x;
-      sM[c] = mf[node_index(gf, fi + cofs(c, 0), fj + cofs(c, 1), fk + (DIM == 3 ? cofs(c, 2) : 0))];
+    if (t < NC) sM[t] = mf[node_index(gf, fi + cofs(t, 0), fj + cofs(t, 1), fk + (DIM == 3 ? cofs(t, 2) : 0))];
+    if (t < NC * NC) {
+      const int n = t / NC, C = t % NC;
+      float w = w1(cofs(C, 0), cx + cofs(n, 0), f) * w1(cofs(C, 1), cy + cofs(n, 1), f);
+      if (DIM == 3) w *= w1(cofs(C, 2), cz + cofs(n, 2), f);
+      sPhi[t] = w;
     }
     __syncthreads();
-    for (int n1 = 0; n1 < NC; n1++) {
-      if ((sM[n1] >> ra) & 1) continue;
-      const int t1x = cx + cofs(n1, 0), t1y = cy + cofs(n1, 1), t1z = cz + (DIM == 3 ? cofs(n1, 2) : 0);
-      float pa = w1(cofs(Ca, 0), t1x, f) * w1(cofs(Ca, 1), t1y, f);
-      if (DIM == 3) pa *= w1(cofs(Ca, 2), t1z, f);
-      if (pa == 0.f) continue;
-      for (int n2 = 0; n2 < NC; n2++) {
-        if ((sM[n2] >> rb) & 1) continue;
-        const int t2x = cx + cofs(n2, 0), t2y = cy + cofs(n2, 1), t2z = cz + (DIM == 3 ? cofs(n2, 2) : 0);
-        float pb = w1(cofs(Cb, 0), t2x, f) * w1(cofs(Cb, 1), t2y, f);
-        if (DIM == 3) pb *= w1(cofs(Cb, 2), t2z, f);
-        acc = fmaf(pa * pb, sK[(n1 * DIM + ra) * ND + n2 * DIM + rb], acc);
-      }
+    const bool fa = (sM[a / DIM] >> (a % DIM)) & 1, fb = (sM[b / DIM] >> (b % DIM)) & 1;
+    sK[t] = (fa || fb) ? 0.f : (Kf ? Kf[e * ND * ND + t] : Ef[e] * sK0[t]);
+    __syncthreads();
+    {  // T[a][(C, s)] = sum_n K[a][(n, s)] Phi[n][C]
+      const int C = b / DIM, s2 = b % DIM;
+      float v = 0.f;
+#pragma unroll
+      for (int n = 0; n < NC; n++) v = fmaf(sK[a * ND + n * DIM + s2], sPhi[n * NC + C], v);
+      sT[t] = v;
+    }
+    __syncthreads();
+    {  // K_E[(C1, r)][b] += sum_n Phi[n][C1] T[(n, r)][b]
+      const int C1 = a / DIM, r = a % DIM;
+#pragma unroll
+      for (int n = 0; n < NC; n++) acc = fmaf(sPhi[n * NC + C1], sT[(n * DIM + r) * ND + b], acc);
     }
   }
   // zero rows and columns of fixed coarse DOFs
+  const int Ca = a / DIM, ra = a % DIM, Cb = b / DIM, rb = b % DIM;
   const uint8_t ma = mc[node_index(gc, I + cofs(Ca, 0), J + cofs(Ca, 1), Kz + (DIM == 3 ? cofs(Ca, 2) : 0))];
   const uint8_t mb = mc[node_index(gc, I + cofs(Cb, 0), J + cofs(Cb, 1), Kz + (DIM == 3 ? cofs(Cb, 2) : 0))];
   if (((ma >> ra) & 1) || ((mb >> rb) & 1)) acc = 0.f;
-  Kc[ec * ND * ND + threadIdx.x] = acc;
+  Kc[ec * ND * ND + t] = acc;
+}
+
+// Smoothing / residual from a precomputed t = A u (finest level):
+//   mode 1: y = u + omega D^-1 (b - t),  mode 2: y = b - t;  0 on fixed DOFs.
+__global__ void update_from_au_kernel(long long n, int dim, int ncopies, const uint8_t* __restrict__ mask,
+                                      const float* __restrict__ invd, const float* __restrict__ u,
+                                      const float* __restrict__ b, const float* __restrict__ t, float* __restrict__ y,
+                                      int mode, float omega) {
+  const int nn = (int)n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    const int node = i / dim, comp = i - node * dim;
+    const bool fx = (mask[node] >> comp) & 1;
+    const float w = omega * invd[i];
+    for (int c = 0; c < ncopies; c++) {
+      const long long k = (long long)c * nn + i;
+      y[k] = fx ? 0.f : (mode == 1 ? u[k] + w * (b[k] - t[k]) : b[k] - t[k]);
+    }
+  }
 }
 
 // b_c = P^T r_f for f = 2 (3^dim fine neighbours): one thread per coarse node.
@@ -507,8 +548,10 @@ double MgHierarchy::fine_bytes() const {
   const int dim = l.g.dim;
   // operator data read once per launch (assembled blocks, or one modulus per
   // element), then per case: u read, b read, y written; the l1 scale per DOF
-  const double op = l.S ? (double)l.g.nn * (dim == 2 ? 36 : 243) * 4.0 : (double)l.g.ne * 4.0;
-  return op + (double)l.g.nn * dim * 4.0 * (1 + 3 * nc);
+  // finest level: the strain-form operator (moduli once per launch; u read and
+  // t written per case) and the update (u, b, t read, y written per case; the
+  // l1 scale once)
+  return (double)l.g.ne * 4.0 + (double)l.g.nn * dim * 4.0 * (1 + 6 * nc);
 }
 
 void MgHierarchy::collect_timing() {
@@ -528,13 +571,15 @@ void MgHierarchy::release() {
   ev.clear();
   ev_used = 0;
   for (auto& l : lv) {
-    void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t};
+    void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t, l.t2};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
   lv.clear();
   if (cinv) cudaFree(cinv);
   cinv = nullptr;
+  if (K0d) cudaFree(K0d);
+  K0d = nullptr;
   built = false;
 }
 
@@ -565,7 +610,8 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
       if (e == cudaSuccess) e = cudaMalloc((void**)&l.mask, l.g.nn);
       l.mask_own = true;
     }
-    if (e == cudaSuccess && (g0.dim == 2 || i > 0)) {
+    if (e == cudaSuccess && i == 0) e = cudaMalloc((void**)&l.t2, nc * ndof * sizeof(float));
+    if (e == cudaSuccess && i > 0) {
       const long long nb = g0.dim == 2 ? 9 * 4 : 27 * 9;
       e = cudaMalloc((void**)&l.S, l.g.nn * nb * sizeof(float));
     }
@@ -584,6 +630,8 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
   std::vector<float> k0f(nd * nd);
   for (int i = 0; i < nd * nd; i++) k0f[i] = (float)K0[i];
   cudaError_t e = cudaMemcpyToSymbolAsync(c_K0, k0f.data(), nd * nd * sizeof(float), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !K0d) e = cudaMalloc((void**)&K0d, nd * nd * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(K0d, k0f.data(), nd * nd * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;
   E0 = E32;
   int nl = 0;
@@ -593,9 +641,11 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
       const MgLevel& fl = lv[i - 1];
       coarse_mask_kernel<<<blocks(l.g.nn), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, l.mask);
       if (dim == 2)
-        galerkin_kernel<2><<<(unsigned)l.g.ne, 64, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, fl.mask, l.mask, l.K);
+        galerkin_kernel<2><<<(unsigned)l.g.ne, 64, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask,
+                                                            l.mask, l.K);
       else
-        galerkin_kernel<3><<<(unsigned)l.g.ne, 576, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, fl.mask, l.mask, l.K);
+        galerkin_kernel<3><<<(unsigned)l.g.ne, 576, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask,
+                                                             l.mask, l.K);
       nl += 2;
     }
     if (l.S) {
@@ -678,8 +728,18 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch) {
   auto apply = [&](const float* u, const float* b, float* y, int mode) {
     const bool tm = timing && li == 0 && ev_used + 2 <= (int)ev.size();
     if (tm) cudaEventRecord(ev[ev_used], s);
-    cudaError_t e = dim == 2 ? apply_level<2>(s, l, E0, nc, u, b, y, mode, omega)
-                             : apply_level<3>(s, l, E0, nc, u, b, y, mode, omega);
+    cudaError_t e;
+    if (li == 0 && fine_op_fn) {  // finest level: the strain-form FP32 operator, then the update
+      e = fine_op(s, u, l.t2);
+      if (e == cudaSuccess) {
+        update_from_au_kernel<<<blocks(ndof), 256, 0, s>>>(ndof, dim, nc, l.mask, l.invd, u, b, l.t2, y, mode, omega);
+        e = cudaGetLastError();
+      }
+      (*nlaunch)++;
+    } else {
+      e = dim == 2 ? apply_level<2>(s, l, E0, nc, u, b, y, mode, omega)
+                   : apply_level<3>(s, l, E0, nc, u, b, y, mode, omega);
+    }
     if (tm) {
       cudaEventRecord(ev[ev_used + 1], s);
       ev_used += 2;

@@ -21,13 +21,19 @@ struct MgLevel {
   float* x[2] = {nullptr, nullptr};  // iterates [case][n_nodes * dim]
   float* b = nullptr;       // right-hand side
   float* t = nullptr;       // residual scratch
+  float* t2 = nullptr;      // A u on the finest level
 };
 
 struct MgHierarchy {
   std::vector<MgLevel> lv;
   int nc = 1, cn = 0;       // cases, DOFs of the coarsest level
   float* cinv = nullptr;    // coarsest dense inverse [cn][cn]
+  float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
   const float* E0 = nullptr;
+  // finest-level operator y = A u for all cases (the library's FP32 operator)
+  cudaError_t (*fine_op_fn)(void* ctx, cudaStream_t s, const float* u, float* y) = nullptr;
+  void* fine_ctx = nullptr;
+  cudaError_t fine_op(cudaStream_t s, const float* u, float* y) const { return fine_op_fn(fine_ctx, s, u, y); }
   float omega = 1.6f;       // l1-Jacobi weight (convergent for any weight below 2)
   int nu = 2;               // sweeps before and after the coarse correction
   bool built = false;

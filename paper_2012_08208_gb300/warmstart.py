@@ -185,6 +185,9 @@ def time_to_tol(p, kind, tol=1e-6, net=None, max_it=400000, drop=0.1, warm_max_r
     residuals."""
     ws_ms = 0.0
     alpha = None
+    # the same density again: every arm pays its setup (moduli, diagonals, and
+    # the multigrid hierarchy) inside its timed solve
+    p.set_density(p.get(topo.TP_RHO))
     if kind == "f64":
         o = topo.solve_opts(tol=tol, max_it=max_it, precision=topo.TP_PREC_F64, warm_start=topo.TP_WARM_ZERO)
     elif kind == "mixed":
