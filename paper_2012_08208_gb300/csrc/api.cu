@@ -48,7 +48,6 @@ void free_all(tp_problem* p) {
     if (q) cudaFree(q);
   delete p->mg;
   p->mg = nullptr;
-  if (p->mg_sc) cudaFree(p->mg_sc);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
   delete p->flt;
@@ -111,13 +110,22 @@ static int pick_zlen(const Grid& g, int resident) {
 tp_status tp_problem_ensure_E(tp_problem* p) { return ensure_E(p); }
 
 // Finest multigrid level: the problem's FP32 strain-form operator on all cases.
-static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, float* y) {
+static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, const float* b, const float* invd, float* y,
+                              int mode, float omega, const int* stop) {
   tp_problem* p = (tp_problem*)ctx;
-  return launch_matvec(s, p->g, p->C.data(), false, p->E32, p->mask, u, y, p->nc, p->zlen);
+  return launch_mg_sweep(s, p->g, p->C.data(), p->E32, p->mask, invd, u, b, y, p->nc, p->zlen, mode, omega, stop);
 }
 
 // CG in FP64 preconditioned by one FP32 multigrid V-cycle per iteration
 // (TP_PRECOND_MG).  Vectors in the ABI layout; the solution ends in x64.
+//
+// The iterations run as replays of a CUDA graph of MgHierarchy::kGraphIters
+// iterations.  The scalar kernel at the end of each iteration evaluates the
+// stopping rule on the device and sets a stop flag; every later kernel of the
+// segment then returns at once, so the host synchronises once per replay
+// instead of once per iteration.  Segments end at the tolerance or when the
+// FP32 operator's error may dominate the recurrence; each is followed by an
+// FP64 true residual (restart).
 static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info) {
   tp_status st = ensure_E(p);
   if (st != TP_OK) return st;
@@ -133,25 +141,27 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
       return cuda_fail(p, e, "multigrid allocation");
     }
   }
-  if (!p->mg_sc) TPCK(dalloc(&p->mg_sc, 64), "alloc");
-  if (p->profile && p->mg->ev.empty()) {
-    p->mg->ev.resize(8192);
-    for (auto& ev : p->mg->ev) TPCK(cudaEventCreate(&ev), "event");
-  }
-  p->mg->timing = p->profile;
-  p->mg->fine_op_fn = mg_fine_op;
-  p->mg->fine_ctx = p;
   MgHierarchy& M = *p->mg;
+  const int kIt = MgHierarchy::kGraphIters;
+  if (p->profile && M.ev.empty()) {
+    M.ev.resize(2 * 2 * M.nu * kIt);  // an event pair per finest-level sweep of one graph
+    for (auto& ev : M.ev) TPCK(cudaEventCreate(&ev), "event");
+  }
+  M.timing = p->profile;
+  M.fine_op_fn = mg_fine_op;
+  M.fine_ctx = p;
   const cudaStream_t s = p->stream;
   const long long n = p->ndof;
   const int nc = p->nc;
   double* x = (double*)p->w[0];
   double* r = (double*)p->w[1];
-  double* z = (double*)p->w[2];
   double* pp = (double*)p->w[3];
   double* q = (double*)p->w[4];
   double* fA = (double*)p->w[5];
-  double* sc = p->mg_sc;
+  MgCtl* ctl = M.ctl;
+  double* sc = ctl->sc;  // device address of the scalars
+  const int* stop = &ctl->stop;
+  MgLevel& l0 = M.lv[0];
   int nl = 0;
   TPCK(cudaEventRecord(p->ev0, s), "event");
   if (M.version != p->E_version) {
@@ -164,39 +174,58 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   else
     TPCK(launch_to_abi(s, p->x64, x, p->nn, p->dim, nc), "layout kernel");
   nl += 2;
-  auto matvec = [&](const double* u, double* y) -> cudaError_t {  // FP64 operator
-    nl++;
-    return launch_matvec(s, p->g, p->C.data(), true, p->E64, p->mask, u, y, nc, p->zlen);
-  };
-  // Inner operator: the FP32 strain-form operator on FP32 copies (the outer
-  // restarts recompute the true residual with the FP64 operator).
-  float* u32 = M.lv[0].t;
-  float* y32 = M.lv[0].x[1];
-  auto matvec32 = [&](const double* u, double* y) -> cudaError_t {
-    cudaError_t e = to_f32(s, (long long)nc * n, u, u32);
-    if (e == cudaSuccess) e = launch_matvec(s, p->g, p->C.data(), false, p->E32, p->mask, u32, y32, nc, p->zlen);
-    if (e == cudaSuccess) e = to_f64(s, (long long)nc * n, y32, y);
-    nl += 3;
-    return e;
-  };
-  auto true_rr = [&](double* rr_out) -> tp_status {  // r = f - K x, rr per case (synchronises)
-    TPCK(matvec(x, q), "matvec");
+  auto true_rr = [&](double* rr_out) -> tp_status {  // r = f - K x with the FP64 operator, rr per case (synchronises)
+    TPCK(launch_matvec(s, p->g, p->C.data(), true, p->E64, p->mask, x, q, nc, p->zlen), "matvec");
     TPCK(pcg_residual(s, n, nc, fA, q, p->mask, p->dim, r), "residual kernel");
     int nb = 0;
     TPCK(pcg_dot2(s, n, nc, r, r, r, r, p->part, &nb), "dot kernel");
     TPCK(pcg_scalars(s, nb, nc, p->part, 2, sc), "scalar kernel");
-    nl += 3;
+    nl += 4;
     double h[64];
     TPCK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
     TPCK(cudaStreamSynchronize(s), "sync");
     for (int c = 0; c < nc; c++) rr_out[c] = h[32 + c];
     return TP_OK;
   };
-  auto precondition = [&]() -> tp_status {  // z = V(r)
-    TPCK(to_f32(s, (long long)nc * n, r, M.lv[0].b), "convert");
-    TPCK(M.vcycle(s, 0, &nl), "v-cycle");
-    TPCK(to_f64(s, (long long)nc * n, M.lv[0].x[0], z), "convert");
-    nl += 2;
+  // One PCG iteration: q = K p, alpha, x and r, z = V(r), beta and the stopping
+  // rule, p.  FP32 operator on an FP32 copy of p unless u64.
+  float* z32 = nullptr;
+  auto issue_iter = [&](cudaStream_t cs, bool u64, int* nlk) -> cudaError_t {
+    cudaError_t e = u64 ? launch_matvec(cs, p->g, p->C.data(), true, p->E64, p->mask, pp, q, nc, p->zlen, stop)
+                        : launch_matvec(cs, p->g, p->C.data(), false, p->E32, p->mask, M.p32, M.q32, nc, p->zlen, stop);
+    const void* qv = u64 ? (const void*)q : (const void*)M.q32;
+    if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, pp, qv, !u64, nullptr, nullptr, p->part, ctl, 0, nullptr);
+    if (e == cudaSuccess) e = mg_update_xr(cs, n, nc, ctl, x, pp, r, qv, !u64, l0.b, l0.x[0], l0.invd, M.omega);
+    *nlk += 3;
+    if (e == cudaSuccess) e = M.vcycle(cs, 0, nlk, stop, &z32);
+    if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, r, z32, true, r, r, p->part, ctl, 1, nullptr);
+    if (e == cudaSuccess) e = mg_update_p(cs, n, nc, ctl, pp, M.p32, z32);
+    *nlk += 2;
+    return e;
+  };
+  auto graph = [&](bool u64) -> tp_status {
+    const int gi = u64 ? 1 : 0, gt = M.timing ? 1 : 0;
+    if (M.gx[gi][gt]) return TP_OK;
+    // captured on a private stream (the problem's stream may be the legacy
+    // default stream, which cannot be captured), replayed on the problem's
+    if (!M.cap) TPCK(cudaStreamCreateWithFlags(&M.cap, cudaStreamNonBlocking), "stream");
+    TPCK(cudaStreamBeginCapture(M.cap, cudaStreamCaptureModeRelaxed), "graph capture");
+    M.capture_events = M.timing;
+    if (M.timing) M.ev_used = 0;
+    int nlk = 0;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kIt && e == cudaSuccess; k++) e = issue_iter(M.cap, u64, &nlk);
+    M.capture_events = false;
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(M.cap, &gr);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&M.gx[gi][gt], gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      M.gx[gi][gt] = nullptr;
+      return cuda_fail(p, e, "multigrid PCG graph");
+    }
+    M.gx_launches[gi][gt] = nlk;
     return TP_OK;
   };
   double rr[kMaxCases] = {}, rel0[kMaxCases] = {};
@@ -213,76 +242,50 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
       if (st != TP_OK) return st;
     }
   }
-  auto done = [&](const double* v, double margin) {
+  auto done = [&](const double* v) {
     for (int c = 0; c < nc; c++)
-      if (!(v[c] <= margin * margin * opts->tol * opts->tol * p->ff[c])) return false;
+      if (!(v[c] <= opts->tol * opts->tol * p->ff[c])) return false;
     return true;
   };
   int it = 0, restarts = 0;
-  bool conv = done(rr, 1.0), brk = false;
+  bool conv = done(rr), brk = false;
   // FP32 inner operator unless FP64 was asked for, or until a restart cycle
-  // gains less than 10x (the FP32 operator's error limits the refinement when
+  // gains less than 100x (the FP32 operator's error limits the refinement when
   // eps32 * cond(K) is not small)
   bool use64 = opts->precision == TP_PREC_F64;
   while (!conv && it < opts->max_it && !brk) {
-    // (re)start from the current residual
-    st = precondition();
-    if (st != TP_OK) return st;
-    int nb = 0;
-    TPCK(pcg_dot2(s, n, nc, r, z, r, r, p->part, &nb), "dot kernel");
-    TPCK(pcg_scalars(s, nb, nc, p->part, 2, sc), "scalar kernel");
-    TPCK(cudaMemcpyAsync(pp, z, (size_t)nc * n * sizeof(double), cudaMemcpyDeviceToDevice, s), "copy");
+    // segment start from the current residual: z = V(r), p = z
+    TPCK(mg_seg_init(s, ctl, nc, opts->tol * opts->tol, p->ff, opts->max_it - it, use64 ? 1 : 0), "control kernel");
+    TPCK(mg_prep(s, n, nc, r, l0.b, l0.x[0], l0.invd, M.omega), "convert kernel");
     nl += 2;
-    double rr_start[kMaxCases], best = 0.0;
-    for (int c = 0; c < nc; c++) rr_start[c] = rr[c];
-    int best_it = it;
-    while (it < opts->max_it) {
-      if (use64) TPCK(matvec(pp, q), "matvec");
-      else TPCK(matvec32(pp, q), "matvec");
-      TPCK(pcg_dot2(s, n, nc, pp, q, nullptr, nullptr, p->part, &nb), "dot kernel");
-      TPCK(pcg_scalars(s, nb, nc, p->part, 0, sc), "scalar kernel");
-      TPCK(pcg_update_xr(s, n, nc, sc, x, pp, r, q), "update kernel");
-      nl += 3;
-      st = precondition();
-      if (st != TP_OK) return st;
-      TPCK(pcg_dot2(s, n, nc, r, z, r, r, p->part, &nb), "dot kernel");
-      TPCK(pcg_scalars(s, nb, nc, p->part, 1, sc), "scalar kernel");
-      nl += 2;
-      it++;
-      double h[64];
-      TPCK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
+    TPCK(M.vcycle(s, 0, &nl, nullptr, &z32), "v-cycle");
+    TPCK(mg_dotscal(s, n, nc, r, z32, true, r, r, p->part, ctl, 2, nullptr), "dot kernel");
+    TPCK(mg_update_p(s, n, nc, ctl, pp, M.p32, z32), "update kernel");
+    nl += 2;
+    st = graph(use64);
+    if (st != TP_OK) return st;
+    const int gi = use64 ? 1 : 0, gt = M.timing ? 1 : 0;
+    int seg_it = 0;
+    for (;;) {
+      TPCK(cudaGraphLaunch(M.gx[gi][gt], s), "graph launch");
+      nl += M.gx_launches[gi][gt];
+      TPCK(cudaMemcpyAsync(M.ctl_h, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s), "copy");
       TPCK(cudaStreamSynchronize(s), "sync");
-      if (M.timing && M.ev_used + 64 > (int)M.ev.size()) M.collect_timing();
-      double rec[kMaxCases];
-      for (int c = 0; c < nc; c++) {
-        rec[c] = h[32 + c];
-        if (!std::isfinite(rec[c]) || !(h[24 + c] > 0.0)) brk = true;
-      }
-      // stop at the tolerance, or when the FP32 operator's error may dominate
-      // the recurrence (1e-5 of the restart residual): then restart with the
-      // FP64 true residual
-      bool inner = !use64;
-      double worst = 0.0;
-      for (int c = 0; c < nc; c++) {
-        inner &= rec[c] <= 1e-10 * rr_start[c];
-        worst = std::max(worst, rec[c] / p->ff[c]);
-      }
-      // stagnation: no halving of the worst recurrence residual in 50 iterations
-      if (best == 0.0 || worst < 0.25 * best) {
-        best = worst;
-        best_it = it;
-      }
-      const bool stalled = it - best_it >= 50;
-      if (brk || done(rec, 0.5) || inner || stalled) break;
-      TPCK(pcg_update_p(s, n, nc, sc, pp, z), "update kernel");
-      nl++;
+      const int now = M.ctl_h->it;
+      if (M.timing) M.collect_timing((now - seg_it) * 2 * M.nu);
+      const bool advanced = now > seg_it;
+      seg_it = now;
+      if (M.ctl_h->stop) break;
+      if (!advanced) return fail(p, TP_ERR_CUDA, "multigrid PCG graph made no progress");
     }
+    it += seg_it;
+    brk = (M.ctl_h->reason & MG_STOP_BREAK) != 0;
     double before = 0.0, after = 0.0;
     for (int c = 0; c < nc; c++) before = std::max(before, rr[c] / p->ff[c]);
     st = true_rr(rr);
     if (st != TP_OK) return st;
     for (int c = 0; c < nc; c++) after = std::max(after, rr[c] / p->ff[c]);
-    conv = done(rr, 1.0);
+    conv = done(rr);
     if (!conv && !(after < 1e-2 * before)) use64 = true;
     if (!conv && ++restarts > 12) break;
   }
@@ -290,7 +293,6 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   nl++;
   TPCK(cudaEventRecord(p->ev1, s), "event");
   TPCK(cudaEventSynchronize(p->ev1), "sync");
-  if (M.timing) M.collect_timing();
   float ms = 0.f;
   cudaEventElapsedTime(&ms, p->ev0, p->ev1);
   p->launches += nl;

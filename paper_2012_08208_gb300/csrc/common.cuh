@@ -25,6 +25,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
+// Stop flag of a graph-captured solver segment: a kernel whose flag is set
+// returns at once (the flag changes only between kernels of the stream).
+__device__ __forceinline__ bool halted(const int* stop) { return stop != nullptr && *stop != 0; }
 // Hint: bring the line holding p into L2 (no register result).
 __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));

@@ -112,12 +112,14 @@ struct MvArgs {
   const T* u;
   T* y;
   long long stride;
+  const int* stop;  // optional: return at once when set
   CMat<DIM, T> C;
 };
 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     matvec_kernel(const __grid_constant__ MvArgs<DIM, T> a) {
+  if (halted(a.stop)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* u = a.u + blockIdx.y * a.stride;
   T* y = a.y + blockIdx.y * a.stride;
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
 
 template <int DIM, typename T>
 static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, const void* E,
-                               const uint8_t* mask, const void* u, void* y, int ncopies, int zlen) {
+                               const uint8_t* mask, const void* u, void* y, int ncopies, int zlen, const int* stop) {
   using Op = TileOp<DIM, T>;
   MvArgs<DIM, T> a;
   a.g = g;
@@ -145,6 +147,7 @@ static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, c
   a.u = (const T*)u;
   a.y = (T*)y;
   a.stride = g.nn * DIM;
+  a.stop = stop;
   fill_c<DIM, T>(a.C, C);
   const size_t smem = Op::smem_bytes();
   auto kern = matvec_kernel<DIM, T>;
@@ -155,12 +158,96 @@ static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, c
 }
 
 cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f64, const void* E,
-                          const uint8_t* mask, const void* u, void* y, int ncopies, int zlen) {
+                          const uint8_t* mask, const void* u, void* y, int ncopies, int zlen, const int* stop) {
   if (g.dim == 2)
-    return f64 ? matvec_impl<2, double>(s, g, C, E, mask, u, y, ncopies, zlen)
-               : matvec_impl<2, float>(s, g, C, E, mask, u, y, ncopies, zlen);
-  return f64 ? matvec_impl<3, double>(s, g, C, E, mask, u, y, ncopies, zlen)
-             : matvec_impl<3, float>(s, g, C, E, mask, u, y, ncopies, zlen);
+    return f64 ? matvec_impl<2, double>(s, g, C, E, mask, u, y, ncopies, zlen, stop)
+               : matvec_impl<2, float>(s, g, C, E, mask, u, y, ncopies, zlen, stop);
+  return f64 ? matvec_impl<3, double>(s, g, C, E, mask, u, y, ncopies, zlen, stop)
+             : matvec_impl<3, float>(s, g, C, E, mask, u, y, ncopies, zlen, stop);
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid finest-level sweep on the FP32 strain-form operator, one pass per
+// case (blockIdx.y):
+//   mode 1: y = u + omega D^-1 (b - K u)   (l1-Jacobi smoothing sweep)
+//   mode 2: y = b - K u                    (residual)
+// K u with the fixed entries of u read as 0; y = 0 on fixed DOFs.  The
+// operator value never leaves registers, so a sweep reads u, b and the l1
+// scale once and writes y once.
+
+template <int DIM>
+struct SweepArgs {
+  Grid g;
+  TileMapG tm;
+  const float* E;
+  const uint8_t* mask;
+  const float* invd;
+  const float* u;
+  const float* b;
+  float* y;
+  long long stride;
+  const int* stop;
+  int mode;
+  float omega;
+  CMat<DIM, float> C;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(TileOp<DIM, float>::THREADS)
+    mg_sweep_kernel(const __grid_constant__ SweepArgs<DIM> a) {
+  if (halted(a.stop)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const float* u = a.u + blockIdx.y * a.stride;
+  const float* b = a.b + blockIdx.y * a.stride;
+  float* y = a.y + blockIdx.y * a.stride;
+  TileOp<DIM, float>::template apply<1>(
+      a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1,
+      [&](long long node, int comp, bool) -> float {
+        return ((a.mask[node] >> comp) & 1) ? 0.f : u[node * DIM + comp];
+      },
+      [&](long long node, int, const float(&kv)[DIM], const float(&us)[DIM]) {
+        const uint8_t mk = a.mask[node];
+#pragma unroll
+        for (int r = 0; r < DIM; r++) {
+          const long long i = node * DIM + r;
+          const float res = b[i] - kv[r];
+          y[i] = ((mk >> r) & 1) ? 0.f : (a.mode == 1 ? us[r] + a.omega * a.invd[i] * res : res);
+        }
+      });
+}
+
+template <int DIM>
+static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
+                              const float* invd, const float* u, const float* b, float* y, int ncopies, int zlen,
+                              int mode, float omega, const int* stop) {
+  using Op = TileOp<DIM, float>;
+  SweepArgs<DIM> a;
+  a.g = g;
+  a.tm = Op::map(g, zlen);
+  a.E = E;
+  a.mask = mask;
+  a.invd = invd;
+  a.u = u;
+  a.b = b;
+  a.y = y;
+  a.stride = g.nn * DIM;
+  a.stop = stop;
+  a.mode = mode;
+  a.omega = omega;
+  fill_c<DIM, float>(a.C, C);
+  const size_t smem = Op::smem_bytes();
+  auto kern = mg_sweep_kernel<DIM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(a.tm.ntiles, ncopies), Op::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mg_sweep(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
+                            const float* invd, const float* u, const float* b, float* y, int ncopies, int zlen,
+                            int mode, float omega, const int* stop) {
+  return g.dim == 2 ? sweep_impl<2>(s, g, C, E, mask, invd, u, b, y, ncopies, zlen, mode, omega, stop)
+                    : sweep_impl<3>(s, g, C, E, mask, invd, u, b, y, ncopies, zlen, mode, omega, stop);
 }
 
 // ---------------------------------------------------------------------------

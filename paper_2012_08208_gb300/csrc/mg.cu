@@ -42,69 +42,6 @@ __device__ __forceinline__ float kentry(const float* K, const float* E, long lon
   return K ? K[e * ND * ND + a * ND + b] : E[e] * c_K0[a * ND + b];
 }
 
-// y = A u on one level (node-centric, fixed DOFs read as 0 and mapped by the
-// identity), optionally fused into a damped-Jacobi sweep:
-//   mode 0: y = A u
-//   mode 1: y = u + omega D^-1 (b - A u)     (smoothing sweep)
-//   mode 2: y = b - A u                       (residual)
-// One thread per node and case (blockIdx.y = case).
-template <int DIM>
-__global__ void apply_kernel(Grid g, const float* __restrict__ K, const float* __restrict__ E,
-                             const uint8_t* __restrict__ mask, const float* __restrict__ invd,
-                             const float* __restrict__ u, const float* __restrict__ b, float* __restrict__ y,
-                             int mode, float omega) {
-  constexpr int NC = MgC<DIM>::NC;
-  const long long ndof = g.nn * DIM;
-  const float* uc = u + blockIdx.y * ndof;
-  const float* bc = b ? b + blockIdx.y * ndof : nullptr;
-  float* yc = y + blockIdx.y * ndof;
-  const int nn = (int)g.nn, nxy = g.nx * g.ny;
-  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
-    const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
-    const uint8_t mk = mask[nd];
-    float acc[DIM];
-#pragma unroll
-    for (int r = 0; r < DIM; r++) acc[r] = 0.f;
-#pragma unroll
-    for (int c = 0; c < NC; c++) {  // this node is corner c of element (i - cx, j - cy, k - cz)
-      const int ei = i - cofs(c, 0), ej = j - cofs(c, 1), ek = k - (DIM == 3 ? cofs(c, 2) : 0);
-      if (ei < 0 || ej < 0 || ek < 0 || ei >= g.ex || ej >= g.ey || ek >= g.ez) continue;
-      const long long e = ei + (long long)g.ex * (ej + (long long)g.ey * ek);
-      constexpr int ND = MgC<DIM>::ND;
-      const float* Ke = K ? K + e * ND * ND : c_K0;  // level 0: E_e K0
-      float part[DIM];
-#pragma unroll
-      for (int r = 0; r < DIM; r++) part[r] = 0.f;
-#pragma unroll
-      for (int cc = 0; cc < NC; cc++) {
-        const long long n2 = node_index(g, ei + cofs(cc, 0), ej + cofs(cc, 1), ek + (DIM == 3 ? cofs(cc, 2) : 0));
-        const uint8_t m2 = mask[n2];
-#pragma unroll
-        for (int s = 0; s < DIM; s++) {
-          if ((m2 >> s) & 1) continue;
-          const float v = uc[n2 * DIM + s];
-#pragma unroll
-          for (int r = 0; r < DIM; r++) part[r] = fmaf(Ke[(c * DIM + r) * ND + cc * DIM + s], v, part[r]);
-        }
-      }
-      const float sc = K ? 1.f : E[e];
-#pragma unroll
-      for (int r = 0; r < DIM; r++) acc[r] = fmaf(sc, part[r], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < DIM; r++) {
-      const long long idx = nd * DIM + r;
-      const bool fx = (mk >> r) & 1;
-      const float au = fx ? uc[idx] : acc[r];
-      float out;
-      if (mode == 0) out = au;
-      else if (mode == 1) out = fx ? 0.f : uc[idx] + omega * invd[idx] * (bc[idx] - au);
-      else out = fx ? 0.f : bc[idx] - au;
-      yc[idx] = out;
-    }
-  }
-}
-
 // Assembled form of a level: per node, the DIM x DIM coupling block to each of
 // its 3^DIM neighbours, S[((nbr * DIM + r) * DIM + s) * n_nodes + node]
 // (structure of arrays: one coalesced load per entry), with the rows and
@@ -152,15 +89,21 @@ __global__ void stencil_kernel(Grid g, const float* __restrict__ K, const float*
   }
 }
 
-// apply_kernel on the assembled form (same modes).
+// y = A u on a coarse level from its assembled form (node-centric; fixed DOFs
+// read as 0 and mapped by the identity), fused into an l1-Jacobi sweep:
+//   mode 1: y = u + omega D^-1 (b - A u)     (smoothing sweep)
+//   mode 2: y = b - A u                       (residual)
+// 0 on fixed DOFs.  One thread per node and case (blockIdx.y = case).
 template <int DIM>
 __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
                                      const float* __restrict__ invd, const float* __restrict__ u,
-                                     const float* __restrict__ b, float* __restrict__ y, int mode, float omega) {
+                                     const float* __restrict__ b, float* __restrict__ y, int mode, float omega,
+                                     const int* __restrict__ stop) {
+  if (halted(stop)) return;
   const int nn = (int)g.nn, nxy = g.nx * g.ny;
   const long long ndof = (long long)nn * DIM;
   const float* uc = u + blockIdx.y * ndof;
-  const float* bc = b ? b + blockIdx.y * ndof : nullptr;
+  const float* bc = b + blockIdx.y * ndof;
   float* yc = y + blockIdx.y * ndof;
   for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
     const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
@@ -191,13 +134,8 @@ __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const 
 #pragma unroll
     for (int r = 0; r < DIM; r++) {
       const long long idx = (long long)nd * DIM + r;
-      const bool fx = (mk >> r) & 1;
-      const float au = fx ? uc[idx] : acc[r];
-      float out;
-      if (mode == 0) out = au;
-      else if (mode == 1) out = fx ? 0.f : uc[idx] + omega * invd[idx] * (bc[idx] - au);
-      else out = fx ? 0.f : bc[idx] - au;
-      yc[idx] = out;
+      const float res = bc[idx] - acc[r];
+      yc[idx] = ((mk >> r) & 1) ? 0.f : (mode == 1 ? uc[idx] + omega * invd[idx] * res : res);
     }
   }
 }
@@ -221,19 +159,10 @@ __global__ void diag_stencil_kernel(Grid g, const float* __restrict__ S, const u
   }
 }
 
-// First sweep from x = 0: y = omega D^-1 b.
-__global__ void jacobi0_kernel(long long n, int ncopies, const float* __restrict__ invd, const float* __restrict__ b,
-                               float* __restrict__ y, float omega) {
-  const int nn = (int)n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
-    const float w = omega * invd[i];
-    for (int c = 0; c < ncopies; c++) y[(long long)c * nn + i] = w * b[(long long)c * nn + i];
-  }
-}
-
 // Inverse l1 row sums of a level, 1 / sum_j |A_ij| (1 on fixed DOFs): the
-// l1-Jacobi smoother x += D_l1^-1 (b - A x) contracts in the A-norm for any
-// SPD A, without a damping parameter to tune.
+// l1-Jacobi smoother x += omega D_l1^-1 (b - A x) contracts in the A-norm for
+// any SPD A and any weight 0 < omega < 2 (the eigenvalues of D_l1^-1 A lie in
+// (0, 1]).
 template <int DIM>
 __global__ void diag_kernel(Grid g, const float* __restrict__ K, const float* __restrict__ E,
                             const uint8_t* __restrict__ mask, float* __restrict__ invd) {
@@ -336,31 +265,18 @@ __global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict
   Kc[ec * ND * ND + t] = acc;
 }
 
-// Smoothing / residual from a precomputed t = A u (finest level):
-//   mode 1: y = u + omega D^-1 (b - t),  mode 2: y = b - t;  0 on fixed DOFs.
-__global__ void update_from_au_kernel(long long n, int dim, int ncopies, const uint8_t* __restrict__ mask,
-                                      const float* __restrict__ invd, const float* __restrict__ u,
-                                      const float* __restrict__ b, const float* __restrict__ t, float* __restrict__ y,
-                                      int mode, float omega) {
-  const int nn = (int)n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
-    const int node = i / dim, comp = i - node * dim;
-    const bool fx = (mask[node] >> comp) & 1;
-    const float w = omega * invd[i];
-    for (int c = 0; c < ncopies; c++) {
-      const long long k = (long long)c * nn + i;
-      y[k] = fx ? 0.f : (mode == 1 ? u[k] + w * (b[k] - t[k]) : b[k] - t[k]);
-    }
-  }
-}
-
 // b_c = P^T r_f for f = 2 (3^dim fine neighbours): one thread per coarse node.
+// With x0 given, also the coarse level's first sweep from zero,
+// x0 = omega D^-1 b_c.
 template <int DIM>
 __global__ void restrict2_kernel(Grid gf, Grid gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                                 const float* __restrict__ rf, float* __restrict__ bc) {
+                                 const float* __restrict__ rf, float* __restrict__ bc, float* __restrict__ x0,
+                                 const float* __restrict__ invd, float omega, const int* __restrict__ stop) {
+  if (halted(stop)) return;
   const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
   const float* r = rf + blockIdx.y * ndf;
   float* out = bc + blockIdx.y * ndc;
+  float* xo = x0 ? x0 + blockIdx.y * ndc : nullptr;
   const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
   for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
     const int Kz = nd / nxy, rem = nd - Kz * nxy, J = rem / gc.nx, I = rem - J * gc.nx;
@@ -390,19 +306,28 @@ __global__ void restrict2_kernel(Grid gf, Grid gc, const uint8_t* __restrict__ m
     }
     const uint8_t mk = mc[nd];
 #pragma unroll
-    for (int s2 = 0; s2 < DIM; s2++) out[(long long)nd * DIM + s2] = ((mk >> s2) & 1) ? 0.f : acc[s2];
+    for (int s2 = 0; s2 < DIM; s2++) {
+      const long long idx = (long long)nd * DIM + s2;
+      const float v = ((mk >> s2) & 1) ? 0.f : acc[s2];
+      out[idx] = v;
+      if (xo) xo[idx] = omega * invd[idx] * v;
+    }
   }
 }
 
 // b_c = P^T r_f (fine fixed DOFs read as 0, coarse fixed DOFs set to 0).  One
 // warp per coarse node: the lanes split the (2f - 1)^dim fine neighbours and
 // the sum is reduced in a fixed order.
+// x0 as in restrict2_kernel.
 template <int DIM>
 __global__ void restrict_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                                const float* __restrict__ rf, float* __restrict__ bc) {
+                                const float* __restrict__ rf, float* __restrict__ bc, float* __restrict__ x0,
+                                const float* __restrict__ invd, float omega, const int* __restrict__ stop) {
+  if (halted(stop)) return;
   const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
   const float* r = rf + blockIdx.y * ndf;
   float* out = bc + blockIdx.y * ndc;
+  float* xo = x0 ? x0 + blockIdx.y * ndc : nullptr;
   const int lane = threadIdx.x & 31;
   const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
   const int w = 2 * f - 1, nz = DIM == 3 ? w : 1, tot = w * w * nz;
@@ -430,7 +355,12 @@ __global__ void restrict_kernel(Grid gf, Grid gc, int f, const uint8_t* __restri
     if (lane == 0) {
       const uint8_t mk = mc[nd];
 #pragma unroll
-      for (int s2 = 0; s2 < DIM; s2++) out[(long long)nd * DIM + s2] = ((mk >> s2) & 1) ? 0.f : acc[s2];
+      for (int s2 = 0; s2 < DIM; s2++) {
+        const long long idx = (long long)nd * DIM + s2;
+        const float v = ((mk >> s2) & 1) ? 0.f : acc[s2];
+        out[idx] = v;
+        if (xo) xo[idx] = omega * invd[idx] * v;
+      }
     }
   }
 }
@@ -438,7 +368,8 @@ __global__ void restrict_kernel(Grid gf, Grid gc, int f, const uint8_t* __restri
 // x_f += P x_c on free fine DOFs.
 template <int DIM>
 __global__ void prolong_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, const float* __restrict__ xc,
-                               float* __restrict__ xf) {
+                               float* __restrict__ xf, const int* __restrict__ stop) {
+  if (halted(stop)) return;
   constexpr int NC = MgC<DIM>::NC;
   const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
   const float* x = xc + blockIdx.y * ndc;
@@ -469,7 +400,9 @@ __global__ void prolong_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
 
 // Coarsest solve: x = A^-1 b with the dense inverse; one warp per row
 // (blockIdx.y = case).
-__global__ void dense_solve_kernel(int n, const float* __restrict__ Ainv, const float* __restrict__ b, float* __restrict__ x) {
+__global__ void dense_solve_kernel(int n, const float* __restrict__ Ainv, const float* __restrict__ b, float* __restrict__ x,
+                                   const int* __restrict__ stop) {
+  if (halted(stop)) return;
   const float* bc = b + (long long)blockIdx.y * n;
   float* xc = x + (long long)blockIdx.y * n;
   const int lane = threadIdx.x & 31;
@@ -545,41 +478,51 @@ bool spd_inverse(std::vector<double>& A, int n) {
 
 double MgHierarchy::fine_bytes() const {
   const MgLevel& l = lv[0];
-  const int dim = l.g.dim;
-  // operator data read once per launch (assembled blocks, or one modulus per
-  // element), then per case: u read, b read, y written; the l1 scale per DOF
-  // finest level: the strain-form operator (moduli once per launch; u read and
-  // t written per case) and the update (u, b, t read, y written per case; the
-  // l1 scale once)
-  return (double)l.g.ne * 4.0 + (double)l.g.nn * dim * 4.0 * (1 + 6 * nc);
+  // finest-level sweep: moduli and the l1 scale once per launch; per case u
+  // and b read, y written
+  return (double)l.g.ne * 4.0 + (double)l.g.nn * l.g.dim * 4.0 * (1 + 3 * nc);
 }
 
-void MgHierarchy::collect_timing() {
-  for (int k = 0; k + 1 < ev_used; k += 2) {
+void MgHierarchy::collect_timing(int npairs) {
+  for (int k = 0; k < npairs && 2 * k + 1 < (int)ev.size(); k++) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) {
       timed_ms += ms;
       timed_launches++;
     }
   }
-  ev_used = 0;
   cudaGetLastError();
 }
 
+void MgHierarchy::drop_graphs() {
+  for (auto& row : gx)
+    for (auto& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
 void MgHierarchy::release() {
+  drop_graphs();
+  if (cap) cudaStreamDestroy(cap);
+  cap = nullptr;
   for (auto& e : ev) cudaEventDestroy(e);
   ev.clear();
   ev_used = 0;
   for (auto& l : lv) {
-    void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t, l.t2};
+    void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
   lv.clear();
-  if (cinv) cudaFree(cinv);
+  for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32})
+    if (q) cudaFree(q);
+  if (ctl_h) cudaFreeHost(ctl_h);
   cinv = nullptr;
-  if (K0d) cudaFree(K0d);
   K0d = nullptr;
+  ctl = nullptr;
+  ctl_h = nullptr;
+  p32 = q32 = nullptr;
   built = false;
 }
 
@@ -610,7 +553,6 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
       if (e == cudaSuccess) e = cudaMalloc((void**)&l.mask, l.g.nn);
       l.mask_own = true;
     }
-    if (e == cudaSuccess && i == 0) e = cudaMalloc((void**)&l.t2, nc * ndof * sizeof(float));
     if (e == cudaSuccess && i > 0) {
       const long long nb = g0.dim == 2 ? 9 * 4 : 27 * 9;
       e = cudaMalloc((void**)&l.S, l.g.nn * nb * sizeof(float));
@@ -622,6 +564,12 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
   }
   cn = (int)(lv.back().g.nn * g0.dim);
   if (e == cudaSuccess) e = cudaMalloc((void**)&cinv, (size_t)cn * cn * sizeof(float));
+  const size_t nv = (size_t)nc * g0.nn * g0.dim;
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p32, nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&q32, nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ctl, sizeof(MgCtl));
+  if (e == cudaSuccess) e = cudaMemset(ctl, 0, sizeof(MgCtl));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctl_h, sizeof(MgCtl));
   return e;
 }
 
@@ -705,87 +653,75 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
   return e;
 }
 
-template <int DIM>
-static cudaError_t apply_level(cudaStream_t s, const MgLevel& l, const float* E0, int nc, const float* u, const float* b,
-                               float* y, int mode, float omega) {
-  dim3 grid(blocks(l.g.nn), nc);
-  if (l.S) apply_stencil_kernel<DIM><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, b, y, mode, omega);
-  else apply_kernel<DIM><<<grid, 256, 0, s>>>(l.g, l.K, l.K ? nullptr : E0, l.mask, l.invd, u, b, y, mode, omega);
-  return cudaGetLastError();
-}
-
-// One V-cycle on level li: x = V(b) with x starting at zero.  The result is
-// left in lv[li].x[0].
-cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch) {
+// One V-cycle on level li (see mg.h for the entry state).  Sweeps alternate
+// between x[0] and x[1]; with nu sweeps before and after, the result lands in
+// a buffer fixed by nu, which *out names.
+cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int* stop, float** out) {
   MgLevel& l = lv[li];
   const int dim = l.g.dim;
   const long long ndof = l.g.nn * dim;
   if (li == (int)lv.size() - 1) {
-    dense_solve_kernel<<<dim3((cn + 7) / 8, nc), 256, 0, s>>>(cn, cinv, l.b, l.x[0]);
+    dense_solve_kernel<<<dim3((cn + 7) / 8, nc), 256, 0, s>>>(cn, cinv, l.b, l.x[0], stop);
     (*nlaunch)++;
+    *out = l.x[0];
     return cudaGetLastError();
   }
-  auto apply = [&](const float* u, const float* b, float* y, int mode) {
-    const bool tm = timing && li == 0 && ev_used + 2 <= (int)ev.size();
-    if (tm) cudaEventRecord(ev[ev_used], s);
+  auto sweep = [&](const float* u, float* y, int mode) -> cudaError_t {
+    const bool tm = capture_events && li == 0 && ev_used + 2 <= (int)ev.size();
+    if (tm) cudaEventRecordWithFlags(ev[ev_used], s, cudaEventRecordExternal);
     cudaError_t e;
-    if (li == 0 && fine_op_fn) {  // finest level: the strain-form FP32 operator, then the update
-      e = fine_op(s, u, l.t2);
-      if (e == cudaSuccess) {
-        update_from_au_kernel<<<blocks(ndof), 256, 0, s>>>(ndof, dim, nc, l.mask, l.invd, u, b, l.t2, y, mode, omega);
-        e = cudaGetLastError();
-      }
-      (*nlaunch)++;
+    if (li == 0) {
+      e = fine_op(s, u, l.b, l.invd, y, mode, stop);
     } else {
-      e = dim == 2 ? apply_level<2>(s, l, E0, nc, u, b, y, mode, omega)
-                   : apply_level<3>(s, l, E0, nc, u, b, y, mode, omega);
+      dim3 grid(blocks(l.g.nn), nc);
+      if (dim == 2) apply_stencil_kernel<2><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, l.b, y, mode, omega, stop);
+      else apply_stencil_kernel<3><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, l.b, y, mode, omega, stop);
+      e = cudaGetLastError();
     }
     if (tm) {
-      cudaEventRecord(ev[ev_used + 1], s);
+      cudaEventRecordWithFlags(ev[ev_used + 1], s, cudaEventRecordExternal);
       ev_used += 2;
     }
+    (*nlaunch)++;
     return e;
   };
-  // pre-smoothing from zero
-  jacobi0_kernel<<<blocks(ndof), 256, 0, s>>>(ndof, nc, l.invd, l.b, l.x[0], omega);
-  (*nlaunch)++;
+  // pre-smoothing: x[0] already holds the first sweep from zero
   int cur = 0;
   for (int k = 1; k < nu; k++) {
-    cudaError_t e = apply(l.x[cur], l.b, l.x[cur ^ 1], 1);
+    cudaError_t e = sweep(l.x[cur], l.x[cur ^ 1], 1);
     if (e != cudaSuccess) return e;
     cur ^= 1;
-    (*nlaunch)++;
   }
-  cudaError_t e = apply(l.x[cur], l.b, l.t, 2);  // residual
+  cudaError_t e = sweep(l.x[cur], l.t, 2);  // residual
   if (e != cudaSuccess) return e;
-  (*nlaunch)++;
   MgLevel& c = lv[li + 1];
+  const bool coarsest = li + 1 == (int)lv.size() - 1;
+  float* cx0 = coarsest ? nullptr : c.x[0];  // the dense solve needs no first sweep
   if (c.f == 2) {
     dim3 gr(blocks(c.g.nn), nc);
-    if (dim == 2) restrict2_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b);
-    else restrict2_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b);
+    if (dim == 2) restrict2_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
+    else restrict2_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
   } else {
     dim3 gr(blocks(c.g.nn * 32), nc);
-    if (dim == 2) restrict_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.mask, l.t, c.b);
-    else restrict_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.mask, l.t, c.b);
+    if (dim == 2)
+      restrict_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
+    else
+      restrict_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
   }
   (*nlaunch)++;
-  e = vcycle(s, li + 1, nlaunch);
+  float* xc = nullptr;
+  e = vcycle(s, li + 1, nlaunch, stop, &xc);
   if (e != cudaSuccess) return e;
   dim3 gp(blocks(l.g.nn), nc);
-  if (dim == 2) prolong_kernel<2><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.x[0], l.x[cur]);
-  else prolong_kernel<3><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, c.x[0], l.x[cur]);
+  if (dim == 2) prolong_kernel<2><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
+  else prolong_kernel<3><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
   (*nlaunch)++;
   for (int k = 0; k < nu; k++) {  // post-smoothing (as many sweeps: symmetric)
-    e = apply(l.x[cur], l.b, l.x[cur ^ 1], 1);
+    e = sweep(l.x[cur], l.x[cur ^ 1], 1);
     if (e != cudaSuccess) return e;
     cur ^= 1;
-    (*nlaunch)++;
   }
-  if (cur != 0) {
-    e = cudaMemcpyAsync(l.x[0], l.x[1], nc * ndof * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-  }
+  *out = l.x[cur];
   return cudaGetLastError();
 }
 
@@ -795,6 +731,10 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch) {
 // FP64 outer-PCG vector kernels.
 namespace tp {
 namespace {
+
+struct FF {
+  double v[8];
+};
 
 // Per-case partial dot products: block (b, c) sums chunk b of case c;
 // part[(c * nb + b) * 2 + k] for the two products k.
@@ -847,26 +787,6 @@ __global__ void scalars_kernel(int nb, int nc, const double* __restrict__ part, 
   }
 }
 
-// One block row per case (blockIdx.y); 32-bit indices within a case.
-__global__ void update_xr_kernel(long long n, const double* __restrict__ sc, double* x, const double* __restrict__ p,
-                                 double* r, const double* __restrict__ q) {
-  const int c = blockIdx.y, nn = (int)n;
-  const double a = sc[c];
-  const long long base = (long long)c * n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
-    x[base + i] = fma(a, p[base + i], x[base + i]);
-    r[base + i] = fma(-a, q[base + i], r[base + i]);
-  }
-}
-
-__global__ void update_p_kernel(long long n, const double* __restrict__ sc, double* p, const double* __restrict__ z) {
-  const int c = blockIdx.y, nn = (int)n;
-  const double b = sc[8 + c];
-  const long long base = (long long)c * n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
-    p[base + i] = fma(b, p[base + i], z[base + i]);
-}
-
 __global__ void residual_abi_kernel(long long n, const double* __restrict__ f, const double* __restrict__ Ax,
                                     const uint8_t* __restrict__ mask, int dim, double* r) {
   const int c = blockIdx.y, nn = (int)n;
@@ -877,13 +797,170 @@ __global__ void residual_abi_kernel(long long n, const double* __restrict__ f, c
   }
 }
 
-__global__ void f32_kernel(long long n, const double* __restrict__ a, float* b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// ---- graph-captured iteration ----------------------------------------------
+
+__global__ void seg_init_kernel(MgCtl* ctl, int nc, double tol2, FF ff, int it_limit, int use64) {
+  const int c = threadIdx.x;
+  if (c < 8) {
+    ctl->ff[c] = c < nc ? ff.v[c] : 0.0;
+    ctl->rr_start[c] = 0.0;
+  }
+  if (c == 0) {
+    ctl->tol2 = tol2;
+    ctl->best = 0.0;
+    ctl->it = 0;
+    ctl->best_it = 0;
+    ctl->it_limit = it_limit;
+    ctl->stop = 0;
+    ctl->reason = 0;
+    ctl->use64 = use64;
+    ctl->nc = nc;
+    ctl->ticket = 0u;
+  }
 }
-__global__ void f64_kernel(long long n, const float* __restrict__ a, double* b) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
+
+// r32 = (float) r, x0 = omega D^-1 r32 (blockIdx.y = case).
+__global__ void prep_kernel(long long n, const double* __restrict__ r, float* __restrict__ r32, float* __restrict__ x0,
+                            const float* __restrict__ invd, float omega) {
+  const int nn = (int)n;
+  const long long base = (long long)blockIdx.y * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    const float v = (float)r[base + i];
+    r32[base + i] = v;
+    x0[base + i] = omega * invd[i] * v;
+  }
+}
+
+template <typename TB>
+__device__ __forceinline__ double as_f64(TB v) {
+  return (double)v;
+}
+
+// Fused dot products and PCG scalars.  Block (b, c) sums chunk b of case c in
+// FP64 and stores its partials; the last block to finish (ticket) sums every
+// case's partials in a fixed order, so the result does not depend on the
+// order in which blocks finish, and then does the scalar work (one thread per
+// case) and, for what 1, the stopping rule of the segment.
+template <typename TB>
+__global__ void dotscal_kernel(long long n, const double* __restrict__ a1, const TB* __restrict__ b1,
+                               const double* __restrict__ a2, const double* __restrict__ b2, double* part, MgCtl* ctl,
+                               int what) {
+  __shared__ double sred[32 * 2];
+  __shared__ double tot[16];
+  __shared__ int is_last;
+  if (what != 2 && ctl->stop) return;  // uniform: the flag changes only in the last block of this kernel
+  const int c = blockIdx.y, nb = gridDim.x;
+  const long long base = (long long)c * n;
+  double acc[2] = {0.0, 0.0};
+  const int nn = (int)n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += nb * blockDim.x) {
+    acc[0] = fma(a1[base + i], as_f64(b1[base + i]), acc[0]);
+    if (a2) acc[1] = fma(a2[base + i], b2[base + i], acc[1]);
+  }
+  block_sum<2>(acc, sred);
+  if (threadIdx.x == 0) {
+    part[((long long)c * nb + blockIdx.x) * 2] = acc[0];
+    part[((long long)c * nb + blockIdx.x) * 2 + 1] = acc[1];
+    __threadfence();
+    const unsigned t = atomicAdd(&ctl->ticket, 1u);
+    is_last = t == gridDim.x * gridDim.y - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  const int nc = gridDim.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int pr = warp; pr < 2 * nc; pr += blockDim.x >> 5) {
+    const int cc = pr >> 1, k = pr & 1;
+    double sum = 0.0;
+    for (int b = lane; b < nb; b += 32) sum += __ldcg(part + ((long long)cc * nb + b) * 2 + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) tot[pr] = sum;
+  }
+  __syncthreads();
+  double* sc = ctl->sc;
+  const int cc = threadIdx.x;
+  if (cc < nc) {
+    const double s1 = tot[2 * cc], s2 = tot[2 * cc + 1];
+    if (what == 0) {  // alpha = rz / pq
+      sc[24 + cc] = s1;
+      sc[cc] = (s1 > 0.0 && isfinite(s1)) ? sc[16 + cc] / s1 : 0.0;
+    } else if (what == 1) {  // beta = rz_new / rz
+      sc[8 + cc] = sc[16 + cc] != 0.0 ? s1 / sc[16 + cc] : 0.0;
+      sc[16 + cc] = s1;
+      sc[32 + cc] = s2;
+    } else {  // segment start
+      sc[16 + cc] = s1;
+      sc[32 + cc] = s2;
+      sc[8 + cc] = 0.0;
+      ctl->rr_start[cc] = s2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (what == 1) {
+      // stop at the tolerance (with margin 1/2 on the recurrence residual),
+      // when the FP32 operator's error may dominate the recurrence (1e-5 of
+      // the segment's starting residual), on stagnation (no halving of the
+      // worst relative residual in 50 iterations), on breakdown, or at the
+      // iteration limit
+      const int it = ctl->it + 1;
+      ctl->it = it;
+      bool brk = false, done = true, inner = ctl->use64 == 0;
+      double worst = 0.0;
+      for (int k = 0; k < nc; k++) {
+        const double rec = sc[32 + k];
+        brk |= !isfinite(rec) || !(sc[24 + k] > 0.0);
+        done &= rec <= 0.25 * ctl->tol2 * ctl->ff[k];
+        inner &= rec <= 1e-10 * ctl->rr_start[k];
+        worst = fmax(worst, rec / ctl->ff[k]);
+      }
+      if (ctl->best == 0.0 || worst < 0.25 * ctl->best) {
+        ctl->best = worst;
+        ctl->best_it = it;
+      }
+      const bool stall = it - ctl->best_it >= 50, limit = it >= ctl->it_limit;
+      const int reason = (done ? MG_STOP_DONE : 0) | (inner ? MG_STOP_INNER : 0) | (stall ? MG_STOP_STALL : 0) |
+                         (brk ? MG_STOP_BREAK : 0) | (limit ? MG_STOP_LIMIT : 0);
+      ctl->reason = reason;
+      ctl->stop = reason != 0;
+    }
+    ctl->ticket = 0u;
+  }
+}
+
+// x += alpha p, r -= alpha q, r32 = (float) r, x0 = omega D^-1 r32.
+template <typename TQ>
+__global__ void update_xr_kernel(long long n, const MgCtl* __restrict__ ctl, double* x, const double* __restrict__ p,
+                                 double* r, const TQ* __restrict__ q, float* __restrict__ r32, float* __restrict__ x0,
+                                 const float* __restrict__ invd, float omega) {
+  if (ctl->stop) return;
+  const int c = blockIdx.y, nn = (int)n;
+  const double a = ctl->sc[c];
+  const long long base = (long long)c * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    x[base + i] = fma(a, p[base + i], x[base + i]);
+    const double rv = fma(-a, as_f64(q[base + i]), r[base + i]);
+    r[base + i] = rv;
+    const float v = (float)rv;
+    r32[base + i] = v;
+    x0[base + i] = omega * invd[i] * v;
+  }
+}
+
+// p = z + beta p (p = z at a segment start, beta = 0), p32 = (float) p.
+__global__ void update_p_kernel(long long n, const MgCtl* __restrict__ ctl, double* p, float* __restrict__ p32,
+                                const float* __restrict__ z) {
+  if (ctl->stop) return;
+  const int c = blockIdx.y, nn = (int)n;
+  const double b = ctl->sc[8 + c];
+  const long long base = (long long)c * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    const double v = b != 0.0 ? fma(b, p[base + i], (double)z[base + i]) : (double)z[base + i];
+    p[base + i] = v;
+    p32[base + i] = (float)v;
+  }
 }
 
 int vblocks(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 8); }
@@ -901,26 +978,41 @@ cudaError_t pcg_scalars(cudaStream_t s, int nblocks, int nc, const double* part,
   scalars_kernel<<<1, 512, 0, s>>>(nblocks, nc, part, what, sc);
   return cudaGetLastError();
 }
-cudaError_t pcg_update_xr(cudaStream_t s, long long n, int nc, const double* sc, double* x, const double* p, double* r,
-                          const double* q) {
-  update_xr_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, sc, x, p, r, q);
-  return cudaGetLastError();
-}
-cudaError_t pcg_update_p(cudaStream_t s, long long n, int nc, const double* sc, double* p, const double* z) {
-  update_p_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, sc, p, z);
-  return cudaGetLastError();
-}
 cudaError_t pcg_residual(cudaStream_t s, long long n, int nc, const double* f, const double* Ax, const uint8_t* mask,
                          int dim, double* r) {
   residual_abi_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, f, Ax, mask, dim, r);
   return cudaGetLastError();
 }
-cudaError_t to_f32(cudaStream_t s, long long n, const double* a, float* b) {
-  f32_kernel<<<vblocks(n), 256, 0, s>>>(n, a, b);
+cudaError_t mg_seg_init(cudaStream_t s, MgCtl* ctl, int nc, double tol2, const double* ff, int it_limit, int use64) {
+  FF f{};
+  for (int c = 0; c < nc && c < 8; c++) f.v[c] = ff[c];
+  seg_init_kernel<<<1, 32, 0, s>>>(ctl, nc, tol2, f, it_limit, use64);
   return cudaGetLastError();
 }
-cudaError_t to_f64(cudaStream_t s, long long n, const float* a, double* b) {
-  f64_kernel<<<vblocks(n), 256, 0, s>>>(n, a, b);
+cudaError_t mg_prep(cudaStream_t s, long long n, int nc, const double* r, float* r32, float* x0, const float* invd,
+                    float omega) {
+  prep_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, r, r32, x0, invd, omega);
+  return cudaGetLastError();
+}
+cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const double* a1, const void* b1, bool b1_f32,
+                       const double* a2, const double* b2, double* part, MgCtl* ctl, int what, int* nblocks) {
+  const int nb = (int)std::min<long long>(std::max<long long>((n + 1023) / 1024, 1), 2 * 152 / nc + 1);
+  if (b1_f32) dotscal_kernel<float><<<dim3(nb, nc), 256, 0, s>>>(n, a1, (const float*)b1, a2, b2, part, ctl, what);
+  else dotscal_kernel<double><<<dim3(nb, nc), 256, 0, s>>>(n, a1, (const double*)b1, a2, b2, part, ctl, what);
+  if (nblocks) *nblocks = nb;
+  return cudaGetLastError();
+}
+cudaError_t mg_update_xr(cudaStream_t s, long long n, int nc, MgCtl* ctl, double* x, const double* p, double* r,
+                         const void* q, bool q_f32, float* r32, float* x0, const float* invd, float omega) {
+  if (q_f32)
+    update_xr_kernel<float><<<dim3(vblocks(n), nc), 256, 0, s>>>(n, ctl, x, p, r, (const float*)q, r32, x0, invd, omega);
+  else
+    update_xr_kernel<double><<<dim3(vblocks(n), nc), 256, 0, s>>>(n, ctl, x, p, r, (const double*)q, r32, x0, invd,
+                                                                  omega);
+  return cudaGetLastError();
+}
+cudaError_t mg_update_p(cudaStream_t s, long long n, int nc, MgCtl* ctl, double* p, float* p32, const float* z) {
+  update_p_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, ctl, p, p32, z);
   return cudaGetLastError();
 }
 

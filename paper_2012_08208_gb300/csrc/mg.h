@@ -21,8 +21,29 @@ struct MgLevel {
   float* x[2] = {nullptr, nullptr};  // iterates [case][n_nodes * dim]
   float* b = nullptr;       // right-hand side
   float* t = nullptr;       // residual scratch
-  float* t2 = nullptr;      // A u on the finest level
 };
+
+// Device control block of the multigrid PCG.  The scalar kernels keep the
+// per-case CG scalars here and, after each iteration, decide on the device
+// whether the segment stops; every kernel of an iteration returns at once
+// when `stop` is set, so a CUDA graph of several iterations can run past the
+// stopping point without changing the iterate.
+struct MgCtl {
+  double sc[64];       // [0,8) alpha, [8,16) beta, [16,24) rz, [24,32) pq, [32,40) rr
+  double rr_start[8];  // rr at the segment start
+  double ff[8];        // ||f_c||^2
+  double best;         // worst relative rr at its last halving
+  double tol2;         // tol^2
+  int it;              // iterations of the segment so far
+  int best_it;         // iteration of `best`
+  int it_limit;        // iterations allowed in the segment
+  int stop;            // 0: run, 1: stop (every later kernel of the segment returns)
+  int reason;          // MG_STOP_* bits
+  int use64;           // FP64 operator (the FP32-accuracy rule does not apply)
+  int nc;
+  unsigned ticket;     // last-block counter of the fused dot/scalar kernel (0 between launches)
+};
+enum : int { MG_STOP_DONE = 1, MG_STOP_INNER = 2, MG_STOP_STALL = 4, MG_STOP_BREAK = 8, MG_STOP_LIMIT = 16 };
 
 struct MgHierarchy {
   std::vector<MgLevel> lv;
@@ -30,10 +51,26 @@ struct MgHierarchy {
   float* cinv = nullptr;    // coarsest dense inverse [cn][cn]
   float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
   const float* E0 = nullptr;
-  // finest-level operator y = A u for all cases (the library's FP32 operator)
-  cudaError_t (*fine_op_fn)(void* ctx, cudaStream_t s, const float* u, float* y) = nullptr;
+  // Finest-level sweep for all cases on the library's strain-form FP32
+  // operator: mode 1 y = u + omega D^-1 (b - A u), mode 2 y = b - A u (0 on
+  // fixed DOFs); returns at once when *stop is set.
+  cudaError_t (*fine_op_fn)(void* ctx, cudaStream_t s, const float* u, const float* b, const float* invd, float* y,
+                            int mode, float omega, const int* stop) = nullptr;
   void* fine_ctx = nullptr;
-  cudaError_t fine_op(cudaStream_t s, const float* u, float* y) const { return fine_op_fn(fine_ctx, s, u, y); }
+  cudaError_t fine_op(cudaStream_t s, const float* u, const float* b, const float* invd, float* y, int mode,
+                      const int* stop) const {
+    return fine_op_fn(fine_ctx, s, u, b, invd, y, mode, omega, stop);
+  }
+  MgCtl* ctl = nullptr;     // device control block
+  MgCtl* ctl_h = nullptr;   // pinned host mirror
+  float* p32 = nullptr;     // FP32 copy of the search direction (finest level, all cases)
+  float* q32 = nullptr;     // FP32 K p
+  // CUDA graphs of kGraphIters PCG iterations, [FP64 operator][timed]
+  static constexpr int kGraphIters = 8;
+  cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int gx_launches[2][2] = {{0, 0}, {0, 0}};
+  bool capture_events = false;  // record finest-sweep event pairs while capturing
+  cudaStream_t cap = nullptr;   // capture stream of the graphs
   float omega = 1.6f;       // l1-Jacobi weight (convergent for any weight below 2)
   int nu = 2;               // sweeps before and after the coarse correction
   bool built = false;
@@ -45,7 +82,7 @@ struct MgHierarchy {
   long long timed_launches = 0;
   double timed_ms = 0.0;
   double fine_bytes() const;  // algorithmic bytes of one finest-level sweep launch
-  void collect_timing();      // after the stream has synchronised
+  void collect_timing(int npairs);  // the first npairs event pairs, after the stream has synchronised
 
   // Level plan for grid g0: 2:1 while possible, then the smallest common odd
   // factor, until the coarsest has <= max_coarse_dofs DOFs.  Allocates all
@@ -53,8 +90,12 @@ struct MgHierarchy {
   cudaError_t plan(const Grid& g0, const uint8_t* mask0, int nc, int max_coarse_dofs = 256);
   // Galerkin coarse operators, diagonals and the coarsest inverse for moduli E32.
   cudaError_t build(cudaStream_t s, const double* K0, const float* E32, int* nlaunch);
-  // x = V(b) on level li (x starts at zero); input lv[li].b, output lv[li].x[0].
-  cudaError_t vcycle(cudaStream_t s, int li, int* nlaunch);
+  // x = V(b) on level li.  On entry lv[li].b holds b and lv[li].x[0] the first
+  // sweep from zero, omega D^-1 b (written by whichever kernel produced b);
+  // *out receives the buffer holding the result (fixed for a given hierarchy).
+  // Every launch returns at once when *stop is set (stop may be null).
+  cudaError_t vcycle(cudaStream_t s, int li, int* nlaunch, const int* stop, float** out);
+  void drop_graphs();
   void release();
   ~MgHierarchy() { release(); }
 };
@@ -66,12 +107,25 @@ cudaError_t pcg_dot2(cudaStream_t s, long long n, int nc, const double* a1, cons
 // what 0: pq = <p,q> -> alpha = rz / pq;  what 1: rz_new, rr -> beta = rz_new / rz, rz = rz_new;
 // what 2: rz, rr (start)
 cudaError_t pcg_scalars(cudaStream_t s, int nblocks, int nc, const double* part, int what, double* sc);
-cudaError_t pcg_update_xr(cudaStream_t s, long long n, int nc, const double* sc, double* x, const double* p, double* r,
-                          const double* q);
-cudaError_t pcg_update_p(cudaStream_t s, long long n, int nc, const double* sc, double* p, const double* z);
 cudaError_t pcg_residual(cudaStream_t s, long long n, int nc, const double* f, const double* Ax, const uint8_t* mask,
                          int dim, double* r);
-cudaError_t to_f32(cudaStream_t s, long long n, const double* a, float* b);
-cudaError_t to_f64(cudaStream_t s, long long n, const float* a, double* b);
+
+// Kernels of the graph-captured iteration (ctl in device memory).  Each
+// returns at once when ctl->stop is set, except the segment start.
+// Segment start: the control block for nc cases (it = 0, stop = 0).
+cudaError_t mg_seg_init(cudaStream_t s, MgCtl* ctl, int nc, double tol2, const double* ff, int it_limit, int use64);
+// r32 = (float) r and x0 = omega D^-1 r32 (the V-cycle's first sweep).
+cudaError_t mg_prep(cudaStream_t s, long long n, int nc, const double* r, float* r32, float* x0, const float* invd,
+                    float omega);
+// Per-case <a1, b1> (and <a2, b2>) in a fixed order, then the PCG scalars and,
+// for what 1, the stopping rule; b1 is FP32 when b1_f32.
+//   what 0: pq -> alpha;  what 1: rz_new, rr -> beta, stop rule;  what 2: rz, rr, beta = 0 (segment start)
+cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const double* a1, const void* b1, bool b1_f32,
+                       const double* a2, const double* b2, double* part, MgCtl* ctl, int what, int* nblocks);
+// x += alpha p, r -= alpha q (q FP32 when q_f32), r32 = (float) r, x0 = omega D^-1 r32.
+cudaError_t mg_update_xr(cudaStream_t s, long long n, int nc, MgCtl* ctl, double* x, const double* p, double* r,
+                         const void* q, bool q_f32, float* r32, float* x0, const float* invd, float omega);
+// p = z + beta p (p = z when beta = 0), p32 = (float) p.
+cudaError_t mg_update_p(cudaStream_t s, long long n, int nc, MgCtl* ctl, double* p, float* p32, const float* z);
 
 }  // namespace tp

@@ -58,7 +58,6 @@ struct tp_problem {
   int last_grid = 0;
   tp::MgHierarchy* mg = nullptr; // multigrid preconditioner (built on first use)
   long long E_version = 0;       // bumped whenever the moduli are recomputed
-  double* mg_sc = nullptr;       // device scalars of the multigrid PCG
   bool profile = false;          // time the multigrid finest-level launches
   int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
   double* rho_phys = nullptr;    // density-filtered densities (filter mode 1)
