@@ -110,10 +110,11 @@ static int pick_zlen(const Grid& g, int resident) {
 tp_status tp_problem_ensure_E(tp_problem* p) { return ensure_E(p); }
 
 // Finest multigrid level: the problem's FP32 strain-form operator on all cases.
-static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, const float* b, const float* invd, float* y,
-                              int mode, float omega, const int* stop) {
+static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, const float* w, const float* b,
+                              const float* invd, float* y, int mode, float a, float c, float om, const int* stop) {
   tp_problem* p = (tp_problem*)ctx;
-  return launch_mg_sweep(s, p->g, p->C.data(), p->E32, p->mask, invd, u, b, y, p->nc, p->zlen, mode, omega, stop);
+  return launch_mg_sweep(s, p->g, p->C.data(), p->E32, p->mask, invd, u, w, b, y, p->nc, p->zlen, mode, a, c, om,
+                         stop);
 }
 
 // CG in FP64 preconditioned by one FP32 multigrid V-cycle per iteration
@@ -187,19 +188,33 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     for (int c = 0; c < nc; c++) rr_out[c] = h[32 + c];
     return TP_OK;
   };
-  // One PCG iteration: q = K p, alpha, x and r, z = V(r), beta and the stopping
-  // rule, p.  FP32 operator on an FP32 copy of p unless u64.
+  // One PCG iteration: q = K p, alpha, the iterate and r, z = V(r), beta and
+  // the stopping rule, p.  Default: the segment solves K d = r for a
+  // correction d with FP32 vectors and the FP32 operator (FP64 scalars); with
+  // u64, x, r, p stay FP64 and the operator is FP64.
   float* z32 = nullptr;
+  float* r32 = l0.b;  // the V-cycle's right-hand side doubles as the FP32 residual
   auto issue_iter = [&](cudaStream_t cs, bool u64, int* nlk) -> cudaError_t {
-    cudaError_t e = u64 ? launch_matvec(cs, p->g, p->C.data(), true, p->E64, p->mask, pp, q, nc, p->zlen, stop)
-                        : launch_matvec(cs, p->g, p->C.data(), false, p->E32, p->mask, M.p32, M.q32, nc, p->zlen, stop);
-    const void* qv = u64 ? (const void*)q : (const void*)M.q32;
-    if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, pp, qv, !u64, nullptr, nullptr, p->part, ctl, 0, nullptr);
-    if (e == cudaSuccess) e = mg_update_xr(cs, n, nc, ctl, x, pp, r, qv, !u64, l0.b, l0.x[0], l0.invd, M.omega);
+    cudaError_t e;
+    if (u64) {
+      e = launch_matvec(cs, p->g, p->C.data(), true, p->E64, p->mask, pp, q, nc, p->zlen, stop);
+      if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, pp, false, q, false, nullptr, nullptr, p->part, ctl, 0, nullptr);
+      if (e == cudaSuccess) e = mg_update_xr(cs, n, nc, ctl, x, pp, r, q, false, r32, l0.x[0], l0.invd, M.omega);
+    } else {
+      e = launch_matvec(cs, p->g, p->C.data(), false, p->E32, p->mask, M.p32, M.q32, nc, p->zlen, stop);
+      if (e == cudaSuccess)
+        e = mg_dotscal(cs, n, nc, M.p32, true, M.q32, true, nullptr, nullptr, p->part, ctl, 0, nullptr);
+      if (e == cudaSuccess) e = mg_update32(cs, n, nc, ctl, M.d32, M.p32, r32, M.q32, l0.x[0], l0.invd, M.omega);
+    }
     *nlk += 3;
     if (e == cudaSuccess) e = M.vcycle(cs, 0, nlk, stop, &z32);
-    if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, r, z32, true, r, r, p->part, ctl, 1, nullptr);
-    if (e == cudaSuccess) e = mg_update_p(cs, n, nc, ctl, pp, M.p32, z32);
+    if (u64) {
+      if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, r, false, z32, true, r, r, p->part, ctl, 1, nullptr);
+      if (e == cudaSuccess) e = mg_update_p(cs, n, nc, ctl, pp, M.p32, z32);
+    } else {
+      if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 1, nullptr);
+      if (e == cudaSuccess) e = mg_update_p32(cs, n, nc, ctl, M.p32, z32);
+    }
     *nlk += 2;
     return e;
   };
@@ -254,13 +269,19 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   // eps32 * cond(K) is not small)
   bool use64 = opts->precision == TP_PREC_F64;
   while (!conv && it < opts->max_it && !brk) {
-    // segment start from the current residual: z = V(r), p = z
+    // segment start from the current residual: z = V(r), p = z (d = 0)
     TPCK(mg_seg_init(s, ctl, nc, opts->tol * opts->tol, p->ff, opts->max_it - it, use64 ? 1 : 0), "control kernel");
-    TPCK(mg_prep(s, n, nc, r, l0.b, l0.x[0], l0.invd, M.omega), "convert kernel");
+    TPCK(mg_prep(s, n, nc, r, r32, l0.x[0], l0.invd, M.omega), "convert kernel");
     nl += 2;
     TPCK(M.vcycle(s, 0, &nl, nullptr, &z32), "v-cycle");
-    TPCK(mg_dotscal(s, n, nc, r, z32, true, r, r, p->part, ctl, 2, nullptr), "dot kernel");
-    TPCK(mg_update_p(s, n, nc, ctl, pp, M.p32, z32), "update kernel");
+    if (use64) {
+      TPCK(mg_dotscal(s, n, nc, r, false, z32, true, r, r, p->part, ctl, 2, nullptr), "dot kernel");
+      TPCK(mg_update_p(s, n, nc, ctl, pp, M.p32, z32), "update kernel");
+    } else {
+      TPCK(cudaMemsetAsync(M.d32, 0, (size_t)nc * n * sizeof(float), s), "memset");
+      TPCK(mg_dotscal(s, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 2, nullptr), "dot kernel");
+      TPCK(mg_update_p32(s, n, nc, ctl, M.p32, z32), "update kernel");
+    }
     nl += 2;
     st = graph(use64);
     if (st != TP_OK) return st;
@@ -280,6 +301,10 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     }
     it += seg_it;
     brk = (M.ctl_h->reason & MG_STOP_BREAK) != 0;
+    if (!use64) {  // x += d
+      TPCK(mg_merge(s, (long long)nc * n, x, M.d32), "merge kernel");
+      nl++;
+    }
     double before = 0.0, after = 0.0;
     for (int c = 0; c < nc; c++) before = std::max(before, rr[c] / p->ff[c]);
     st = true_rr(rr);

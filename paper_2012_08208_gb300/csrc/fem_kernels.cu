@@ -169,11 +169,12 @@ cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f
 // ---------------------------------------------------------------------------
 // Multigrid finest-level sweep on the FP32 strain-form operator, one pass per
 // case (blockIdx.y):
-//   mode 1: y = u + omega D^-1 (b - K u)   (l1-Jacobi smoothing sweep)
-//   mode 2: y = b - K u                    (residual)
+//   mode 1: y = a u + c w + om D^-1 (b - K u)   (Chebyshev smoothing step; w
+//           may be null, and y may alias w, which is read at the own DOF only)
+//   mode 2: y = b - K u                          (residual)
 // K u with the fixed entries of u read as 0; y = 0 on fixed DOFs.  The
-// operator value never leaves registers, so a sweep reads u, b and the l1
-// scale once and writes y once.
+// operator value never leaves registers, so a step reads u, b (and w) and the
+// l1 scale once and writes y once.
 
 template <int DIM>
 struct SweepArgs {
@@ -183,12 +184,13 @@ struct SweepArgs {
   const uint8_t* mask;
   const float* invd;
   const float* u;
+  const float* w;
   const float* b;
   float* y;
   long long stride;
   const int* stop;
   int mode;
-  float omega;
+  float a, c, om;
   CMat<DIM, float> C;
 };
 
@@ -199,6 +201,7 @@ __global__ void __launch_bounds__(TileOp<DIM, float>::THREADS)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const float* u = a.u + blockIdx.y * a.stride;
   const float* b = a.b + blockIdx.y * a.stride;
+  const float* w = a.w ? a.w + blockIdx.y * a.stride : nullptr;
   float* y = a.y + blockIdx.y * a.stride;
   TileOp<DIM, float>::template apply<1>(
       a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1,
@@ -211,15 +214,20 @@ __global__ void __launch_bounds__(TileOp<DIM, float>::THREADS)
         for (int r = 0; r < DIM; r++) {
           const long long i = node * DIM + r;
           const float res = b[i] - kv[r];
-          y[i] = ((mk >> r) & 1) ? 0.f : (a.mode == 1 ? us[r] + a.omega * a.invd[i] * res : res);
+          float out = res;
+          if (a.mode == 1) {
+            out = fmaf(a.a, us[r], a.om * a.invd[i] * res);
+            if (w) out = fmaf(a.c, w[i], out);
+          }
+          y[i] = ((mk >> r) & 1) ? 0.f : out;
         }
       });
 }
 
 template <int DIM>
 static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
-                              const float* invd, const float* u, const float* b, float* y, int ncopies, int zlen,
-                              int mode, float omega, const int* stop) {
+                              const float* invd, const float* u, const float* w, const float* b, float* y,
+                              int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop) {
   using Op = TileOp<DIM, float>;
   SweepArgs<DIM> a;
   a.g = g;
@@ -228,12 +236,15 @@ static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, co
   a.mask = mask;
   a.invd = invd;
   a.u = u;
+  a.w = w;
   a.b = b;
   a.y = y;
   a.stride = g.nn * DIM;
   a.stop = stop;
   a.mode = mode;
-  a.omega = omega;
+  a.a = ca;
+  a.c = cc;
+  a.om = om;
   fill_c<DIM, float>(a.C, C);
   const size_t smem = Op::smem_bytes();
   auto kern = mg_sweep_kernel<DIM>;
@@ -244,10 +255,10 @@ static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, co
 }
 
 cudaError_t launch_mg_sweep(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
-                            const float* invd, const float* u, const float* b, float* y, int ncopies, int zlen,
-                            int mode, float omega, const int* stop) {
-  return g.dim == 2 ? sweep_impl<2>(s, g, C, E, mask, invd, u, b, y, ncopies, zlen, mode, omega, stop)
-                    : sweep_impl<3>(s, g, C, E, mask, invd, u, b, y, ncopies, zlen, mode, omega, stop);
+                            const float* invd, const float* u, const float* w, const float* b, float* y,
+                            int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop) {
+  return g.dim == 2 ? sweep_impl<2>(s, g, C, E, mask, invd, u, w, b, y, ncopies, zlen, mode, ca, cc, om, stop)
+                    : sweep_impl<3>(s, g, C, E, mask, invd, u, w, b, y, ncopies, zlen, mode, ca, cc, om, stop);
 }
 
 // ---------------------------------------------------------------------------

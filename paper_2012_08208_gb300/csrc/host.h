@@ -68,12 +68,13 @@ cudaError_t launch_diag(cudaStream_t s, const Grid& g, const double* K0, const d
 cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f64, const void* E,
                           const uint8_t* mask, const void* u, void* y, int ncopies, int zlen,
                           const int* stop = nullptr);
-// Multigrid finest-level sweep on the FP32 operator (mode 1: l1-Jacobi sweep
-// y = u + omega D^-1 (b - K u); mode 2: residual y = b - K u; 0 on fixed DOFs),
-// ncopies vectors of stride n_dof; returns at once when *stop is set.
+// Multigrid finest-level sweep on the FP32 operator (mode 1: smoothing step
+// y = ca u + cc w + om D^-1 (b - K u), w optional and y may alias w; mode 2:
+// residual y = b - K u; 0 on fixed DOFs), ncopies vectors of stride n_dof;
+// returns at once when *stop is set.
 cudaError_t launch_mg_sweep(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
-                            const float* invd, const float* u, const float* b, float* y, int ncopies, int zlen,
-                            int mode, float omega, const int* stop);
+                            const float* invd, const float* u, const float* w, const float* b, float* y,
+                            int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop);
 // FP64 update: x64 += x_l, x_l = 0; r = f - K64 x64; z = D^-1 r; CgState update.
 // `init` starts a solve (beta = 0, counters reset).  Returns the number of
 // kernels launched through *nlaunch.

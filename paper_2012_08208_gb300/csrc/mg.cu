@@ -1,7 +1,7 @@
 // Geometric multigrid preconditioner for the CG solve (not in the paper, which
 // factorises K directly): nested structured grids, Galerkin coarse operators
-// held as per-element matrices, damped-Jacobi smoothing, and an exact solve
-// on the coarsest grid.
+// held as per-element matrices, Chebyshev smoothing on the l1-Jacobi scaling,
+// and an exact solve on the coarsest grid.
 //
 // Level 0 is the problem's grid with element matrices E_e K0.  A coarse
 // element of level l + 1 covers f^dim elements of level l (f = 2 while every
@@ -14,6 +14,7 @@
 // identity there.  Restriction is P^T.  All vectors are [case][node * dim + comp]
 // (the ABI layout), FP32 inside the V-cycle.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -90,20 +91,21 @@ __global__ void stencil_kernel(Grid g, const float* __restrict__ K, const float*
 }
 
 // y = A u on a coarse level from its assembled form (node-centric; fixed DOFs
-// read as 0 and mapped by the identity), fused into an l1-Jacobi sweep:
-//   mode 1: y = u + omega D^-1 (b - A u)     (smoothing sweep)
-//   mode 2: y = b - A u                       (residual)
+// read as 0), fused into a smoothing step or a residual:
+//   mode 1: y = ca u + cc w + om D^-1 (b - A u)   (Chebyshev step; w may be null)
+//   mode 2: y = b - A u                            (residual)
 // 0 on fixed DOFs.  One thread per node and case (blockIdx.y = case).
 template <int DIM>
 __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
-                                     const float* __restrict__ invd, const float* __restrict__ u,
-                                     const float* __restrict__ b, float* __restrict__ y, int mode, float omega,
+                                     const float* __restrict__ invd, const float* __restrict__ u, const float* w,
+                                     const float* __restrict__ b, float* y, int mode, float ca, float cc, float om,
                                      const int* __restrict__ stop) {
   if (halted(stop)) return;
   const int nn = (int)g.nn, nxy = g.nx * g.ny;
   const long long ndof = (long long)nn * DIM;
   const float* uc = u + blockIdx.y * ndof;
   const float* bc = b + blockIdx.y * ndof;
+  const float* wc = w ? w + blockIdx.y * ndof : nullptr;
   float* yc = y + blockIdx.y * ndof;
   for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
     const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
@@ -135,7 +137,12 @@ __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const 
     for (int r = 0; r < DIM; r++) {
       const long long idx = (long long)nd * DIM + r;
       const float res = bc[idx] - acc[r];
-      yc[idx] = ((mk >> r) & 1) ? 0.f : (mode == 1 ? uc[idx] + omega * invd[idx] * res : res);
+      float out = res;
+      if (mode == 1) {
+        out = fmaf(ca, uc[idx], om * invd[idx] * res);
+        if (wc) out = fmaf(cc, wc[idx], out);  // w read at this DOF only: y may alias w
+      }
+      yc[idx] = ((mk >> r) & 1) ? 0.f : out;
     }
   }
 }
@@ -515,20 +522,40 @@ void MgHierarchy::release() {
       if (q) cudaFree(q);
   }
   lv.clear();
-  for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32})
+  for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32, (void*)d32})
     if (q) cudaFree(q);
   if (ctl_h) cudaFreeHost(ctl_h);
   cinv = nullptr;
   K0d = nullptr;
   ctl = nullptr;
   ctl_h = nullptr;
-  p32 = q32 = nullptr;
+  p32 = q32 = d32 = nullptr;
   built = false;
+}
+
+// Chebyshev coefficients for the interval [1 / ratio, 1] (centre theta,
+// half-width delta, sigma = theta / delta): with rho_1 = 1 / sigma and
+// rho_k = 1 / (2 sigma - rho_{k-1}), the step direction d_k = rho_k rho_{k-1}
+// d_{k-1} + (2 rho_k / delta) D^-1 r_k gives the three-term form above.
+void MgHierarchy::set_smoother(int degree, float ratio) {
+  nu = std::max(1, std::min(degree, 7));
+  cheb_ratio = ratio;
+  const double lo = 1.0 / ratio, theta = 0.5 * (1.0 + lo), delta = 0.5 * (1.0 - lo), sigma = theta / delta;
+  omega = (float)(1.0 / theta);
+  double rho_prev = 1.0 / sigma;
+  for (int k = 2; k <= nu; k++) {
+    const double rho = 1.0 / (2.0 * sigma - rho_prev);
+    ca[k] = (float)(1.0 + rho * rho_prev);
+    cc[k] = (float)(-rho * rho_prev);
+    cw[k] = (float)(2.0 * rho / delta);
+    rho_prev = rho;
+  }
 }
 
 cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int max_coarse_dofs) {
   release();
   nc = nc_;
+  set_smoother(nu, cheb_ratio);
   MgLevel l0;
   l0.g = g0;
   l0.f = 1;
@@ -567,6 +594,7 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
   const size_t nv = (size_t)nc * g0.nn * g0.dim;
   if (e == cudaSuccess) e = cudaMalloc((void**)&p32, nv * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&q32, nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d32, nv * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctl, sizeof(MgCtl));
   if (e == cudaSuccess) e = cudaMemset(ctl, 0, sizeof(MgCtl));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctl_h, sizeof(MgCtl));
@@ -666,16 +694,18 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
     *out = l.x[0];
     return cudaGetLastError();
   }
-  auto sweep = [&](const float* u, float* y, int mode) -> cudaError_t {
+  auto sweep = [&](const float* u, const float* w, float* y, int mode, float a, float c, float om) -> cudaError_t {
     const bool tm = capture_events && li == 0 && ev_used + 2 <= (int)ev.size();
     if (tm) cudaEventRecordWithFlags(ev[ev_used], s, cudaEventRecordExternal);
     cudaError_t e;
     if (li == 0) {
-      e = fine_op(s, u, l.b, l.invd, y, mode, stop);
+      e = fine_op_fn(fine_ctx, s, u, w, l.b, l.invd, y, mode, a, c, om, stop);
     } else {
       dim3 grid(blocks(l.g.nn), nc);
-      if (dim == 2) apply_stencil_kernel<2><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, l.b, y, mode, omega, stop);
-      else apply_stencil_kernel<3><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, l.b, y, mode, omega, stop);
+      if (dim == 2)
+        apply_stencil_kernel<2><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y, mode, a, c, om, stop);
+      else
+        apply_stencil_kernel<3><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y, mode, a, c, om, stop);
       e = cudaGetLastError();
     }
     if (tm) {
@@ -685,14 +715,15 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
     (*nlaunch)++;
     return e;
   };
-  // pre-smoothing: x[0] already holds the first sweep from zero
+  // pre-smoothing from zero: x[0] already holds step 1, omega D^-1 b; step k
+  // needs x_{k-2}, which is 0 for k = 2
   int cur = 0;
-  for (int k = 1; k < nu; k++) {
-    cudaError_t e = sweep(l.x[cur], l.x[cur ^ 1], 1);
+  for (int k = 2; k <= nu; k++) {
+    cudaError_t e = sweep(l.x[cur], k == 2 ? nullptr : l.x[cur ^ 1], l.x[cur ^ 1], 1, ca[k], cc[k], cw[k]);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
-  cudaError_t e = sweep(l.x[cur], l.t, 2);  // residual
+  cudaError_t e = sweep(l.x[cur], nullptr, l.t, 2, 0.f, 0.f, 0.f);  // residual
   if (e != cudaSuccess) return e;
   MgLevel& c = lv[li + 1];
   const bool coarsest = li + 1 == (int)lv.size() - 1;
@@ -716,8 +747,10 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   if (dim == 2) prolong_kernel<2><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
   else prolong_kernel<3><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
   (*nlaunch)++;
-  for (int k = 0; k < nu; k++) {  // post-smoothing (as many sweeps: symmetric)
-    e = sweep(l.x[cur], l.x[cur ^ 1], 1);
+  // post-smoothing with the same polynomial from the corrected iterate
+  for (int k = 1; k <= nu; k++) {
+    e = k == 1 ? sweep(l.x[cur], nullptr, l.x[cur ^ 1], 1, 1.f, 0.f, omega)
+               : sweep(l.x[cur], l.x[cur ^ 1], l.x[cur ^ 1], 1, ca[k], cc[k], cw[k]);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
@@ -835,15 +868,19 @@ template <typename TB>
 __device__ __forceinline__ double as_f64(TB v) {
   return (double)v;
 }
+// Per-thread partial sums: FP64 when either operand is FP64, else FP32 (a
+// thread sums about ten products; the block and grid totals are FP64).
+template <typename TA, typename TB>
+using acc_t = typename std::conditional<sizeof(TA) == 8 || sizeof(TB) == 8, double, float>::type;
 
 // Fused dot products and PCG scalars.  Block (b, c) sums chunk b of case c in
 // FP64 and stores its partials; the last block to finish (ticket) sums every
 // case's partials in a fixed order, so the result does not depend on the
 // order in which blocks finish, and then does the scalar work (one thread per
 // case) and, for what 1, the stopping rule of the segment.
-template <typename TB>
-__global__ void dotscal_kernel(long long n, const double* __restrict__ a1, const TB* __restrict__ b1,
-                               const double* __restrict__ a2, const double* __restrict__ b2, double* part, MgCtl* ctl,
+template <typename TA, typename TB>
+__global__ void dotscal_kernel(long long n, const TA* __restrict__ a1, const TB* __restrict__ b1,
+                               const TA* __restrict__ a2, const TA* __restrict__ b2, double* part, MgCtl* ctl,
                                int what) {
   __shared__ double sred[32 * 2];
   __shared__ double tot[16];
@@ -851,12 +888,14 @@ __global__ void dotscal_kernel(long long n, const double* __restrict__ a1, const
   if (what != 2 && ctl->stop) return;  // uniform: the flag changes only in the last block of this kernel
   const int c = blockIdx.y, nb = gridDim.x;
   const long long base = (long long)c * n;
-  double acc[2] = {0.0, 0.0};
+  using A = acc_t<TA, TB>;
+  A t0 = A(0), t1 = A(0);
   const int nn = (int)n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += nb * blockDim.x) {
-    acc[0] = fma(a1[base + i], as_f64(b1[base + i]), acc[0]);
-    if (a2) acc[1] = fma(a2[base + i], b2[base + i], acc[1]);
+    t0 = fma((A)a1[base + i], (A)b1[base + i], t0);
+    if (a2) t1 = fma((A)a2[base + i], (A)b2[base + i], t1);
   }
+  double acc[2] = {(double)t0, (double)t1};
   block_sum<2>(acc, sred);
   if (threadIdx.x == 0) {
     part[((long long)c * nb + blockIdx.x) * 2] = acc[0];
@@ -949,6 +988,39 @@ __global__ void update_xr_kernel(long long n, const MgCtl* __restrict__ ctl, dou
   }
 }
 
+// FP32 inner iteration (correction d of the segment): d += alpha p,
+// r -= alpha q, x0 = omega D^-1 r (r is the V-cycle's right-hand side).
+__global__ void update32_kernel(long long n, const MgCtl* __restrict__ ctl, float* d, const float* __restrict__ p,
+                                float* r, const float* __restrict__ q, float* __restrict__ x0,
+                                const float* __restrict__ invd, float omega) {
+  if (ctl->stop) return;
+  const int c = blockIdx.y, nn = (int)n;
+  const float a = (float)ctl->sc[c];
+  const long long base = (long long)c * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x) {
+    d[base + i] = fmaf(a, p[base + i], d[base + i]);
+    const float v = fmaf(-a, q[base + i], r[base + i]);
+    r[base + i] = v;
+    x0[base + i] = omega * invd[i] * v;
+  }
+}
+
+// p = z + beta p in FP32 (p = z when beta = 0).
+__global__ void update_p32_kernel(long long n, const MgCtl* __restrict__ ctl, float* p, const float* __restrict__ z) {
+  if (ctl->stop) return;
+  const int c = blockIdx.y, nn = (int)n;
+  const float b = (float)ctl->sc[8 + c];
+  const long long base = (long long)c * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += gridDim.x * blockDim.x)
+    p[base + i] = b != 0.f ? fmaf(b, p[base + i], z[base + i]) : z[base + i];
+}
+
+// x += (double) d (end of an FP32 segment).
+__global__ void merge_kernel(long long n, double* x, const float* __restrict__ d) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
 // p = z + beta p (p = z at a segment start, beta = 0), p32 = (float) p.
 __global__ void update_p_kernel(long long n, const MgCtl* __restrict__ ctl, double* p, float* __restrict__ p32,
                                 const float* __restrict__ z) {
@@ -994,12 +1066,35 @@ cudaError_t mg_prep(cudaStream_t s, long long n, int nc, const double* r, float*
   prep_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, r, r32, x0, invd, omega);
   return cudaGetLastError();
 }
-cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const double* a1, const void* b1, bool b1_f32,
-                       const double* a2, const double* b2, double* part, MgCtl* ctl, int what, int* nblocks) {
+cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const void* a1, bool a_f32, const void* b1, bool b1_f32,
+                       const void* a2, const void* b2, double* part, MgCtl* ctl, int what, int* nblocks) {
   const int nb = (int)std::min<long long>(std::max<long long>((n + 1023) / 1024, 1), 2 * 152 / nc + 1);
-  if (b1_f32) dotscal_kernel<float><<<dim3(nb, nc), 256, 0, s>>>(n, a1, (const float*)b1, a2, b2, part, ctl, what);
-  else dotscal_kernel<double><<<dim3(nb, nc), 256, 0, s>>>(n, a1, (const double*)b1, a2, b2, part, ctl, what);
+  const dim3 grid(nb, nc);
+  if (a_f32 && b1_f32)
+    dotscal_kernel<float, float><<<grid, 256, 0, s>>>(n, (const float*)a1, (const float*)b1, (const float*)a2,
+                                                      (const float*)b2, part, ctl, what);
+  else if (a_f32)
+    return cudaErrorInvalidValue;
+  else if (b1_f32)
+    dotscal_kernel<double, float><<<grid, 256, 0, s>>>(n, (const double*)a1, (const float*)b1, (const double*)a2,
+                                                       (const double*)b2, part, ctl, what);
+  else
+    dotscal_kernel<double, double><<<grid, 256, 0, s>>>(n, (const double*)a1, (const double*)b1, (const double*)a2,
+                                                        (const double*)b2, part, ctl, what);
   if (nblocks) *nblocks = nb;
+  return cudaGetLastError();
+}
+cudaError_t mg_update32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* d, const float* p, float* r,
+                        const float* q, float* x0, const float* invd, float omega) {
+  update32_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, ctl, d, p, r, q, x0, invd, omega);
+  return cudaGetLastError();
+}
+cudaError_t mg_update_p32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* p, const float* z) {
+  update_p32_kernel<<<dim3(vblocks(n), nc), 256, 0, s>>>(n, ctl, p, z);
+  return cudaGetLastError();
+}
+cudaError_t mg_merge(cudaStream_t s, long long n, double* x, const float* d) {
+  merge_kernel<<<vblocks(n), 256, 0, s>>>(n, x, d);
   return cudaGetLastError();
 }
 cudaError_t mg_update_xr(cudaStream_t s, long long n, int nc, MgCtl* ctl, double* x, const double* p, double* r,

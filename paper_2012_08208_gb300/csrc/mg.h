@@ -52,27 +52,35 @@ struct MgHierarchy {
   float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
   const float* E0 = nullptr;
   // Finest-level sweep for all cases on the library's strain-form FP32
-  // operator: mode 1 y = u + omega D^-1 (b - A u), mode 2 y = b - A u (0 on
-  // fixed DOFs); returns at once when *stop is set.
-  cudaError_t (*fine_op_fn)(void* ctx, cudaStream_t s, const float* u, const float* b, const float* invd, float* y,
-                            int mode, float omega, const int* stop) = nullptr;
+  // operator: mode 1 y = a u + c w + om D^-1 (b - A u) (w may be null when
+  // c = 0; y may alias w), mode 2 y = b - A u; 0 on fixed DOFs; returns at
+  // once when *stop is set.
+  cudaError_t (*fine_op_fn)(void* ctx, cudaStream_t s, const float* u, const float* w, const float* b,
+                            const float* invd, float* y, int mode, float a, float c, float om,
+                            const int* stop) = nullptr;
   void* fine_ctx = nullptr;
-  cudaError_t fine_op(cudaStream_t s, const float* u, const float* b, const float* invd, float* y, int mode,
-                      const int* stop) const {
-    return fine_op_fn(fine_ctx, s, u, b, invd, y, mode, omega, stop);
-  }
   MgCtl* ctl = nullptr;     // device control block
   MgCtl* ctl_h = nullptr;   // pinned host mirror
-  float* p32 = nullptr;     // FP32 copy of the search direction (finest level, all cases)
+  float* p32 = nullptr;     // FP32 search direction (finest level, all cases)
   float* q32 = nullptr;     // FP32 K p
+  float* d32 = nullptr;     // FP32 correction of the current segment
   // CUDA graphs of kGraphIters PCG iterations, [FP64 operator][timed]
   static constexpr int kGraphIters = 8;
   cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int gx_launches[2][2] = {{0, 0}, {0, 0}};
   bool capture_events = false;  // record finest-sweep event pairs while capturing
   cudaStream_t cap = nullptr;   // capture stream of the graphs
-  float omega = 1.6f;       // l1-Jacobi weight (convergent for any weight below 2)
-  int nu = 2;               // sweeps before and after the coarse correction
+  // Smoother: Chebyshev iteration of degree nu on D_l1^-1 A, whose spectrum
+  // lies in (0, 1] (l1 row sums), for the interval [1 / cheb_ratio, 1].
+  // Step 1 from x: x + omega D^-1 (b - A x); step k >= 2 (x_k from x_{k-1}, x_{k-2}):
+  //   x_k = ca[k] x_{k-1} + cc[k] x_{k-2} + cw[k] D^-1 (b - A x_{k-1}).
+  // The same polynomial before and after the coarse correction keeps the
+  // V-cycle symmetric.
+  int nu = 2;
+  float cheb_ratio = 60.f;
+  float omega = 0.f;
+  float ca[8] = {}, cc[8] = {}, cw[8] = {};
+  void set_smoother(int degree, float ratio);
   bool built = false;
   long long version = -1;   // moduli version the operators were built for
   // optional timing of the finest level's operator launches (event pairs)
@@ -118,10 +126,18 @@ cudaError_t mg_seg_init(cudaStream_t s, MgCtl* ctl, int nc, double tol2, const d
 cudaError_t mg_prep(cudaStream_t s, long long n, int nc, const double* r, float* r32, float* x0, const float* invd,
                     float omega);
 // Per-case <a1, b1> (and <a2, b2>) in a fixed order, then the PCG scalars and,
-// for what 1, the stopping rule; b1 is FP32 when b1_f32.
+// for what 1, the stopping rule.  a1, a2, b2 are FP32 when a_f32 (then b1
+// must be FP32 too), b1 is FP32 when b1_f32; the rest FP64.
 //   what 0: pq -> alpha;  what 1: rz_new, rr -> beta, stop rule;  what 2: rz, rr, beta = 0 (segment start)
-cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const double* a1, const void* b1, bool b1_f32,
-                       const double* a2, const double* b2, double* part, MgCtl* ctl, int what, int* nblocks);
+cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const void* a1, bool a_f32, const void* b1, bool b1_f32,
+                       const void* a2, const void* b2, double* part, MgCtl* ctl, int what, int* nblocks);
+// FP32 inner iteration: d += alpha p, r -= alpha q, x0 = omega D^-1 r.
+cudaError_t mg_update32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* d, const float* p, float* r,
+                        const float* q, float* x0, const float* invd, float omega);
+// p = z + beta p in FP32 (p = z when beta = 0).
+cudaError_t mg_update_p32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* p, const float* z);
+// x += d over n values (end of an FP32 segment).
+cudaError_t mg_merge(cudaStream_t s, long long n, double* x, const float* d);
 // x += alpha p, r -= alpha q (q FP32 when q_f32), r32 = (float) r, x0 = omega D^-1 r32.
 cudaError_t mg_update_xr(cudaStream_t s, long long n, int nc, MgCtl* ctl, double* x, const double* p, double* r,
                          const void* q, bool q_f32, float* r32, float* x0, const float* invd, float omega);
