@@ -134,8 +134,8 @@ def run_ours(args):
             p.simp_step(opts, check=False)
             flush.add_(1.0)
         barrier()
-        if args.solver == 1:
-            p.set_profile(True)  # event pairs around the finest-level multigrid launches
+        if args.solver in (1, 2):
+            p.set_profile(True)  # event pairs around the dominant multigrid launches
         clocks = ClockSampler(local)
         clocks.start()
         launches0 = p.launch_count()
@@ -151,8 +151,8 @@ def run_ours(args):
         barrier()
         t_wall = time.perf_counter() - t_wall0
         launches = p.launch_count() - launches0
-        prof = p.get_profile() if args.solver == 1 else None
-        if args.solver == 1:
+        prof = p.get_profile() if args.solver in (1, 2) else None
+        if args.solver in (1, 2):
             p.set_profile(False)
         step_ms = [a.elapsed_time(b) for a, b in ev]
         # end-to-end through the public API with host buffers: H2D of the step's
@@ -193,16 +193,22 @@ def run_ours(args):
     # the library's CUDA-event pair around the cooperative launch on `stream`
     solve_ms = [i.solve.ms for i in infos]
     avg_ms = float(np.mean(solve_ms))
-    if args.solver == 1:
-        # dominant kernel: the finest-level operator launches of the multigrid
-        # V-cycles (l1-Jacobi sweeps and residuals), timed live by event pairs
+    if args.solver in (1, 2):
+        # dominant kernel, timed live by CUDA event pairs on the problem's
+        # stream: the finest-level sweep launches (event nodes in the replayed
+        # graph), or the persistent segment kernel (--solver 2)
         n_l, ms_l, bytes_l, levels = prof
-        achieved = bytes_l / (ms_l / max(n_l, 1) * 1e-3) / 1e9
-        roof_kernel = ("mg_sweep_kernel<2> (finest multigrid level: l1-Jacobi sweep or residual on the "
-                       "strain-form FP32 operator, 3 cases per launch, inside the graph-captured PCG iterations)")
+        achieved = bytes_l / (ms_l * 1e-3) / 1e9 if ms_l > 0 else 0.0
+        if args.solver == 1:
+            roof_kernel = ("mg_sweep_kernel<2> (finest multigrid level: Chebyshev step or residual on the strain-form "
+                           "FP32 operator, 3 cases per launch, graph-replayed PCG iterations)")
+            note = "see profiles/mg_sweep_cantilever2d_600x200.md"
+        else:
+            roof_kernel = ("mg_seg_kernel<2,4> (persistent multigrid-preconditioned CG segment: FP32 correction CG, "
+                           "Chebyshev V-cycle with grid barriers between phases, 3 cases)")
+            note = "see profiles/mg_seg_cantilever2d_600x200.md"
         roof_extra = {"launches_timed": n_l, "us_per_launch": round(1e3 * ms_l / max(n_l, 1), 3),
-                      "bytes_per_launch": bytes_l, "levels": levels,
-                      "traffic_note": "see profiles/mg_sweep_cantilever2d_600x200.md"}
+                      "bytes_per_launch": round(bytes_l / max(n_l, 1)), "levels": levels, "traffic_note": note}
     else:
         byts = [algorithmic_bytes_pcg(i.solve, w.n_dof, w.n_el, w.n_cases) for i in infos]
         avg_bytes = float(np.mean(byts))
@@ -223,7 +229,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "grid": "600x200 Q4", "n_dof": w.n_dof, "n_cases": w.n_cases,
                    "tol": w.tol, "precision": "FP32 operator + FP64 reductions/reliable updates",
                    "warm_start": "previous iteration's displacement", "l2": "flushed between timed steps",
-                   "solver": "multigrid-preconditioned CG (FP32 V-cycle, FP64 CG)" if args.solver == 1
+                   "solver": "multigrid-preconditioned CG (FP32 V-cycle, FP32 correction segments, FP64 restarts)"
+                   if args.solver in (1, 2)
                    else "Jacobi-PCG (persistent, FP32 + FP64 reliable updates)",
                    "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(ws * e2e_steps / t_e2e, 4), "unit": "SIMP iter/s",
@@ -458,8 +465,10 @@ def main():
     ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned", "cg2d", "cg3d"], default=None,
                     help="run one extra measurement alone (for profiling)")
     ap.add_argument("--copies", type=int, default=8)
-    ap.add_argument("--precond", type=int, default=0, help="0 Jacobi-PCG, 1 multigrid-PCG (--only cg2d / cg3d)")
-    ap.add_argument("--solver", type=int, default=1, help="solver of the timed SIMP step: 0 Jacobi-PCG, 1 multigrid-PCG")
+    ap.add_argument("--precond", type=int, default=0,
+                    help="0 Jacobi-PCG, 1 multigrid-PCG, 2 multigrid-PCG persistent kernel (--only cg2d / cg3d)")
+    ap.add_argument("--solver", type=int, default=1, help="solver of the timed SIMP step: 0 Jacobi-PCG, 1 multigrid-PCG, 2 the same with "
+                                                      "persistent segment kernels")
     ap.add_argument("--reps", type=int, default=10)
     args = ap.parse_args()
     if args.only:

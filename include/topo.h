@@ -58,13 +58,19 @@ typedef struct tp_params {
 enum { TP_PREC_F64 = 0, TP_PREC_MIXED = 1 };
 enum { TP_WARM_ZERO = 0, TP_WARM_PREVIOUS = 1, TP_WARM_USER = 2 };
 /* Preconditioner of tp_solve.  TP_PRECOND_JACOBI: the persistent Jacobi-PCG
- * described above.  TP_PRECOND_MG: CG in FP64 preconditioned by one geometric
+ * described above.  TP_PRECOND_MG: CG preconditioned by one geometric
  * multigrid V-cycle in FP32 per iteration (nested structured grids coarsened
  * 2:1 while the element counts are even, then by their smallest common odd
- * factor; Galerkin coarse operators; damped-Jacobi smoothing; exact solve on a
- * coarsest grid of at most 256 DOFs).  Needs element counts that reach such a
- * coarsest grid (else TP_ERR_ARG); `precision` and `update_drop` are ignored. */
-enum { TP_PRECOND_JACOBI = 0, TP_PRECOND_MG = 1 };
+ * factor; Galerkin coarse operators; degree-2 Chebyshev smoothing on the
+ * l1-Jacobi scaling; exact solve on a coarsest grid of at most 256 DOFs), in
+ * segments that solve for an FP32 correction and restart from the FP64 true
+ * residual (FP64 vectors and operator after a segment that gains less than
+ * 100x).  The iterations run as replays of a CUDA graph.
+ * TP_PRECOND_MG_FUSED: the same method with each FP32 segment in one
+ * persistent cooperative kernel.  Both need element counts that reach such a
+ * coarsest grid (else TP_ERR_ARG); `precision` = TP_PREC_F64 starts with FP64
+ * segments; `update_drop` is ignored. */
+enum { TP_PRECOND_JACOBI = 0, TP_PRECOND_MG = 1, TP_PRECOND_MG_FUSED = 2 };
 enum { TP_FILTER_SENSITIVITY = 0, TP_FILTER_DENSITY = 1 };
 /* Quantities for tp_get / tp_set (all FP64):
  *   TP_RHO   design densities rho[n_el]
@@ -95,7 +101,7 @@ typedef struct tp_solve_opts {
   double update_drop;
   double warm_max_rel;  /* TP_WARM_USER: largest accepted starting true relative
                            residual (0 means 1, i.e. no worse than u = 0) */
-  int precond;          /* TP_PRECOND_JACOBI (default) or TP_PRECOND_MG */
+  int precond;          /* TP_PRECOND_JACOBI (default), TP_PRECOND_MG or TP_PRECOND_MG_FUSED */
 } tp_solve_opts;
 
 typedef struct tp_solve_info {
@@ -289,13 +295,17 @@ tp_status tp_oc_update_noalloc(const double* rho, const double* dcf, const int8_
 tp_status tp_set_trace(tp_problem* p, int enable);
 tp_status tp_get_trace(tp_problem* p, long long* out);
 
-/* Launch timing of the multigrid solver's finest-level operator (profiling
- * aid).  When enabled, every finest-level smoothing / residual launch of
- * TP_PRECOND_MG solves is bracketed by a CUDA event pair on the problem's
- * stream; tp_get_profile writes out[4] (host): the number of timed launches,
- * their total device time in ms, the algorithmic bytes of one launch (the
- * finest level's operator data, plus per case u read, b read and y written, and
- * one scale per DOF) and the number of levels.  Enabling resets the totals. */
+/* Launch timing of the multigrid solver (profiling aid).  When enabled, the
+ * dominant kernel of each multigrid solve is bracketed by CUDA event pairs on
+ * the problem's stream: with TP_PRECOND_MG every finest-level sweep launch
+ * (mg_sweep_kernel; event nodes in the replayed graph), with
+ * TP_PRECOND_MG_FUSED every persistent segment launch.  tp_get_profile writes
+ * out[4] (host): the number of timed launches, their total device time in ms,
+ * their total algorithmic bytes (a sweep: the finest moduli and l1 scale, per
+ * case u and b read and y written; a segment: one V-cycle plus, per CG
+ * iteration, a V-cycle, the operator phase and the vector update, each value
+ * read or written once per phase and operator data once per sweep) and the
+ * number of multigrid levels.  Enabling resets the totals. */
 tp_status tp_set_profile(tp_problem* p, int enable);
 tp_status tp_get_profile(tp_problem* p, double* out);
 

@@ -117,17 +117,24 @@ static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, const f
                          stop);
 }
 
-// CG in FP64 preconditioned by one FP32 multigrid V-cycle per iteration
-// (TP_PRECOND_MG).  Vectors in the ABI layout; the solution ends in x64.
+// CG preconditioned by one FP32 multigrid V-cycle per iteration
+// (TP_PRECOND_MG, TP_PRECOND_MG_FUSED).  Vectors in the ABI layout; the
+// solution ends in x64.
 //
-// The iterations run as replays of a CUDA graph of MgHierarchy::kGraphIters
-// iterations.  The scalar kernel at the end of each iteration evaluates the
-// stopping rule on the device and sets a stop flag; every later kernel of the
-// segment then returns at once, so the host synchronises once per replay
-// instead of once per iteration.  Segments end at the tolerance or when the
-// FP32 operator's error may dominate the recurrence; each is followed by an
-// FP64 true residual (restart).
+// The solve is a sequence of segments, each followed by an FP64 true residual
+// (restart).  A segment solves K d = r for a correction d with FP32 vectors
+// and the FP32 operator and ends with x += d; after a segment that gained less
+// than 100x, the segments switch to FP64 vectors and the FP64 operator.  A
+// segment stops at the tolerance, when the FP32 operator's error may dominate
+// the recurrence, on stagnation, breakdown or the iteration limit; the rule is
+// evaluated on the device after every iteration.
+//   TP_PRECOND_MG: the iterations run as replays of a CUDA graph of
+//     MgHierarchy::kGraphIters iterations; after the stop every later kernel
+//     of the replay returns at once, and the host synchronises once per replay.
+//   TP_PRECOND_MG_FUSED: an FP32 segment is one persistent cooperative kernel
+//     (mg_pcg.cu) with grid barriers between its phases.
 static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info) {
+  const bool fused = opts->precond == TP_PRECOND_MG_FUSED;
   tp_status st = ensure_E(p);
   if (st != TP_OK) return st;
   if (!p->mg) {
@@ -144,10 +151,8 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   }
   MgHierarchy& M = *p->mg;
   const int kIt = MgHierarchy::kGraphIters;
-  if (p->profile && M.ev.empty()) {
-    M.ev.resize(2 * 2 * M.nu * kIt);  // an event pair per finest-level sweep of one graph
+  if (p->profile && !M.ev[0])
     for (auto& ev : M.ev) TPCK(cudaEventCreate(&ev), "event");
-  }
   M.timing = p->profile;
   M.fine_op_fn = mg_fine_op;
   M.fine_ctx = p;
@@ -218,15 +223,21 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     *nlk += 2;
     return e;
   };
+  // The graph of kGraphIters iterations for u64, with the finest sweeps
+  // bracketed by event nodes when timing.
   auto graph = [&](bool u64) -> tp_status {
     const int gi = u64 ? 1 : 0, gt = M.timing ? 1 : 0;
     if (M.gx[gi][gt]) return TP_OK;
+    if (gt && M.sweep_ev.empty()) {
+      M.sweep_ev.resize(2 * 2 * M.nu * kIt);  // an event pair per finest-level sweep of the graph
+      for (auto& ev : M.sweep_ev) TPCK(cudaEventCreate(&ev), "event");
+    }
     // captured on a private stream (the problem's stream may be the legacy
     // default stream, which cannot be captured), replayed on the problem's
     if (!M.cap) TPCK(cudaStreamCreateWithFlags(&M.cap, cudaStreamNonBlocking), "stream");
     TPCK(cudaStreamBeginCapture(M.cap, cudaStreamCaptureModeRelaxed), "graph capture");
-    M.capture_events = M.timing;
-    if (M.timing) M.ev_used = 0;
+    M.capture_events = gt != 0;
+    if (gt) M.ev_used = 0;
     int nlk = 0;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kIt && e == cudaSuccess; k++) e = issue_iter(M.cap, u64, &nlk);
@@ -269,35 +280,60 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   // eps32 * cond(K) is not small)
   bool use64 = opts->precision == TP_PREC_F64;
   while (!conv && it < opts->max_it && !brk) {
-    // segment start from the current residual: z = V(r), p = z (d = 0)
+    // segment start from the current residual: r32 = r, the first smoothing
+    // step, d = 0; then z = V(r), p = z
     TPCK(mg_seg_init(s, ctl, nc, opts->tol * opts->tol, p->ff, opts->max_it - it, use64 ? 1 : 0), "control kernel");
     TPCK(mg_prep(s, n, nc, r, r32, l0.x[0], l0.invd, M.omega), "convert kernel");
     nl += 2;
-    TPCK(M.vcycle(s, 0, &nl, nullptr, &z32), "v-cycle");
-    if (use64) {
-      TPCK(mg_dotscal(s, n, nc, r, false, z32, true, r, r, p->part, ctl, 2, nullptr), "dot kernel");
-      TPCK(mg_update_p(s, n, nc, ctl, pp, M.p32, z32), "update kernel");
-    } else {
-      TPCK(cudaMemsetAsync(M.d32, 0, (size_t)nc * n * sizeof(float), s), "memset");
-      TPCK(mg_dotscal(s, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 2, nullptr), "dot kernel");
-      TPCK(mg_update_p32(s, n, nc, ctl, M.p32, z32), "update kernel");
-    }
-    nl += 2;
-    st = graph(use64);
-    if (st != TP_OK) return st;
-    const int gi = use64 ? 1 : 0, gt = M.timing ? 1 : 0;
     int seg_it = 0;
-    for (;;) {
-      TPCK(cudaGraphLaunch(M.gx[gi][gt], s), "graph launch");
-      nl += M.gx_launches[gi][gt];
+    if (!use64 && fused) {
+      // FP32 segment as one persistent cooperative launch
+      TPCK(cudaMemsetAsync(M.d32, 0, (size_t)nc * n * sizeof(float), s), "memset");
+      if (M.timing) TPCK(cudaEventRecord(M.ev[0], s), "event");
+      int grid = 0;
+      TPCK(launch_mg_segment(s, M, p->C.data(), p->E32, p->zlen, p->part, p->bar, p->trace, p->nsm, &grid),
+           "multigrid kernel");
+      if (M.timing) TPCK(cudaEventRecord(M.ev[1], s), "event");
+      nl++;
       TPCK(cudaMemcpyAsync(M.ctl_h, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s), "copy");
       TPCK(cudaStreamSynchronize(s), "sync");
-      const int now = M.ctl_h->it;
-      if (M.timing) M.collect_timing((now - seg_it) * 2 * M.nu);
-      const bool advanced = now > seg_it;
-      seg_it = now;
-      if (M.ctl_h->stop) break;
-      if (!advanced) return fail(p, TP_ERR_CUDA, "multigrid PCG graph made no progress");
+      if (M.ctl_h->timeout) return fail(p, TP_ERR_TIMEOUT, "multigrid PCG kernel: grid barrier timed out");
+      seg_it = M.ctl_h->it;
+      if (M.timing) {
+        float ms = 0.f;
+        TPCK(cudaEventElapsedTime(&ms, M.ev[0], M.ev[1]), "event");
+        M.timed_ms += ms;
+        M.timed_launches++;
+        M.timed_bytes += M.vcycle_bytes() + seg_it * M.iter_bytes();
+      }
+    } else {
+      // segment start z = V(r), p = z (d = 0), then replays of the graph of
+      // kGraphIters iterations with the device-side stop flag
+      TPCK(M.vcycle(s, 0, &nl, nullptr, &z32), "v-cycle");
+      if (use64) {
+        TPCK(mg_dotscal(s, n, nc, r, false, z32, true, r, r, p->part, ctl, 2, nullptr), "dot kernel");
+        TPCK(mg_update_p(s, n, nc, ctl, pp, M.p32, z32), "update kernel");
+      } else {
+        TPCK(cudaMemsetAsync(M.d32, 0, (size_t)nc * n * sizeof(float), s), "memset");
+        TPCK(mg_dotscal(s, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 2, nullptr), "dot kernel");
+        TPCK(mg_update_p32(s, n, nc, ctl, M.p32, z32), "update kernel");
+      }
+      nl += 2;
+      st = graph(use64);
+      if (st != TP_OK) return st;
+      const int gi = use64 ? 1 : 0, gt = M.timing ? 1 : 0;
+      for (;;) {
+        TPCK(cudaGraphLaunch(M.gx[gi][gt], s), "graph launch");
+        nl += M.gx_launches[gi][gt];
+        TPCK(cudaMemcpyAsync(M.ctl_h, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s), "copy");
+        TPCK(cudaStreamSynchronize(s), "sync");
+        const int now = M.ctl_h->it;
+        if (gt) M.collect_sweeps((now - seg_it) * 2 * M.nu);  // sweeps of the iterations that ran
+        const bool advanced = now > seg_it;
+        seg_it = now;
+        if (M.ctl_h->stop) break;
+        if (!advanced) return fail(p, TP_ERR_CUDA, "multigrid PCG graph made no progress");
+      }
     }
     it += seg_it;
     brk = (M.ctl_h->reason & MG_STOP_BREAK) != 0;
@@ -471,7 +507,7 @@ tp_status tp_set_profile(tp_problem* p, int enable) {
   p->profile = enable != 0;
   if (p->mg) {
     p->mg->timed_launches = 0;
-    p->mg->timed_ms = 0.0;
+    p->mg->timed_ms = p->mg->timed_bytes = 0.0;
   }
   return TP_OK;
 }
@@ -482,7 +518,7 @@ tp_status tp_get_profile(tp_problem* p, double* out) {
   if (p->mg) {
     out[0] = (double)p->mg->timed_launches;
     out[1] = p->mg->timed_ms;
-    out[2] = p->mg->fine_bytes();
+    out[2] = p->mg->timed_bytes;
     out[3] = (double)p->mg->lv.size();
   }
   return TP_OK;
@@ -580,9 +616,9 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
     return fail(p, TP_ERR_ARG, "unknown warm_start");
   if (opts->warm_start == TP_WARM_USER && !p->has_u)
     return fail(p, TP_ERR_STATE, "TP_WARM_USER needs tp_set(TP_U, ...) first");
-  if (opts->precond != TP_PRECOND_JACOBI && opts->precond != TP_PRECOND_MG)
+  if (opts->precond != TP_PRECOND_JACOBI && opts->precond != TP_PRECOND_MG && opts->precond != TP_PRECOND_MG_FUSED)
     return fail(p, TP_ERR_ARG, "unknown preconditioner");
-  if (opts->precond == TP_PRECOND_MG) return mg_solve(p, opts, info);
+  if (opts->precond == TP_PRECOND_MG || opts->precond == TP_PRECOND_MG_FUSED) return mg_solve(p, opts, info);
   double drop = opts->update_drop;
   if (opts->precision == TP_PREC_MIXED) {
     if (drop == 0.0) drop = 1e-2;

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "mg.h"
+#include "mg_ops.cuh"
 
 namespace tp {
 namespace {
@@ -32,9 +33,8 @@ struct MgC {
 
 __constant__ float c_K0[24 * 24];  // level-0 element matrix (unit modulus), row-major
 
-__device__ __forceinline__ long long node_index(const Grid& g, int i, int j, int k) {
-  return i + (long long)g.nx * (j + (long long)g.ny * k);
-}
+using mgops::node_index;
+using mgops::w1;
 
 // Element matrix entry (row a, column b) of element e on a level.
 template <int DIM>
@@ -90,61 +90,17 @@ __global__ void stencil_kernel(Grid g, const float* __restrict__ K, const float*
   }
 }
 
-// y = A u on a coarse level from its assembled form (node-centric; fixed DOFs
-// read as 0), fused into a smoothing step or a residual:
-//   mode 1: y = ca u + cc w + om D^-1 (b - A u)   (Chebyshev step; w may be null)
-//   mode 2: y = b - A u                            (residual)
-// 0 on fixed DOFs.  One thread per node and case (blockIdx.y = case).
+// Chebyshev step / residual on an assembled coarse level (mgops::stencil_node);
+// one thread per node and case (blockIdx.y = case).
 template <int DIM>
 __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
-                                     const float* __restrict__ invd, const float* __restrict__ u, const float* w,
-                                     const float* __restrict__ b, float* y, int mode, float ca, float cc, float om,
-                                     const int* __restrict__ stop) {
+                                     const float* __restrict__ invd, const float* u, const float* w, const float* b,
+                                     float* y, int mode, float ca, float cc, float om, const int* __restrict__ stop) {
   if (halted(stop)) return;
-  const int nn = (int)g.nn, nxy = g.nx * g.ny;
-  const long long ndof = (long long)nn * DIM;
-  const float* uc = u + blockIdx.y * ndof;
-  const float* bc = b + blockIdx.y * ndof;
-  const float* wc = w ? w + blockIdx.y * ndof : nullptr;
-  float* yc = y + blockIdx.y * ndof;
-  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
-    const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
-    float acc[DIM];
-#pragma unroll
-    for (int r = 0; r < DIM; r++) acc[r] = 0.f;
-#pragma unroll
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
-      if (k + dz < 0 || k + dz >= g.nz) continue;
-#pragma unroll
-      for (int dy = -1; dy <= 1; dy++) {
-        if (j + dy < 0 || j + dy >= g.ny) continue;
-#pragma unroll
-        for (int dx = -1; dx <= 1; dx++) {
-          if (i + dx < 0 || i + dx >= g.nx) continue;
-          const int nbr = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
-          const int n2 = nd + dx + g.nx * dy + nxy * dz;
-#pragma unroll
-          for (int s2 = 0; s2 < DIM; s2++) {
-            const float v = uc[(long long)n2 * DIM + s2];
-#pragma unroll
-            for (int r = 0; r < DIM; r++) acc[r] = fmaf(S[((long long)(nbr * DIM + r) * DIM + s2) * nn + nd], v, acc[r]);
-          }
-        }
-      }
-    }
-    const uint8_t mk = mask[nd];
-#pragma unroll
-    for (int r = 0; r < DIM; r++) {
-      const long long idx = (long long)nd * DIM + r;
-      const float res = bc[idx] - acc[r];
-      float out = res;
-      if (mode == 1) {
-        out = fmaf(ca, uc[idx], om * invd[idx] * res);
-        if (wc) out = fmaf(cc, wc[idx], out);  // w read at this DOF only: y may alias w
-      }
-      yc[idx] = ((mk >> r) & 1) ? 0.f : out;
-    }
-  }
+  const int nn = (int)g.nn;
+  const long long off = (long long)blockIdx.y * nn * DIM;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x)
+    mgops::stencil_node<DIM, false>(g, S, mask, invd, u, w, b, y, mode, ca, cc, om, nd, off);
 }
 
 // Inverse l1 row sums from the assembled form (see diag_kernel).
@@ -210,8 +166,6 @@ __global__ void coarse_mask_kernel(Grid gf, Grid gc, int f, const uint8_t* __res
   }
 }
 
-// 1D multilinear weight of coarse corner offset `o` (0 or 1) at fine position t in [0, f].
-__device__ __forceinline__ float w1(int o, int t, int f) { return o ? (float)t / f : 1.f - (float)t / f; }
 
 // Galerkin coarse element matrices: one CTA per coarse element, one thread per
 // entry.  For each child c (fine DOFs masked), with Phi_c[n][C] the weight of
@@ -272,154 +226,49 @@ __global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict
   Kc[ec * ND * ND + t] = acc;
 }
 
-// b_c = P^T r_f for f = 2 (3^dim fine neighbours): one thread per coarse node.
-// With x0 given, also the coarse level's first sweep from zero,
-// x0 = omega D^-1 b_c.
+// Restriction (mgops::restrict2_node, restrict_warp) with the coarse level's
+// first smoothing step when x0 is given; blockIdx.y = case.
 template <int DIM>
 __global__ void restrict2_kernel(Grid gf, Grid gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                                 const float* __restrict__ rf, float* __restrict__ bc, float* __restrict__ x0,
-                                 const float* __restrict__ invd, float omega, const int* __restrict__ stop) {
+                                 const float* rf, float* bc, float* x0, const float* __restrict__ invd, float omega,
+                                 const int* __restrict__ stop) {
   if (halted(stop)) return;
-  const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
-  const float* r = rf + blockIdx.y * ndf;
-  float* out = bc + blockIdx.y * ndc;
-  float* xo = x0 ? x0 + blockIdx.y * ndc : nullptr;
-  const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
-  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
-    const int Kz = nd / nxy, rem = nd - Kz * nxy, J = rem / gc.nx, I = rem - J * gc.nx;
-    float acc[DIM];
-#pragma unroll
-    for (int s2 = 0; s2 < DIM; s2++) acc[s2] = 0.f;
-#pragma unroll
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
-      const int fk = 2 * Kz + dz;
-      if (fk < 0 || fk >= gf.nz) continue;
-#pragma unroll
-      for (int dy = -1; dy <= 1; dy++) {
-        const int fj = 2 * J + dy;
-        if (fj < 0 || fj >= gf.ny) continue;
-#pragma unroll
-        for (int dx = -1; dx <= 1; dx++) {
-          const int fi = 2 * I + dx;
-          if (fi < 0 || fi >= gf.nx) continue;
-          const float wgt = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f);
-          const long long n2 = node_index(gf, fi, fj, fk);
-          const uint8_t m2 = mf[n2];
-#pragma unroll
-          for (int s2 = 0; s2 < DIM; s2++)
-            if (!((m2 >> s2) & 1)) acc[s2] = fmaf(wgt, r[n2 * DIM + s2], acc[s2]);
-        }
-      }
-    }
-    const uint8_t mk = mc[nd];
-#pragma unroll
-    for (int s2 = 0; s2 < DIM; s2++) {
-      const long long idx = (long long)nd * DIM + s2;
-      const float v = ((mk >> s2) & 1) ? 0.f : acc[s2];
-      out[idx] = v;
-      if (xo) xo[idx] = omega * invd[idx] * v;
-    }
-  }
+  const long long offf = (long long)blockIdx.y * gf.nn * DIM, offc = (long long)blockIdx.y * gc.nn * DIM;
+  const int nn = (int)gc.nn;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x)
+    mgops::restrict2_node<DIM, false>(gf, gc, mf, mc, rf, bc, x0, invd, omega, nd, offf, offc);
 }
 
-// b_c = P^T r_f (fine fixed DOFs read as 0, coarse fixed DOFs set to 0).  One
-// warp per coarse node: the lanes split the (2f - 1)^dim fine neighbours and
-// the sum is reduced in a fixed order.
-// x0 as in restrict2_kernel.
 template <int DIM>
 __global__ void restrict_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                                const float* __restrict__ rf, float* __restrict__ bc, float* __restrict__ x0,
-                                const float* __restrict__ invd, float omega, const int* __restrict__ stop) {
+                                const float* rf, float* bc, float* x0, const float* __restrict__ invd, float omega,
+                                const int* __restrict__ stop) {
   if (halted(stop)) return;
-  const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
-  const float* r = rf + blockIdx.y * ndf;
-  float* out = bc + blockIdx.y * ndc;
-  float* xo = x0 ? x0 + blockIdx.y * ndc : nullptr;
-  const int lane = threadIdx.x & 31;
-  const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
-  const int w = 2 * f - 1, nz = DIM == 3 ? w : 1, tot = w * w * nz;
-  for (int nd = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; nd < nn; nd += (gridDim.x * blockDim.x) >> 5) {
-    const int Kz = nd / nxy, rem = nd - Kz * nxy, J = rem / gc.nx, I = rem - J * gc.nx;
-    float acc[DIM];
-#pragma unroll
-    for (int s2 = 0; s2 < DIM; s2++) acc[s2] = 0.f;
-    for (int q = lane; q < tot; q += 32) {
-      const int dx = q % w - (f - 1), dy = (q / w) % w - (f - 1), dz = DIM == 3 ? q / (w * w) - (f - 1) : 0;
-      const int fi = f * I + dx, fj = f * J + dy, fk = f * Kz + dz;
-      if (fi < 0 || fi >= gf.nx || fj < 0 || fj >= gf.ny || fk < 0 || fk >= gf.nz) continue;
-      float wgt = (1.f - fabsf((float)dx) / f) * (1.f - fabsf((float)dy) / f);
-      if (DIM == 3) wgt *= 1.f - fabsf((float)dz) / f;
-      const long long n2 = node_index(gf, fi, fj, fk);
-      const uint8_t m2 = mf[n2];
-#pragma unroll
-      for (int s2 = 0; s2 < DIM; s2++)
-        if (!((m2 >> s2) & 1)) acc[s2] = fmaf(wgt, r[n2 * DIM + s2], acc[s2]);
-    }
-#pragma unroll
-    for (int s2 = 0; s2 < DIM; s2++)
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc[s2] += __shfl_xor_sync(0xffffffffu, acc[s2], o);
-    if (lane == 0) {
-      const uint8_t mk = mc[nd];
-#pragma unroll
-      for (int s2 = 0; s2 < DIM; s2++) {
-        const long long idx = (long long)nd * DIM + s2;
-        const float v = ((mk >> s2) & 1) ? 0.f : acc[s2];
-        out[idx] = v;
-        if (xo) xo[idx] = omega * invd[idx] * v;
-      }
-    }
-  }
+  const long long offf = (long long)blockIdx.y * gf.nn * DIM, offc = (long long)blockIdx.y * gc.nn * DIM;
+  const int nn = (int)gc.nn, lane = threadIdx.x & 31;
+  for (int nd = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; nd < nn; nd += (gridDim.x * blockDim.x) >> 5)
+    mgops::restrict_warp<DIM, false>(gf, gc, f, mf, mc, rf, bc, x0, invd, omega, nd, offf, offc, lane);
 }
 
-// x_f += P x_c on free fine DOFs.
+// x_f += P x_c on free fine DOFs (mgops::prolong_node); blockIdx.y = case.
 template <int DIM>
-__global__ void prolong_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, const float* __restrict__ xc,
-                               float* __restrict__ xf, const int* __restrict__ stop) {
+__global__ void prolong_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, const float* xc, float* xf,
+                               const int* __restrict__ stop) {
   if (halted(stop)) return;
-  constexpr int NC = MgC<DIM>::NC;
-  const long long ndf = gf.nn * DIM, ndc = gc.nn * DIM;
-  const float* x = xc + blockIdx.y * ndc;
-  float* out = xf + blockIdx.y * ndf;
-  const int nn = (int)gf.nn, nxy = gf.nx * gf.ny;
-  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
-    const int k = nd / nxy, rem = nd - k * nxy, j = rem / gf.nx, i = rem - j * gf.nx;
-    const int I = min(i / f, gc.ex - 1), J = min(j / f, gc.ey - 1), Kz = DIM == 3 ? min(k / f, gc.ez - 1) : 0;
-    const int tx = i - f * I, ty = j - f * J, tz = k - f * Kz;
-    float acc[DIM];
-#pragma unroll
-    for (int s = 0; s < DIM; s++) acc[s] = 0.f;
-#pragma unroll
-    for (int C = 0; C < NC; C++) {
-      float wgt = w1(cofs(C, 0), tx, f) * w1(cofs(C, 1), ty, f);
-      if (DIM == 3) wgt *= w1(cofs(C, 2), tz, f);
-      if (wgt == 0.f) continue;
-      const long long n2 = node_index(gc, I + cofs(C, 0), J + cofs(C, 1), Kz + (DIM == 3 ? cofs(C, 2) : 0));
-#pragma unroll
-      for (int s = 0; s < DIM; s++) acc[s] = fmaf(wgt, x[n2 * DIM + s], acc[s]);
-    }
-    const uint8_t mk = mf[nd];
-#pragma unroll
-    for (int s = 0; s < DIM; s++)
-      if (!((mk >> s) & 1)) out[nd * DIM + s] += acc[s];
-  }
+  const long long offf = (long long)blockIdx.y * gf.nn * DIM, offc = (long long)blockIdx.y * gc.nn * DIM;
+  const int nn = (int)gf.nn;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x)
+    mgops::prolong_node<DIM, false>(gf, gc, f, mf, xc, xf, nd, offf, offc);
 }
 
-// Coarsest solve: x = A^-1 b with the dense inverse; one warp per row
-// (blockIdx.y = case).
-__global__ void dense_solve_kernel(int n, const float* __restrict__ Ainv, const float* __restrict__ b, float* __restrict__ x,
+// Coarsest solve: x = A^-1 b with the dense inverse (mgops::dense_row); one
+// warp per row, blockIdx.y = case.
+__global__ void dense_solve_kernel(int n, const float* __restrict__ Ainv, const float* b, float* x,
                                    const int* __restrict__ stop) {
   if (halted(stop)) return;
-  const float* bc = b + (long long)blockIdx.y * n;
-  float* xc = x + (long long)blockIdx.y * n;
   const int lane = threadIdx.x & 31;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
-    float s = 0.f;
-    for (int j = lane; j < n; j += 32) s = fmaf(Ainv[(long long)i * n + j], bc[j], s);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) xc[i] = s;
-  }
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5)
+    mgops::dense_row<false>(n, Ainv, b, x, i, (long long)blockIdx.y * n, lane);
 }
 
 int blocks(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
@@ -483,6 +332,28 @@ bool spd_inverse(std::vector<double>& A, int n) {
 
 // ---------------------------------------------------------------------------
 
+double MgHierarchy::vcycle_bytes() const {
+  const int dim = lv[0].g.dim, L = (int)lv.size();
+  const double nbr = dim == 2 ? 9.0 * 4.0 : 27.0 * 9.0;  // coupling entries per node of an assembled level
+  double total = 0.0;
+  for (int li = 0; li + 1 < L; li++) {
+    const MgLevel& l = lv[li];
+    const double nodes = (double)l.g.nn, vals = (double)nc * nodes * dim;
+    // operator data of one sweep: moduli (finest) or assembled blocks, plus the scale
+    const double op = (li == 0 ? 4.0 * l.g.ne : 4.0 * nbr * nodes) + 4.0 * nodes * dim;
+    // Chebyshev steps before (nu - 1), residual, after (nu): u, b read, y
+    // written; w read by the steps that use x_{k-2}
+    const int steps = 2 * nu, w_reads = std::max(0, nu - 2) + (nu - 1);
+    total += steps * (op + 12.0 * vals) + w_reads * 4.0 * vals;
+    const MgLevel& c = lv[li + 1];
+    const double cvals = (double)nc * c.g.nn * dim;
+    total += 4.0 * vals + 8.0 * cvals;   // restriction: r read, b (and x0) written
+    total += 8.0 * vals + 4.0 * cvals;   // prolongation: x read and written, coarse x read
+  }
+  total += 4.0 * (double)cn * cn + 8.0 * nc * cn;  // dense coarsest solve
+  return total;
+}
+
 double MgHierarchy::fine_bytes() const {
   const MgLevel& l = lv[0];
   // finest-level sweep: moduli and the l1 scale once per launch; per case u
@@ -490,15 +361,24 @@ double MgHierarchy::fine_bytes() const {
   return (double)l.g.ne * 4.0 + (double)l.g.nn * l.g.dim * 4.0 * (1 + 3 * nc);
 }
 
-void MgHierarchy::collect_timing(int npairs) {
-  for (int k = 0; k < npairs && 2 * k + 1 < (int)ev.size(); k++) {
+void MgHierarchy::collect_sweeps(int npairs) {
+  for (int k = 0; k < npairs && 2 * k + 1 < (int)sweep_ev.size(); k++) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]) == cudaSuccess) {
+    if (cudaEventElapsedTime(&ms, sweep_ev[2 * k], sweep_ev[2 * k + 1]) == cudaSuccess) {
       timed_ms += ms;
       timed_launches++;
+      timed_bytes += fine_bytes();
     }
   }
   cudaGetLastError();
+}
+
+double MgHierarchy::iter_bytes() const {
+  const MgLevel& l = lv[0];
+  const double vals = (double)nc * l.g.nn * l.g.dim;
+  // operator phase: moduli, z and p_old read, q and p_new written; update: d,
+  // p, q, r read, d, r, x0 written, the scale once
+  return vcycle_bytes() + (4.0 * l.g.ne + 16.0 * vals) + (28.0 * vals + 4.0 * l.g.nn * l.g.dim);
 }
 
 void MgHierarchy::drop_graphs() {
@@ -513,8 +393,12 @@ void MgHierarchy::release() {
   drop_graphs();
   if (cap) cudaStreamDestroy(cap);
   cap = nullptr;
-  for (auto& e : ev) cudaEventDestroy(e);
-  ev.clear();
+  for (auto& e : ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
+  for (auto& e : sweep_ev) cudaEventDestroy(e);
+  sweep_ev.clear();
   ev_used = 0;
   for (auto& l : lv) {
     void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t};
@@ -522,14 +406,14 @@ void MgHierarchy::release() {
       if (q) cudaFree(q);
   }
   lv.clear();
-  for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32, (void*)d32})
+  for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32, (void*)d32, (void*)p32b})
     if (q) cudaFree(q);
   if (ctl_h) cudaFreeHost(ctl_h);
   cinv = nullptr;
   K0d = nullptr;
   ctl = nullptr;
   ctl_h = nullptr;
-  p32 = q32 = d32 = nullptr;
+  p32 = q32 = d32 = p32b = nullptr;
   built = false;
 }
 
@@ -595,6 +479,7 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
   if (e == cudaSuccess) e = cudaMalloc((void**)&p32, nv * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&q32, nv * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&d32, nv * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&p32b, nv * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&ctl, sizeof(MgCtl));
   if (e == cudaSuccess) e = cudaMemset(ctl, 0, sizeof(MgCtl));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctl_h, sizeof(MgCtl));
@@ -695,8 +580,8 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
     return cudaGetLastError();
   }
   auto sweep = [&](const float* u, const float* w, float* y, int mode, float a, float c, float om) -> cudaError_t {
-    const bool tm = capture_events && li == 0 && ev_used + 2 <= (int)ev.size();
-    if (tm) cudaEventRecordWithFlags(ev[ev_used], s, cudaEventRecordExternal);
+    const bool tm = capture_events && li == 0 && ev_used + 2 <= (int)sweep_ev.size();
+    if (tm) cudaEventRecordWithFlags(sweep_ev[ev_used], s, cudaEventRecordExternal);
     cudaError_t e;
     if (li == 0) {
       e = fine_op_fn(fine_ctx, s, u, w, l.b, l.invd, y, mode, a, c, om, stop);
@@ -709,7 +594,7 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
       e = cudaGetLastError();
     }
     if (tm) {
-      cudaEventRecordWithFlags(ev[ev_used + 1], s, cudaEventRecordExternal);
+      cudaEventRecordWithFlags(sweep_ev[ev_used + 1], s, cudaEventRecordExternal);
       ev_used += 2;
     }
     (*nlaunch)++;

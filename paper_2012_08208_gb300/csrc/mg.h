@@ -41,6 +41,7 @@ struct MgCtl {
   int reason;          // MG_STOP_* bits
   int use64;           // FP64 operator (the FP32-accuracy rule does not apply)
   int nc;
+  int timeout;         // set by the persistent kernel when a grid barrier timed out
   unsigned ticket;     // last-block counter of the fused dot/scalar kernel (0 between launches)
 };
 enum : int { MG_STOP_DONE = 1, MG_STOP_INNER = 2, MG_STOP_STALL = 4, MG_STOP_BREAK = 8, MG_STOP_LIMIT = 16 };
@@ -64,11 +65,11 @@ struct MgHierarchy {
   float* p32 = nullptr;     // FP32 search direction (finest level, all cases)
   float* q32 = nullptr;     // FP32 K p
   float* d32 = nullptr;     // FP32 correction of the current segment
+  float* p32b = nullptr;    // second FP32 search-direction buffer (persistent kernel)
   // CUDA graphs of kGraphIters PCG iterations, [FP64 operator][timed]
   static constexpr int kGraphIters = 8;
   cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int gx_launches[2][2] = {{0, 0}, {0, 0}};
-  bool capture_events = false;  // record finest-sweep event pairs while capturing
   cudaStream_t cap = nullptr;   // capture stream of the graphs
   // Smoother: Chebyshev iteration of degree nu on D_l1^-1 A, whose spectrum
   // lies in (0, 1] (l1 row sums), for the interval [1 / cheb_ratio, 1].
@@ -83,14 +84,23 @@ struct MgHierarchy {
   void set_smoother(int degree, float ratio);
   bool built = false;
   long long version = -1;   // moduli version the operators were built for
-  // optional timing of the finest level's operator launches (event pairs)
+  // Optional timing (profiling aid): the persistent segment launches (an
+  // event pair each), or in the graph path the finest-level sweeps (event
+  // nodes captured into the timed graph, read after each replay).
   bool timing = false;
-  std::vector<cudaEvent_t> ev;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> sweep_ev;
   int ev_used = 0;
+  bool capture_events = false;
   long long timed_launches = 0;
-  double timed_ms = 0.0;
-  double fine_bytes() const;  // algorithmic bytes of one finest-level sweep launch
-  void collect_timing(int npairs);  // the first npairs event pairs, after the stream has synchronised
+  double timed_ms = 0.0, timed_bytes = 0.0;
+  double fine_bytes() const;          // algorithmic bytes of one finest-level sweep launch
+  void collect_sweeps(int npairs);    // the first npairs sweep event pairs (stream synchronised)
+  // Algorithmic bytes (each value read or written once per phase; operator
+  // data once per sweep) of one V-cycle, and of one FP32 PCG iteration
+  // (V-cycle plus the operator phase and the vector update).
+  double vcycle_bytes() const;
+  double iter_bytes() const;
 
   // Level plan for grid g0: 2:1 while possible, then the smallest common odd
   // factor, until the coarsest has <= max_coarse_dofs DOFs.  Allocates all
@@ -138,6 +148,15 @@ cudaError_t mg_update32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* 
 cudaError_t mg_update_p32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* p, const float* z);
 // x += d over n values (end of an FP32 segment).
 cudaError_t mg_merge(cudaStream_t s, long long n, double* x, const float* d);
+// One FP32 segment as a persistent cooperative kernel (mg_pcg.cu): before the
+// launch the control block (mg_seg_init), the finest b = (float) r and x[0] =
+// omega D^-1 b (mg_prep) and d = 0 must be in place; zeroes the barrier word.
+// The finest operator is the strain-form FP32 operator (constitutive matrix C,
+// moduli E32, tile depth zlen).
+// trace (optional, 64 int64): globaltimer of CTA 0 after each grid barrier of
+// the segment's third iteration.
+cudaError_t launch_mg_segment(cudaStream_t s, const MgHierarchy& M, const double* C, const float* E32, int zlen,
+                              double* part, GridBar* bar, long long* trace, int nsm, int* grid_out);
 // x += alpha p, r -= alpha q (q FP32 when q_f32), r32 = (float) r, x0 = omega D^-1 r32.
 cudaError_t mg_update_xr(cudaStream_t s, long long n, int nc, MgCtl* ctl, double* x, const double* p, double* r,
                          const void* q, bool q_f32, float* r32, float* x0, const float* invd, float omega);

@@ -52,6 +52,12 @@ struct Q4Tile {
     return (size_t)(HX * HY * 2 * ncm + EX * EY) * sizeof(T);
   }
 
+  // Input value v of the tile-local output node (tx, ty) as staged by the last
+  // apply on this shared memory (valid until the next apply writes it).
+  __device__ static T staged(const unsigned char* smem, int v, int tx, int ty) {
+    return reinterpret_cast<const T*>(smem)[v * (HX * HY) + (ty + 1) * HX + tx + 1];
+  }
+
   // Calls fn(node) for every output node of tile t, with the thread / node
   // assignment of apply (the thread that emitted a node visits it).
   template <class Fn>

@@ -25,6 +25,7 @@ TP_FILTER_SENSITIVITY = 0
 TP_FILTER_DENSITY = 1
 TP_PRECOND_JACOBI = 0
 TP_PRECOND_MG = 1
+TP_PRECOND_MG_FUSED = 2
 TP_RHO, TP_U, TP_DC, TP_DCF, TP_CE, TP_RHO_PHYS = range(6)
 
 
@@ -256,8 +257,9 @@ class Problem:
         self._check(lib.tp_set_profile(self.h, 1 if enable else 0))
 
     def get_profile(self):
-        """(timed finest-level multigrid launches, their total ms, algorithmic
-        bytes per launch, levels)."""
+        """(timed multigrid launches -- finest-level sweeps, or persistent
+        segments with TP_PRECOND_MG_FUSED -- their total ms, their total
+        algorithmic bytes, levels)."""
         out = np.zeros(4)
         self._check(lib.tp_get_profile(self.h, out.ctypes.data_as(C.c_void_p)))
         return int(out[0]), float(out[1]), float(out[2]), int(out[3])

@@ -33,7 +33,7 @@ def topo():
     return t
 
 
-@pytest.mark.parametrize("precond", [0, 1], ids=["jacobi", "multigrid"])
+@pytest.mark.parametrize("precond", [0, 1, 2], ids=["jacobi", "multigrid", "multigrid_fused"])
 def test_cantilever2d_full_step(topo, precond):
     w = W.cantilever2d()
     rho0 = w.initial_density()

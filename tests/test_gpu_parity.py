@@ -233,15 +233,24 @@ MG_GRIDS = [W.small2d(40, 12, n_cases=3, passive_disk=(12, 6, 3)), W.small2d(60,
             W.small3d(20, 10, 10, n_cases=2)]
 
 
+MG_KINDS = ["graph", "fused"]
+
+
+def _mg(topo, kind):
+    return topo.TP_PRECOND_MG if kind == "graph" else topo.TP_PRECOND_MG_FUSED
+
+
+@pytest.mark.parametrize("kind", MG_KINDS)
 @pytest.mark.parametrize("prob", MG_GRIDS, ids=lambda p: p.name + f"_nc{p.n_cases}")
-def test_multigrid_solve_matches_direct_solve(topo, prob):
-    """Multigrid-preconditioned CG (FP64 outer, FP32 V-cycle) against the
-    oracle's LU solve on a random density: true residual <= tol, compliance
-    rel <= 1e-8, displacements rel <= 1e-6."""
+def test_multigrid_solve_matches_direct_solve(topo, prob, kind):
+    """Multigrid-preconditioned CG (FP32 correction segments with FP64
+    restarts, FP32 V-cycle), graph-replayed and as a persistent kernel, against
+    the oracle's LU solve on a random density: true residual <= tol,
+    compliance rel <= 1e-8, displacements rel <= 1e-6."""
     rho = W.random_density(prob.n_el, seed=51, lo=0.05)
     p = topo.Problem.from_workload(prob)
     p.set_density(rho)
-    info = p.solve(topo.solve_opts(tol=1e-11, max_it=5000, precond=topo.TP_PRECOND_MG))
+    info = p.solve(topo.solve_opts(tol=1e-11, max_it=5000, precond=_mg(topo, kind)))
     assert info.converged == 1 and max(info.rel_res[c] for c in range(prob.n_cases)) <= 1e-11
     assert info.iters < 200
     U = fem.solve(prob, rho)
@@ -252,7 +261,8 @@ def test_multigrid_solve_matches_direct_solve(topo, prob):
     p.close()
 
 
-def test_multigrid_simp_iterations_mbb(topo):
+@pytest.mark.parametrize("kind", MG_KINDS)
+def test_multigrid_simp_iterations_mbb(topo, kind):
     """Config 1 SIMP iterations with the multigrid solver, each against the
     oracle on the GPU's own density (compliance <= 1e-8, rho <= 1e-6, lambda
     <= 1e-9 of the exact root)."""
@@ -260,7 +270,7 @@ def test_multigrid_simp_iterations_mbb(topo):
     Wm = filt.weights_for(prob)
     p = topo.Problem.from_workload(prob)
     rho = prob.initial_density()
-    opts = topo.solve_opts(tol=1e-10, max_it=5000, warm_start=topo.TP_WARM_PREVIOUS, precond=topo.TP_PRECOND_MG)
+    opts = topo.solve_opts(tol=1e-10, max_it=5000, warm_start=topo.TP_WARM_PREVIOUS, precond=_mg(topo, kind))
     for it in range(8):
         info = p.simp_step(opts)
         assert info.solve.iters < 100
@@ -276,9 +286,32 @@ def test_multigrid_simp_iterations_mbb(topo):
 def test_multigrid_needs_a_hierarchy(topo):
     prob = W.small2d(37, 11)  # prime element counts: no coarse grid
     p = topo.Problem.from_workload(prob)
-    with pytest.raises(topo.TopoError) as e:
-        p.solve(topo.solve_opts(tol=1e-8, precond=topo.TP_PRECOND_MG))
-    assert e.value.status == topo.TP_ERR_ARG
+    for kind in MG_KINDS:
+        with pytest.raises(topo.TopoError) as e:
+            p.solve(topo.solve_opts(tol=1e-8, precond=_mg(topo, kind)))
+        assert e.value.status == topo.TP_ERR_ARG
     info = p.solve(topo.solve_opts(tol=1e-8, max_it=20000))  # the handle stays usable
     assert info.converged == 1
+    with pytest.raises(topo.TopoError) as e:
+        p.solve(topo.solve_opts(tol=1e-8, precond=7))
+    assert e.value.status == topo.TP_ERR_ARG
     p.close()
+
+
+@pytest.mark.parametrize("prob", [W.small2d(40, 12, n_cases=3, passive_disk=(12, 6, 3)), W.small3d(16, 8, 6)],
+                         ids=lambda p: p.name)
+def test_multigrid_variants_agree(topo, prob):
+    """The graph-replayed and the persistent-kernel solvers run the same
+    method; their reductions differ in rounding order only: iteration counts
+    within 10 %, solutions within 1e-6."""
+    rho = W.random_density(prob.n_el, seed=52, lo=0.05)
+    out = {}
+    for kind in MG_KINDS:
+        p = topo.Problem.from_workload(prob)
+        p.set_density(rho)
+        info = p.solve(topo.solve_opts(tol=1e-10, max_it=5000, precond=_mg(topo, kind)))
+        out[kind] = (info.iters, info.updates, p.get(topo.TP_U))
+        p.close()
+    assert abs(out["graph"][0] - out["fused"][0]) <= max(2, 0.1 * out["graph"][0])
+    ug, uf = out["graph"][2], out["fused"][2]
+    assert np.linalg.norm(ug - uf) <= 1e-6 * np.linalg.norm(ug)
