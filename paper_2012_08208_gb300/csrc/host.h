@@ -109,6 +109,9 @@ cudaError_t launch_oc(cudaStream_t s, long long ne, const double* rho, const dou
                       double* rho_new, double* bscratch, double* part, GridBar* bar, OcStatus* st,
                       int nsm, int* grid_out, int max_grid = 0);
 // Partial-sum slots the OC kernel needs for `grid` CTAs (doubles).
-constexpr long long oc_part_doubles(int grid) { return (long long)(2 * 15 + 2) * grid; }
+// partial sums of the OC kernel (two slots of 15 values and the final 2 per
+// CTA), then the list of elements that change clamp state inside the final
+// bracket (a counter and 32 entries of 3 doubles)
+constexpr long long oc_part_doubles(int grid) { return (long long)(2 * 15 + 2) * grid + 1 + 32 * 3; }
 
 }  // namespace tp

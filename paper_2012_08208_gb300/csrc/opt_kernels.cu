@@ -127,19 +127,104 @@ cudaError_t launch_filter(cudaStream_t s, const FilterLaunch& Fl, int mode, cons
 }
 
 // ---------------------------------------------------------------------------
-// OC update with a 16-way bisection.
+// OC update (Eq. "update"): rho_new(lambda) per element, lambda from the
+// volume constraint by a 16-way bisection.
 //
-// V(lambda) = sum_e rho_new_e(lambda) is non-increasing in lambda.  Each pass
+// V(lambda) = sum_e rho_new_e(lambda) is non-increasing in lambda.  A pass
 // evaluates V at 15 interior points of the bracket [l1, l2] in one sweep over
 // the elements (B_e = rho_e sqrt(max(-dc~_e, 0)) precomputed, candidate
-// rho_e B_e / sqrt(lambda_j)), then keeps the sub-interval where
-// V - target changes sign: points with V - target > 0 move l1 up, the first
-// point with V - target <= 0 becomes l2 (the paper's rule, Section 4.4 code).
-// The first pass widens the bracket: l2 = 1e9 * 10^j for the first j with
-// V <= target.  Stop when l2 - l1 <= 1e-10 (l1 + l2); final rho_new uses the
-// midpoint.  Passive elements are held at dmin inside the search.
+// B_e / sqrt(lambda_j)) and keeps the sub-interval where V - target changes
+// sign: points with V - target > 0 move l1 up, the first point with
+// V - target <= 0 becomes l2 (the paper's rule, Section 4.4 code).  A first
+// pass widens the bracket: l2 = 1e9 * 10^j for the first j with V <= target.
+// Passive elements are held at dmin inside the search.
+//
+// GB300 issues an FP64 operation at 1/64 of the FP32 rate, so the passes run
+// in FP32 (double-float totals) until the bracket is 1e-5 wide relative to
+// lambda (well above the FP32 evaluation error of V even when few elements are
+// interior).  One FP64 pass then classifies every element at both ends of the
+// bracket, widened by 4e-5: clamped high at both, clamped low at both, or
+// interior at both.  If none changes state inside the bracket, V there is
+// exactly C + A / sqrt(lambda) (C the clamped values, A the sum of B_e over the
+// interior elements) and the root is lambda* = (A / (target - C))^2, checked
+// against V at both ends in FP64.  If a few elements (at most kOcList) change
+// state inside the bracket, their breakpoints (B_e / hi_e)^2 and
+// (B_e / lo_e)^2 split it into pieces on each of which V has that form; the
+// piece where V - target changes sign gives the exact root.  Otherwise FP64
+// passes continue from the bracket (from scratch if V does not change sign
+// across it) until l2 - l1 <= 1e-10 (l1 + l2), and the final update uses the
+// midpoint.
 
 constexpr int kOcK = 15;
+constexpr int kOcList = 32;
+
+// Exact root on [c1, c2] given the totals over the elements that keep their
+// state (C: clamped values, A: sum of B_e of interior ones) and the m <=
+// kOcList elements that change state, list[3 k .. 3 k + 2] = (B, lo, hi).
+// One thread.  The elements and then the breakpoints are sorted, so the result
+// does not depend on the order in which the list was filled.  Returns 0 if no
+// piece brackets the root (the caller falls back to bisection).
+__device__ double oc_piecewise_root(const double* list, int m, double c1, double c2, double C, double A,
+                                    double target) {
+  double e[kOcList][3];
+  for (int k = 0; k < m; k++)
+    for (int q = 0; q < 3; q++) e[k][q] = __ldcg(list + 3 * k + q);
+  for (int k = 1; k < m; k++)  // insertion sort by (B, lo, hi)
+    for (int j = k; j > 0; j--) {
+      const bool gt = e[j - 1][0] > e[j][0] || (e[j - 1][0] == e[j][0] &&
+                      (e[j - 1][1] > e[j][1] || (e[j - 1][1] == e[j][1] && e[j - 1][2] > e[j][2])));
+      if (!gt) break;
+      for (int q = 0; q < 3; q++) {
+        const double t = e[j][q];
+        e[j][q] = e[j - 1][q];
+        e[j - 1][q] = t;
+      }
+    }
+  // state at c1 and the breakpoints inside (c1, c2): kind 0 high -> interior,
+  // kind 1 interior -> low (candidate B / sqrt(lambda) decreases with lambda)
+  double tv[2 * kOcList];
+  int tk[2 * kOcList], te[2 * kOcList], nt = 0;
+  const double s1 = 1.0 / sqrt(c1);
+  for (int k = 0; k < m; k++) {
+    const double b = e[k][0], lo = e[k][1], hi = e[k][2], k1 = b * s1;
+    if (k1 >= hi) C += hi;
+    else if (k1 <= lo) C += lo;
+    else A += b;
+    const double la = (b / hi) * (b / hi), lb = (b / lo) * (b / lo);
+    if (la > c1 && la < c2) { tv[nt] = la; tk[nt] = 0; te[nt++] = k; }
+    if (lb > c1 && lb < c2) { tv[nt] = lb; tk[nt] = 1; te[nt++] = k; }
+  }
+  for (int k = 1; k < nt; k++)  // by value, ties by element then kind
+    for (int j = k; j > 0; j--) {
+      const bool gt = tv[j - 1] > tv[j] || (tv[j - 1] == tv[j] && (te[j - 1] > te[j] ||
+                      (te[j - 1] == te[j] && tk[j - 1] > tk[j])));
+      if (!gt) break;
+      const double t = tv[j]; tv[j] = tv[j - 1]; tv[j - 1] = t;
+      const int a1 = tk[j]; tk[j] = tk[j - 1]; tk[j - 1] = a1;
+      const int a2 = te[j]; te[j] = te[j - 1]; te[j - 1] = a2;
+    }
+  double lo_end = c1;
+  for (int i = 0; i <= nt; i++) {
+    const double hi_end = i < nt ? tv[i] : c2;
+    if (C + A / sqrt(hi_end) - target <= 0.0) {  // V crosses the target on [lo_end, hi_end]
+      if (!(A > 0.0) || !(target > C)) return 0.0;
+      const double rt = A / (target - C), lam = rt * rt;
+      return (lam >= lo_end * (1.0 - 1e-12) && lam <= hi_end * (1.0 + 1e-12)) ? lam : 0.0;
+    }
+    if (i < nt) {
+      const int k = te[i];
+      if (tk[i] == 0) {
+        C -= e[k][2];
+        A += e[k][0];
+      } else {
+        A -= e[k][0];
+        C += e[k][1];
+      }
+      lo_end = hi_end;
+    }
+  }
+  return 0.0;
+}
 
 struct OcArgs {
   long long ne;
@@ -160,6 +245,7 @@ __device__ __forceinline__ double oc_clamp(double rho, double cand, double move,
 
 __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs a) {
   __shared__ double sRed[32 * kOcK];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(sRed);
   const int nb = gridDim.x;
   const long long stride = (long long)nb * blockDim.x;
   const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -167,26 +253,57 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
   bool ok = true;
   int passes = 0;
   double lam[kOcK], s[kOcK];
+  // (B_e, rho_e) in FP32 during the search, in the memory of rho_new (written
+  // last); B_e < 0 marks a passive element.  Every thread reads back only the
+  // elements it wrote.
+  float2* S2 = reinterpret_cast<float2*>(a.rho_new);
+  double* list = a.part + (size_t)(2 * kOcK + 2) * nb + 1;
+  unsigned* list_n = reinterpret_cast<unsigned*>(list - 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *list_n = 0u;  // read after at least one grid barrier
+  for (long long e = first; e < a.ne; e += stride) {
+    const double r = a.rho[e];
+    const bool pas = a.passive != nullptr && a.passive[e] == 1;
+    const double b = pas ? -1.0 : r * sqrt(fmax(-a.dcf[e], 0.0));
+    a.B[e] = b;
+    S2[e] = make_float2((float)b, (float)r);
+  }
 
-  // Partial sums alternate between two slots so that the totals of pass k can
-  // be read while pass k+1 already writes its partials.
-  auto sweep = [&](bool init, double (&tot)[kOcK]) -> bool {
+  // one pass: V at lam[0..14]; partial sums alternate between two slots so
+  // that the totals of pass k can be read while pass k+1 writes its partials
+  auto sweep32 = [&](double (&tot)[kOcK]) -> bool {
+    float2* slot = reinterpret_cast<float2*>(a.part + (size_t)(passes & 1) * kOcK * nb);
+    float sf[kOcK], acc[kOcK];
+#pragma unroll
+    for (int j = 0; j < kOcK; j++) {
+      sf[j] = (float)s[j];
+      acc[j] = 0.f;
+    }
+    const float mv = (float)a.move, dm = (float)a.dmin;
+    for (long long e = first; e < a.ne; e += stride) {
+      const float2 v = S2[e];
+      if (v.x < 0.f) {
+#pragma unroll
+        for (int j = 0; j < kOcK; j++) acc[j] += dm;
+      } else {
+        const float lo = fmaxf(dm, v.y - mv), hi = fminf(1.f, v.y + mv);
+#pragma unroll
+        for (int j = 0; j < kOcK; j++) acc[j] += fminf(hi, fmaxf(lo, v.x * sf[j]));
+      }
+    }
+    block_partial_f<kOcK>(acc, slot, sm);
+    if (!grid_sync(a.bar, gen)) return false;
+    grid_total_f<kOcK>(slot, tot, sm);
+    return true;
+  };
+  auto sweep64 = [&](double (&tot)[kOcK]) -> bool {
     double* slot = a.part + (size_t)(passes & 1) * kOcK * nb;
     double acc[kOcK];
 #pragma unroll
     for (int j = 0; j < kOcK; j++) acc[j] = 0.0;
     for (long long e = first; e < a.ne; e += stride) {
-      const double r = a.rho[e];
-      double b;
-      if (init) {
-        b = r * sqrt(fmax(-a.dcf[e], 0.0));
-        a.B[e] = b;
-      } else {
-        b = a.B[e];
-      }
-      const bool pas = a.passive != nullptr && a.passive[e] == 1;
+      const double r = a.rho[e], b = a.B[e];
 #pragma unroll
-      for (int j = 0; j < kOcK; j++) acc[j] += pas ? a.dmin : oc_clamp(r, b * s[j], a.move, a.dmin);
+      for (int j = 0; j < kOcK; j++) acc[j] += b < 0.0 ? a.dmin : oc_clamp(r, b * s[j], a.move, a.dmin);
     }
     block_sum<kOcK>(acc, sRed);
     if (threadIdx.x == 0)
@@ -195,69 +312,156 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
     grid_total<kOcK>(slot, tot, sRed);
     return true;
   };
-
-  // widening pass: lambda_j = 1e9 * 10^j
-  double l1 = 0.0, l2 = 1e9;
-  bool found = false;
-  for (int round = 0; round < 20 && ok && !found; round++) {
+  // The 15 points of a pass: lambda_j and 1 / sqrt(lambda_j), formed once per
+  // CTA by 15 lanes (an FP64 square root and division cost dozens of FP64
+  // issue slots each) and shared.  Every thread holds the same l1, l2.
+  __shared__ double sh_lam[kOcK], sh_s[kOcK];
+  auto set_points = [&](bool decades, double l1, double l2) {
+    __syncthreads();  // the previous pass has read the shared points
+    if (threadIdx.x < kOcK) {
+      const int j = threadIdx.x;
+      constexpr double p10[kOcK] = {1e0, 1e1, 1e2, 1e3, 1e4, 1e5, 1e6, 1e7, 1e8, 1e9, 1e10, 1e11, 1e12, 1e13, 1e14};
+      const double lj = decades ? l2 * p10[j] : l1 + (l2 - l1) / (kOcK + 1) * (j + 1);
+      sh_lam[j] = lj;
+      sh_s[j] = 1.0 / sqrt(lj);
+    }
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < kOcK; j++) {
-      lam[j] = l2 * pow(10.0, (double)j);
-      s[j] = 1.0 / sqrt(lam[j]);
+      lam[j] = sh_lam[j];
+      s[j] = sh_s[j];
     }
-    double tot[kOcK];
-    ok = sweep(round == 0, tot);
-    passes++;
-    if (!ok) break;
-    int jf = -1;
+  };
+  // widening pass(es) from l2 = 1e9
+  auto widen = [&](bool f32, double& l1, double& l2) -> bool {
+    l1 = 0.0;
+    l2 = 1e9;
+    for (int round = 0; round < 20 && ok; round++) {
+      set_points(true, l1, l2);
+      double tot[kOcK];
+      ok = f32 ? sweep32(tot) : sweep64(tot);
+      passes++;
+      if (!ok) break;
+      int jf = -1;
 #pragma unroll
-    for (int j = kOcK - 1; j >= 0; j--)
-      if (tot[j] - a.target <= 0.0) jf = j;
-    if (jf >= 0) {
-      found = true;
-      if (jf > 0) l1 = lam[jf - 1];
-      l2 = lam[jf];
-    } else {
+      for (int j = kOcK - 1; j >= 0; j--)
+        if (tot[j] - a.target <= 0.0) jf = j;
+      if (jf >= 0) {
+        if (jf > 0) l1 = lam[jf - 1];
+        l2 = lam[jf];
+        return true;
+      }
       l1 = lam[kOcK - 1];
       l2 = lam[kOcK - 1] * 10.0;
       if (!isfinite(l2)) break;
     }
-  }
-  // multi-point bisection
-  while (ok && found && (l2 - l1) > 1e-10 * (l1 + l2) && passes < 200) {
-    const double h = (l2 - l1) / (kOcK + 1);
+    return false;
+  };
+  // 16-way bisection until l2 - l1 <= rel (l1 + l2)
+  auto bisect = [&](bool f32, double rel, double& l1, double& l2) {
+    while (ok && (l2 - l1) > rel * (l1 + l2) && passes < 200) {
+      set_points(false, l1, l2);
+      double tot[kOcK];
+      ok = f32 ? sweep32(tot) : sweep64(tot);
+      passes++;
+      if (!ok) break;
+      int jf = kOcK;
 #pragma unroll
-    for (int j = 0; j < kOcK; j++) {
-      lam[j] = l1 + h * (j + 1);
-      s[j] = 1.0 / sqrt(lam[j]);
+      for (int j = kOcK - 1; j >= 0; j--)
+        if (tot[j] - a.target <= 0.0) jf = j;
+      const double nl1 = jf > 0 ? lam[jf - 1] : l1;
+      const double nl2 = jf < kOcK ? lam[jf] : l2;
+      if (nl1 == l1 && nl2 == l2) break;  // the bracket cannot shrink further in this precision
+      l1 = nl1;
+      l2 = nl2;
     }
-    double tot[kOcK];
-    ok = sweep(false, tot);
+  };
+
+  double l1 = 0.0, l2 = 1e9, lfinal = 0.0;
+  bool found = widen(true, l1, l2), exact = false;
+  if (found) {
+    bisect(true, 1e-5, l1, l2);
+    // certification of the FP32 bracket in FP64
+    const double c1 = l1 * (1.0 - 4e-5), c2 = l2 * (1.0 + 4e-5);
+    __shared__ double sh_s12[2];
+    if (threadIdx.x == 0) {
+      sh_s12[0] = c1 > 0.0 ? 1.0 / sqrt(c1) : 1e300;
+      sh_s12[1] = 1.0 / sqrt(c2);
+    }
+    __syncthreads();
+    const double s1 = sh_s12[0], s2 = sh_s12[1];
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // V(c1), V(c2), A, C, changing
+    for (long long e = first; e < a.ne && ok; e += stride) {
+      const double b = a.B[e];
+      if (b < 0.0) {
+        acc[0] += a.dmin;
+        acc[1] += a.dmin;
+        acc[3] += a.dmin;
+        continue;
+      }
+      const double r = a.rho[e];
+      const double lo = fmax(a.dmin, r - a.move), hi = fmin(1.0, r + a.move);
+      const double k1 = b * s1, k2 = b * s2;  // k1 >= k2
+      acc[0] += fmax(lo, fmin(hi, k1));
+      acc[1] += fmax(lo, fmin(hi, k2));
+      if (k2 >= hi) acc[3] += hi;
+      else if (k1 <= lo) acc[3] += lo;
+      else if (k2 > lo && k1 < hi) acc[2] += b;
+      else {
+        acc[4] += 1.0;
+        const unsigned k = atomicAdd(list_n, 1u);
+        if (k < (unsigned)kOcList) {
+          list[3 * k] = b;
+          list[3 * k + 1] = lo;
+          list[3 * k + 2] = hi;
+        }
+      }
+    }
+    double* slot = a.part + (size_t)(passes & 1) * kOcK * nb;
+    block_sum<5>(acc, sRed);
+    if (threadIdx.x == 0)
+      for (int j = 0; j < 5; j++) slot[(size_t)j * nb + blockIdx.x] = acc[j];
+    if (ok) ok = grid_sync(a.bar, gen);
     passes++;
-    if (!ok) break;
-    int jf = kOcK;
-#pragma unroll
-    for (int j = kOcK - 1; j >= 0; j--)
-      if (tot[j] - a.target <= 0.0) jf = j;
-    const double nl1 = jf > 0 ? lam[jf - 1] : l1;
-    const double nl2 = jf < kOcK ? lam[jf] : l2;
-    if (nl1 == l1 && nl2 == l2) break;  // bracket cannot shrink further in FP64
-    l1 = nl1;
-    l2 = nl2;
+    double tot[5];
+    grid_total<5>(slot, tot, sRed);
+    const bool sign = tot[0] - a.target > 0.0 && tot[1] - a.target <= 0.0;
+    if (ok && sign && tot[4] == 0.0 && tot[2] > 0.0 && a.target > tot[3]) {
+      const double rt = tot[2] / (a.target - tot[3]);
+      lfinal = rt * rt;
+      exact = lfinal >= c1 && lfinal <= c2;
+    } else if (ok && sign && tot[4] <= (double)kOcList && c1 > 0.0) {
+      __shared__ double s_root;
+      if (threadIdx.x == 0) s_root = oc_piecewise_root(list, (int)tot[4], c1, c2, tot[3], tot[2], a.target);
+      __syncthreads();
+      lfinal = s_root;
+      exact = lfinal > 0.0;
+    }
+    if (!exact) {
+      if (sign) {
+        l1 = c1;
+        l2 = c2;
+      } else {
+        found = false;
+      }
+    }
   }
-  // final update at the midpoint
-  const double lmid = 0.5 * (l1 + l2);
+  if (ok && !exact) {
+    if (!found) found = widen(false, l1, l2);
+    if (found) bisect(false, 1e-10, l1, l2);
+    lfinal = 0.5 * (l1 + l2);
+  }
+  // final update
+  __shared__ double sh_sfin;
+  __syncthreads();
+  if (threadIdx.x == 0) sh_sfin = 1.0 / sqrt(lfinal);
+  __syncthreads();
+  const double sfin = sh_sfin;
   double accv[2] = {0.0, 0.0};
   if (ok) {
     for (long long e = first; e < a.ne; e += stride) {
-      const double r = a.rho[e];
-      double nv;
-      if (a.passive != nullptr && a.passive[e] == 1) {
-        nv = a.dmin;
-      } else {
-        const double cand = r * sqrt(fmax(-a.dcf[e], 0.0) / lmid);
-        nv = oc_clamp(r, cand, a.move, a.dmin);
-      }
+      const double r = a.rho[e], b = a.B[e];
+      const double nv = b < 0.0 ? a.dmin : oc_clamp(r, b * sfin, a.move, a.dmin);
       a.rho_new[e] = nv;
       accv[0] += nv;
       accv[1] = fmax(accv[1], fabs(nv - r));
@@ -284,11 +488,11 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
     block_sum<1>(v, sRed);
     m = block_max(m, sRed);
     if (threadIdx.x == 0) {
-      a.st->lambda = lmid;
+      a.st->lambda = lfinal;
       a.st->volume = v[0];
       a.st->change = m;
       a.st->passes = passes;
-      a.st->flags = (ok ? 0 : ERR_TIMEOUT) | (found ? 0 : ERR_NAN);
+      a.st->flags = (ok ? 0 : ERR_TIMEOUT) | (found || exact ? 0 : ERR_NAN);
     }
   }
 }

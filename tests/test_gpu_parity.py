@@ -141,6 +141,34 @@ def test_oc_update(topo, n, vf, passive):
     p.close()
 
 
+@pytest.mark.parametrize("n_special", [1, 100])
+def test_oc_update_breakpoint_at_root(topo, n_special):
+    """Clamp breakpoints exactly at the root (lambda* = 1): the FP64
+    classification finds elements changing state inside the FP32 bracket.  One
+    such element: the piecewise exact root decides; 100: more than the list
+    holds, so FP64 bisection passes decide.  Lambda within 1e-9 of the exact
+    root either way."""
+    n = 4000
+    rng = np.random.default_rng(77)
+    rho = rng.uniform(0.3, 0.6, n)
+    dcf = -np.ones(n)
+    ks = rng.choice(n, size=n_special, replace=False)
+    rho[ks] = 0.5
+    dcf[ks] = -1.96  # B = 0.5 * 1.4 = rho + move: clamped high from lambda = 1 down
+    vf = (rho.sum() + 0.2 * n_special) / n  # V(1) = sum rho + 0.2 per special element
+    prob = W.small2d(n, 1, volfrac=vf)
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    p.set(topo.TP_DCF, dcf)
+    lam, vol, ch = p.oc_update()
+    lam_exact = oc.exact_lambda(rho, dcf, vf)
+    assert lam_exact == pytest.approx(1.0, rel=1e-12)
+    assert lam == pytest.approx(lam_exact, rel=1e-9)
+    assert np.max(np.abs(p.get(topo.TP_RHO) - oc.update(rho, dcf, lam_exact))) <= 1e-6
+    assert vol == pytest.approx(vf * n, rel=1e-8)
+    p.close()
+
+
 def test_simp_iterations_on_identical_density_mbb(topo):
     """Config 1 (MBB 60 x 20, FP64): every iteration compared with the oracle on the
     GPU's own density (compliance <= 1e-8, rho <= 1e-6, lambda <= 1e-9)."""
