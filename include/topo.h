@@ -121,6 +121,9 @@ typedef struct tp_step_info {
   double lambda;        /* OC multiplier */
   double volume;        /* sum rho_new */
   double change;        /* max |rho_new - rho| */
+  int oc_passes;        /* passes over the elements in the OC multiplier search */
+  int oc_root;          /* how lambda was fixed: 1 closed form on a bracket with no
+                           clamp change, 2 exact piecewise root, 0 bisection midpoint */
 } tp_step_info;
 
 typedef struct tp_problem tp_problem;

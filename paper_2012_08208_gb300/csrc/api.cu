@@ -793,6 +793,8 @@ tp_status tp_oc_update(tp_problem* p, double* lambda, double* volume, double* ch
   if (lambda) *lambda = st.lambda;
   if (volume) *volume = st.volume;
   if (change) *change = st.change;
+  p->oc_passes = st.passes;
+  p->oc_root = st.root;
   return TP_OK;
 }
 
@@ -808,6 +810,10 @@ tp_status tp_simp_step(tp_problem* p, const tp_solve_opts* opts, tp_step_info* i
   tp_status s2 = tp_sensitivities(p, &loc.compliance);
   if (s2 == TP_OK) s2 = tp_filter(p, p->filter_mode);
   if (s2 == TP_OK) s2 = tp_oc_update(p, &loc.lambda, &loc.volume, &loc.change);
+  if (s2 == TP_OK) {
+    loc.oc_passes = p->oc_passes;
+    loc.oc_root = p->oc_root;
+  }
   if (info) *info = loc;
   if (s2 != TP_OK) return s2;
   return s;

@@ -103,6 +103,8 @@ struct OcStatus {
   double change;
   int passes;
   int flags;
+  int root;  // 1 closed form, 2 piecewise exact root, 0 bisection midpoint
+  int pad;
 };
 cudaError_t launch_oc(cudaStream_t s, long long ne, const double* rho, const double* dcf,
                       const int8_t* passive, double volfrac, double move, double dmin,

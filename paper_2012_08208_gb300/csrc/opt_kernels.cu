@@ -252,7 +252,6 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
   unsigned gen = 0;
   bool ok = true;
   int passes = 0;
-  double lam[kOcK], s[kOcK];
   // (B_e, rho_e) in FP32 during the search, in the memory of rho_new (written
   // last); B_e < 0 marks a passive element.  Every thread reads back only the
   // elements it wrote.
@@ -268,121 +267,160 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
     S2[e] = make_float2((float)b, (float)r);
   }
 
-  // one pass: V at lam[0..14]; partial sums alternate between two slots so
-  // that the totals of pass k can be read while pass k+1 writes its partials
-  auto sweep32 = [&](double (&tot)[kOcK]) -> bool {
-    float2* slot = reinterpret_cast<float2*>(a.part + (size_t)(passes & 1) * kOcK * nb);
-    float sf[kOcK], acc[kOcK];
-#pragma unroll
-    for (int j = 0; j < kOcK; j++) {
-      sf[j] = (float)s[j];
-      acc[j] = 0.f;
-    }
-    const float mv = (float)a.move, dm = (float)a.dmin;
-    for (long long e = first; e < a.ne; e += stride) {
-      const float2 v = S2[e];
-      if (v.x < 0.f) {
-#pragma unroll
-        for (int j = 0; j < kOcK; j++) acc[j] += dm;
-      } else {
-        const float lo = fmaxf(dm, v.y - mv), hi = fminf(1.f, v.y + mv);
-#pragma unroll
-        for (int j = 0; j < kOcK; j++) acc[j] += fminf(hi, fmaxf(lo, v.x * sf[j]));
-      }
-    }
-    block_partial_f<kOcK>(acc, slot, sm);
-    if (!grid_sync(a.bar, gen)) return false;
-    grid_total_f<kOcK>(slot, tot, sm);
-    return true;
-  };
-  auto sweep64 = [&](double (&tot)[kOcK]) -> bool {
-    double* slot = a.part + (size_t)(passes & 1) * kOcK * nb;
-    double acc[kOcK];
-#pragma unroll
-    for (int j = 0; j < kOcK; j++) acc[j] = 0.0;
-    for (long long e = first; e < a.ne; e += stride) {
-      const double r = a.rho[e], b = a.B[e];
-#pragma unroll
-      for (int j = 0; j < kOcK; j++) acc[j] += b < 0.0 ? a.dmin : oc_clamp(r, b * s[j], a.move, a.dmin);
-    }
-    block_sum<kOcK>(acc, sRed);
-    if (threadIdx.x == 0)
-      for (int j = 0; j < kOcK; j++) slot[(size_t)j * nb + blockIdx.x] = acc[j];
-    if (!grid_sync(a.bar, gen)) return false;
-    grid_total<kOcK>(slot, tot, sRed);
-    return true;
-  };
-  // The 15 points of a pass: lambda_j and 1 / sqrt(lambda_j), formed once per
-  // CTA by 15 lanes (an FP64 square root and division cost dozens of FP64
-  // issue slots each) and shared.  Every thread holds the same l1, l2.
-  __shared__ double sh_lam[kOcK], sh_s[kOcK];
-  auto set_points = [&](bool decades, double l1, double l2) {
-    __syncthreads();  // the previous pass has read the shared points
+  // Search state.  Thread 0 takes every decision from the totals and
+  // publishes it through shared memory; the 15 points of a pass (lambda_j,
+  // 1 / sqrt(lambda_j) in FP64 and FP32) are formed once per CTA by 15 lanes.
+  // Every CTA holds the same totals, so all take the same decisions.
+  __shared__ double sh_l[2], sh_tot[kOcK], sh_lam[kOcK], sh_s[kOcK];
+  __shared__ float sh_sf[kOcK];
+  __shared__ int sh_state;
+  auto set_points = [&](bool decades) {
     if (threadIdx.x < kOcK) {
       const int j = threadIdx.x;
       constexpr double p10[kOcK] = {1e0, 1e1, 1e2, 1e3, 1e4, 1e5, 1e6, 1e7, 1e8, 1e9, 1e10, 1e11, 1e12, 1e13, 1e14};
+      const double l1 = sh_l[0], l2 = sh_l[1];
       const double lj = decades ? l2 * p10[j] : l1 + (l2 - l1) / (kOcK + 1) * (j + 1);
       sh_lam[j] = lj;
       sh_s[j] = 1.0 / sqrt(lj);
+      sh_sf[j] = (float)sh_s[j];
     }
     __syncthreads();
-#pragma unroll
-    for (int j = 0; j < kOcK; j++) {
-      lam[j] = sh_lam[j];
-      s[j] = sh_s[j];
-    }
   };
-  // widening pass(es) from l2 = 1e9
-  auto widen = [&](bool f32, double& l1, double& l2) -> bool {
-    l1 = 0.0;
-    l2 = 1e9;
+  // one pass: V at the points into sh_tot; partial sums alternate between
+  // two slots so that the totals of pass k can be read while pass k+1 writes
+  // its partials
+  auto pass = [&](bool f32) -> bool {
+    double* slot8 = a.part + (size_t)(passes & 1) * kOcK * nb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (f32) {
+      float2* slot = reinterpret_cast<float2*>(slot8);
+      float sf[kOcK], acc[kOcK];
+#pragma unroll
+      for (int j = 0; j < kOcK; j++) {
+        sf[j] = sh_sf[j];
+        acc[j] = 0.f;
+      }
+      const float mv = (float)a.move, dm = (float)a.dmin;
+      for (long long e = first; e < a.ne; e += stride) {
+        const float2 v = S2[e];
+        if (v.x < 0.f) {
+#pragma unroll
+          for (int j = 0; j < kOcK; j++) acc[j] += dm;
+        } else {
+          const float lo = fmaxf(dm, v.y - mv), hi = fminf(1.f, v.y + mv);
+#pragma unroll
+          for (int j = 0; j < kOcK; j++) acc[j] += fminf(hi, fmaxf(lo, v.x * sf[j]));
+        }
+      }
+      block_partial_f<kOcK>(acc, slot, sm);
+      if (!grid_sync(a.bar, gen)) return false;
+      for (int i = warp; i < kOcK; i += nw) {  // double-float totals, fixed order
+        dfl t{0.f, 0.f};
+        for (int b = lane; b < nb; b += 32) {
+          const float2 q = __ldcg(slot + (size_t)i * nb + b);
+          t = dfl_add(t, dfl{q.x, q.y});
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+          t = dfl_add(t, dfl{__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)});
+        if (lane == 0) sh_tot[i] = (double)t.hi + (double)t.lo;
+      }
+    } else {
+      double sd[kOcK], acc[kOcK];
+#pragma unroll
+      for (int j = 0; j < kOcK; j++) {
+        sd[j] = sh_s[j];
+        acc[j] = 0.0;
+      }
+      for (long long e = first; e < a.ne; e += stride) {
+        const double r = a.rho[e], b = a.B[e];
+#pragma unroll
+        for (int j = 0; j < kOcK; j++) acc[j] += b < 0.0 ? a.dmin : oc_clamp(r, b * sd[j], a.move, a.dmin);
+      }
+      block_sum<kOcK>(acc, sRed);
+      if (threadIdx.x == 0)
+        for (int j = 0; j < kOcK; j++) slot8[(size_t)j * nb + blockIdx.x] = acc[j];
+      if (!grid_sync(a.bar, gen)) return false;
+      for (int i = warp; i < kOcK; i += nw) {
+        double t = 0.0;
+        for (int b = lane; b < nb; b += 32) t += __ldcg(slot8 + (size_t)i * nb + b);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) sh_tot[i] = t;
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+  // widening pass(es) from l2 = 1e9; true when a bracket was found
+  auto widen = [&](bool f32) -> bool {
+    if (threadIdx.x == 0) {
+      sh_l[0] = 0.0;
+      sh_l[1] = 1e9;
+    }
+    __syncthreads();
     for (int round = 0; round < 20 && ok; round++) {
-      set_points(true, l1, l2);
-      double tot[kOcK];
-      ok = f32 ? sweep32(tot) : sweep64(tot);
+      set_points(true);
+      ok = pass(f32);
       passes++;
       if (!ok) break;
-      int jf = -1;
-#pragma unroll
-      for (int j = kOcK - 1; j >= 0; j--)
-        if (tot[j] - a.target <= 0.0) jf = j;
-      if (jf >= 0) {
-        if (jf > 0) l1 = lam[jf - 1];
-        l2 = lam[jf];
-        return true;
+      if (threadIdx.x == 0) {
+        int jf = -1;
+        for (int j = kOcK - 1; j >= 0; j--)
+          if (sh_tot[j] - a.target <= 0.0) jf = j;
+        if (jf >= 0) {
+          if (jf > 0) sh_l[0] = sh_lam[jf - 1];
+          sh_l[1] = sh_lam[jf];
+          sh_state = 1;
+        } else {
+          sh_l[0] = sh_lam[kOcK - 1];
+          sh_l[1] = sh_lam[kOcK - 1] * 10.0;
+          sh_state = isfinite(sh_l[1]) ? 0 : -1;
+        }
       }
-      l1 = lam[kOcK - 1];
-      l2 = lam[kOcK - 1] * 10.0;
-      if (!isfinite(l2)) break;
+      __syncthreads();
+      const int st = sh_state;
+      __syncthreads();
+      if (st != 0) return st == 1;
     }
     return false;
   };
-  // 16-way bisection until l2 - l1 <= rel (l1 + l2)
-  auto bisect = [&](bool f32, double rel, double& l1, double& l2) {
-    while (ok && (l2 - l1) > rel * (l1 + l2) && passes < 200) {
-      set_points(false, l1, l2);
-      double tot[kOcK];
-      ok = f32 ? sweep32(tot) : sweep64(tot);
+  // 16-way bisection until l2 - l1 <= rel (l1 + l2), or no progress
+  auto bisect = [&](bool f32, double rel) {
+    for (;;) {
+      if (threadIdx.x == 0) sh_state = (sh_l[1] - sh_l[0]) > rel * (sh_l[0] + sh_l[1]) && passes < 200;
+      __syncthreads();
+      const int go = sh_state;
+      __syncthreads();
+      if (!go || !ok) break;
+      set_points(false);
+      ok = pass(f32);
       passes++;
       if (!ok) break;
-      int jf = kOcK;
-#pragma unroll
-      for (int j = kOcK - 1; j >= 0; j--)
-        if (tot[j] - a.target <= 0.0) jf = j;
-      const double nl1 = jf > 0 ? lam[jf - 1] : l1;
-      const double nl2 = jf < kOcK ? lam[jf] : l2;
-      if (nl1 == l1 && nl2 == l2) break;  // the bracket cannot shrink further in this precision
-      l1 = nl1;
-      l2 = nl2;
+      if (threadIdx.x == 0) {
+        int jf = kOcK;
+        for (int j = kOcK - 1; j >= 0; j--)
+          if (sh_tot[j] - a.target <= 0.0) jf = j;
+        const double nl1 = jf > 0 ? sh_lam[jf - 1] : sh_l[0];
+        const double nl2 = jf < kOcK ? sh_lam[jf] : sh_l[1];
+        sh_state = !(nl1 == sh_l[0] && nl2 == sh_l[1]);  // the bracket cannot shrink further in this precision
+        sh_l[0] = nl1;
+        sh_l[1] = nl2;
+      }
+      __syncthreads();
+      const int moved = sh_state;
+      __syncthreads();
+      if (!moved) break;
     }
   };
 
-  double l1 = 0.0, l2 = 1e9, lfinal = 0.0;
-  bool found = widen(true, l1, l2), exact = false;
+  double lfinal = 0.0;
+  bool found = widen(true), exact = false;
+  int root = 0;
   if (found) {
-    bisect(true, 1e-5, l1, l2);
+    bisect(true, 1e-5);
     // certification of the FP32 bracket in FP64
-    const double c1 = l1 * (1.0 - 4e-5), c2 = l2 * (1.0 + 4e-5);
+    const double c1 = sh_l[0] * (1.0 - 4e-5), c2 = sh_l[1] * (1.0 + 4e-5);
     __shared__ double sh_s12[2];
     if (threadIdx.x == 0) {
       sh_s12[0] = c1 > 0.0 ? 1.0 / sqrt(c1) : 1e300;
@@ -430,26 +468,32 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
       const double rt = tot[2] / (a.target - tot[3]);
       lfinal = rt * rt;
       exact = lfinal >= c1 && lfinal <= c2;
+      root = exact ? 1 : 0;
     } else if (ok && sign && tot[4] <= (double)kOcList && c1 > 0.0) {
       __shared__ double s_root;
       if (threadIdx.x == 0) s_root = oc_piecewise_root(list, (int)tot[4], c1, c2, tot[3], tot[2], a.target);
       __syncthreads();
       lfinal = s_root;
       exact = lfinal > 0.0;
+      root = exact ? 2 : 0;
     }
     if (!exact) {
       if (sign) {
-        l1 = c1;
-        l2 = c2;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          sh_l[0] = c1;
+          sh_l[1] = c2;
+        }
+        __syncthreads();
       } else {
         found = false;
       }
     }
   }
   if (ok && !exact) {
-    if (!found) found = widen(false, l1, l2);
-    if (found) bisect(false, 1e-10, l1, l2);
-    lfinal = 0.5 * (l1 + l2);
+    if (!found) found = widen(false);
+    if (found) bisect(false, 1e-10);
+    lfinal = 0.5 * (sh_l[0] + sh_l[1]);
   }
   // final update
   __shared__ double sh_sfin;
@@ -492,6 +536,7 @@ __global__ void __launch_bounds__(256) oc_kernel(const __grid_constant__ OcArgs 
       a.st->volume = v[0];
       a.st->change = m;
       a.st->passes = passes;
+      a.st->root = root;
       a.st->flags = (ok ? 0 : ERR_TIMEOUT) | (found || exact ? 0 : ERR_NAN);
     }
   }

@@ -60,6 +60,7 @@ struct tp_problem {
   long long E_version = 0;       // bumped whenever the moduli are recomputed
   bool profile = false;          // time the multigrid finest-level launches
   int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
+  int oc_passes = 0, oc_root = 0;  // diagnostics of the last OC update
   double* rho_phys = nullptr;    // density-filtered densities (filter mode 1)
   double* rowsum = nullptr;      // sum_b W_ab per element (filter mode 1)
   double fmax[kMaxCases] = {};   // max |f| per load case (warm-start feature scale)

@@ -55,7 +55,7 @@ class tp_batch_info(C.Structure):
 
 class tp_step_info(C.Structure):
     _fields_ = [("solve", tp_solve_info), ("compliance", C.c_double), ("lambda_", C.c_double),
-                ("volume", C.c_double), ("change", C.c_double)]
+                ("volume", C.c_double), ("change", C.c_double), ("oc_passes", C.c_int), ("oc_root", C.c_int)]
 
 
 def _load():
