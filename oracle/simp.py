@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import fem, filt, oc, sens
+from . import fem, filt, helm, oc, sens
 
 
 def iteration(prob, rho, W=None, solve_method="lu", rtol=1e-13, filter_mode=0, K0cache=None):
@@ -17,17 +17,22 @@ def iteration(prob, rho, W=None, solve_method="lu", rtol=1e-13, filter_mode=0, K
     rho_new, lam, vol, change."""
     W = filt.weights_for(prob) if W is None else W
     passive = prob.passive
+    AT = helm.operator(prob) if filter_mode == 2 else None
     if filter_mode == 0:
         rho_phys = rho
-    else:
+    elif filter_mode == 1:
         rho_phys = filt.density_filter(W, rho)
+    else:  # the Helmholtz (PDE) filter of the paper's parallel runs
+        rho_phys = helm.apply(prob, rho, AT=AT)
     K = fem.assemble(prob, rho_phys)
     U = fem.solve(prob, rho_phys, method=solve_method, rtol=rtol, K=K)
     c, ce, dc = sens.sensitivities(prob, rho_phys, U)
     if filter_mode == 0:
         dcf = filt.sensitivity_filter(W, rho, dc)
-    else:
+    elif filter_mode == 1:
         dcf = filt.density_filter_chain(W, dc)
+    else:  # H is symmetric: d c / d rho = H (d c / d rho~)
+        dcf = helm.apply(prob, dc, AT=AT)
     rho_new, lam, vol, change, nb = oc.bisect(rho, dcf, prob.volfrac, prob.move, prob.dmin, passive)
     return dict(u=U, c=c, ce=ce, dc=dc, dcf=dcf, rho_new=rho_new, lam=lam, vol=vol,
                 change=change, n_bisect=nb)
