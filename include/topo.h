@@ -71,7 +71,7 @@ enum { TP_WARM_ZERO = 0, TP_WARM_PREVIOUS = 1, TP_WARM_USER = 2 };
  * coarsest grid (else TP_ERR_ARG); `precision` = TP_PREC_F64 starts with FP64
  * segments; `update_drop` is ignored. */
 enum { TP_PRECOND_JACOBI = 0, TP_PRECOND_MG = 1, TP_PRECOND_MG_FUSED = 2 };
-enum { TP_FILTER_SENSITIVITY = 0, TP_FILTER_DENSITY = 1 };
+enum { TP_FILTER_SENSITIVITY = 0, TP_FILTER_DENSITY = 1, TP_FILTER_HELMHOLTZ = 2 };
 /* Quantities for tp_get / tp_set (all FP64):
  *   TP_RHO   design densities rho[n_el]
  *   TP_U     displacements u[n_cases][n_dof] (the solution, or the warm start)
@@ -79,7 +79,7 @@ enum { TP_FILTER_SENSITIVITY = 0, TP_FILTER_DENSITY = 1 };
  *   TP_DCF   filtered sensitivities dc~[n_el] (after tp_filter)
  *   TP_CE    element energies sum_k u_e^T K0 u_e [n_el] (after tp_sensitivities)
  *   TP_RHO_PHYS  physical densities used for stiffness [n_el] (rho, or rho~ in
- *                the density-filter mode) */
+ *                the density and Helmholtz filter modes) */
 enum { TP_RHO = 0, TP_U = 1, TP_DC = 2, TP_DCF = 3, TP_CE = 4, TP_RHO_PHYS = 5 };
 
 /* Solver options.  tol: target TRUE relative residual ||f - K u||_2 / ||f||_2
@@ -167,11 +167,19 @@ tp_status tp_sensitivities(tp_problem* p, double* compliance);
  *   rho~ = W rho / rowsum (tp_set_filter_mode); dc then holds d c / d rho~
  *   and this call applies the chain rule dc~ = W^T (dc / rowsum).  The OC
  *   update keeps its volume constraint on rho.
+ * mode TP_FILTER_HELMHOLTZ: the PDE filter of the paper's parallel runs
+ *   (Section "Parallel implementation of topology optimization", after Lazarov
+ *   and Sigmund): rho~ = H rho with H = T^T (R^2 K_F + M_F)^-1 T, K_F and M_F
+ *   the bilinear / trilinear Laplacian stiffness and mass with natural
+ *   (Neumann) boundaries, T the element-to-node integral of the shape
+ *   functions, R = rmin / (2 sqrt 3).  H is symmetric, so dc~ = H dc.  Each
+ *   application solves the nodal system by Jacobi-PCG in FP64 to relative
+ *   residual 1e-14 (TP_ERR_NOT_CONVERGED otherwise) and synchronises.
  * `mode` must equal the problem's filter mode (else TP_ERR_STATE). */
 tp_status tp_filter(tp_problem* p, int mode);
 /* Filter mode of the problem (default TP_FILTER_SENSITIVITY); also the mode
- * tp_simp_step uses.  TP_FILTER_DENSITY makes tp_solve / tp_sensitivities use
- * rho~ = W rho / rowsum (TP_RHO_PHYS). */
+ * tp_simp_step uses.  TP_FILTER_DENSITY and TP_FILTER_HELMHOLTZ make tp_solve /
+ * tp_sensitivities use the filtered densities rho~ (TP_RHO_PHYS). */
 tp_status tp_set_filter_mode(tp_problem* p, int mode);
 
 /* OC update with bisection on lambda (Section 3.2, Eq. "update", Section 3.2.1):

@@ -43,7 +43,7 @@ void free_all(tp_problem* p) {
   void* ptrs[] = {p->rho, p->rho_new, p->E32, p->E64, p->mask, p->passive, p->f, p->x64,
                   p->inv32, p->inv64, p->w[0], p->w[1], p->w[2], p->w[3], p->w[4], p->w[5],
                   p->part, p->bar, p->cgs, p->tol2, p->ost, p->scal, p->dc, p->dcf, p->ce, p->bscr, p->abi,
-                  p->trace, p->nn_feat, p->nn_out, p->nn_scal, p->rho_phys, p->rowsum};
+                  p->trace, p->nn_feat, p->nn_out, p->nn_scal, p->rho_phys, p->rowsum, p->helm, p->hst};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete p->mg;
@@ -60,13 +60,30 @@ bool finite_all(const double* a, size_t n) {
 }
 
 // Densities that set the stiffness: rho, or its density filter in mode 1.
-const double* phys(const tp_problem* p) { return p->filter_mode == TP_FILTER_DENSITY ? p->rho_phys : p->rho; }
+const double* phys(const tp_problem* p) { return p->filter_mode == TP_FILTER_SENSITIVITY ? p->rho : p->rho_phys; }
+
+// out = H in with the Helmholtz filter (elements in and out); synchronises to
+// read the solver status.
+tp_status helm_filter(tp_problem* p, const double* in, double* out) {
+  TPCK(launch_helm_filter(p->stream, p->g, p->helm_a, in, out, p->helm, p->part, p->bar, p->hst, 1e-14, 2000, p->nsm),
+       "Helmholtz filter kernels");
+  p->launches += 3;
+  tp::HelmStatus st;
+  TPCK(cudaMemcpyAsync(&st, p->hst, sizeof(st), cudaMemcpyDeviceToHost, p->stream), "copy status");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");
+  if (st.flags & ERR_TIMEOUT) return fail(p, TP_ERR_TIMEOUT, "a device-side wait timed out in the Helmholtz filter");
+  if (st.flags) return fail(p, TP_ERR_NOT_CONVERGED, "the Helmholtz filter solve did not converge");
+  return TP_OK;
+}
 
 tp_status ensure_E(tp_problem* p) {
   if (!p->E_dirty) return TP_OK;
   if (p->filter_mode == TP_FILTER_DENSITY) {
     TPCK(launch_filter(p->stream, *p->flt, 1, p->rho, nullptr, p->rho_phys), "density filter kernel");
     p->launches++;
+  } else if (p->filter_mode == TP_FILTER_HELMHOLTZ) {
+    const tp_status st = helm_filter(p, p->rho, p->rho_phys);
+    if (st != TP_OK) return st;
   }
   TPCK(launch_young(p->stream, phys(p), p->E32, p->E64, p->ne, p->prm.E0, p->prm.Emin, p->prm.penal),
        "young kernel");
@@ -742,11 +759,19 @@ tp_status tp_sensitivities(tp_problem* p, double* compliance) {
 
 tp_status tp_set_filter_mode(tp_problem* p, int mode) {
   if (!p) return TP_ERR_ARG;
-  if (mode != TP_FILTER_SENSITIVITY && mode != TP_FILTER_DENSITY) return fail(p, TP_ERR_ARG, "unknown filter mode");
-  if (mode == TP_FILTER_DENSITY && !p->rho_phys) {
-    TPCK(dalloc(&p->rho_phys, p->ne), "alloc");
+  if (mode != TP_FILTER_SENSITIVITY && mode != TP_FILTER_DENSITY && mode != TP_FILTER_HELMHOLTZ)
+    return fail(p, TP_ERR_ARG, "unknown filter mode");
+  if (mode != TP_FILTER_SENSITIVITY && !p->rho_phys) TPCK(dalloc(&p->rho_phys, p->ne), "alloc");
+  if (mode == TP_FILTER_DENSITY && !p->rowsum) {
     TPCK(dalloc(&p->rowsum, p->ne), "alloc");
     TPCK(launch_filter(p->stream, *p->flt, 3, nullptr, nullptr, p->rowsum), "row-sum kernel");
+    p->launches++;
+  }
+  if (mode == TP_FILTER_HELMHOLTZ && !p->helm) {
+    TPCK(dalloc(&p->helm, helm_scratch_doubles(p->g)), "alloc");
+    TPCK(cudaMalloc((void**)&p->hst, sizeof(tp::HelmStatus)), "alloc");
+    helm_coefficients(p->dim, p->prm.rmin / (2.0 * std::sqrt(3.0)), p->helm_a);
+    TPCK(launch_helm_setup(p->stream, p->g, p->helm_a, p->helm), "Helmholtz setup kernel");
     p->launches++;
   }
   if (mode != p->filter_mode) {
@@ -760,15 +785,21 @@ tp_status tp_set_filter_mode(tp_problem* p, int mode) {
 
 tp_status tp_filter(tp_problem* p, int mode) {
   if (!p) return TP_ERR_ARG;
-  if (mode != TP_FILTER_SENSITIVITY && mode != TP_FILTER_DENSITY) return fail(p, TP_ERR_ARG, "unknown filter mode");
+  if (mode != TP_FILTER_SENSITIVITY && mode != TP_FILTER_DENSITY && mode != TP_FILTER_HELMHOLTZ)
+    return fail(p, TP_ERR_ARG, "unknown filter mode");
   if (mode != p->filter_mode)
     return fail(p, TP_ERR_STATE, "tp_filter mode differs from the problem's filter mode (tp_set_filter_mode)");
   if (!p->has_dc || !p->has_density) return fail(p, TP_ERR_STATE, "tp_sensitivities must precede tp_filter");
-  if (mode == TP_FILTER_SENSITIVITY)
+  if (mode == TP_FILTER_SENSITIVITY) {
     TPCK(launch_filter(p->stream, *p->flt, 0, p->rho, p->dc, p->dcf), "filter kernel");
-  else
+    p->launches++;
+  } else if (mode == TP_FILTER_DENSITY) {
     TPCK(launch_filter(p->stream, *p->flt, 2, p->rowsum, p->dc, p->dcf), "filter chain kernel");
-  p->launches++;
+    p->launches++;
+  } else {
+    const tp_status st = helm_filter(p, p->dc, p->dcf);  // H is symmetric: dc~ = H dc
+    if (st != TP_OK) return st;
+  }
   p->has_dcf = true;
   return TP_OK;
 }

@@ -97,6 +97,24 @@ struct FilterLaunch {
 };
 cudaError_t launch_filter(cudaStream_t s, const FilterLaunch& F, int mode, const double* rho,
                           const double* dc, double* out);
+// Helmholtz (PDE) filter (helm.cu): out = T^T (R^2 K_F + M_F)^-1 T in, element
+// values in and out.  a[4]: element-matrix entries by corner Hamming distance
+// (helm_coefficients); scratch: helm_scratch_doubles(g) doubles, whose last n_nodes
+// hold the inverse diagonal written by launch_helm_setup.  The nodal solve is
+// Jacobi-PCG in FP64 to relative residual tol (a persistent cooperative kernel;
+// zeroes the barrier word); st receives iterations, residual and error bits.
+struct HelmStatus {
+  int it;
+  int flags;
+  double rel;
+};
+void helm_coefficients(int dim, double R, double* a);
+size_t helm_scratch_doubles(const Grid& g);
+cudaError_t launch_helm_setup(cudaStream_t s, const Grid& g, const double* a, double* scratch);
+cudaError_t launch_helm_filter(cudaStream_t s, const Grid& g, const double* a, const double* in, double* out,
+                               double* scratch, double* part, GridBar* bar, HelmStatus* st, double tol, int max_it,
+                               int nsm);
+
 struct OcStatus {
   double lambda;
   double volume;

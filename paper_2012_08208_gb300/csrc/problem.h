@@ -61,7 +61,10 @@ struct tp_problem {
   bool profile = false;          // time the multigrid finest-level launches
   int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
   int oc_passes = 0, oc_root = 0;  // diagnostics of the last OC update
-  double* rho_phys = nullptr;    // density-filtered densities (filter mode 1)
+  double* rho_phys = nullptr;    // filtered densities (filter modes 1, 2)
+  double* helm = nullptr;        // Helmholtz filter scratch (filter mode 2)
+  tp::HelmStatus* hst = nullptr;
+  double helm_a[4] = {};         // its element-matrix entries
   double* rowsum = nullptr;      // sum_b W_ab per element (filter mode 1)
   double fmax[kMaxCases] = {};   // max |f| per load case (warm-start feature scale)
   // learned warm start scratch (allocated on first use)

@@ -23,6 +23,7 @@ TP_PREC_F64, TP_PREC_MIXED = 0, 1
 TP_WARM_ZERO, TP_WARM_PREVIOUS, TP_WARM_USER = 0, 1, 2
 TP_FILTER_SENSITIVITY = 0
 TP_FILTER_DENSITY = 1
+TP_FILTER_HELMHOLTZ = 2
 TP_PRECOND_JACOBI = 0
 TP_PRECOND_MG = 1
 TP_PRECOND_MG_FUSED = 2
