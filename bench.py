@@ -182,6 +182,7 @@ def run_ours(args):
             extras["matvec_2d"] = matvec_roofline(topo, torch, dev, stream, w,
                                                   "cantilever2d_600x200 Q4 FP32 K(rho)u", copies=96, reps=5)
             extras["learned"] = learned_extra(topo)
+            extras["helmholtz"] = helmholtz_extra(topo, torch, dev, stream)
         p.close()
 
     if rank != 0:
@@ -324,6 +325,51 @@ def learned_extra(topo, n_oc=(0, 5)):
                     "48x16x16 / 96x32x32 trajectories by paper_2012_08208_gb300.warmstart"}
 
 
+def helmholtz_extra(topo, torch, dev, stream, reps=5, steps=5, warmup=3):
+    """Helmholtz (PDE) filter mode: device time of one application rho~ = H rho
+    (right-hand side, FP64 Jacobi-PCG as one persistent kernel, element means;
+    the moduli and diagonal kernels that follow are included) at 600 x 200 and
+    240 x 80 x 80 on a random density, and SIMP iterations/s of the 600 x 200
+    cantilever in this filter mode with the multigrid solver."""
+    import workloads as W
+    out = {}
+    for w, label in ((W.cantilever2d(), "cantilever2d_600x200"), (W.cantilever3d_large(), "cantilever3d_240x80x80")):
+        p = topo.Problem.from_workload(w, stream=stream.cuda_stream)
+        p.set_filter_mode(topo.TP_FILTER_HELMHOLTZ)
+        rho = torch.tensor(W.random_density(w.n_el, seed=63, lo=0.001), dtype=torch.float64, device=dev)
+        phys = torch.empty_like(rho)
+        ms = []
+        for k in range(reps + 1):
+            p.set_density(rho)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.get(topo.TP_RHO_PHYS, out=phys)
+            e1.record(stream)
+            stream.synchronize()
+            if k:
+                ms.append(e0.elapsed_time(e1))
+        out[label] = {"n_el": w.n_el, "ms_per_filter": round(float(np.median(ms)), 4)}
+        p.close()
+    w = W.cantilever2d()
+    p = topo.Problem.from_workload(w, stream=stream.cuda_stream)
+    p.set_filter_mode(topo.TP_FILTER_HELMHOLTZ)
+    opts = topo.solve_opts(tol=w.tol, max_it=100000, warm_start=topo.TP_WARM_PREVIOUS, precond=topo.TP_PRECOND_MG)
+    for _ in range(warmup):
+        p.simp_step(opts, check=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        p.simp_step(opts, check=False)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out["simp_cantilever2d_600x200"] = {"ms_per_step": round(ms, 3), "simp_iter_s": round(1e3 / ms, 3),
+                                        "filter": "Helmholtz (two applications per step)", "solver": "multigrid-PCG"}
+    p.close()
+    return out
+
+
 def batch_extra(topo, torch, dev, stream, steps=5, warmup=3, ws=1, rank=0):
     """64 uneven 2D cantilevers (batch2d, seed 0) in one persistent graph-captured
     launch per step with the autotuned tile shape: instance SIMP iterations/s.
@@ -453,6 +499,8 @@ def run_only(args):
             out = {"workload": w.name, "n_dof": w.n_dof, "n_cases": w.n_cases, "iters": info.iters,
                    "updates": info.updates, "ms": round(info.ms, 3)}
             p.close()
+        elif args.only == "helmholtz":
+            out = helmholtz_extra(topo, torch, dev, stream)
         else:
             out = learned_extra(topo)
     print(json.dumps({args.only: out}))
@@ -467,13 +515,15 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned", "cg2d", "cg3d"], default=None,
+    ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned", "cg2d", "cg3d", "helmholtz"],
+                    default=None,
                     help="run one extra measurement alone (for profiling)")
     ap.add_argument("--copies", type=int, default=8)
     ap.add_argument("--precond", type=int, default=0,
                     help="0 Jacobi-PCG, 1 multigrid-PCG, 2 multigrid-PCG persistent kernel (--only cg2d / cg3d)")
-    ap.add_argument("--solver", type=int, default=1, help="solver of the timed SIMP step: 0 Jacobi-PCG, 1 multigrid-PCG, 2 the same with "
-                                                      "persistent segment kernels")
+    ap.add_argument("--solver", type=int, default=1,
+                    help="solver of the timed SIMP step: 0 Jacobi-PCG, 1 multigrid-PCG, 2 the same with persistent "
+                         "segment kernels")
     ap.add_argument("--reps", type=int, default=10)
     args = ap.parse_args()
     if args.only:
