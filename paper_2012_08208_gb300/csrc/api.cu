@@ -189,6 +189,7 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   TPCK(cudaEventRecord(p->ev0, s), "event");
   if (M.version != p->E_version) {
     TPCK(M.build(s, p->K0.data(), p->E32, &nl), "multigrid setup");
+    if (!M.coarse_ok) return fail(p, TP_ERR_BREAKDOWN, "multigrid coarsest FP32 inverse met a non-positive pivot");
     M.version = p->E_version;
   }
   TPCK(launch_to_abi(s, p->f, fA, p->nn, p->dim, nc), "layout kernel");

@@ -261,14 +261,14 @@ __global__ void prolong_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
     mgops::prolong_node<DIM, false>(gf, gc, f, mf, xc, xf, nd, offf, offc);
 }
 
-// Coarsest solve: x = A^-1 b with the dense inverse (mgops::dense_row); one
-// warp per row, blockIdx.y = case.
-__global__ void dense_solve_kernel(int n, const float* __restrict__ Ainv, const float* b, float* x,
+// Coarsest solve: x = A^-1 b with the dense inverse (mgops::dense_row), all
+// cases per row; one warp per row.
+__global__ void dense_solve_kernel(int n, int nc, const float* __restrict__ Ainv, const float* b, float* x,
                                    const int* __restrict__ stop) {
   if (halted(stop)) return;
   const int lane = threadIdx.x & 31;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5)
-    mgops::dense_row<false>(n, Ainv, b, x, i, (long long)blockIdx.y * n, lane);
+    mgops::dense_row<false>(n, nc, Ainv, b, x, i, lane);
 }
 
 int blocks(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152 * 16); }
@@ -294,38 +294,6 @@ Grid coarsen(const Grid& g, int f) {
   c.nn = (long long)c.nx * c.ny * c.nz;
   c.ne = (long long)c.ex * c.ey * c.ez;
   return c;
-}
-
-// In-place inverse of an SPD matrix (Cholesky, FP64, row-major n x n).
-bool spd_inverse(std::vector<double>& A, int n) {
-  std::vector<double> L(A);
-  for (int j = 0; j < n; j++) {
-    double d = L[(size_t)j * n + j];
-    for (int k = 0; k < j; k++) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-    if (!(d > 0.0)) return false;
-    const double ljj = std::sqrt(d);
-    L[(size_t)j * n + j] = ljj;
-    for (int i = j + 1; i < n; i++) {
-      double s = L[(size_t)i * n + j];
-      for (int k = 0; k < j; k++) s -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-      L[(size_t)i * n + j] = s / ljj;
-    }
-  }
-  // columns of A^-1: solve L L^T x = e_c
-  std::vector<double> y(n);
-  for (int c = 0; c < n; c++) {
-    for (int i = 0; i < n; i++) {
-      double s = i == c ? 1.0 : 0.0;
-      for (int k = 0; k < i; k++) s -= L[(size_t)i * n + k] * y[k];
-      y[i] = s / L[(size_t)i * n + i];
-    }
-    for (int i = n - 1; i >= 0; i--) {
-      double s = y[i];
-      for (int k = i + 1; k < n; k++) s -= L[(size_t)k * n + i] * A[(size_t)k * n + c];
-      A[(size_t)i * n + c] = s / L[(size_t)i * n + i];
-    }
-  }
-  return true;
 }
 
 }  // namespace
@@ -406,14 +374,16 @@ void MgHierarchy::release() {
       if (q) cudaFree(q);
   }
   lv.clear();
-  for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32, (void*)d32, (void*)p32b})
+  for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32, (void*)d32, (void*)p32b,
+                  (void*)dscratch, (void*)dflag})
     if (q) cudaFree(q);
   if (ctl_h) cudaFreeHost(ctl_h);
   cinv = nullptr;
   K0d = nullptr;
   ctl = nullptr;
   ctl_h = nullptr;
-  p32 = q32 = d32 = p32b = nullptr;
+  p32 = q32 = d32 = p32b = dscratch = nullptr;
+  dflag = nullptr;
   built = false;
 }
 
@@ -446,7 +416,9 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
   l0.mask = const_cast<uint8_t*>(mask0);
   l0.mask_own = false;
   lv.push_back(l0);
-  while ((int)lv.size() < 12 && lv.back().g.nn * g0.dim > max_coarse_dofs) {
+  // coarsen until the first level with at most max_coarse_dofs DOFs (the
+  // largest coarsest grid the dense inverse takes), at least once
+  while ((int)lv.size() < 12 && (lv.size() < 2 || lv.back().g.nn * g0.dim > max_coarse_dofs)) {
     const int f = common_factor(lv.back().g);
     if (!f) break;
     MgLevel l;
@@ -454,7 +426,7 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
     l.f = f;
     lv.push_back(l);
   }
-  if (lv.back().g.nn * g0.dim > 4096 || lv.size() < 2) return cudaErrorInvalidValue;
+  if (lv.back().g.nn * g0.dim > max_coarse_dofs || lv.size() < 2) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   for (size_t i = 0; i < lv.size() && e == cudaSuccess; i++) {
     MgLevel& l = lv[i];
@@ -475,6 +447,8 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
   }
   cn = (int)(lv.back().g.nn * g0.dim);
   if (e == cudaSuccess) e = cudaMalloc((void**)&cinv, (size_t)cn * cn * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dscratch, dense_scratch_floats(cn) * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dflag, sizeof(int));
   const size_t nv = (size_t)nc * g0.nn * g0.dim;
   if (e == cudaSuccess) e = cudaMalloc((void**)&p32, nv * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&q32, nv * sizeof(float));
@@ -526,44 +500,17 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // coarsest: assemble on the host in FP64 and invert (a few hundred DOFs)
+  // coarsest: dense FP32 inverse on the device (blocked Gauss-Jordan sweep)
   const MgLevel& c = lv.back();
-  std::vector<float> Kc((size_t)c.g.ne * nd * nd);
-  std::vector<uint8_t> mc(c.g.nn);
-  e = cudaMemcpyAsync(Kc.data(), c.K, Kc.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(mc.data(), c.mask, mc.size(), cudaMemcpyDeviceToHost, s);
+  e = dense_coarse_inverse(s, c.g, c.S, c.mask, cinv, dscratch, dflag, &nl);
+  int flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e;
-  const int n = cn, nce = dim == 2 ? 4 : 8;
-  std::vector<double> A((size_t)n * n, 0.0);
-  for (long long el = 0; el < c.g.ne; el++) {
-    const int I = (int)(el % c.g.ex), J = (int)((el / c.g.ex) % c.g.ey), Kz = (int)(el / ((long long)c.g.ex * c.g.ey));
-    long long nodes[8];
-    for (int q = 0; q < nce; q++)
-      nodes[q] = (I + cofs(q, 0)) + (long long)c.g.nx * ((J + cofs(q, 1)) + (long long)c.g.ny * (Kz + (dim == 3 ? cofs(q, 2) : 0)));
-    for (int a = 0; a < nd; a++)
-      for (int b = 0; b < nd; b++)
-        A[(size_t)(nodes[a / dim] * dim + a % dim) * n + nodes[b / dim] * dim + b % dim] += Kc[(size_t)el * nd * nd + a * nd + b];
-  }
-  for (int i = 0; i < n; i++)
-    if ((mc[i / dim] >> (i % dim)) & 1) {
-      for (int j = 0; j < n; j++) A[(size_t)i * n + j] = A[(size_t)j * n + i] = 0.0;
-      A[(size_t)i * n + i] = 1.0;
-    }
-  // symmetrise the FP32 sums
-  for (int i = 0; i < n; i++)
-    for (int j = i + 1; j < n; j++) {
-      const double v = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
-      A[(size_t)i * n + j] = A[(size_t)j * n + i] = v;
-    }
-  if (!spd_inverse(A, n)) return cudaErrorInvalidValue;
-  std::vector<float> Af((size_t)n * n);
-  for (size_t i = 0; i < Af.size(); i++) Af[i] = (float)A[i];
-  e = cudaMemcpyAsync(cinv, Af.data(), Af.size() * sizeof(float), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  built = e == cudaSuccess;
   if (nlaunch) *nlaunch += nl;
-  return e;
+  if (e != cudaSuccess) return e;
+  coarse_ok = flag == 0;
+  built = true;
+  return cudaSuccess;
 }
 
 // One V-cycle on level li (see mg.h for the entry state).  Sweeps alternate
@@ -574,7 +521,7 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   const int dim = l.g.dim;
   const long long ndof = l.g.nn * dim;
   if (li == (int)lv.size() - 1) {
-    dense_solve_kernel<<<dim3((cn + 7) / 8, nc), 256, 0, s>>>(cn, cinv, l.b, l.x[0], stop);
+    dense_solve_kernel<<<(cn + 7) / 8, 256, 0, s>>>(cn, nc, cinv, l.b, l.x[0], stop);
     (*nlaunch)++;
     *out = l.x[0];
     return cudaGetLastError();

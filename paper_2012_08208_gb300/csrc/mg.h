@@ -49,7 +49,10 @@ enum : int { MG_STOP_DONE = 1, MG_STOP_INNER = 2, MG_STOP_STALL = 4, MG_STOP_BRE
 struct MgHierarchy {
   std::vector<MgLevel> lv;
   int nc = 1, cn = 0;       // cases, DOFs of the coarsest level
-  float* cinv = nullptr;    // coarsest dense inverse [cn][cn]
+  float* cinv = nullptr;    // coarsest dense inverse [cn][cn] (FP32)
+  float* dscratch = nullptr;  // panels of the dense inversion
+  int* dflag = nullptr;       // set when a pivot of the dense inversion is not positive
+  bool coarse_ok = true;      // the last build's dense inversion met only positive pivots
   float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
   const float* E0 = nullptr;
   // Finest-level sweep for all cases on the library's strain-form FP32
@@ -103,10 +106,12 @@ struct MgHierarchy {
   double iter_bytes() const;
 
   // Level plan for grid g0: 2:1 while possible, then the smallest common odd
-  // factor, until the coarsest has <= max_coarse_dofs DOFs.  Allocates all
-  // buffers.  cudaErrorInvalidValue when no plan reaches <= 4096 coarse DOFs.
-  cudaError_t plan(const Grid& g0, const uint8_t* mask0, int nc, int max_coarse_dofs = 256);
-  // Galerkin coarse operators, diagonals and the coarsest inverse for moduli E32.
+  // factor, until the first level with <= max_coarse_dofs DOFs (coarsening at
+  // least once); that level is solved with a dense inverse.  Allocates all
+  // buffers.  cudaErrorInvalidValue when no plan reaches it.
+  cudaError_t plan(const Grid& g0, const uint8_t* mask0, int nc, int max_coarse_dofs = 4096);
+  // Galerkin coarse operators, diagonals and the coarsest dense inverse for
+  // moduli E32 (FP32 on the device; coarse_ok false if a pivot was not positive).
   cudaError_t build(cudaStream_t s, const double* K0, const float* E32, int* nlaunch);
   // x = V(b) on level li.  On entry lv[li].b holds b and lv[li].x[0] the first
   // sweep from zero, omega D^-1 b (written by whichever kernel produced b);
@@ -148,6 +153,13 @@ cudaError_t mg_update32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* 
 cudaError_t mg_update_p32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* p, const float* z);
 // x += d over n values (end of an FP32 segment).
 cudaError_t mg_merge(cudaStream_t s, long long n, double* x, const float* d);
+// Dense FP32 inverse of the coarsest level (mg_dense.cu): assembles the level's
+// coupling blocks S into A (n x n, n = nodes * dim; rows and columns of fixed
+// DOFs zero, 1 on their diagonal) and inverts it in place.  scratch holds
+// dense_scratch_floats(n) floats; *flag is set when a pivot is not positive.
+size_t dense_scratch_floats(int n);
+cudaError_t dense_coarse_inverse(cudaStream_t s, const Grid& g, const float* S, const uint8_t* mask, float* A,
+                                 float* scratch, int* flag, int* nlaunch);
 // One FP32 segment as a persistent cooperative kernel (mg_pcg.cu): before the
 // launch the control block (mg_seg_init), the finest b = (float) r and x[0] =
 // omega D^-1 b (mg_prep) and d = 0 must be in place; zeroes the barrier word.

@@ -198,16 +198,30 @@ __device__ __forceinline__ void prolong_node(const Grid& gf, const Grid& gc, int
     }
 }
 
-// Coarsest solve, row i of case offset off: x_i = sum_j Ainv_ij b_j; one warp
-// per row (all lanes call it), lane 0 stores.
+// Coarsest solve, row i for every case: x_c,i = sum_j Ainv_ij b_c,j (case
+// stride n); one warp per row (all lanes call it), the matrix read once for
+// all cases; lane 0 stores.
 template <bool CG>
-__device__ __forceinline__ void dense_row(int n, const float* __restrict__ Ainv, const float* b, float* x, int i,
-                                          long long off, int lane) {
-  float s = 0.f;
-  for (int j = lane; j < n; j += 32) s = fmaf(Ainv[(long long)i * n + j], ldv<CG>(b + off + j), s);
+__device__ __forceinline__ void dense_row(int n, int nc, const float* __restrict__ Ainv, const float* b, float* x,
+                                          int i, int lane) {
+  constexpr int kCases = 8;
+  float acc[kCases];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[off + i] = s;
+  for (int c = 0; c < kCases; c++) acc[c] = 0.f;
+  const float* Ar = Ainv + (long long)i * n;
+  for (int j = lane; j < n; j += 32) {
+    const float a = Ar[j];
+#pragma unroll
+    for (int c = 0; c < kCases; c++)
+      if (c < nc) acc[c] = fmaf(a, ldv<CG>(b + (long long)c * n + j), acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < kCases; c++) {
+    if (c >= nc) break;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+    if (lane == 0) x[(long long)c * n + i] = acc[c];
+  }
 }
 
 }  // namespace mgops

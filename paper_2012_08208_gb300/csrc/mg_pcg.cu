@@ -320,10 +320,7 @@ __global__ void __launch_bounds__(256, 2) mg_seg_kernel(const __grid_constant__ 
     }
     {
       const MgLevelArgs& l = a.lv[L - 1];
-      for (int it = (int)gwarp; it < nc * a.cn; it += (int)gwarps) {
-        const int cs = it / a.cn, i = it - cs * a.cn;
-        mgops::dense_row<true>(a.cn, a.cinv, l.b, l.x[0], i, (long long)cs * a.cn, lane);
-      }
+      for (int i = (int)gwarp; i < a.cn; i += (int)gwarps) mgops::dense_row<true>(a.cn, nc, a.cinv, l.b, l.x[0], i, lane);
       sync();
     }
     const float* xc = a.lv[L - 1].x[0];
