@@ -61,54 +61,104 @@ __global__ void copy_panel_kernel(const float* __restrict__ A, int n, int k0, in
   }
 }
 
-// P = A_kk^-1 (A_kk = R[:, k0 .. k0 + bk], padded with the identity) by an
-// unblocked sweep; one CTA of 256 threads, thread t holding row t / 4,
-// columns 16 (t % 4) .. + 16 in registers.  Pivot row and column go through
-// double-buffered shared arrays, so one barrier per pivot suffices (a thread
-// cannot overwrite a buffer before every thread has passed the barrier that
-// follows its last use).  A pivot that is not positive and finite sets *flag.
+// P = A_kk^-1 (A_kk = R[:, k0 .. k0 + bk], padded with the identity); one CTA
+// of 256 threads, the block in shared memory.  The block sweep runs over four
+// 16 x 16 sub-blocks: warp 0 inverts the diagonal sub-block by an unblocked
+// sweep held in registers (8 entries per lane, pivot row and column by warp
+// shuffles, no CTA barrier per pivot), then the whole CTA applies that
+// sub-block's rank-16 sweep to the 64 x 64 block.  A pivot that is not
+// positive and finite sets *flag.
 __global__ void __launch_bounds__(256) block_inverse_kernel(const float* __restrict__ R, int n, int k0, int bk,
                                                             float* __restrict__ P, int* flag) {
-  __shared__ float srow[2][kB], scol[2][kB];
-  const int r = threadIdx.x >> 2, ch = threadIdx.x & 3;
-  float m[16];
-#pragma unroll
-  for (int q = 0; q < 16; q++) {
-    const int d = 16 * ch + q;
-    m[q] = (r < bk && d < bk) ? R[(size_t)r * n + k0 + d] : (r == d ? 1.f : 0.f);
+  constexpr int kS = 16;
+  __shared__ float M[kB][kB + 1];
+  __shared__ float sQ[kS][kS + 1];  // inverse of the diagonal sub-block
+  __shared__ float sV[kB][kS + 1];  // M_:s Q
+  __shared__ float sW[kS][kB + 1];  // Q M_s:
+  for (int t = threadIdx.x; t < kB * kB; t += blockDim.x) {
+    const int c = t / kB, d = t - c * kB;
+    M[c][d] = (c < bk && d < bk) ? R[(size_t)c * n + k0 + d] : (c == d ? 1.f : 0.f);
   }
-  bool bad = false;
-  for (int p = 0; p < kB; p++) {
-    const int bsel = p & 1;
-    if (r == p) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int sb = 0; sb < kB / kS; sb++) {
+    const int s0 = sb * kS;
+    if (warp == 0) {
+      // lane: row lr = lane & 15, columns 8 * (lane >> 4) .. + 8 of the sub-block
+      const int lr = lane & 15, half = lane >> 4;
+      float m[8];
 #pragma unroll
-      for (int q = 0; q < 16; q++) srow[bsel][16 * ch + q] = m[q];
-    }
-    if (ch == (p >> 4)) {
-      float mp = 0.f;
+      for (int q = 0; q < 8; q++) m[q] = M[s0 + lr][s0 + 8 * half + q];
+      bool bad = false;
+#pragma unroll 1
+      for (int p = 0; p < kS; p++) {
+        float sel = 0.f;  // this lane's entry in column p (meaningful for lanes of column half p >> 3)
 #pragma unroll
-      for (int q = 0; q < 16; q++)
-        if (q == (p & 15)) mp = m[q];
-      scol[bsel][r] = mp;
+        for (int q = 0; q < 8; q++)
+          if (q == (p & 7)) sel = m[q];
+        const float dp = __shfl_sync(0xffffffffu, sel, p + 16 * (p >> 3));    // M[p][p]
+        const float colv = __shfl_sync(0xffffffffu, sel, lr + 16 * (p >> 3)); // M[lr][p]
+        float rd[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) rd[q] = __shfl_sync(0xffffffffu, m[q], p + 16 * half);  // M[p][8 half + q]
+        bad |= !(dp > 0.f && isfinite(dp));
+        const float inv = 1.f / dp, cr = colv * inv;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const int d = 8 * half + q;
+          float v;
+          if (lr == p) v = d == p ? -inv : m[q] * inv;
+          else if (d == p) v = cr;
+          else v = fmaf(-cr, rd[q], m[q]);
+          m[q] = v;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; q++) sQ[lr][8 * half + q] = -m[q];  // the sweep leaves -B^-1
+      if (lane == 0 && bad) atomicOr(flag, 1);
     }
     __syncthreads();
-    const float dp = srow[bsel][p];
-    bad |= !(dp > 0.f && isfinite(dp));
-    const float inv = __frcp_rn(dp), cr = scol[bsel][r] * inv;
+    // V = M_:s Q (kB x kS), W = Q M_s: (kS x kB) from the old block
+    for (int t = threadIdx.x; t < kB * kS; t += blockDim.x) {
+      const int i = t / kS, c = t - i * kS;
+      float v = 0.f;
 #pragma unroll
-    for (int q = 0; q < 16; q++) {
-      const int d = 16 * ch + q;
-      const float rd = srow[bsel][d];
-      float v;
-      if (r == p) v = d == p ? -inv : m[q] * inv;
-      else if (d == p) v = cr;
-      else v = fmaf(-cr, rd, m[q]);
-      m[q] = v;
+      for (int q = 0; q < kS; q++) v = fmaf(M[i][s0 + q], sQ[q][c], v);
+      sV[i][c] = v;
+      const int c2 = t / kB, j = t - c2 * kB;
+      float w = 0.f;
+#pragma unroll
+      for (int q = 0; q < kS; q++) w = fmaf(sQ[c2][q], M[s0 + q][j], w);
+      sW[c2][j] = w;
     }
-  }
-  if (threadIdx.x == 0 && bad) atomicOr(flag, 1);
+    __syncthreads();
+    // M_ij -= M_is Q M_sj = sV_i M_sj (i, j outside s) and the panels: all new
+    // values from the old block first (16 per thread), then the writes
+    float nv[kB * kB / 256];
 #pragma unroll
-  for (int q = 0; q < 16; q++) P[r * kB + 16 * ch + q] = -m[q];  // the sweep leaves -A_kk^-1
+    for (int k = 0; k < kB * kB / 256; k++) {
+      const int t = threadIdx.x + 256 * k, i = t / kB, j = t - i * kB;
+      const bool is = i >= s0 && i < s0 + kS, js = j >= s0 && j < s0 + kS;
+      float v;
+      if (is && js) v = -sQ[i - s0][j - s0];
+      else if (is) v = sW[i - s0][j];
+      else if (js) v = sV[i][j - s0];
+      else {
+        v = M[i][j];
+#pragma unroll
+        for (int q = 0; q < kS; q++) v = fmaf(-sV[i][q], M[s0 + q][j], v);
+      }
+      nv[k] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kB * kB / 256; k++) {
+      const int t = threadIdx.x + 256 * k;
+      M[t / kB][t % kB] = nv[k];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kB * kB; t += blockDim.x) P[t] = -M[t / kB][t % kB];  // -A_kk^-1 -> A_kk^-1
 }
 
 // W = P R (kB x n); one output per thread.
