@@ -61,8 +61,10 @@ enum { TP_WARM_ZERO = 0, TP_WARM_PREVIOUS = 1, TP_WARM_USER = 2 };
  * described above.  TP_PRECOND_MG: CG preconditioned by one geometric
  * multigrid V-cycle in FP32 per iteration (nested structured grids coarsened
  * 2:1 while the element counts are even, then by their smallest common odd
- * factor; Galerkin coarse operators; degree-2 Chebyshev smoothing on the
- * l1-Jacobi scaling; exact solve on a coarsest grid of at most 256 DOFs), in
+ * factor, down to the first grid of at most 4096 DOFs; Galerkin coarse
+ * operators; degree-2 Chebyshev smoothing on the l1-Jacobi scaling; a dense
+ * FP32 inverse of the coarsest operator formed on the device at every rebuild,
+ * TP_ERR_BREAKDOWN if it meets a non-positive pivot), in
  * segments that solve for an FP32 correction and restart from the FP64 true
  * residual (FP64 vectors and operator after a segment that gains less than
  * 100x).  The iterations run as replays of a CUDA graph.

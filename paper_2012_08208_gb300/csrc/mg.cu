@@ -1,7 +1,8 @@
 // Geometric multigrid preconditioner for the CG solve (not in the paper, which
 // factorises K directly): nested structured grids, Galerkin coarse operators
 // held as per-element matrices, Chebyshev smoothing on the l1-Jacobi scaling,
-// and an exact solve on the coarsest grid.
+// and a dense FP32 inverse of the coarsest grid (at most 4096 DOFs, formed on
+// the device; mg_dense.cu).
 //
 // Level 0 is the problem's grid with element matrices E_e K0.  A coarse
 // element of level l + 1 covers f^dim elements of level l (f = 2 while every
