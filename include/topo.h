@@ -297,6 +297,24 @@ tp_status tp_oc_update_noalloc(const double* rho, const double* dcf, const int8_
                                double volfrac, double move, double dmin, double* rho_new, void* cuda_stream,
                                double* lambda, double* volume, double* change);
 
+/* Dense SPD inverse in FP32: the coarsest-level solve of the multigrid
+ * preconditioner (TP_PRECOND_MG), exposed on its own.  Not in the paper, which
+ * factorises K directly; a multigrid coarsest grid small enough for a dense
+ * inverse is this library's choice.
+ * Method: a blocked symmetric sweep (Gauss-Jordan elimination without
+ * pivoting, 64-row pivot blocks, the upper triangle only; Beaton-Goodnight
+ * sweep operator in block form), every rank-64 update on the device in FP32.
+ * Arguments: a[n * n] (host, row-major; the upper triangle j >= i is read, the
+ * matrix is taken as symmetric) and ainv[n * n] (host, receives the full
+ * inverse); 1 <= n <= TP_SPD_INVERSE_MAX_N.  cuda_stream: the stream to run on
+ * (NULL = legacy default stream).  The call allocates n * n + 192 n + 8192
+ * floats of device memory for its duration and synchronises before it returns.
+ * Errors: TP_ERR_ARG for NULL arrays or n out of range; TP_ERR_BREAKDOWN when a
+ * pivot is not positive and finite (the matrix is not positive definite, or
+ * not in FP32; ainv then holds no inverse); TP_ERR_OOM, TP_ERR_CUDA. */
+#define TP_SPD_INVERSE_MAX_N 16384
+tp_status tp_spd_inverse_f32(const float* a, float* ainv, int n, void* cuda_stream);
+
 /* Phase tracing of the persistent CG (not in the paper; a profiling aid).
  * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at eight
  * points of each iteration into a ring of 32 iterations: 0 start, 1 operator

@@ -46,12 +46,22 @@ struct MgCtl {
 };
 enum : int { MG_STOP_DONE = 1, MG_STOP_INNER = 2, MG_STOP_STALL = 4, MG_STOP_BREAK = 8, MG_STOP_LIMIT = 16 };
 
+// Second stream and its two events for the look-ahead of the dense inversion
+// (mg_dense.cu): the pivot-block inversion of the next block runs on `side`.
+struct DenseStreams {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ready = nullptr, done = nullptr;
+  cudaError_t create();
+  void destroy();
+};
+
 struct MgHierarchy {
   std::vector<MgLevel> lv;
   int nc = 1, cn = 0;       // cases, DOFs of the coarsest level
   float* cinv = nullptr;    // coarsest dense inverse [cn][cn] (FP32)
   float* dscratch = nullptr;  // panels of the dense inversion
   int* dflag = nullptr;       // set when a pivot of the dense inversion is not positive
+  DenseStreams dstreams;
   bool coarse_ok = true;      // the last build's dense inversion met only positive pivots
   float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
   const float* E0 = nullptr;
@@ -153,13 +163,19 @@ cudaError_t mg_update32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* 
 cudaError_t mg_update_p32(cudaStream_t s, long long n, int nc, MgCtl* ctl, float* p, const float* z);
 // x += d over n values (end of an FP32 segment).
 cudaError_t mg_merge(cudaStream_t s, long long n, double* x, const float* d);
-// Dense FP32 inverse of the coarsest level (mg_dense.cu): assembles the level's
-// coupling blocks S into A (n x n, n = nodes * dim; rows and columns of fixed
-// DOFs zero, 1 on their diagonal) and inverts it in place.  scratch holds
-// dense_scratch_floats(n) floats; *flag is set when a pivot is not positive.
+// Dense FP32 inverse of an SPD matrix in place (mg_dense.cu): A (n x n,
+// row-major, device) holds the matrix (at least its upper triangle) and
+// receives the full inverse.  scratch holds dense_scratch_floats(n) floats;
+// *flag (device) is set when a pivot is not positive.  With ds.side set the
+// pivot inversions run on that stream, joined back into s before the return.
 size_t dense_scratch_floats(int n);
-cudaError_t dense_coarse_inverse(cudaStream_t s, const Grid& g, const float* S, const uint8_t* mask, float* A,
-                                 float* scratch, int* flag, int* nlaunch);
+cudaError_t dense_spd_inverse(cudaStream_t s, const DenseStreams& ds, float* A, int n, float* scratch, int* flag,
+                              int* nlaunch);
+// The coarsest level: assembles its coupling blocks S into A (n = nodes * dim;
+// rows and columns of fixed DOFs zero, 1 on their diagonal), then
+// dense_spd_inverse.
+cudaError_t dense_coarse_inverse(cudaStream_t s, const DenseStreams& ds, const Grid& g, const float* S,
+                                 const uint8_t* mask, float* A, float* scratch, int* flag, int* nlaunch);
 // One FP32 segment as a persistent cooperative kernel (mg_pcg.cu): before the
 // launch the control block (mg_seg_init), the finest b = (float) r and x[0] =
 // omega D^-1 b (mg_prep) and d = 0 must be in place; zeroes the barrier word.

@@ -12,8 +12,14 @@
 // their mirror), and a last pass negates and mirrors it.  Every step but the
 // small pivot inversion is a rank-kB update done by a tiled FP32 kernel.
 // (The sweep operator of Beaton and Goodnight, in block form.)
+//
+// Look-ahead: the row panel of block k + 1 after step k is formed directly
+// from the matrix before step k and the panels of step k (next_panel_kernel),
+// so the pivot inversion of block k + 1, a one-CTA kernel, runs on a second
+// stream while the trailing update of step k runs on the first.
 #include <algorithm>
 
+#include "../../include/topo.h"
 #include "mg.h"
 
 namespace tp {
@@ -21,7 +27,6 @@ namespace {
 
 constexpr int kB = 64;    // pivot block
 constexpr int kT = 128;   // trailing-update tile (kT x kT outputs per CTA)
-constexpr int kQ = 32;    // inner-dimension chunk staged in shared memory
 
 template <int DIM>
 __global__ void dense_assemble_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
@@ -175,15 +180,38 @@ __global__ void panel_kernel(const float* __restrict__ R, const float* __restric
   }
 }
 
+// Asynchronous global -> shared copies (cp.async); a zero source size fills
+// the destination with zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+constexpr size_t kTrailingSmem = (size_t)2 * kB * kT * sizeof(float);
+
 // A_ij -= sum_q R[q][i] W[q][j] on the upper-triangular tiles (J >= I): a
-// kT x kT tile per CTA (blockIdx.x enumerates the upper tiles row by row), a
-// contiguous 8 x 8 block of outputs per thread (rows 8 ty .., columns 8 tx ..),
-// so each inner step reads its 16 operands with four 128-bit shared loads; the
-// inner dimension in chunks of kQ staged in shared memory.
-__global__ void __launch_bounds__(256) trailing_kernel(float* __restrict__ A, int n, int nt, const float* __restrict__ R,
-                                                       const float* __restrict__ W) {
-  __shared__ __align__(16) float sU[kQ][kT];
-  __shared__ __align__(16) float sW[kQ][kT];
+// kT x kT tile per CTA (blockIdx.x enumerates the upper tiles row by row).
+// Both kB x kT panels are copied to shared memory asynchronously while the
+// CTA loads its tile of A into the accumulators; then kB rank-1 steps, each
+// thread owning rows 4 ty .. 4 ty + 3 and 64 + 4 ty .. of the tile and the
+// same pattern of columns (4 tx ..), so its operands are four 128-bit shared
+// loads and its tile rows are read and written as 128-bit words that a warp
+// covers contiguously.  V4 (n a multiple of 4: every row starts on a 16-byte
+// boundary) selects the 128-bit global accesses; otherwise scalar ones.
+template <bool V4>
+__global__ void __launch_bounds__(256, 2) trailing_kernel(float* __restrict__ A, int n, int nt,
+                                                          const float* __restrict__ R, const float* __restrict__ W) {
+  extern __shared__ __align__(16) float dsm[];
+  float* sU = dsm;            // [kB][kT]: R[q][i0 + c]
+  float* sW = dsm + kB * kT;  // [kB][kT]: W[q][j0 + c]
   int I = 0, rem = blockIdx.x;  // tile row I holds nt - I tiles
   while (rem >= nt - I) {
     rem -= nt - I;
@@ -191,44 +219,124 @@ __global__ void __launch_bounds__(256) trailing_kernel(float* __restrict__ A, in
   }
   const int J = I + rem;
   const int i0 = I * kT, j0 = J * kT;
+  if (V4) {
+    for (int t = threadIdx.x; t < kB * kT / 4; t += blockDim.x) {
+      const int q = t / (kT / 4), c = 4 * (t - q * (kT / 4));
+      const int i = i0 + c, j = j0 + c;
+      cp_async16(sU + q * kT + c, i < n ? R + (size_t)q * n + i : R, i < n);
+      cp_async16(sW + q * kT + c, j < n ? W + (size_t)q * n + j : W, j < n);
+    }
+  } else {
+#pragma unroll 1
+    for (int t = threadIdx.x; t < kB * kT; t += blockDim.x) {
+      const int q = t / kT, c = t - q * kT;
+      const int i = i0 + c, j = j0 + c;
+      cp_async4(sU + q * kT + c, i < n ? R + (size_t)q * n + i : R, i < n);
+      cp_async4(sW + q * kT + c, j < n ? W + (size_t)q * n + j : W, j < n);
+    }
+  }
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   float acc[8][8];
 #pragma unroll
-  for (int a = 0; a < 8; a++)
+  for (int a = 0; a < 8; a++) {
+    const int i = i0 + 4 * ty + (a & 3) + (kT / 2) * (a >> 2);
 #pragma unroll
-    for (int b = 0; b < 8; b++) acc[a][b] = 0.f;
-  for (int q0 = 0; q0 < kB; q0 += kQ) {
-    for (int t = threadIdx.x; t < kT * kQ; t += blockDim.x) {
-      const int q = t / kT, c = t - q * kT;  // both panels row-major in q: consecutive columns
-      const int i = i0 + c, j = j0 + c;
-      sU[q][c] = i < n ? R[(size_t)(q0 + q) * n + i] : 0.f;
-      sW[q][c] = j < n ? W[(size_t)(q0 + q) * n + j] : 0.f;
+    for (int h = 0; h < 2; h++) {
+      const int j = j0 + 4 * tx + (kT / 2) * h;
+      if (V4) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n && j < n) v = *reinterpret_cast<const float4*>(A + (size_t)i * n + j);
+        acc[a][4 * h] = v.x;
+        acc[a][4 * h + 1] = v.y;
+        acc[a][4 * h + 2] = v.z;
+        acc[a][4 * h + 3] = v.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) acc[a][4 * h + e] = (i < n && j + e < n) ? A[(size_t)i * n + j + e] : 0.f;
+      }
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int q = 0; q < kQ; q++) {
-      const float4 u0 = *reinterpret_cast<const float4*>(&sU[q][8 * ty]);
-      const float4 u1 = *reinterpret_cast<const float4*>(&sU[q][8 * ty + 4]);
-      const float4 w0 = *reinterpret_cast<const float4*>(&sW[q][8 * tx]);
-      const float4 w1 = *reinterpret_cast<const float4*>(&sW[q][8 * tx + 4]);
-      const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-      const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+  }
+  cp_async_wait_all();
+  __syncthreads();
+#pragma unroll 2
+  for (int q = 0; q < kB; q++) {
+    const float4 u0 = *reinterpret_cast<const float4*>(sU + q * kT + 4 * ty);
+    const float4 u1 = *reinterpret_cast<const float4*>(sU + q * kT + kT / 2 + 4 * ty);
+    const float4 w0 = *reinterpret_cast<const float4*>(sW + q * kT + 4 * tx);
+    const float4 w1 = *reinterpret_cast<const float4*>(sW + q * kT + kT / 2 + 4 * tx);
+    const float u[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+    const float w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
-      for (int a = 0; a < 8; a++)
+    for (int a = 0; a < 8; a++)
 #pragma unroll
-        for (int b = 0; b < 8; b++) acc[a][b] = fmaf(u[a], w[b], acc[a][b]);
-    }
-    __syncthreads();
+      for (int b = 0; b < 8; b++) acc[a][b] = fmaf(-u[a], w[b], acc[a][b]);
   }
 #pragma unroll
   for (int a = 0; a < 8; a++) {
-    const int i = i0 + 8 * ty + a;
+    const int i = i0 + 4 * ty + (a & 3) + (kT / 2) * (a >> 2);
     if (i >= n) continue;
 #pragma unroll
-    for (int b = 0; b < 8; b++) {
-      const int j = j0 + 8 * tx + b;
-      if (j < n) A[(size_t)i * n + j] -= acc[a][b];
+    for (int h = 0; h < 2; h++) {
+      const int j = j0 + 4 * tx + (kT / 2) * h;
+      if (V4) {
+        if (j < n)
+          *reinterpret_cast<float4*>(A + (size_t)i * n + j) =
+              make_float4(acc[a][4 * h], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+          if (j + e < n) A[(size_t)i * n + j + e] = acc[a][4 * h + e];
+      }
     }
+  }
+}
+
+// Row panel of the next pivot block: R1[c][j] = row k1 + c (k1 = k0 + bk,
+// c < bk1; zero rows below) of the matrix that step k (trailing update, then
+// panel writes) leaves, formed from the matrix before step k.  Columns of
+// block k are the written panel, W[j - k0][k1 + c]; every other entry is its
+// stored (upper-triangle) value minus the rank-kB update in the order and
+// operand pairing trailing_kernel uses, so R1 equals those rows bit for bit.
+// kNP columns per CTA; the panels' columns it needs staged in shared memory.
+constexpr int kNP = 16;
+__global__ void __launch_bounds__(256) next_panel_kernel(const float* __restrict__ A, int n, int k0, int bk, int bk1,
+                                                         const float* __restrict__ R, const float* __restrict__ W,
+                                                         float* __restrict__ R1) {
+  __shared__ float sRr[kB][kB], sWr[kB][kB];     // R[q][k1 + c], W[q][k1 + c]
+  __shared__ float sRj[kB][kNP], sWj[kB][kNP];   // R[q][j0 + jj], W[q][j0 + jj]
+  const int k1 = k0 + bk, j0 = blockIdx.x * kNP;
+  for (int t = threadIdx.x; t < kB * kB; t += blockDim.x) {
+    const int q = t / kB, c = t - q * kB;
+    const bool ok = c < bk1;
+    sRr[q][c] = ok ? R[(size_t)q * n + k1 + c] : 0.f;
+    sWr[q][c] = ok ? W[(size_t)q * n + k1 + c] : 0.f;
+  }
+  for (int t = threadIdx.x; t < kB * kNP; t += blockDim.x) {
+    const int q = t / kNP, jj = t - q * kNP, j = j0 + jj;
+    sRj[q][jj] = j < n ? R[(size_t)q * n + j] : 0.f;
+    sWj[q][jj] = j < n ? W[(size_t)q * n + j] : 0.f;
+  }
+  __syncthreads();
+  const int jj = threadIdx.x % kNP, cg = threadIdx.x / kNP;
+  const int j = j0 + jj;
+  if (j >= n) return;
+  for (int c = cg; c < kB; c += 256 / kNP) {
+    float v = 0.f;
+    if (c < bk1) {
+      const int r = k1 + c;
+      if (j >= k0 && j < k1) {
+        v = W[(size_t)(j - k0) * n + r];
+      } else if (j >= r) {  // stored at (r, j)
+        v = A[(size_t)r * n + j];
+#pragma unroll 8
+        for (int q = 0; q < kB; q++) v = fmaf(-sRr[q][c], sWj[q][jj], v);
+      } else {  // stored at (j, r)
+        v = A[(size_t)j * n + r];
+#pragma unroll 8
+        for (int q = 0; q < kB; q++) v = fmaf(-sRj[q][jj], sWr[q][c], v);
+      }
+    }
+    R1[(size_t)c * n + j] = v;
   }
 }
 
@@ -260,30 +368,67 @@ int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>(
 
 }  // namespace
 
-size_t dense_scratch_floats(int n) { return (size_t)2 * n * kB + kB * kB; }
+size_t dense_scratch_floats(int n) { return (size_t)3 * n * kB + 2 * kB * kB; }
 
-cudaError_t dense_coarse_inverse(cudaStream_t s, const Grid& g, const float* S, const uint8_t* mask, float* A,
-                                 float* scratch, int* flag, int* nlaunch) {
-  const int n = (int)(g.nn * g.dim);
-  float* R = scratch;
-  float* W = R + (size_t)n * kB;
-  float* P = W + (size_t)n * kB;
-  cudaError_t e = cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(float), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+cudaError_t DenseStreams::create() {
+  if (side) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+  if (e != cudaSuccess) destroy();
+  return e;
+}
+
+void DenseStreams::destroy() {
+  if (ready) cudaEventDestroy(ready);
+  if (done) cudaEventDestroy(done);
+  if (side) cudaStreamDestroy(side);
+  side = nullptr;
+  ready = done = nullptr;
+}
+
+cudaError_t dense_spd_inverse(cudaStream_t s, const DenseStreams& ds, float* A, int n, float* scratch, int* flag,
+                              int* nlaunch) {
+  float* Rb[2] = {scratch, scratch + (size_t)n * kB};
+  float* W = scratch + (size_t)2 * n * kB;
+  float* Pb[2] = {W + (size_t)n * kB, W + (size_t)n * kB + kB * kB};
+  const bool v4 = (n & 3) == 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(v4 ? (const void*)trailing_kernel<true> : (const void*)trailing_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrailingSmem);
   if (e != cudaSuccess) return e;
-  if (g.dim == 2) dense_assemble_kernel<2><<<grid_for(n), 256, 0, s>>>(g, S, mask, A);
-  else dense_assemble_kernel<3><<<grid_for(n), 256, 0, s>>>(g, S, mask, A);
-  int nl = 1;
+  int nl = 0;
   const int nt = (n + kT - 1) / kT, ntiles = nt * (nt + 1) / 2;
-  for (int k0 = 0; k0 < n; k0 += kB) {
-    const int bk = std::min(kB, n - k0);
-    copy_panel_kernel<<<grid_for((long long)n * kB), 256, 0, s>>>(A, n, k0, bk, R);
-    block_inverse_kernel<<<1, 256, 0, s>>>(R, n, k0, bk, P, flag);
-    panel_kernel<<<grid_for((long long)n * kB), 256, 0, s>>>(R, P, n, W);
-    trailing_kernel<<<ntiles, 256, 0, s>>>(A, n, nt, R, W);
-    write_panels_kernel<<<grid_for((long long)n * bk), 256, 0, s>>>(A, n, k0, bk, W, P);
-    nl += 5;
-    e = cudaGetLastError();
+  copy_panel_kernel<<<grid_for((long long)n * kB), 256, 0, s>>>(A, n, 0, std::min(kB, n), Rb[0]);
+  block_inverse_kernel<<<1, 256, 0, s>>>(Rb[0], n, 0, std::min(kB, n), Pb[0], flag);
+  nl += 2;
+  for (int k0 = 0, it = 0; k0 < n; k0 += kB, it++) {
+    const int cur = it & 1, bk = std::min(kB, n - k0), k1 = k0 + bk;
+    panel_kernel<<<grid_for((long long)n * kB), 256, 0, s>>>(Rb[cur], Pb[cur], n, W);
+    nl++;
+    if (k1 < n) {
+      const int bk1 = std::min(kB, n - k1);
+      next_panel_kernel<<<(n + kNP - 1) / kNP, 256, 0, s>>>(A, n, k0, bk, bk1, Rb[cur], W, Rb[cur ^ 1]);
+      nl++;
+      cudaStream_t sb = s;
+      if (ds.side) {
+        e = cudaEventRecord(ds.ready, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ds.side, ds.ready, 0);
+        if (e != cudaSuccess) return e;
+        sb = ds.side;
+      }
+      block_inverse_kernel<<<1, 256, 0, sb>>>(Rb[cur ^ 1], n, k1, bk1, Pb[cur ^ 1], flag);
+      nl++;
+      if (ds.side) e = cudaEventRecord(ds.done, ds.side);
+      if (e != cudaSuccess) return e;
+    }
+    if (v4) trailing_kernel<true><<<ntiles, 256, kTrailingSmem, s>>>(A, n, nt, Rb[cur], W);
+    else trailing_kernel<false><<<ntiles, 256, kTrailingSmem, s>>>(A, n, nt, Rb[cur], W);
+    write_panels_kernel<<<grid_for((long long)n * bk), 256, 0, s>>>(A, n, k0, bk, W, Pb[cur]);
+    nl += 2;
+    if (k1 < n && ds.side) e = cudaStreamWaitEvent(s, ds.done, 0);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   negate_mirror_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(A, n);
@@ -292,4 +437,45 @@ cudaError_t dense_coarse_inverse(cudaStream_t s, const Grid& g, const float* S, 
   return cudaGetLastError();
 }
 
+cudaError_t dense_coarse_inverse(cudaStream_t s, const DenseStreams& ds, const Grid& g, const float* S,
+                                 const uint8_t* mask, float* A, float* scratch, int* flag, int* nlaunch) {
+  const int n = (int)(g.nn * g.dim);
+  cudaError_t e = cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  if (g.dim == 2) dense_assemble_kernel<2><<<grid_for(n), 256, 0, s>>>(g, S, mask, A);
+  else dense_assemble_kernel<3><<<grid_for(n), 256, 0, s>>>(g, S, mask, A);
+  if (nlaunch) (*nlaunch)++;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return dense_spd_inverse(s, ds, A, n, scratch, flag, nlaunch);
+}
+
 }  // namespace tp
+
+extern "C" tp_status tp_spd_inverse_f32(const float* a, float* ainv, int n, void* cuda_stream) {
+  if (!a || !ainv || n < 1 || n > TP_SPD_INVERSE_MAX_N) return TP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t bytes = (size_t)n * n * sizeof(float);
+  float *dA = nullptr, *scr = nullptr;
+  int* flag = nullptr;
+  tp::DenseStreams ds;
+  cudaError_t e = cudaMalloc((void**)&dA, bytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&scr, tp::dense_scratch_floats(n) * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&flag, sizeof(int));
+  const bool oom = e == cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = ds.create();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dA, a, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = tp::dense_spd_inverse(s, ds, dA, n, scr, flag, nullptr);
+  int hflag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ainv, dA, bytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  ds.destroy();
+  for (void* q : {(void*)dA, (void*)scr, (void*)flag})
+    if (q) cudaFree(q);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return oom ? TP_ERR_OOM : TP_ERR_CUDA;
+  }
+  return hflag ? TP_ERR_BREAKDOWN : TP_OK;
+}

@@ -200,7 +200,11 @@ __device__ __forceinline__ void prolong_node(const Grid& gf, const Grid& gc, int
 
 // Coarsest solve, row i for every case: x_c,i = sum_j Ainv_ij b_c,j (case
 // stride n); one warp per row (all lanes call it), the matrix read once for
-// all cases; lane 0 stores.
+// all cases; lane 0 stores.  When n is a multiple of 4 (rows and case vectors
+// then start on 16-byte boundaries: the buffers are whole allocations) each
+// lane reads 128-bit words (four in flight in the standalone kernel, one in
+// the register-bound persistent kernel); the row is otherwise read one float
+// per lane.
 template <bool CG>
 __device__ __forceinline__ void dense_row(int n, int nc, const float* __restrict__ Ainv, const float* b, float* x,
                                           int i, int lane) {
@@ -209,11 +213,27 @@ __device__ __forceinline__ void dense_row(int n, int nc, const float* __restrict
 #pragma unroll
   for (int c = 0; c < kCases; c++) acc[c] = 0.f;
   const float* Ar = Ainv + (long long)i * n;
-  for (int j = lane; j < n; j += 32) {
-    const float a = Ar[j];
+  if ((n & 3) == 0) {
+    const float4* A4 = reinterpret_cast<const float4*>(Ar);
+    const int n4 = n >> 2;
+#pragma unroll(CG ? 1 : 4)
+    for (int j = lane; j < n4; j += 32) {
+      const float4 a = __ldg(A4 + j);
 #pragma unroll
-    for (int c = 0; c < kCases; c++)
-      if (c < nc) acc[c] = fmaf(a, ldv<CG>(b + (long long)c * n + j), acc[c]);
+      for (int c = 0; c < kCases; c++)
+        if (c < nc) {
+          const float4* bp = reinterpret_cast<const float4*>(b + (long long)c * n) + j;
+          const float4 v = CG ? __ldcg(bp) : *bp;
+          acc[c] = fmaf(a.x, v.x, fmaf(a.y, v.y, fmaf(a.z, v.z, fmaf(a.w, v.w, acc[c]))));
+        }
+    }
+  } else {
+    for (int j = lane; j < n; j += 32) {
+      const float a = Ar[j];
+#pragma unroll
+      for (int c = 0; c < kCases; c++)
+        if (c < nc) acc[c] = fmaf(a, ldv<CG>(b + (long long)c * n + j), acc[c]);
+    }
   }
 #pragma unroll
   for (int c = 0; c < kCases; c++) {

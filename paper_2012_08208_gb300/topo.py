@@ -98,6 +98,7 @@ def _load():
         "tp_batch_launch_count": (C.c_longlong, [P]),
         "tp_oc_update_noalloc": (C.c_int, [P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double, P, P,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "tp_spd_inverse_f32": (C.c_int, [P, P, C.c_int, P]),
         "tp_get_trace": (C.c_int, [P, P]),
         "tp_set_profile": (C.c_int, [P, C.c_int]),
         "tp_get_profile": (C.c_int, [P, P]),
@@ -134,7 +135,7 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
-            "tp_oc_update_noalloc", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
@@ -143,6 +144,7 @@ EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_laun
             "tp_warm_start_nn"]
 TPNN_FEATURES = 8
 NOALLOC_MAX_ELEMENTS = 1048576
+SPD_INVERSE_MAX_N = 16384
 
 
 def oc_update_noalloc(rho, dcf, rho_new, volfrac, move=0.2, dmin=1e-3, passive=None, stream=None):
@@ -158,6 +160,22 @@ def oc_update_noalloc(rho, dcf, rho_new, volfrac, move=0.2, dmin=1e-3, passive=N
     if st != TP_OK:
         raise TopoError(st, "tp_oc_update_noalloc failed")
     return lam.value, vol.value, ch.value
+
+
+def spd_inverse(a, stream=None):
+    """Inverse of a symmetric positive definite matrix in FP32 by the library's
+    dense blocked sweep (tp_spd_inverse_f32 in include/topo.h; the multigrid
+    coarsest-level solve).  a: (n, n) NumPy array, read as float32 (upper
+    triangle).  Returns the (n, n) float32 inverse."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("a must be square")
+    out = np.empty_like(a)
+    st = lib.tp_spd_inverse_f32(a.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p), a.shape[0],
+                                C.c_void_p(0 if stream is None else int(stream)))
+    if st != TP_OK:
+        raise TopoError(st, "tp_spd_inverse_f32 failed")
+    return out
 
 
 class TopoError(RuntimeError):

@@ -141,6 +141,47 @@ def test_oc_update(topo, n, vf, passive):
     p.close()
 
 
+@pytest.mark.parametrize("n", [1, 5, 64, 130, 300, 1000, 3952])
+def test_spd_inverse_against_fp64(topo, n):
+    """Dense FP32 inverse (the multigrid coarsest solve) against the FP64
+    inverse of the same float32 matrix.  Sizes span one pivot block, ragged
+    pivot blocks and trailing tiles, the scalar path (n = 130, 5: not a
+    multiple of 4) and the coarsest size of the 600 x 200 cantilever (3952).
+    Condition number 100: the FP32 sweep keeps |X - A^-1| / max|A^-1| within
+    kappa * u * O(10) ~ 1e-4; the bound written is 1e-3.  The result is
+    mirrored from one triangle, so it is exactly symmetric."""
+    a = W.random_spd(n, cond=100.0, seed=n)
+    x = topo.spd_inverse(a)
+    ref = np.linalg.inv(a.astype(np.float64))
+    err = np.abs(x - ref).max() / np.abs(ref).max()
+    assert err <= 1e-3, err
+    assert np.array_equal(x, x.T)
+
+
+def test_spd_inverse_diagonal_exact(topo):
+    """A diagonal matrix: every off-diagonal product is an exact zero, so the
+    sweep returns the correctly rounded reciprocals bit for bit."""
+    d = np.random.default_rng(3).uniform(0.5, 2.0, size=300).astype(np.float32)
+    x = topo.spd_inverse(np.diag(d))
+    assert np.array_equal(x, np.diag(np.float32(1.0) / d))
+
+
+def test_spd_inverse_errors(topo):
+    """A negative pivot (indefinite matrix) gives TP_ERR_BREAKDOWN; n out of
+    range gives TP_ERR_ARG before any device work."""
+    d = np.ones(200, dtype=np.float32)
+    d[70] = -1.0
+    with pytest.raises(topo.TopoError) as ei:
+        topo.spd_inverse(np.diag(d))
+    assert ei.value.status == topo.TP_ERR_BREAKDOWN
+    import ctypes
+    buf = np.zeros(4, dtype=np.float32)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    assert topo.lib.tp_spd_inverse_f32(ptr, ptr, 0, None) == topo.TP_ERR_ARG
+    assert topo.lib.tp_spd_inverse_f32(ptr, ptr, topo.SPD_INVERSE_MAX_N + 1, None) == topo.TP_ERR_ARG
+    assert topo.lib.tp_spd_inverse_f32(None, ptr, 2, None) == topo.TP_ERR_ARG
+
+
 @pytest.mark.parametrize("n_special", [1, 100])
 def test_oc_update_breakpoint_at_root(topo, n_special):
     """Clamp breakpoints exactly at the root (lambda* = 1): the FP64

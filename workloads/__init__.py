@@ -260,6 +260,16 @@ def random_sensitivity(n_el: int, seed: int = 5) -> np.ndarray:
     return -rng.uniform(1e-4, 1.0, size=n_el) * 10.0 ** rng.uniform(-2, 2, size=n_el)
 
 
+def random_spd(n: int, cond: float = 100.0, seed: int = 7) -> np.ndarray:
+    """Symmetric positive definite float32 matrix Q diag(lam) Q^T: Q from the QR
+    factorisation of a Gaussian matrix, lam log-uniform in [1, cond], seeded."""
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    lam = cond ** rng.uniform(0.0, 1.0, size=n)
+    a = (q * lam) @ q.T
+    return (0.5 * (a + a.T)).astype(np.float32)
+
+
 CONFIGS = {
     "mbb2d_60x20": mbb2d,
     "cantilever2d_600x200": cantilever2d,
