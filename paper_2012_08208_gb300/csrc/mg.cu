@@ -385,7 +385,7 @@ void MgHierarchy::release() {
   ctl_h = nullptr;
   p32 = q32 = d32 = p32b = dscratch = nullptr;
   dflag = nullptr;
-  dstreams.destroy();
+  dinv.destroy();
   built = false;
 }
 
@@ -504,8 +504,8 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
   }
   // coarsest: dense FP32 inverse on the device (blocked Gauss-Jordan sweep)
   const MgLevel& c = lv.back();
-  e = dstreams.create();
-  if (e == cudaSuccess) e = dense_coarse_inverse(s, dstreams, c.g, c.S, c.mask, cinv, dscratch, dflag, &nl);
+  e = dinv.create();
+  if (e == cudaSuccess) e = dense_coarse_inverse(s, dinv, c.g, c.S, c.mask, cinv, dscratch, dflag, &nl);
   int flag = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

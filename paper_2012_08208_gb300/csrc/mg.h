@@ -46,11 +46,17 @@ struct MgCtl {
 };
 enum : int { MG_STOP_DONE = 1, MG_STOP_INNER = 2, MG_STOP_STALL = 4, MG_STOP_BREAK = 8, MG_STOP_LIMIT = 16 };
 
-// Second stream and its two events for the look-ahead of the dense inversion
-// (mg_dense.cu): the pivot-block inversion of the next block runs on `side`.
-struct DenseStreams {
-  cudaStream_t side = nullptr;
+// Runs the dense inversion (mg_dense.cu) as one CUDA graph: the launches
+// are captured once per (matrix, operands, scratch, size) on the private
+// stream `cap`, with the second stream `side` and the two events giving the
+// look-ahead its fork and join, and each later call replays the graph on the
+// caller's stream (several hundred launches for one host call).
+struct DenseInverter {
+  cudaStream_t side = nullptr, cap = nullptr;
   cudaEvent_t ready = nullptr, done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* key[5] = {};
+  int key_n = 0, launches = 0;
   cudaError_t create();
   void destroy();
 };
@@ -61,7 +67,7 @@ struct MgHierarchy {
   float* cinv = nullptr;    // coarsest dense inverse [cn][cn] (FP32)
   float* dscratch = nullptr;  // panels of the dense inversion
   int* dflag = nullptr;       // set when a pivot of the dense inversion is not positive
-  DenseStreams dstreams;
+  DenseInverter dinv;
   bool coarse_ok = true;      // the last build's dense inversion met only positive pivots
   float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
   const float* E0 = nullptr;
@@ -166,15 +172,15 @@ cudaError_t mg_merge(cudaStream_t s, long long n, double* x, const float* d);
 // Dense FP32 inverse of an SPD matrix in place (mg_dense.cu): A (n x n,
 // row-major, device) holds the matrix (at least its upper triangle) and
 // receives the full inverse.  scratch holds dense_scratch_floats(n) floats;
-// *flag (device) is set when a pivot is not positive.  With ds.side set the
-// pivot inversions run on that stream, joined back into s before the return.
+// *flag (device) is set when a pivot is not positive.  Replays (capturing
+// first when needed) the inverter's graph on s; ds must have been created.
 size_t dense_scratch_floats(int n);
-cudaError_t dense_spd_inverse(cudaStream_t s, const DenseStreams& ds, float* A, int n, float* scratch, int* flag,
+cudaError_t dense_spd_inverse(cudaStream_t s, DenseInverter& ds, float* A, int n, float* scratch, int* flag,
                               int* nlaunch);
 // The coarsest level: assembles its coupling blocks S into A (n = nodes * dim;
-// rows and columns of fixed DOFs zero, 1 on their diagonal), then
-// dense_spd_inverse.
-cudaError_t dense_coarse_inverse(cudaStream_t s, const DenseStreams& ds, const Grid& g, const float* S,
+// rows and columns of fixed DOFs zero, 1 on their diagonal), then inverts it
+// as dense_spd_inverse does; one graph for both.
+cudaError_t dense_coarse_inverse(cudaStream_t s, DenseInverter& ds, const Grid& g, const float* S,
                                  const uint8_t* mask, float* A, float* scratch, int* flag, int* nlaunch);
 // One FP32 segment as a persistent cooperative kernel (mg_pcg.cu): before the
 // launch the control block (mg_seg_init), the finest b = (float) r and x[0] =

@@ -15,8 +15,10 @@
 //
 // Look-ahead: the row panel of block k + 1 after step k is formed directly
 // from the matrix before step k and the panels of step k (next_panel_kernel),
-// so the pivot inversion of block k + 1, a one-CTA kernel, runs on a second
-// stream while the trailing update of step k runs on the first.
+// and the trailing update of step k skips the rows and columns of block k + 1
+// (the panel writes of step k + 1 replace them).  So that panel and the pivot
+// inversion of block k + 1, a one-CTA kernel, run on a second stream while
+// the trailing update of step k runs on the first.
 #include <algorithm>
 
 #include "../../include/topo.h"
@@ -71,21 +73,26 @@ __global__ void copy_panel_kernel(const float* __restrict__ A, int n, int k0, in
 // 16 x 16 sub-blocks: warp 0 inverts the diagonal sub-block by an unblocked
 // sweep held in registers (8 entries per lane, pivot row and column by warp
 // shuffles, no CTA barrier per pivot), then the whole CTA applies that
-// sub-block's rank-16 sweep to the 64 x 64 block.  A pivot that is not
-// positive and finite sets *flag.
+// sub-block's rank-16 sweep to the 64 x 64 block, each thread owning a 4 x 4
+// tile (rows 4 ty .., columns 4 tx ..) so that every inner step is two
+// 128-bit shared loads for 16 FMAs.  A pivot that is not positive and finite
+// sets *flag.
+constexpr int kS = 16;       // sub-block of the pivot-block sweep
+constexpr int kLd = kB + 4;  // row stride of the shared block (16-byte rows, rotated banks)
 __global__ void __launch_bounds__(256) block_inverse_kernel(const float* __restrict__ R, int n, int k0, int bk,
                                                             float* __restrict__ P, int* flag) {
-  constexpr int kS = 16;
-  __shared__ float M[kB][kB + 1];
-  __shared__ float sQ[kS][kS + 1];  // inverse of the diagonal sub-block
-  __shared__ float sV[kB][kS + 1];  // M_:s Q
-  __shared__ float sW[kS][kB + 1];  // Q M_s:
+  __shared__ __align__(16) float M[kB * kLd];
+  __shared__ __align__(16) float sQ[kS * (kS + 4)];  // inverse of the diagonal sub-block, stride kS + 4
+  __shared__ __align__(16) float sVt[kS * kLd];      // (M_:s Q)^T: sVt[c][i]
+  __shared__ __align__(16) float sW[kS * kLd];       // Q M_s:   : sW[c][j]
+  constexpr int kQd = kS + 4;
   for (int t = threadIdx.x; t < kB * kB; t += blockDim.x) {
     const int c = t / kB, d = t - c * kB;
-    M[c][d] = (c < bk && d < bk) ? R[(size_t)c * n + k0 + d] : (c == d ? 1.f : 0.f);
+    M[c * kLd + d] = (c < bk && d < bk) ? R[(size_t)c * n + k0 + d] : (c == d ? 1.f : 0.f);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int sb = 0; sb < kB / kS; sb++) {
     const int s0 = sb * kS;
     if (warp == 0) {
@@ -93,7 +100,7 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(const float* __restr
       const int lr = lane & 15, half = lane >> 4;
       float m[8];
 #pragma unroll
-      for (int q = 0; q < 8; q++) m[q] = M[s0 + lr][s0 + 8 * half + q];
+      for (int q = 0; q < 8; q++) m[q] = M[(s0 + lr) * kLd + s0 + 8 * half + q];
       bool bad = false;
 #pragma unroll 1
       for (int p = 0; p < kS; p++) {
@@ -119,51 +126,88 @@ __global__ void __launch_bounds__(256) block_inverse_kernel(const float* __restr
         }
       }
 #pragma unroll
-      for (int q = 0; q < 8; q++) sQ[lr][8 * half + q] = -m[q];  // the sweep leaves -B^-1
+      for (int q = 0; q < 8; q++) sQ[lr * kQd + 8 * half + q] = -m[q];  // the sweep leaves -B^-1
       if (lane == 0 && bad) atomicOr(flag, 1);
     }
     __syncthreads();
-    // V = M_:s Q (kB x kS), W = Q M_s: (kS x kB) from the old block
-    for (int t = threadIdx.x; t < kB * kS; t += blockDim.x) {
-      const int i = t / kS, c = t - i * kS;
-      float v = 0.f;
+    // V = M_:s Q (kB x kS, stored transposed) and W = Q M_s: (kS x kB) from the
+    // old block; four outputs per thread each.
+    {
+      const int i = threadIdx.x >> 2, c4 = 4 * (threadIdx.x & 3);
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int q = 0; q < kS; q++) v = fmaf(M[i][s0 + q], sQ[q][c], v);
-      sV[i][c] = v;
-      const int c2 = t / kB, j = t - c2 * kB;
-      float w = 0.f;
-#pragma unroll
-      for (int q = 0; q < kS; q++) w = fmaf(sQ[c2][q], M[s0 + q][j], w);
-      sW[c2][j] = w;
-    }
-    __syncthreads();
-    // M_ij -= M_is Q M_sj = sV_i M_sj (i, j outside s) and the panels: all new
-    // values from the old block first (16 per thread), then the writes
-    float nv[kB * kB / 256];
-#pragma unroll
-    for (int k = 0; k < kB * kB / 256; k++) {
-      const int t = threadIdx.x + 256 * k, i = t / kB, j = t - i * kB;
-      const bool is = i >= s0 && i < s0 + kS, js = j >= s0 && j < s0 + kS;
-      float v;
-      if (is && js) v = -sQ[i - s0][j - s0];
-      else if (is) v = sW[i - s0][j];
-      else if (js) v = sV[i][j - s0];
-      else {
-        v = M[i][j];
-#pragma unroll
-        for (int q = 0; q < kS; q++) v = fmaf(-sV[i][q], M[s0 + q][j], v);
+      for (int q = 0; q < kS; q++) {
+        const float a = M[i * kLd + s0 + q];
+        const float4 b = *reinterpret_cast<const float4*>(&sQ[q * kQd + c4]);
+        v[0] = fmaf(a, b.x, v[0]);
+        v[1] = fmaf(a, b.y, v[1]);
+        v[2] = fmaf(a, b.z, v[2]);
+        v[3] = fmaf(a, b.w, v[3]);
       }
-      nv[k] = v;
+#pragma unroll
+      for (int e = 0; e < 4; e++) sVt[(c4 + e) * kLd + i] = v[e];
+      const int c2 = threadIdx.x >> 4, j4 = 4 * (threadIdx.x & 15);
+      float w[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < kS; q++) {
+        const float a = sQ[c2 * kQd + q];
+        const float4 b = *reinterpret_cast<const float4*>(&M[(s0 + q) * kLd + j4]);
+        w[0] = fmaf(a, b.x, w[0]);
+        w[1] = fmaf(a, b.y, w[1]);
+        w[2] = fmaf(a, b.z, w[2]);
+        w[3] = fmaf(a, b.w, w[3]);
+      }
+      *reinterpret_cast<float4*>(&sW[c2 * kLd + j4]) = make_float4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();
+    // M_ij -= M_is Q M_sj = V_i M_sj (i, j outside s) and the panels: all new
+    // values from the old block first, then the writes.
+    const int i0 = 4 * ty, j0 = 4 * tx;
+    const bool is = i0 >= s0 && i0 < s0 + kS, js = j0 >= s0 && j0 < s0 + kS;
+    float nv[4][4];
+    if (is && js) {
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) nv[a][b] = -sQ[(i0 - s0 + a) * kQd + j0 - s0 + b];
+    } else if (is) {
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) nv[a][b] = sW[(i0 - s0 + a) * kLd + j0 + b];
+    } else if (js) {
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) nv[a][b] = sVt[(j0 - s0 + b) * kLd + i0 + a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; a++) {
+        const float4 r = *reinterpret_cast<const float4*>(&M[(i0 + a) * kLd + j0]);
+        nv[a][0] = r.x;
+        nv[a][1] = r.y;
+        nv[a][2] = r.z;
+        nv[a][3] = r.w;
+      }
+#pragma unroll
+      for (int q = 0; q < kS; q++) {
+        const float4 vv = *reinterpret_cast<const float4*>(&sVt[q * kLd + i0]);
+        const float4 mm = *reinterpret_cast<const float4*>(&M[(s0 + q) * kLd + j0]);
+        const float va[4] = {vv.x, vv.y, vv.z, vv.w};
+        const float mb[4] = {mm.x, mm.y, mm.z, mm.w};
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+          for (int b = 0; b < 4; b++) nv[a][b] = fmaf(-va[a], mb[b], nv[a][b]);
+      }
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kB * kB / 256; k++) {
-      const int t = threadIdx.x + 256 * k;
-      M[t / kB][t % kB] = nv[k];
-    }
+    for (int a = 0; a < 4; a++)
+      *reinterpret_cast<float4*>(&M[(i0 + a) * kLd + j0]) = make_float4(nv[a][0], nv[a][1], nv[a][2], nv[a][3]);
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < kB * kB; t += blockDim.x) P[t] = -M[t / kB][t % kB];  // -A_kk^-1 -> A_kk^-1
+  for (int t = threadIdx.x; t < kB * kB; t += blockDim.x) P[t] = -M[(t / kB) * kLd + t % kB];  // -A_kk^-1 -> A_kk^-1
 }
 
 // W = P R (kB x n); one output per thread.
@@ -206,9 +250,13 @@ constexpr size_t kTrailingSmem = (size_t)2 * kB * kT * sizeof(float);
 // loads and its tile rows are read and written as 128-bit words that a warp
 // covers contiguously.  V4 (n a multiple of 4: every row starts on a 16-byte
 // boundary) selects the 128-bit global accesses; otherwise scalar ones.
+// Rows and columns in [x0, x1) (the next pivot block, whose rows the
+// look-ahead panel reads concurrently and the next step's panel writes
+// replace) are left unwritten; x0 and x1 are multiples of 4 when V4.
 template <bool V4>
 __global__ void __launch_bounds__(256, 2) trailing_kernel(float* __restrict__ A, int n, int nt,
-                                                          const float* __restrict__ R, const float* __restrict__ W) {
+                                                          const float* __restrict__ R, const float* __restrict__ W,
+                                                          int x0, int x1) {
   extern __shared__ __align__(16) float dsm[];
   float* sU = dsm;            // [kB][kT]: R[q][i0 + c]
   float* sW = dsm + kB * kT;  // [kB][kT]: W[q][j0 + c]
@@ -274,30 +322,32 @@ __global__ void __launch_bounds__(256, 2) trailing_kernel(float* __restrict__ A,
 #pragma unroll
   for (int a = 0; a < 8; a++) {
     const int i = i0 + 4 * ty + (a & 3) + (kT / 2) * (a >> 2);
-    if (i >= n) continue;
+    if (i >= n || (i >= x0 && i < x1)) continue;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       const int j = j0 + 4 * tx + (kT / 2) * h;
       if (V4) {
-        if (j < n)
+        if (j < n && !(j >= x0 && j < x1))
           *reinterpret_cast<float4*>(A + (size_t)i * n + j) =
               make_float4(acc[a][4 * h], acc[a][4 * h + 1], acc[a][4 * h + 2], acc[a][4 * h + 3]);
       } else {
 #pragma unroll
         for (int e = 0; e < 4; e++)
-          if (j + e < n) A[(size_t)i * n + j + e] = acc[a][4 * h + e];
+          if (j + e < n && !(j + e >= x0 && j + e < x1)) A[(size_t)i * n + j + e] = acc[a][4 * h + e];
       }
     }
   }
 }
 
 // Row panel of the next pivot block: R1[c][j] = row k1 + c (k1 = k0 + bk,
-// c < bk1; zero rows below) of the matrix that step k (trailing update, then
-// panel writes) leaves, formed from the matrix before step k.  Columns of
-// block k are the written panel, W[j - k0][k1 + c]; every other entry is its
-// stored (upper-triangle) value minus the rank-kB update in the order and
-// operand pairing trailing_kernel uses, so R1 equals those rows bit for bit.
-// kNP columns per CTA; the panels' columns it needs staged in shared memory.
+// c < bk1; zero rows below) of the matrix after step k (trailing update, then
+// panel writes), formed from the matrix before step k.  Columns of block k are
+// the written panel, W[j - k0][k1 + c]; every other entry is its stored
+// (upper-triangle) value minus the rank-kB update, in the order and operand
+// pairing of trailing_kernel.  It reads only entries in the rows and columns
+// of block k + 1, which the trailing update of step k leaves unwritten, so
+// the two run concurrently.  kNP columns per CTA; the panels' columns it
+// needs staged in shared memory.
 constexpr int kNP = 16;
 __global__ void __launch_bounds__(256) next_panel_kernel(const float* __restrict__ A, int n, int k0, int bk, int bk1,
                                                          const float* __restrict__ R, const float* __restrict__ W,
@@ -370,33 +420,38 @@ int grid_for(long long n) { return (int)std::min<long long>(std::max<long long>(
 
 size_t dense_scratch_floats(int n) { return (size_t)3 * n * kB + 2 * kB * kB; }
 
-cudaError_t DenseStreams::create() {
+cudaError_t DenseInverter::create() {
   if (side) return cudaSuccess;
   cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
   if (e != cudaSuccess) destroy();
   return e;
 }
 
-void DenseStreams::destroy() {
+void DenseInverter::destroy() {
+  if (exec) cudaGraphExecDestroy(exec);
   if (ready) cudaEventDestroy(ready);
   if (done) cudaEventDestroy(done);
   if (side) cudaStreamDestroy(side);
-  side = nullptr;
+  if (cap) cudaStreamDestroy(cap);
+  exec = nullptr;
+  side = cap = nullptr;
   ready = done = nullptr;
+  key_n = launches = 0;
 }
 
-cudaError_t dense_spd_inverse(cudaStream_t s, const DenseStreams& ds, float* A, int n, float* scratch, int* flag,
+namespace {
+
+// The launches of the inversion on stream s (captured into the graph).
+cudaError_t issue_spd_inverse(cudaStream_t s, const DenseInverter& ds, float* A, int n, float* scratch, int* flag,
                               int* nlaunch) {
   float* Rb[2] = {scratch, scratch + (size_t)n * kB};
   float* W = scratch + (size_t)2 * n * kB;
   float* Pb[2] = {W + (size_t)n * kB, W + (size_t)n * kB + kB * kB};
   const bool v4 = (n & 3) == 0;
   cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), s);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(v4 ? (const void*)trailing_kernel<true> : (const void*)trailing_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrailingSmem);
   if (e != cudaSuccess) return e;
   int nl = 0;
   const int nt = (n + kT - 1) / kT, ntiles = nt * (nt + 1) / 2;
@@ -405,12 +460,10 @@ cudaError_t dense_spd_inverse(cudaStream_t s, const DenseStreams& ds, float* A, 
   nl += 2;
   for (int k0 = 0, it = 0; k0 < n; k0 += kB, it++) {
     const int cur = it & 1, bk = std::min(kB, n - k0), k1 = k0 + bk;
+    const int bk1 = k1 < n ? std::min(kB, n - k1) : 0;
     panel_kernel<<<grid_for((long long)n * kB), 256, 0, s>>>(Rb[cur], Pb[cur], n, W);
     nl++;
-    if (k1 < n) {
-      const int bk1 = std::min(kB, n - k1);
-      next_panel_kernel<<<(n + kNP - 1) / kNP, 256, 0, s>>>(A, n, k0, bk, bk1, Rb[cur], W, Rb[cur ^ 1]);
-      nl++;
+    if (bk1 > 0) {
       cudaStream_t sb = s;
       if (ds.side) {
         e = cudaEventRecord(ds.ready, s);
@@ -418,16 +471,17 @@ cudaError_t dense_spd_inverse(cudaStream_t s, const DenseStreams& ds, float* A, 
         if (e != cudaSuccess) return e;
         sb = ds.side;
       }
+      next_panel_kernel<<<(n + kNP - 1) / kNP, 256, 0, sb>>>(A, n, k0, bk, bk1, Rb[cur], W, Rb[cur ^ 1]);
       block_inverse_kernel<<<1, 256, 0, sb>>>(Rb[cur ^ 1], n, k1, bk1, Pb[cur ^ 1], flag);
-      nl++;
+      nl += 2;
       if (ds.side) e = cudaEventRecord(ds.done, ds.side);
       if (e != cudaSuccess) return e;
     }
-    if (v4) trailing_kernel<true><<<ntiles, 256, kTrailingSmem, s>>>(A, n, nt, Rb[cur], W);
-    else trailing_kernel<false><<<ntiles, 256, kTrailingSmem, s>>>(A, n, nt, Rb[cur], W);
+    if (v4) trailing_kernel<true><<<ntiles, 256, kTrailingSmem, s>>>(A, n, nt, Rb[cur], W, k1, k1 + bk1);
+    else trailing_kernel<false><<<ntiles, 256, kTrailingSmem, s>>>(A, n, nt, Rb[cur], W, k1, k1 + bk1);
     write_panels_kernel<<<grid_for((long long)n * bk), 256, 0, s>>>(A, n, k0, bk, W, Pb[cur]);
     nl += 2;
-    if (k1 < n && ds.side) e = cudaStreamWaitEvent(s, ds.done, 0);
+    if (bk1 > 0 && ds.side) e = cudaStreamWaitEvent(s, ds.done, 0);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -437,17 +491,64 @@ cudaError_t dense_spd_inverse(cudaStream_t s, const DenseStreams& ds, float* A, 
   return cudaGetLastError();
 }
 
-cudaError_t dense_coarse_inverse(cudaStream_t s, const DenseStreams& ds, const Grid& g, const float* S,
+
+// Replays ds's graph on s, capturing `issue` (launches on the stream it is
+// given) first when the key differs from the captured one.
+template <class F>
+cudaError_t replay(cudaStream_t s, DenseInverter& ds, const void* const (&key)[5], int n, int* nlaunch, F issue) {
+  bool same = ds.exec && ds.key_n == n;
+  for (int i = 0; i < 5 && same; i++) same = ds.key[i] == key[i];
+  if (!same) {
+    if (ds.exec) cudaGraphExecDestroy(ds.exec);
+    ds.exec = nullptr;
+    cudaError_t e = cudaFuncSetAttribute((n & 3) == 0 ? (const void*)trailing_kernel<true>
+                                                      : (const void*)trailing_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTrailingSmem);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(ds.cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    int nl = 0;
+    e = issue(ds.cap, &nl);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(ds.cap, &gr);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ds.exec, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      ds.exec = nullptr;
+      return e;
+    }
+    for (int i = 0; i < 5; i++) ds.key[i] = key[i];
+    ds.key_n = n;
+    ds.launches = nl;
+  }
+  const cudaError_t e = cudaGraphLaunch(ds.exec, s);
+  if (e == cudaSuccess && nlaunch) *nlaunch += ds.launches;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t dense_spd_inverse(cudaStream_t s, DenseInverter& ds, float* A, int n, float* scratch, int* flag,
+                              int* nlaunch) {
+  const void* const key[5] = {A, nullptr, nullptr, scratch, flag};
+  return replay(s, ds, key, n, nlaunch,
+                [&](cudaStream_t cs, int* nl) { return issue_spd_inverse(cs, ds, A, n, scratch, flag, nl); });
+}
+
+cudaError_t dense_coarse_inverse(cudaStream_t s, DenseInverter& ds, const Grid& g, const float* S,
                                  const uint8_t* mask, float* A, float* scratch, int* flag, int* nlaunch) {
   const int n = (int)(g.nn * g.dim);
-  cudaError_t e = cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(float), s);
-  if (e != cudaSuccess) return e;
-  if (g.dim == 2) dense_assemble_kernel<2><<<grid_for(n), 256, 0, s>>>(g, S, mask, A);
-  else dense_assemble_kernel<3><<<grid_for(n), 256, 0, s>>>(g, S, mask, A);
-  if (nlaunch) (*nlaunch)++;
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  return dense_spd_inverse(s, ds, A, n, scratch, flag, nlaunch);
+  const void* const key[5] = {A, S, mask, scratch, flag};
+  return replay(s, ds, key, n, nlaunch, [&](cudaStream_t cs, int* nl) {
+    cudaError_t e = cudaMemsetAsync(A, 0, (size_t)n * n * sizeof(float), cs);
+    if (e != cudaSuccess) return e;
+    if (g.dim == 2) dense_assemble_kernel<2><<<grid_for(n), 256, 0, cs>>>(g, S, mask, A);
+    else dense_assemble_kernel<3><<<grid_for(n), 256, 0, cs>>>(g, S, mask, A);
+    (*nl)++;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return issue_spd_inverse(cs, ds, A, n, scratch, flag, nl);
+  });
 }
 
 }  // namespace tp
@@ -458,7 +559,7 @@ extern "C" tp_status tp_spd_inverse_f32(const float* a, float* ainv, int n, void
   const size_t bytes = (size_t)n * n * sizeof(float);
   float *dA = nullptr, *scr = nullptr;
   int* flag = nullptr;
-  tp::DenseStreams ds;
+  tp::DenseInverter ds;
   cudaError_t e = cudaMalloc((void**)&dA, bytes);
   if (e == cudaSuccess) e = cudaMalloc((void**)&scr, tp::dense_scratch_floats(n) * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&flag, sizeof(int));
