@@ -15,6 +15,9 @@ Modules (each function cites the passage of the paper it follows):
   oc       optimality-criteria update with bisection, and the exact multiplier
   simp     the SIMP loop
   nn       reference 3D conv network (FP64) for the learned warm start
+  helm     Helmholtz (PDE) filter of the paper's parallel runs
+  p1       the paper's own elements: vector P1 on triangulated / tetrahedralised
+           structured grids, DG0 density, one SIMP iteration
 
 Parity status: every function here is pinned by `-m "not gpu"` tests
 (closed forms, invariants, exact arithmetic, brute force, finite differences),

@@ -260,6 +260,93 @@ def random_sensitivity(n_el: int, seed: int = 5) -> np.ndarray:
     return -rng.uniform(1e-4, 1.0, size=n_el) * 10.0 ** rng.uniform(-2, 2, size=n_el)
 
 
+@dataclass
+class SimplexProblem:
+    """A problem on the paper's own elements (inputs only): the structured grid
+    of unit squares (cubes) with each square split into 2 triangles along the
+    diagonal pattern `diagonal` ("right", "left" or "right/left"), each cube into
+    6 tetrahedra, vector P1 displacements and one density per cell.  Nodes and
+    DOFs are numbered as for the Q4 / H8 problems; cells are numbered
+    (2 or 6) * (element of the square / cube) + local cell.  The material is
+    given by its Lame constants (the paper: mu = 0.4, lambda = 0.6), which set
+    sigma = 2 mu eps + lambda tr(eps) I in 2D and 3D alike."""
+
+    name: str
+    dim: int
+    nelx: int
+    nely: int
+    nelz: int
+    diagonal: str
+    volfrac: float
+    rmin: float
+    fixed: np.ndarray  # uint8[n_dof]
+    loads: np.ndarray  # float64[n_cases, n_dof]
+    passive: Optional[np.ndarray] = None  # int8[n_el] (cells)
+    lam: float = 0.6
+    mu: float = 0.4
+    Emin: float = 1e-9
+    penal: float = 3.0
+    move: float = 0.2
+    dmin: float = 1e-3
+    n_iter: int = 50
+
+    @property
+    def n_nodes(self) -> int:
+        n = (self.nelx + 1) * (self.nely + 1)
+        return n * (self.nelz + 1) if self.dim == 3 else n
+
+    @property
+    def n_el(self) -> int:
+        """Number of cells (triangles or tetrahedra)."""
+        return 2 * self.nelx * self.nely if self.dim == 2 else 6 * self.nelx * self.nely * self.nelz
+
+    @property
+    def n_dof(self) -> int:
+        return self.dim * self.n_nodes
+
+    @property
+    def n_cases(self) -> int:
+        return int(self.loads.shape[0])
+
+    def passive_mask(self) -> np.ndarray:
+        return np.zeros(self.n_el, dtype=np.int8) if self.passive is None else self.passive
+
+    def initial_density(self) -> np.ndarray:
+        rho = np.full(self.n_el, self.volfrac, dtype=np.float64)
+        rho[self.passive_mask() == 1] = self.dmin
+        return rho
+
+
+def p1_cantilever2d(nelx: int = 60, nely: int = 20, volfrac: float = 0.5, rmin: float = 1.5,
+                    diagonal: str = "right/left", n_iter: int = 50) -> SimplexProblem:
+    """The paper's 2D cantilever on its own mesh: x = 0 clamped; a downward
+    traction of unit intensity on the right edge x = nelx over y in [0, 2] (the
+    facets whose points all satisfy x = nelx, y <= 2).  Its consistent nodal
+    loads on the linear edge segments are -0.5, -1, -0.5 at y = 0, 1, 2."""
+    fixed, f = _empty(2, nelx, nely, 0, 1)
+    _fix_face_x0(fixed, 2, nelx, nely, 0)
+    top = min(2, nely)
+    for j in range(top + 1):
+        w = 0.5 if j in (0, top) else 1.0
+        f[0, 2 * (nelx + (nelx + 1) * j) + 1] = -w
+    return SimplexProblem(f"p1_cantilever2d_{nelx}x{nely}_{diagonal.replace('/', '')}", 2, nelx, nely, 0,
+                          diagonal, volfrac, rmin, fixed, f, n_iter=n_iter)
+
+
+def p1_cantilever3d(nelx: int = 60, nely: int = 20, nelz: int = 4, volfrac: float = 0.3, rmin: float = 1.5,
+                    n_iter: int = 30) -> SimplexProblem:
+    """The paper's 3D cantilever on tetrahedra (6 per cube): x = 0 face
+    clamped, the unit downward line load along the bottom edge (y = 0) of the
+    x = nelx face, lumped as -0.5 at the end nodes and -1 between."""
+    fixed, f = _empty(3, nelx, nely, nelz, 1)
+    _fix_face_x0(fixed, 3, nelx, nely, nelz)
+    for k in range(nelz + 1):
+        n = nelx + (nelx + 1) * (0 + (nely + 1) * k)
+        f[0, 3 * n + 1] = -0.5 if k in (0, nelz) else -1.0
+    return SimplexProblem(f"p1_cantilever3d_{nelx}x{nely}x{nelz}", 3, nelx, nely, nelz, "kuhn", volfrac, rmin,
+                          fixed, f, n_iter=n_iter)
+
+
 def random_spd(n: int, cond: float = 100.0, seed: int = 7) -> np.ndarray:
     """Symmetric positive definite float32 matrix Q diag(lam) Q^T: Q from the QR
     factorisation of a Gaussian matrix, lam log-uniform in [1, cond], seeded."""
