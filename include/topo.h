@@ -315,6 +315,31 @@ tp_status tp_oc_update_noalloc(const double* rho, const double* dcf, const int8_
 #define TP_SPD_INVERSE_MAX_N 16384
 tp_status tp_spd_inverse_f32(const float* a, float* ainv, int n, void* cuda_stream);
 
+/* The paper's own elements (Section 4 "Discretization the problem", Section 5
+ * "Working with 3D problems"): the boundary-conditioned operator
+ * y = K(rho) u for vector P1 on the structured grid of unit squares cut into 2
+ * triangles each, or unit cubes cut into the 6 Kuhn tetrahedra, one density
+ * per cell, sigma = 2 mu eps + lambda tr(eps) I (Section 4.3) scaled by
+ * Emin + rho^penal (1 - Emin).  FP64.
+ * Cells: square / cube e = i + nelx (j + nely k) holds cells 2 e, 2 e + 1 (2D)
+ * or 6 e .. 6 e + 5 (3D).  diagonal (2D): 0 cuts along (i, j)-(i+1, j+1) into
+ * (v00, v10, v11), (v00, v11, v01); 1 along (i+1, j)-(i, j+1) into
+ * (v00, v10, v01), (v10, v11, v01); 2 alternates by row (even rows 0, odd
+ * rows 1).  3D (diagonal 0): cell 6 e + t is the Kuhn tetrahedron of the
+ * t-th axis ordering in lexicographic order (012, 021, 102, 120, 201, 210):
+ * the path from the cube's lowest corner stepping along those axes.
+ * Arguments (device pointers on the current device): rho[n_cells];
+ * fixed[n_dof] (1 = Dirichlet DOF); u, y [ncases][n_dof] with DOF = dim *
+ * node + component, nodes x fastest.  y = u on fixed rows; u is read as 0 on
+ * fixed DOFs elsewhere.  nelz = 0 in 2D.  The call synchronises the stream.
+ * Calls on different streams must not overlap (the cell matrices sit in
+ * constant memory).  Errors: TP_ERR_ARG for sizes, dim, diagonal, material
+ * (mu > 0, lambda + 2 mu / dim > 0), Emin outside [0, 1), penal outside
+ * [1, 10], ncases outside 1..8 or NULL pointers; TP_ERR_CUDA. */
+tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int diagonal, double lam, double mu, double Emin,
+                       double penal, const double* rho, const uint8_t* fixed, const double* u, double* y,
+                       int ncases, void* cuda_stream);
+
 /* Phase tracing of the persistent CG (not in the paper; a profiling aid).
  * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at eight
  * points of each iteration into a ring of 32 iterations: 0 start, 1 operator

@@ -1,0 +1,234 @@
+// The paper's own elements: the boundary-conditioned operator K(rho) u for
+// vector P1 on the structured grid cut into triangles (each unit square into
+// 2, along the "right" / "left" diagonal or alternating by row) or
+// tetrahedra (each unit cube into the 6 Kuhn tetrahedra), with one density
+// per cell (Section 4 "Discretization the problem", Section 5 "Working with
+// 3D problems"; bilinear form d^p sigma(u) : grad(v), sigma = 2 mu eps +
+// lambda tr(eps) I, Section 4.3).
+//
+// Every cell of the structured grid is a translate of one of a few shapes (4
+// triangles, 6 tetrahedra), so the host forms the unit-modulus matrix of each
+// shape once, in FP64, from the cell's barycentric gradients, and the kernel
+// gathers, for each node, the rows of the cells around it.  FP64 throughout:
+// this is the parity form of the operator.
+#include <algorithm>
+#include <cmath>
+
+#include "../../include/topo.h"
+#include "common.cuh"
+
+namespace tp {
+namespace {
+
+constexpr int kMaxTypes = 6;
+constexpr int kMaxNd = 12;  // DOFs of a tetrahedron
+
+__constant__ double cP1K[kMaxTypes][kMaxNd * kMaxNd];  // unit-modulus cell matrices, row-major
+__constant__ int cP1Off[kMaxTypes][4][3];              // vertex offsets within the square / cube
+
+// Vertex offsets of each shape.  2D: 0, 1 = the two cells of a square cut
+// along (0,0)-(1,1); 2, 3 = cut along (1,0)-(0,1) (cell 0 holds (0,0) and
+// (1,0), cell 1 the rest).  3D: the Kuhn path for the axis orderings in
+// lexicographic order.
+void shape_offsets(int dim, int type, int off[4][3]) {
+  for (int v = 0; v < 4; v++)
+    for (int a = 0; a < 3; a++) off[v][a] = 0;
+  if (dim == 2) {
+    static const int tri[4][3][2] = {{{0, 0}, {1, 0}, {1, 1}},
+                                     {{0, 0}, {1, 1}, {0, 1}},
+                                     {{0, 0}, {1, 0}, {0, 1}},
+                                     {{1, 0}, {1, 1}, {0, 1}}};
+    for (int v = 0; v < 3; v++) {
+      off[v][0] = tri[type][v][0];
+      off[v][1] = tri[type][v][1];
+    }
+    return;
+  }
+  static const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  int p[3] = {0, 0, 0};
+  for (int v = 1; v < 4; v++) {
+    p[order[type][v - 1]] = 1;
+    for (int a = 0; a < 3; a++) off[v][a] = p[a];
+  }
+}
+
+// Unit-modulus matrix of the simplex with vertices X (nv = dim + 1): the
+// barycentric gradients are the rows 1.. of [1 | X]^-1 (Gauss-Jordan with
+// partial pivoting), the measure |det [1 | X]| / dim!, and
+// K[d i + a][d j + b] = |T| (mu (delta_ab g_i . g_j + g_i[b] g_j[a]) + lambda g_i[a] g_j[b]).
+void simplex_matrix(int dim, const double X[4][3], double lam, double mu, double* K) {
+  const int nv = dim + 1;
+  double M[4][8];
+  for (int r = 0; r < nv; r++) {
+    M[r][0] = 1.0;
+    for (int a = 0; a < dim; a++) M[r][1 + a] = X[r][a];
+    for (int c = 0; c < nv; c++) M[r][nv + c] = r == c ? 1.0 : 0.0;
+  }
+  double det = 1.0;
+  for (int c = 0; c < nv; c++) {
+    int piv = c;
+    for (int r = c + 1; r < nv; r++)
+      if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+    if (piv != c) {
+      for (int q = 0; q < 2 * nv; q++) std::swap(M[c][q], M[piv][q]);
+      det = -det;
+    }
+    const double d = M[c][c];
+    det *= d;
+    for (int q = 0; q < 2 * nv; q++) M[c][q] /= d;
+    for (int r = 0; r < nv; r++) {
+      if (r == c) continue;
+      const double f = M[r][c];
+      for (int q = 0; q < 2 * nv; q++) M[r][q] -= f * M[c][q];
+    }
+  }
+  // inverse in M[.][nv ..]; lambda_v = sum_r inv[r][v] * (1, x)_r
+  double g[4][3];
+  for (int v = 0; v < nv; v++)
+    for (int a = 0; a < dim; a++) g[v][a] = M[1 + a][nv + v];
+  const double meas = std::fabs(det) / (dim == 2 ? 2.0 : 6.0);
+  const int nd = dim * nv;
+  for (int i = 0; i < nv; i++)
+    for (int j = 0; j < nv; j++) {
+      double gg = 0.0;
+      for (int a = 0; a < dim; a++) gg += g[i][a] * g[j][a];
+      for (int a = 0; a < dim; a++)
+        for (int b = 0; b < dim; b++)
+          K[(dim * i + a) * nd + dim * j + b] =
+              meas * (mu * ((a == b ? gg : 0.0) + g[i][b] * g[j][a]) + lam * g[i][a] * g[j][b]);
+    }
+}
+
+struct P1Args {
+  int nx, ny, nz, diag, nc;
+  long long ndof;
+  double Emin, penal;
+  const double* rho;
+  const uint8_t* fixed;
+  const double* u;
+  double* y;
+};
+
+// One thread per (node, case): y_i = sum over the cells around the node of
+// E_c (K_c u_c) rows of the node, u masked on fixed DOFs; fixed rows y = u.
+template <int DIM>
+__global__ void p1_matvec_kernel(P1Args a) {
+  constexpr int NV = DIM + 1, ND = DIM * NV, NCELL = DIM == 2 ? 2 : 6;
+  const long long nxy = (long long)(a.nx + 1) * (a.ny + 1);
+  const long long nn = nxy * (DIM == 3 ? a.nz + 1 : 1);
+  const int c = blockIdx.y;
+  const double* u = a.u + (long long)c * a.ndof;
+  double* y = a.y + (long long)c * a.ndof;
+  for (long long nd = blockIdx.x * (long long)blockDim.x + threadIdx.x; nd < nn;
+       nd += (long long)gridDim.x * blockDim.x) {
+    const int k = DIM == 3 ? (int)(nd / nxy) : 0;
+    const long long rem = nd - (long long)k * nxy;
+    const int j = (int)(rem / (a.nx + 1)), i = (int)(rem - (long long)j * (a.nx + 1));
+    double acc[DIM];
+#pragma unroll
+    for (int q = 0; q < DIM; q++) acc[q] = 0.0;
+    for (int ek = (DIM == 3 ? k - 1 : 0); ek <= (DIM == 3 ? k : 0); ek++) {
+      if (DIM == 3 && (ek < 0 || ek >= a.nz)) continue;
+      for (int ej = j - 1; ej <= j; ej++) {
+        if (ej < 0 || ej >= a.ny) continue;
+        const int tbase = DIM == 2 ? 2 * (a.diag == 2 ? (ej & 1) : a.diag) : 0;
+        for (int ei = i - 1; ei <= i; ei++) {
+          if (ei < 0 || ei >= a.nx) continue;
+          const long long e = ei + (long long)a.nx * (ej + (long long)a.ny * ek);
+          const int li = i - ei, lj = j - ej, lk = k - ek;
+          for (int t = 0; t < NCELL; t++) {
+            const int type = tbase + t;
+            int av = -1;
+#pragma unroll
+            for (int v = 0; v < NV; v++)
+              if (cP1Off[type][v][0] == li && cP1Off[type][v][1] == lj && (DIM == 2 || cP1Off[type][v][2] == lk))
+                av = v;
+            if (av < 0) continue;
+            const double E = a.Emin + pow(a.rho[NCELL * e + t], a.penal) * (1.0 - a.Emin);
+#pragma unroll
+            for (int m = 0; m < NV; m++) {
+              const long long nm = (ei + cP1Off[type][m][0]) +
+                                   (long long)(a.nx + 1) * ((ej + cP1Off[type][m][1]) +
+                                                            (long long)(a.ny + 1) * (DIM == 3 ? ek + cP1Off[type][m][2] : 0));
+#pragma unroll
+              for (int s = 0; s < DIM; s++) {
+                const long long dof = DIM * nm + s;
+                if (a.fixed[dof]) continue;
+                const double uv = u[dof];
+#pragma unroll
+                for (int q = 0; q < DIM; q++) acc[q] += E * cP1K[type][(DIM * av + q) * ND + DIM * m + s] * uv;
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < DIM; q++) {
+      const long long dof = DIM * nd + q;
+      y[dof] = a.fixed[dof] ? u[dof] : acc[q];
+    }
+  }
+}
+
+}  // namespace
+}  // namespace tp
+
+extern "C" tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int diagonal, double lam, double mu,
+                                  double Emin, double penal, const double* rho, const uint8_t* fixed,
+                                  const double* u, double* y, int ncases, void* cuda_stream) {
+  if (dim != 2 && dim != 3) return TP_ERR_ARG;
+  if (nelx < 1 || nely < 1 || (dim == 3 ? nelz < 1 : nelz != 0)) return TP_ERR_ARG;
+  if (dim == 2 ? (diagonal < 0 || diagonal > 2) : diagonal != 0) return TP_ERR_ARG;
+  if (!(mu > 0.0) || !(lam + 2.0 * mu / dim > 0.0) || !std::isfinite(lam) || !std::isfinite(mu)) return TP_ERR_ARG;
+  if (!(Emin >= 0.0 && Emin < 1.0) || !(penal >= 1.0 && penal <= 10.0)) return TP_ERR_ARG;
+  if (ncases < 1 || ncases > 8 || !rho || !fixed || !u || !y) return TP_ERR_ARG;
+  const long long nn = (long long)(nelx + 1) * (nely + 1) * (dim == 3 ? nelz + 1 : 1);
+  if (nn > (1LL << 31)) return TP_ERR_ARG;
+  const int ntypes = dim == 2 ? 4 : 6, nv = dim + 1, nd = dim * nv;
+  double K[tp::kMaxTypes][tp::kMaxNd * tp::kMaxNd] = {};
+  int off[tp::kMaxTypes][4][3] = {};
+  for (int t = 0; t < ntypes; t++) {
+    int o[4][3];
+    tp::shape_offsets(dim, t, o);
+    double X[4][3];
+    for (int v = 0; v < 4; v++)
+      for (int q = 0; q < 3; q++) {
+        off[t][v][q] = o[v][q];
+        X[v][q] = o[v][q];
+      }
+    double Kt[tp::kMaxNd * tp::kMaxNd];
+    tp::simplex_matrix(dim, X, lam, mu, Kt);
+    for (int r = 0; r < nd * nd; r++) K[t][r] = Kt[r];
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemcpyToSymbolAsync(tp::cP1K, K, sizeof(K), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(tp::cP1Off, off, sizeof(off), 0, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TP_ERR_CUDA;
+  }
+  tp::P1Args a;
+  a.nx = nelx;
+  a.ny = nely;
+  a.nz = dim == 3 ? nelz : 0;
+  a.diag = diagonal;
+  a.nc = ncases;
+  a.ndof = dim * nn;
+  a.Emin = Emin;
+  a.penal = penal;
+  a.rho = rho;
+  a.fixed = fixed;
+  a.u = u;
+  a.y = y;
+  const dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 152 * 8), ncases);
+  if (dim == 2) tp::p1_matvec_kernel<2><<<grid, 256, 0, s>>>(a);
+  else tp::p1_matvec_kernel<3><<<grid, 256, 0, s>>>(a);
+  e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TP_ERR_CUDA;
+  }
+  return TP_OK;
+}

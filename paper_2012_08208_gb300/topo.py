@@ -99,6 +99,8 @@ def _load():
         "tp_oc_update_noalloc": (C.c_int, [P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double, P, P,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_spd_inverse_f32": (C.c_int, [P, P, C.c_int, P]),
+        "tp_p1_matvec": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, P, P, P, P, C.c_int, P]),
         "tp_get_trace": (C.c_int, [P, P]),
         "tp_set_profile": (C.c_int, [P, C.c_int]),
         "tp_get_profile": (C.c_int, [P, P]),
@@ -135,7 +137,7 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
-            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
@@ -176,6 +178,22 @@ def spd_inverse(a, stream=None):
     if st != TP_OK:
         raise TopoError(st, "tp_spd_inverse_f32 failed")
     return out
+
+
+P1_DIAGONALS = {"right": 0, "left": 1, "right/left": 2, "kuhn": 0}
+
+
+def p1_matvec(dim, nelx, nely, nelz, diagonal, lam, mu, Emin, penal, rho, fixed, u, y, stream=None):
+    """y = K(rho) u for the paper's P1 cells (tp_p1_matvec in include/topo.h).
+    rho (float64), fixed (uint8), u and y (float64, [ncases, n_dof]): CUDA
+    tensors; diagonal: "right", "left", "right/left" (2D) or "kuhn" (3D)."""
+    nc = u.shape[0] if u.dim() == 2 else 1
+    st = lib.tp_p1_matvec(dim, nelx, nely, nelz, P1_DIAGONALS[diagonal], lam, mu, Emin, penal,
+                          C.c_void_p(rho.data_ptr()), C.c_void_p(fixed.data_ptr()), C.c_void_p(u.data_ptr()),
+                          C.c_void_p(y.data_ptr()), nc, C.c_void_p(0 if stream is None else int(stream)))
+    if st != TP_OK:
+        raise TopoError(st, "tp_p1_matvec failed")
+    return y
 
 
 class TopoError(RuntimeError):

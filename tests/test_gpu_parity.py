@@ -141,6 +141,51 @@ def test_oc_update(topo, n, vf, passive):
     p.close()
 
 
+P1_CASES = [("right", (7, 5, 0), 1), ("left", (1, 1, 0), 1), ("right/left", (9, 6, 0), 2),
+            ("kuhn", (1, 1, 1), 1), ("kuhn", (3, 2, 2), 1), ("kuhn", (5, 3, 4), 2)]
+
+
+@pytest.mark.parametrize("diagonal,size,nc", P1_CASES, ids=lambda v: str(v).replace("/", ""))
+def test_p1_matvec_against_oracle(topo, diagonal, size, nc):
+    """The paper's P1 operator (tp_p1_matvec, FP64) against the oracle's
+    assembled K(rho) on random densities and vectors, fixed rows y = u:
+    |y - y_ref| <= 1e-12 (|K| |u|)_i (rounding order only)."""
+    import torch
+    nx, ny, nz = size
+    prob = (W.p1_cantilever2d(nx, ny, diagonal=diagonal) if nz == 0 else W.p1_cantilever3d(nx, ny, nz))
+    rho = W.random_density(prob.n_el, seed=21)
+    U = np.stack([W.random_vector(prob.n_dof, seed=22 + c) for c in range(nc)])
+    from oracle import p1
+    K = p1.assemble(prob, rho)
+    fixed = prob.fixed.astype(bool)
+    dev = torch.device("cuda")
+    y = torch.zeros((nc, prob.n_dof), dtype=torch.float64, device=dev)
+    topo.p1_matvec(prob.dim, nx, ny, nz, diagonal, prob.lam, prob.mu, prob.Emin, prob.penal,
+                   torch.tensor(rho, device=dev), torch.tensor(prob.fixed, device=dev),
+                   torch.tensor(U, device=dev), y)
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    Ka = abs(K)
+    for c in range(nc):
+        um = np.where(fixed, 0.0, U[c])
+        ref = np.where(fixed, U[c], K @ um)
+        scale = np.where(fixed, np.abs(U[c]), Ka @ np.abs(um))
+        assert np.all(np.abs(y[c] - ref) <= 1e-12 * scale + 1e-300), np.abs(y[c] - ref).max()
+
+
+def test_p1_matvec_errors(topo):
+    """Bad dimension, diagonal or material give TP_ERR_ARG before any launch."""
+    import ctypes
+    buf = np.zeros(64)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    f = topo.lib.tp_p1_matvec
+    assert f(2, 2, 2, 0, 3, 0.6, 0.4, 1e-9, 3.0, ptr, ptr, ptr, ptr, 1, None) == topo.TP_ERR_ARG
+    assert f(3, 2, 2, 2, 1, 0.6, 0.4, 1e-9, 3.0, ptr, ptr, ptr, ptr, 1, None) == topo.TP_ERR_ARG
+    assert f(2, 2, 2, 0, 0, 0.6, -0.4, 1e-9, 3.0, ptr, ptr, ptr, ptr, 1, None) == topo.TP_ERR_ARG
+    assert f(4, 2, 2, 0, 0, 0.6, 0.4, 1e-9, 3.0, ptr, ptr, ptr, ptr, 1, None) == topo.TP_ERR_ARG
+    assert f(2, 2, 2, 0, 0, 0.6, 0.4, 1e-9, 3.0, ptr, ptr, ptr, ptr, 9, None) == topo.TP_ERR_ARG
+
+
 @pytest.mark.parametrize("n", [1, 5, 64, 130, 300, 1000, 3952])
 def test_spd_inverse_against_fp64(topo, n):
     """Dense FP32 inverse (the multigrid coarsest solve) against the FP64
