@@ -340,6 +340,16 @@ tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int diagonal, doub
                        double penal, const double* rho, const uint8_t* fixed, const double* u, double* y,
                        int ncases, void* cuda_stream);
 
+/* Host-side cell shapes of tp_p1_matvec (no device work): for each shape t
+ * (4 in 2D: types 0, 1 = the cells of a "right" cut square, 2, 3 = of a
+ * "left" cut square; 6 in 3D: the Kuhn tetrahedra in the order of
+ * tp_p1_matvec), K[t][nd][nd] (nd = dim (dim + 1), unit modulus, DOF order
+ * vertex-major then component) and offsets[t][dim + 1][dim] (vertex offsets
+ * within the unit square / cube).  K holds 4 * 36 (2D) or 6 * 144 (3D)
+ * doubles, offsets 4 * 3 * 2 or 6 * 4 * 3 ints.  TP_ERR_ARG for a bad
+ * dimension, material or NULL pointer. */
+tp_status tp_p1_shape_matrices(int dim, double lam, double mu, double* K, int* offsets);
+
 /* Phase tracing of the persistent CG (not in the paper; a profiling aid).
  * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at eight
  * points of each iteration into a ring of 32 iterations: 0 start, 1 operator

@@ -99,6 +99,20 @@ void simplex_matrix(int dim, const double X[4][3], double lam, double mu, double
     }
 }
 
+// Unit matrices and vertex offsets of every cell shape of the grid (4 in 2D,
+// 6 in 3D), K[t] row-major with dim * (dim + 1) rows.
+int p1_shapes(int dim, double lam, double mu, double K[kMaxTypes][kMaxNd * kMaxNd], int off[kMaxTypes][4][3]) {
+  const int ntypes = dim == 2 ? 4 : 6;
+  for (int t = 0; t < ntypes; t++) {
+    shape_offsets(dim, t, off[t]);
+    double X[4][3];
+    for (int v = 0; v < 4; v++)
+      for (int q = 0; q < 3; q++) X[v][q] = off[t][v][q];
+    simplex_matrix(dim, X, lam, mu, K[t]);
+  }
+  return ntypes;
+}
+
 struct P1Args {
   int nx, ny, nz, diag, nc;
   long long ndof;
@@ -185,22 +199,9 @@ extern "C" tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int dia
   if (ncases < 1 || ncases > 8 || !rho || !fixed || !u || !y) return TP_ERR_ARG;
   const long long nn = (long long)(nelx + 1) * (nely + 1) * (dim == 3 ? nelz + 1 : 1);
   if (nn > (1LL << 31)) return TP_ERR_ARG;
-  const int ntypes = dim == 2 ? 4 : 6, nv = dim + 1, nd = dim * nv;
   double K[tp::kMaxTypes][tp::kMaxNd * tp::kMaxNd] = {};
   int off[tp::kMaxTypes][4][3] = {};
-  for (int t = 0; t < ntypes; t++) {
-    int o[4][3];
-    tp::shape_offsets(dim, t, o);
-    double X[4][3];
-    for (int v = 0; v < 4; v++)
-      for (int q = 0; q < 3; q++) {
-        off[t][v][q] = o[v][q];
-        X[v][q] = o[v][q];
-      }
-    double Kt[tp::kMaxNd * tp::kMaxNd];
-    tp::simplex_matrix(dim, X, lam, mu, Kt);
-    for (int r = 0; r < nd * nd; r++) K[t][r] = Kt[r];
-  }
+  tp::p1_shapes(dim, lam, mu, K, off);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaMemcpyToSymbolAsync(tp::cP1K, K, sizeof(K), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(tp::cP1Off, off, sizeof(off), 0, cudaMemcpyHostToDevice, s);
@@ -229,6 +230,21 @@ extern "C" tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int dia
   if (e != cudaSuccess) {
     cudaGetLastError();
     return TP_ERR_CUDA;
+  }
+  return TP_OK;
+}
+
+extern "C" tp_status tp_p1_shape_matrices(int dim, double lam, double mu, double* K, int* offsets) {
+  if ((dim != 2 && dim != 3) || !K || !offsets) return TP_ERR_ARG;
+  if (!(mu > 0.0) || !(lam + 2.0 * mu / dim > 0.0) || !std::isfinite(lam) || !std::isfinite(mu)) return TP_ERR_ARG;
+  double Kt[tp::kMaxTypes][tp::kMaxNd * tp::kMaxNd] = {};
+  int off[tp::kMaxTypes][4][3] = {};
+  const int ntypes = tp::p1_shapes(dim, lam, mu, Kt, off);
+  const int nd = dim * (dim + 1);
+  for (int t = 0; t < ntypes; t++) {
+    for (int r = 0; r < nd * nd; r++) K[t * nd * nd + r] = Kt[t][r];
+    for (int v = 0; v < dim + 1; v++)
+      for (int q = 0; q < dim; q++) offsets[(t * (dim + 1) + v) * dim + q] = off[t][v][q];
   }
   return TP_OK;
 }

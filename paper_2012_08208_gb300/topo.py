@@ -99,6 +99,7 @@ def _load():
         "tp_oc_update_noalloc": (C.c_int, [P, P, P, C.c_longlong, C.c_double, C.c_double, C.c_double, P, P,
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_spd_inverse_f32": (C.c_int, [P, P, C.c_int, P]),
+        "tp_p1_shape_matrices": (C.c_int, [C.c_int, C.c_double, C.c_double, P, P]),
         "tp_p1_matvec": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                    C.c_double, C.c_double, P, P, P, P, C.c_int, P]),
         "tp_get_trace": (C.c_int, [P, P]),
@@ -137,7 +138,7 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
-            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_p1_shape_matrices", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
@@ -194,6 +195,18 @@ def p1_matvec(dim, nelx, nely, nelz, diagonal, lam, mu, Emin, penal, rho, fixed,
     if st != TP_OK:
         raise TopoError(st, "tp_p1_matvec failed")
     return y
+
+
+def p1_shape_matrices(dim, lam, mu):
+    """(K[ntypes, nd, nd], offsets[ntypes, dim + 1, dim]) of the P1 cell
+    shapes (tp_p1_shape_matrices in include/topo.h); host only."""
+    nt, nd = (4, 6) if dim == 2 else (6, 12)
+    K = np.zeros((nt, nd, nd))
+    off = np.zeros((nt, dim + 1, dim), dtype=np.int32)
+    st = lib.tp_p1_shape_matrices(dim, lam, mu, K.ctypes.data_as(C.c_void_p), off.ctypes.data_as(C.c_void_p))
+    if st != TP_OK:
+        raise TopoError(st, "tp_p1_shape_matrices failed")
+    return K, off
 
 
 class TopoError(RuntimeError):
