@@ -66,3 +66,29 @@ def test_p1_shape_matrices_match_the_oracle(lib, dim):
             assert got == {tuple(X[n]) for n in cell}
     with pytest.raises(lib.TopoError):
         lib.p1_shape_matrices(dim, lam, -1.0)
+
+
+def test_dense_and_p1_entry_points_reject_bad_arguments_without_the_gpu(lib):
+    """Argument checks of tp_spd_inverse_f32 and tp_p1_matvec return
+    TP_ERR_ARG before any CUDA call (so they run without a GPU)."""
+    import ctypes as C
+    import numpy as np
+    buf = np.zeros(64)
+    p = buf.ctypes.data_as(C.c_void_p)
+    f = lib.lib.tp_spd_inverse_f32
+    assert f(p, p, 0, None) == lib.TP_ERR_ARG
+    assert f(p, p, lib.SPD_INVERSE_MAX_N + 1, None) == lib.TP_ERR_ARG
+    assert f(None, p, 4, None) == lib.TP_ERR_ARG and f(p, None, 4, None) == lib.TP_ERR_ARG
+    g = lib.lib.tp_p1_matvec
+    ok = (0.6, 0.4, 1e-9, 3.0)
+    assert g(1, 2, 2, 0, 0, *ok, p, p, p, p, 1, None) == lib.TP_ERR_ARG        # dim
+    assert g(2, 0, 2, 0, 0, *ok, p, p, p, p, 1, None) == lib.TP_ERR_ARG        # nelx
+    assert g(2, 2, 2, 1, 0, *ok, p, p, p, p, 1, None) == lib.TP_ERR_ARG        # nelz in 2D
+    assert g(3, 2, 2, 0, 0, *ok, p, p, p, p, 1, None) == lib.TP_ERR_ARG        # nelz in 3D
+    assert g(2, 2, 2, 0, 3, *ok, p, p, p, p, 1, None) == lib.TP_ERR_ARG        # diagonal
+    assert g(2, 2, 2, 0, 0, 0.6, 0.0, 1e-9, 3.0, p, p, p, p, 1, None) == lib.TP_ERR_ARG  # mu
+    assert g(2, 2, 2, 0, 0, -1.0, 0.4, 1e-9, 3.0, p, p, p, p, 1, None) == lib.TP_ERR_ARG  # lambda + mu
+    assert g(2, 2, 2, 0, 0, 0.6, 0.4, 1.0, 3.0, p, p, p, p, 1, None) == lib.TP_ERR_ARG   # Emin
+    assert g(2, 2, 2, 0, 0, 0.6, 0.4, 1e-9, 0.5, p, p, p, p, 1, None) == lib.TP_ERR_ARG  # penal
+    assert g(2, 2, 2, 0, 0, *ok, p, p, p, p, 0, None) == lib.TP_ERR_ARG        # ncases
+    assert g(2, 2, 2, 0, 0, *ok, None, p, p, p, 1, None) == lib.TP_ERR_ARG     # NULL rho
