@@ -350,6 +350,20 @@ tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int diagonal, doub
  * dimension, material or NULL pointer. */
 tp_status tp_p1_shape_matrices(int dim, double lam, double mu, double* K, int* offsets);
 
+/* Host-side filter stencil for the P1 cells (no device work): the paper's
+ * weights W = max(0, rmin - distance) between cell midpoints (centroids),
+ * for a centre cell of each type (the types of tp_p1_shape_matrices; in 2D
+ * the types a diagonal pattern does not use get no entries).  An entry is
+ * the neighbour cell local index l of the square / cube displaced by
+ * (dx, dy, dz) from the centre's; in 2D the neighbour's cut follows from its
+ * row.  Outputs (host): count[ntypes] entries per type, entries[n][4] =
+ * (dx, dy, dz, l) grouped by type, weights[n]; n_entries = n.  cap is the
+ * capacity of entries / weights.  Rows are not truncated at the domain
+ * boundary: a caller skips neighbours outside the grid.  TP_ERR_ARG for a bad
+ * dim, diagonal, rmin (0 < rmin <= 16), NULL pointers or too small a cap. */
+tp_status tp_p1_filter_stencil(int dim, int diagonal, double rmin, int cap, int* count, int* entries,
+                               double* weights, int* n_entries);
+
 /* Phase tracing of the persistent CG (not in the paper; a profiling aid).
  * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at eight
  * points of each iteration into a ring of 32 iterations: 0 start, 1 operator

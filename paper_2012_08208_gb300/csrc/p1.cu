@@ -113,6 +113,59 @@ int p1_shapes(int dim, double lam, double mu, double K[kMaxTypes][kMaxNd * kMaxN
   return ntypes;
 }
 
+// Filter stencil on cell midpoints (the paper's weights rmin - distance,
+// clipped at 0, between cell centroids): for each cell type tau, every cell
+// of a square / cube displaced by d (|d_a| <= ceil(rmin) + 1) whose centroid
+// lies closer than rmin.  In 2D the neighbour square's cut follows from its
+// row: the centre's cut is type / 2, and with the alternating pattern each
+// row step flips it.  An entry is (dx, dy, dz, local cell index, weight);
+// entries are grouped by centre type.  Returns the number of entries, or -1
+// when they exceed `cap`.
+int p1_filter_stencil(int dim, int diagonal, double rmin, int cap, int* count, int (*ent)[4], double* w) {
+  const int ntypes = dim == 2 ? 4 : 6, ncell = dim == 2 ? 2 : 6;
+  double cen[kMaxTypes][3] = {};
+  for (int t = 0; t < ntypes; t++) {
+    int off[4][3];
+    shape_offsets(dim, t, off);
+    for (int a = 0; a < 3; a++) {
+      double sum = 0.0;
+      for (int v = 0; v < dim + 1; v++) sum += off[v][a];
+      cen[t][a] = sum / (dim + 1);
+    }
+  }
+  const int r = (int)std::ceil(rmin) + 1;
+  int n = 0;
+  for (int t = 0; t < ntypes; t++) {
+    if (dim == 2 && ((diagonal == 0 && t >= 2) || (diagonal == 1 && t < 2))) {
+      count[t] = 0;
+      continue;
+    }
+    int c0 = 0;
+    for (int dz = (dim == 3 ? -r : 0); dz <= (dim == 3 ? r : 0); dz++)
+      for (int dy = -r; dy <= r; dy++)
+        for (int dx = -r; dx <= r; dx++) {
+          const int cut = dim == 2 ? (diagonal == 2 ? ((t / 2 + dy) % 2 + 2) % 2 : diagonal) : 0;
+          for (int l = 0; l < ncell; l++) {
+            const int s2 = dim == 2 ? 2 * cut + l : l;
+            const double ex = dx + cen[s2][0] - cen[t][0], ey = dy + cen[s2][1] - cen[t][1],
+                         ez = dz + cen[s2][2] - cen[t][2];
+            const double wt = rmin - std::sqrt(ex * ex + ey * ey + ez * ez);
+            if (!(wt > 0.0)) continue;
+            if (n >= cap) return -1;
+            ent[n][0] = dx;
+            ent[n][1] = dy;
+            ent[n][2] = dz;
+            ent[n][3] = l;
+            w[n] = wt;
+            n++;
+            c0++;
+          }
+        }
+    count[t] = c0;
+  }
+  return n;
+}
+
 struct P1Args {
   int nx, ny, nz, diag, nc;
   long long ndof;
@@ -246,5 +299,15 @@ extern "C" tp_status tp_p1_shape_matrices(int dim, double lam, double mu, double
     for (int v = 0; v < dim + 1; v++)
       for (int q = 0; q < dim; q++) offsets[(t * (dim + 1) + v) * dim + q] = off[t][v][q];
   }
+  return TP_OK;
+}
+
+extern "C" tp_status tp_p1_filter_stencil(int dim, int diagonal, double rmin, int cap, int* count, int* entries,
+                                          double* weights, int* n_entries) {
+  if ((dim != 2 && dim != 3) || (dim == 2 ? (diagonal < 0 || diagonal > 2) : diagonal != 0)) return TP_ERR_ARG;
+  if (!(rmin > 0.0 && rmin <= 16.0) || cap < 1 || !count || !entries || !weights || !n_entries) return TP_ERR_ARG;
+  const int n = tp::p1_filter_stencil(dim, diagonal, rmin, cap, count, reinterpret_cast<int(*)[4]>(entries), weights);
+  if (n < 0) return TP_ERR_ARG;
+  *n_entries = n;
   return TP_OK;
 }

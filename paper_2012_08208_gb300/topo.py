@@ -100,6 +100,8 @@ def _load():
                                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tp_spd_inverse_f32": (C.c_int, [P, P, C.c_int, P]),
         "tp_p1_shape_matrices": (C.c_int, [C.c_int, C.c_double, C.c_double, P, P]),
+        "tp_p1_filter_stencil": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, P, P, P,
+                                           C.POINTER(C.c_int)]),
         "tp_p1_matvec": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                    C.c_double, C.c_double, P, P, P, P, C.c_int, P]),
         "tp_get_trace": (C.c_int, [P, P]),
@@ -138,7 +140,7 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
-            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_p1_shape_matrices", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_p1_shape_matrices", "tp_p1_filter_stencil", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
@@ -207,6 +209,21 @@ def p1_shape_matrices(dim, lam, mu):
     if st != TP_OK:
         raise TopoError(st, "tp_p1_shape_matrices failed")
     return K, off
+
+
+def p1_filter_stencil(dim, diagonal, rmin, cap=65536):
+    """(count[ntypes], entries[n, 4], weights[n]) of the P1 midpoint filter
+    (tp_p1_filter_stencil in include/topo.h); host only."""
+    nt = 4 if dim == 2 else 6
+    count = np.zeros(nt, dtype=np.int32)
+    ent = np.zeros((cap, 4), dtype=np.int32)
+    w = np.zeros(cap)
+    n = C.c_int()
+    st = lib.tp_p1_filter_stencil(dim, P1_DIAGONALS[diagonal], rmin, cap, count.ctypes.data_as(C.c_void_p),
+                                  ent.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p), C.byref(n))
+    if st != TP_OK:
+        raise TopoError(st, "tp_p1_filter_stencil failed")
+    return count, ent[:n.value].copy(), w[:n.value].copy()
 
 
 class TopoError(RuntimeError):

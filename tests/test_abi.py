@@ -92,3 +92,41 @@ def test_dense_and_p1_entry_points_reject_bad_arguments_without_the_gpu(lib):
     assert g(2, 2, 2, 0, 0, 0.6, 0.4, 1e-9, 0.5, p, p, p, p, 1, None) == lib.TP_ERR_ARG  # penal
     assert g(2, 2, 2, 0, 0, *ok, p, p, p, p, 0, None) == lib.TP_ERR_ARG        # ncases
     assert g(2, 2, 2, 0, 0, *ok, None, p, p, p, 1, None) == lib.TP_ERR_ARG     # NULL rho
+
+
+@pytest.mark.parametrize("dim,diagonal,rmin", [(2, "right", 1.5), (2, "left", 2.5), (2, "right/left", 1.5),
+                                               (2, "right/left", 3.0), (3, "kuhn", 1.5), (3, "kuhn", 2.0)])
+def test_p1_filter_stencil_rebuilds_the_oracle_weights(lib, dim, diagonal, rmin):
+    """The host stencil of the P1 midpoint filter (tp_p1_filter_stencil), laid
+    over a small grid with neighbours outside it skipped, gives exactly the
+    oracle's paper-literal dense weight matrix."""
+    import numpy as np
+    import workloads as W
+    from oracle import p1
+    if dim == 2:
+        prob = W.p1_cantilever2d(7, 6, diagonal=diagonal, rmin=rmin)
+    else:
+        prob = W.p1_cantilever3d(4, 3, 3, rmin=rmin)
+    count, ent, w = lib.p1_filter_stencil(dim, diagonal, rmin)
+    nx, ny, nz = prob.nelx, prob.nely, max(prob.nelz, 1)
+    nc = 2 if dim == 2 else 6
+    starts = np.concatenate([[0], np.cumsum(count)])
+    Wg = np.zeros((prob.n_el, prob.n_el))
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                e = i + nx * (j + ny * k)
+                for l0 in range(nc):
+                    if dim == 2:
+                        cut = {"right": 0, "left": 1}.get(diagonal, j % 2)
+                        t = 2 * cut + l0
+                    else:
+                        t = l0
+                    for q in range(starts[t], starts[t + 1]):
+                        dx, dy, dz, l = ent[q]
+                        i2, j2, k2 = i + dx, j + dy, k + dz
+                        if not (0 <= i2 < nx and 0 <= j2 < ny and 0 <= k2 < nz):
+                            continue
+                        e2 = i2 + nx * (j2 + ny * k2)
+                        Wg[nc * e + l0, nc * e2 + l] = w[q]
+    assert np.allclose(Wg, p1.dense_weights(prob), rtol=0, atol=1e-13)
