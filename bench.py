@@ -1,17 +1,22 @@
 """Benchmark of the GB300 SIMP hot path.
 
-Default workload: the 2D cantilever, 600 x 200 Q4 elements (241,602 DOFs), three
-load cases, passive void disk (r = 40 at (150, 100)), volfrac 0.4, rmin 3.0,
-FP32 operator with FP64 reductions and FP64 reliable updates.  One step = one
-SIMP iteration (three-case solve, sensitivities, filter, OC update) on
-device-resident data.  Metric: SIMP iterations per second (higher is better).
+Default workload: the 3D cantilever, 240 x 80 x 80 H8 elements (4,743,603
+DOFs), x = 0 face clamped, unit line load along the bottom edge of the x = 240
+face, volfrac 0.1, rmin 2.0, solved to true relative residual 1e-6 by
+multigrid-preconditioned CG (FP32 operator and V-cycle, FP64 restarts), warm
+started from the previous iteration's displacement.  One step = one SIMP
+iteration (solve, sensitivities, filter, OC update) on device-resident data.
+Metric: SIMP iterations per second (higher is better).  The 60 x 20 MBB beam,
+the 600 x 200 three-case cantilever and the 120 x 40 x 40 cantilever are
+reported beside it (`simp_configs`).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 (the single-problem path does not shard); value = iterations of all ranks / the
 slowest rank's time.  `--impl reference` times the FP64 CPU oracle on the host
-cores for the same workload and metric (rank 0 only).
+cores for the same workload and metric (rank 0 only), on a bounded sample of
+each step.
 """
 from __future__ import annotations
 
@@ -30,8 +35,11 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "SIMP iter/s; K(rho)u GDOF/s vs HBM roofline; learned+mixed vs plain PCG @1e-6"
-WORKLOAD = "cantilever2d_600x200_3cases_passive_disk"
+WORKLOAD = "cantilever3d_240x80x80_line_load"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM read + write of one finest-level 3D sweep launch at 240 x 80 x 80, from
+# an ncu capture of the same kernel (None until captured for the current kernel)
+TRAFFIC_FINE_SWEEP_3D = None
 
 
 def _peaks():
@@ -104,6 +112,20 @@ def algorithmic_bytes_pcg(info, n_dof, n_el, nc):
 # our arm
 
 
+SOLVER_NAMES = {0: "Jacobi-PCG (persistent, FP32 + FP64 reliable updates)",
+                1: "multigrid-preconditioned CG (FP32 V-cycle, FP32 correction segments, FP64 restarts; "
+                   "graph-replayed iterations)",
+                2: "multigrid-preconditioned CG (FP32 V-cycle, one persistent cooperative kernel per segment)"}
+
+
+def step_opts(topo, w, solver):
+    """Solver options of one SIMP step of workload w: its own tolerance and
+    precision, previous displacement as the start."""
+    prec = topo.TP_PREC_F64 if w.precision == "f64" else topo.TP_PREC_MIXED
+    return topo.solve_opts(tol=w.tol, max_it=100000, precision=prec, warm_start=topo.TP_WARM_PREVIOUS,
+                           update_drop=1e-1, precond=solver)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -117,9 +139,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    w = W.cantilever2d()
-    opts = topo.solve_opts(tol=w.tol, max_it=100000, precision=topo.TP_PREC_MIXED,
-                           warm_start=topo.TP_WARM_PREVIOUS, update_drop=1e-1, precond=args.solver)
+    w = W.cantilever3d_large()
+    opts = step_opts(topo, w, args.solver)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -129,7 +150,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     with torch.cuda.stream(stream):
-        p = topo.Problem.from_workload(w, stream=stream.cuda_stream)
+        p = topo.Problem.from_workload(w, stream=stream)
         for _ in range(args.warmup):
             p.simp_step(opts, check=False)
             flush.add_(1.0)
@@ -177,9 +198,10 @@ def run_ours(args):
         if not args.no_extras:
             extras["batch"] = batch_extra(topo, torch, dev, stream, ws=ws, rank=rank)
         if not args.no_extras and rank == 0:
+            extras["simp_configs"] = simp_configs_extra(topo, torch, dev, stream, args.solver)
             extras["matvec"] = matvec_roofline(topo, torch, dev, stream, W.cantilever3d_large(),
                                                "cantilever3d_240x80x80 H8 FP32 K(rho)u")
-            extras["matvec_2d"] = matvec_roofline(topo, torch, dev, stream, w,
+            extras["matvec_2d"] = matvec_roofline(topo, torch, dev, stream, W.cantilever2d(),
                                                   "cantilever2d_600x200 Q4 FP32 K(rho)u", copies=96, reps=5)
             extras["learned"] = learned_extra(topo)
             extras["helmholtz"] = helmholtz_extra(topo, torch, dev, stream)
@@ -190,8 +212,6 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     hbm, peak_kind = _peaks()
-    # dominant kernel: the persistent CG launch (one per step); its duration is
-    # the library's CUDA-event pair around the cooperative launch on `stream`
     solve_ms = [i.solve.ms for i in infos]
     traffic = None
     avg_ms = float(np.mean(solve_ms))
@@ -202,27 +222,23 @@ def run_ours(args):
         n_l, ms_l, bytes_l, levels = prof
         achieved = bytes_l / (ms_l * 1e-3) / 1e9 if ms_l > 0 else 0.0
         if args.solver == 1:
-            roof_kernel = ("mg_sweep_kernel<2> (finest multigrid level: Chebyshev step or residual on the strain-form "
-                           "FP32 operator, 3 cases per launch, graph-replayed PCG iterations)")
-            note = "see profiles/mg_sweep_cantilever2d_600x200.md"
+            roof_kernel = ("mg_sweep_kernel<3> (finest multigrid level: Chebyshev step or residual on the "
+                           "strain-form FP32 H8 operator, graph-replayed PCG iterations)")
         else:
-            roof_kernel = ("mg_seg_kernel<2,4> (persistent multigrid-preconditioned CG segment: FP32 correction CG, "
-                           "Chebyshev V-cycle with grid barriers between phases, 3 cases)")
-            note = "see profiles/mg_seg_cantilever2d_600x200.md"
+            roof_kernel = ("mg_seg_kernel<3,1> (persistent multigrid-preconditioned CG segment: FP32 correction "
+                           "CG, Chebyshev V-cycle with grid barriers between phases)")
         roof_extra = {"launches_timed": n_l, "us_per_launch": round(1e3 * ms_l / max(n_l, 1), 3),
-                      "bytes_per_launch": round(bytes_l / max(n_l, 1)), "levels": levels, "traffic_note": note}
+                      "bytes_per_launch": round(bytes_l / max(n_l, 1)), "levels": levels,
+                      "bytes_note": "per launch: 4 B per element (moduli), 4 B per DOF (l1 scale), 12 B per DOF "
+                                    "and case (u, b read, y written)"}
         if args.solver == 1:
-            # DRAM read + write of one mg_sweep_kernel<2> launch in the cold-cache ncu capture
-            # (profiles/mg_sweep_cantilever2d_600x200.md); in the timed step the level is L2-resident
-            traffic = 7389440.0
+            traffic = TRAFFIC_FINE_SWEEP_3D
     else:
         byts = [algorithmic_bytes_pcg(i.solve, w.n_dof, w.n_el, w.n_cases) for i in infos]
         avg_bytes = float(np.mean(byts))
         achieved = avg_bytes / (avg_ms * 1e-3) / 1e9
-        roof_kernel = "pcg_kernel<2,float,4> (persistent CG, 3 cases)"
-        roof_extra = {"traffic_note": "L2-resident working set: ncu of a 68-iteration launch reads 10.3 MB and "
-                                      "writes 1.5 MB of DRAM, with 32 MB of L2 reads per iteration against 42 MB "
-                                      "algorithmic (profiles/cg_segment_cantilever2d_600x200_full.md)"}
+        roof_kernel = "pcg_kernel<3,float,1> (persistent Jacobi-PCG)"
+        roof_extra = {}
     value = ws * args.steps / (total_ms * 1e-3)
     cpu = None
     if not args.no_cpu:
@@ -232,13 +248,11 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": "600x200 Q4", "n_dof": w.n_dof, "n_cases": w.n_cases,
-                   "tol": w.tol, "precision": "FP32 operator + FP64 reductions/reliable updates",
+        "config": {"workload": WORKLOAD, "grid": "240x80x80 H8", "n_dof": w.n_dof, "n_cases": w.n_cases,
+                   "volfrac": w.volfrac, "rmin": w.rmin, "tol": w.tol,
+                   "precision": "FP32 operator + FP64 reductions/restarts",
                    "warm_start": "previous iteration's displacement", "l2": "flushed between timed steps",
-                   "solver": "multigrid-preconditioned CG (FP32 V-cycle, FP32 correction segments, FP64 restarts)"
-                   if args.solver in (1, 2)
-                   else "Jacobi-PCG (persistent, FP32 + FP64 reliable updates)",
-                   "parallelism": f"replicas x{ws}"},
+                   "solver": SOLVER_NAMES[args.solver], "parallelism": f"replicas x{ws}"},
         "e2e": {"value": round(ws * e2e_steps / t_e2e, 4), "unit": "SIMP iter/s",
                 "h2d_bytes_per_step": w.n_el * 8, "d2h_bytes_per_step": w.n_el * 8},
         "gpu_launches": int(launches),
@@ -259,6 +273,57 @@ def run_ours(args):
     print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def simp_rate(topo, torch, dev, stream, w, solver, steps, warmup, profile=False):
+    """SIMP iterations/s of workload w on device-resident data (L2 flushed
+    between timed steps, outside the events), with the finest-sweep profile
+    when asked."""
+    opts = step_opts(topo, w, solver)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    p = topo.Problem.from_workload(w, stream=stream)
+    for _ in range(warmup):
+        p.simp_step(opts, check=False)
+        flush.add_(1.0)
+    torch.cuda.synchronize(dev)
+    if profile:
+        p.set_profile(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = []
+    for k in range(steps):
+        ev[k][0].record(stream)
+        infos.append(p.simp_step(opts, check=False))
+        ev[k][1].record(stream)
+        flush.add_(1.0)
+    torch.cuda.synchronize(dev)
+    ms = [a.elapsed_time(b) for a, b in ev]
+    out = {"workload": w.name, "n_dof": w.n_dof, "n_cases": w.n_cases, "tol": w.tol,
+           "precision": w.precision, "ms_per_step": round(float(np.mean(ms)), 3),
+           "simp_iter_s": round(1e3 * steps / float(np.sum(ms)), 3),
+           "solver_iters_per_step": float(np.mean([i.solve.iters for i in infos])),
+           "converged_steps": int(sum(i.solve.converged for i in infos)), "steps": steps,
+           "max_true_rel_res": float(max(max(i.solve.rel_res[c] for c in range(w.n_cases)) for i in infos))}
+    if profile:
+        n_l, ms_l, bytes_l, levels = p.get_profile()
+        out["fine_sweep"] = {"launches": n_l, "us_per_launch": round(1e3 * ms_l / max(n_l, 1), 3),
+                             "bytes_per_launch": round(bytes_l / max(n_l, 1)),
+                             "share_of_step": round(ms_l / float(np.sum(ms)), 4), "levels": levels}
+    p.close()
+    return out
+
+
+def simp_configs_extra(topo, torch, dev, stream, solver, steps=10, warmup=3):
+    """SIMP iterations/s of the other single-problem configurations: the
+    60 x 20 MBB beam (FP64, 1e-10), the 600 x 200 three-case cantilever with
+    the passive disk (mixed, 1e-8) and the 120 x 40 x 40 cantilever (mixed,
+    1e-6)."""
+    import workloads as W
+    out = {}
+    for key, w in (("mbb2d_60x20", W.mbb2d()), ("cantilever2d_600x200", W.cantilever2d()),
+                   ("cantilever3d_120x40x40", W.cantilever3d())):
+        out[key] = simp_rate(topo, torch, dev, stream, w, solver, steps, warmup, profile=solver in (1, 2))
+    out["solver"] = SOLVER_NAMES[solver]
+    return out
 
 
 def matvec_roofline(topo, torch, dev, stream, w, label, copies=8, reps=10):
@@ -501,6 +566,11 @@ def run_only(args):
             p.close()
         elif args.only == "helmholtz":
             out = helmholtz_extra(topo, torch, dev, stream)
+        elif args.only == "simp":
+            wl = {"mbb2d": W.mbb2d, "cantilever2d": W.cantilever2d, "cantilever3d": W.cantilever3d,
+                  "cantilever3d_large": W.cantilever3d_large}[args.workload]()
+            out = simp_rate(topo, torch, dev, stream, wl, args.solver, args.steps, args.warmup,
+                            profile=args.solver in (1, 2))
         else:
             out = learned_extra(topo)
     print(json.dumps({args.only: out}))
@@ -515,10 +585,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned", "cg2d", "cg3d", "helmholtz"],
+    ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned", "cg2d", "cg3d", "helmholtz",
+                                       "simp"],
                     default=None,
                     help="run one extra measurement alone (for profiling)")
     ap.add_argument("--copies", type=int, default=8)
+    ap.add_argument("--workload", default="cantilever3d_large",
+                    choices=["mbb2d", "cantilever2d", "cantilever3d", "cantilever3d_large"],
+                    help="workload of --only simp")
     ap.add_argument("--precond", type=int, default=0,
                     help="0 Jacobi-PCG, 1 multigrid-PCG, 2 multigrid-PCG persistent kernel (--only cg2d / cg3d)")
     ap.add_argument("--solver", type=int, default=1,

@@ -150,8 +150,8 @@ tp_status tp_set_passive(tp_problem* p, const int8_t* passive);
 tp_status tp_set_density(tp_problem* p, const double* rho, int on_device);
 
 /* Solve K(rho) u_k = f_k for every case (replaces the sparse LU of Section 4.3)
- * by Jacobi-preconditioned CG in one persistent launch.  Fills `info` (may be
- * NULL).  Returns TP_ERR_NOT_CONVERGED / TP_ERR_BREAKDOWN / TP_ERR_TIMEOUT when the
+ * by preconditioned CG: opts->precond selects the persistent Jacobi-PCG launch
+ * or the multigrid-PCG (TP_PRECOND_*).  Fills `info` (may be NULL).  Returns TP_ERR_NOT_CONVERGED / TP_ERR_BREAKDOWN / TP_ERR_TIMEOUT when the
  * solve did not reach opts->tol (the solution is still stored). */
 tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info);
 
@@ -332,8 +332,8 @@ tp_status tp_spd_inverse_f32(const float* a, float* ainv, int n, void* cuda_stre
  * fixed[n_dof] (1 = Dirichlet DOF); u, y [ncases][n_dof] with DOF = dim *
  * node + component, nodes x fastest.  y = u on fixed rows; u is read as 0 on
  * fixed DOFs elsewhere.  nelz = 0 in 2D.  The call synchronises the stream.
- * Calls on different streams must not overlap (the cell matrices sit in
- * constant memory).  Errors: TP_ERR_ARG for sizes, dim, diagonal, material
+ * The cell matrices travel with each launch (kernel parameters), so calls on
+ * different streams or threads may overlap.  Errors: TP_ERR_ARG for sizes, dim, diagonal, material
  * (mu > 0, lambda + 2 mu / dim > 0), Emin outside [0, 1), penal outside
  * [1, 10], ncases outside 1..8 or NULL pointers; TP_ERR_CUDA. */
 tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int diagonal, double lam, double mu, double Emin,
@@ -374,6 +374,15 @@ tp_status tp_p1_filter_stencil(int dim, int diagonal, double rmin, int cap, int*
  * point and stays off by default. */
 tp_status tp_set_trace(tp_problem* p, int enable);
 tp_status tp_get_trace(tp_problem* p, long long* out);
+
+/* Wait limit of the grid barriers (not in the paper; a test aid for the
+ * failure path).  Every grid-wide wait of the persistent Jacobi-PCG and of the
+ * OC kernel gives up after `cycles` SM clock cycles (0 restores the default,
+ * about 1 s at 2 GHz), records TP_ERR_TIMEOUT and returns, so the context and
+ * the handle stay usable.  A tiny value (e.g. 1) makes the next solve return
+ * TP_ERR_TIMEOUT.  Synchronises the problem's stream.  TP_ERR_ARG outside
+ * [0, 4e9]. */
+tp_status tp_set_wait_budget(tp_problem* p, long long cycles);
 
 /* Launch timing of the multigrid solver (profiling aid).  When enabled, the
  * dominant kernel of each multigrid solve is bracketed by CUDA event pairs on

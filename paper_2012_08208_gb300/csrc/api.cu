@@ -126,6 +126,15 @@ static int pick_zlen(const Grid& g, int resident) {
 
 tp_status tp_problem_ensure_E(tp_problem* p) { return ensure_E(p); }
 
+// Zero the grid-barrier word before a persistent launch, then install the
+// problem's wait limit (tp_set_wait_budget) if one is set.
+static cudaError_t reset_bar(tp_problem* p) {
+  cudaError_t e = cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream);
+  if (e == cudaSuccess && p->wait_budget)
+    e = cudaMemcpyAsync(&p->bar->budget, &p->wait_budget, sizeof(unsigned), cudaMemcpyHostToDevice, p->stream);
+  return e;
+}
+
 // Finest multigrid level: the problem's FP32 strain-form operator on all cases.
 static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, const float* w, const float* b,
                               const float* invd, float* y, int mode, float a, float c, float om, const int* stop) {
@@ -542,6 +551,14 @@ tp_status tp_get_profile(tp_problem* p, double* out) {
   return TP_OK;
 }
 
+tp_status tp_set_wait_budget(tp_problem* p, long long cycles) {
+  if (!p) return TP_ERR_ARG;
+  if (cycles < 0 || cycles > 4000000000LL) return fail(p, TP_ERR_ARG, "wait budget outside [0, 4e9] cycles");
+  TPCK(cudaStreamSynchronize(p->stream), "sync");  // no launch in flight reads the old value
+  p->wait_budget = (unsigned)cycles;
+  return TP_OK;
+}
+
 tp_status tp_get_trace(tp_problem* p, long long* out) {
   if (!p || !out) return TP_ERR_ARG;
   if (!p->trace) return fail(p, TP_ERR_STATE, "tracing is not enabled");
@@ -702,7 +719,7 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
     bool active = false;
     for (int c = 0; c < p->nc; c++) active |= st.state[c] == 0;
     if (!active || st.it >= opts->max_it || (st.flags & ERR_TIMEOUT)) break;
-    TPCK(cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream), "memset");
+    TPCK(reset_bar(p), "reset barrier");
     TPCK(launch_cg_segment(p->stream, S, f64, p->nsm, &p->last_grid), "cg kernel");
     p->launches++;
     TPCK(launch_true_residual(p->stream, S, f64, false, &nl), "residual kernel");
@@ -808,7 +825,7 @@ tp_status tp_filter(tp_problem* p, int mode) {
 tp_status tp_oc_update(tp_problem* p, double* lambda, double* volume, double* change) {
   if (!p) return TP_ERR_ARG;
   if (!p->has_dcf) return fail(p, TP_ERR_STATE, "tp_filter (or tp_set(TP_DCF)) must precede tp_oc_update");
-  TPCK(cudaMemsetAsync(p->bar, 0, sizeof(GridBar), p->stream), "memset");
+  TPCK(reset_bar(p), "reset barrier");
   int grid = 0;
   TPCK(launch_oc(p->stream, p->ne, p->rho, p->dcf, p->has_passive ? p->passive : nullptr, p->prm.volfrac,
                  p->prm.move, p->prm.dmin, p->rho_new, p->bscr, p->part, p->bar, p->ost, p->nsm, &grid),

@@ -16,7 +16,7 @@ struct GridBar {
   unsigned int count;
   unsigned int gen;
   int err;
-  int pad;
+  unsigned int budget;  // wait limit of grid_sync in clock cycles; 0 = kSpinCycles
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -39,7 +39,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 // counter with release semantics and waits (acquire) until the counter reaches
 // gridDim.x * (gen + 1).  The wait is bounded: on expiry the CTA records
 // ERR_TIMEOUT and returns false, and every CTA returns false once the error word
-// is set, so no CTA can wait forever.
+// is set, so no CTA can wait forever.  The limit is kSpinCycles unless the
+// barrier word's `budget` holds a smaller nonzero cycle count (a test aid).
 // The returned flag is decided by thread 0 and shared through shared memory, so
 // it is uniform across the CTA (all threads take the same branch afterwards).
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned& gen) {
@@ -49,9 +50,11 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned& gen) {
   if (threadIdx.x == 0) {
     const unsigned target = gen * gridDim.x;
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&b->count), "r"(1u) : "memory");
+    const unsigned bud = *(volatile const unsigned*)&b->budget;
+    const long long limit = bud ? (long long)bud : kSpinCycles;
     const long long t0 = clock64();
     while (ld_acquire_u32(&b->count) < target) {
-      if (clock64() - t0 > kSpinCycles) {
+      if (clock64() - t0 > limit) {
         atomicOr(&b->err, ERR_TIMEOUT);
         break;
       }

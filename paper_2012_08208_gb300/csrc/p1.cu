@@ -23,8 +23,15 @@ namespace {
 constexpr int kMaxTypes = 6;
 constexpr int kMaxNd = 12;  // DOFs of a tetrahedron
 
-__constant__ double cP1K[kMaxTypes][kMaxNd * kMaxNd];  // unit-modulus cell matrices, row-major
-__constant__ int cP1Off[kMaxTypes][4][3];              // vertex offsets within the square / cube
+// Unit-modulus cell matrices (row-major) and vertex offsets within the square
+// / cube of every cell shape.  They travel with each launch as part of the
+// kernel's __grid_constant__ parameter block (about 7.2 KB, within the 32 KB
+// parameter limit), so concurrent calls with different materials cannot see
+// each other's matrices.
+struct P1Shapes {
+  double K[kMaxTypes][kMaxNd * kMaxNd];
+  int off[kMaxTypes][4][3];
+};
 
 // Vertex offsets of each shape.  2D: 0, 1 = the two cells of a square cut
 // along (0,0)-(1,1); 2, 3 = cut along (1,0)-(0,1) (cell 0 holds (0,0) and
@@ -174,12 +181,13 @@ struct P1Args {
   const uint8_t* fixed;
   const double* u;
   double* y;
+  P1Shapes sh;
 };
 
 // One thread per (node, case): y_i = sum over the cells around the node of
 // E_c (K_c u_c) rows of the node, u masked on fixed DOFs; fixed rows y = u.
 template <int DIM>
-__global__ void p1_matvec_kernel(P1Args a) {
+__global__ void p1_matvec_kernel(const __grid_constant__ P1Args a) {
   constexpr int NV = DIM + 1, ND = DIM * NV, NCELL = DIM == 2 ? 2 : 6;
   const long long nxy = (long long)(a.nx + 1) * (a.ny + 1);
   const long long nn = nxy * (DIM == 3 ? a.nz + 1 : 1);
@@ -208,22 +216,22 @@ __global__ void p1_matvec_kernel(P1Args a) {
             int av = -1;
 #pragma unroll
             for (int v = 0; v < NV; v++)
-              if (cP1Off[type][v][0] == li && cP1Off[type][v][1] == lj && (DIM == 2 || cP1Off[type][v][2] == lk))
+              if (a.sh.off[type][v][0] == li && a.sh.off[type][v][1] == lj && (DIM == 2 || a.sh.off[type][v][2] == lk))
                 av = v;
             if (av < 0) continue;
             const double E = a.Emin + pow(a.rho[NCELL * e + t], a.penal) * (1.0 - a.Emin);
 #pragma unroll
             for (int m = 0; m < NV; m++) {
-              const long long nm = (ei + cP1Off[type][m][0]) +
-                                   (long long)(a.nx + 1) * ((ej + cP1Off[type][m][1]) +
-                                                            (long long)(a.ny + 1) * (DIM == 3 ? ek + cP1Off[type][m][2] : 0));
+              const long long nm = (ei + a.sh.off[type][m][0]) +
+                                   (long long)(a.nx + 1) * ((ej + a.sh.off[type][m][1]) +
+                                                            (long long)(a.ny + 1) * (DIM == 3 ? ek + a.sh.off[type][m][2] : 0));
 #pragma unroll
               for (int s = 0; s < DIM; s++) {
                 const long long dof = DIM * nm + s;
                 if (a.fixed[dof]) continue;
                 const double uv = u[dof];
 #pragma unroll
-                for (int q = 0; q < DIM; q++) acc[q] += E * cP1K[type][(DIM * av + q) * ND + DIM * m + s] * uv;
+                for (int q = 0; q < DIM; q++) acc[q] += E * a.sh.K[type][(DIM * av + q) * ND + DIM * m + s] * uv;
               }
             }
           }
@@ -252,17 +260,9 @@ extern "C" tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int dia
   if (ncases < 1 || ncases > 8 || !rho || !fixed || !u || !y) return TP_ERR_ARG;
   const long long nn = (long long)(nelx + 1) * (nely + 1) * (dim == 3 ? nelz + 1 : 1);
   if (nn > (1LL << 31)) return TP_ERR_ARG;
-  double K[tp::kMaxTypes][tp::kMaxNd * tp::kMaxNd] = {};
-  int off[tp::kMaxTypes][4][3] = {};
-  tp::p1_shapes(dim, lam, mu, K, off);
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  cudaError_t e = cudaMemcpyToSymbolAsync(tp::cP1K, K, sizeof(K), 0, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(tp::cP1Off, off, sizeof(off), 0, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return TP_ERR_CUDA;
-  }
-  tp::P1Args a;
+  tp::P1Args a = {};
+  tp::p1_shapes(dim, lam, mu, a.sh.K, a.sh.off);
   a.nx = nelx;
   a.ny = nely;
   a.nz = dim == 3 ? nelz : 0;
@@ -275,7 +275,15 @@ extern "C" tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int dia
   a.fixed = fixed;
   a.u = u;
   a.y = y;
-  const dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 152 * 8), ncases);
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TP_ERR_CUDA;
+  }
+  // grid-stride loop: at most 8 resident CTAs of 256 threads per SM
+  const dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 8LL * std::max(nsm, 1)), ncases);
   if (dim == 2) tp::p1_matvec_kernel<2><<<grid, 256, 0, s>>>(a);
   else tp::p1_matvec_kernel<3><<<grid, 256, 0, s>>>(a);
   e = cudaStreamSynchronize(s);

@@ -334,7 +334,10 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
     a.cs->it = ctl->it;
     a.cs->pbuf = ctl->pbuf;
     a.cs->need = ctl->need;
-    a.cs->flags |= ctl->flags | (ok ? 0 : ERR_TIMEOUT);
+    // a CTA that gave up at a barrier leaves the launch early; its error bit in
+    // the barrier word reaches the host even if CTA 0's own waits all ended
+    const bool timed_out = !ok || (ld_volatile_i32(&a.bar->err) & ERR_TIMEOUT);
+    a.cs->flags |= ctl->flags | (timed_out ? ERR_TIMEOUT : 0);
     for (int c = 0; c < NCM && c < kMaxCases; c++) {
       if (c < nc) a.cs->state[c] = ctl->state[c];
       a.cs->rz[c] = ctl->rz[c];

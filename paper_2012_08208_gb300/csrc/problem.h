@@ -61,6 +61,7 @@ struct tp_problem {
   bool profile = false;          // time the multigrid finest-level launches
   int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
   int oc_passes = 0, oc_root = 0;  // diagnostics of the last OC update
+  unsigned wait_budget = 0;      // grid-barrier wait limit in cycles (0 = default, ~1 s)
   double* rho_phys = nullptr;    // filtered densities (filter modes 1, 2)
   double* helm = nullptr;        // Helmholtz filter scratch (filter mode 2)
   tp::HelmStatus* hst = nullptr;

@@ -85,6 +85,7 @@ def _load():
         "tp_set": (C.c_int, [P, C.c_int, P, C.c_int]),
         "tp_matvec": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int]),
         "tp_set_trace": (C.c_int, [P, C.c_int]),
+        "tp_set_wait_budget": (C.c_int, [P, C.c_longlong]),
         "tp_batch_create": (C.c_int, [C.c_int, C.POINTER(tp_params), P, C.POINTER(P)]),
         "tp_batch_destroy": (None, [P]),
         "tp_batch_last_error": (C.c_char_p, [P]),
@@ -139,7 +140,7 @@ lib = _load()
 # Every name the header declares (checked by the CPU test suite).
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
-            "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace",
+            "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace", "tp_set_wait_budget",
             "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_p1_shape_matrices", "tp_p1_filter_stencil", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
@@ -152,15 +153,62 @@ NOALLOC_MAX_ELEMENTS = 1048576
 SPD_INVERSE_MAX_N = 16384
 
 
+def _stream_handle(stream):
+    """cudaStream_t of `stream` as an int: a torch.cuda.Stream (its
+    cuda_stream), a raw handle, or None for torch's current stream on the
+    current device (the legacy default stream, 0, when CUDA is unavailable)."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:  # pragma: no cover
+            pass
+        return 0
+    cs = getattr(stream, "cuda_stream", None)
+    return int(cs if cs is not None else stream)
+
+
+def _device_tensors(*specs):
+    """Pointers of tensors the C-ABI reads or writes as device memory of the
+    current device.  specs: (tensor, name, dtype, numel).  Every tensor's type,
+    dtype, contiguity and element count is checked first, then that each is a
+    CUDA tensor on the current device.  A mismatch raises (the library would
+    otherwise read or write out of bounds)."""
+    import torch
+    for t, name, dtype, numel in specs:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name}: a torch tensor is required, got {type(t).__name__}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: the tensor must be contiguous")
+        if t.numel() != numel:
+            raise ValueError(f"{name}: {t.numel()} elements, expected {numel}")
+    for t, name, _, _ in specs:
+        if not t.is_cuda:
+            raise ValueError(f"{name}: a CUDA tensor is required")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name}: on {t.device}, but the current device is cuda:{torch.cuda.current_device()}")
+    return [C.c_void_p(t.data_ptr()) for t, _, _, _ in specs]
+
+
 def oc_update_noalloc(rho, dcf, rho_new, volfrac, move=0.2, dmin=1e-3, passive=None, stream=None):
     """Allocation-free OC update on device tensors (see tp_oc_update_noalloc in
-    include/topo.h).  rho, dcf, rho_new: CUDA float64 tensors; passive: CUDA int8
-    tensor or None.  Returns (lambda, volume, change)."""
+    include/topo.h).  rho, dcf, rho_new: contiguous CUDA float64 tensors of n_el
+    elements on the current device; passive: CUDA int8 tensor of n_el elements
+    or None.  stream: torch.cuda.Stream, raw handle, or None for torch's current
+    stream.  Returns (lambda, volume, change)."""
+    import torch
+    n = rho.numel() if isinstance(rho, torch.Tensor) else -1
+    specs = [(rho, "rho", torch.float64, n), (dcf, "dcf", torch.float64, n), (rho_new, "rho_new", torch.float64, n)]
+    if passive is not None:
+        specs.append((passive, "passive", torch.int8, n))
+    ptrs = _device_tensors(*specs)
+    pr, pd, po = ptrs[:3]
+    pp = ptrs[3] if passive is not None else None
     lam, vol, ch = C.c_double(), C.c_double(), C.c_double()
-    pp = C.c_void_p(passive.data_ptr()) if passive is not None else None
-    st = lib.tp_oc_update_noalloc(C.c_void_p(rho.data_ptr()), C.c_void_p(dcf.data_ptr()), pp, rho.numel(),
-                                  volfrac, move, dmin, C.c_void_p(rho_new.data_ptr()),
-                                  C.c_void_p(0 if stream is None else int(stream)),
+    st = lib.tp_oc_update_noalloc(pr, pd, pp, n, volfrac, move, dmin, po, C.c_void_p(_stream_handle(stream)),
                                   C.byref(lam), C.byref(vol), C.byref(ch))
     if st != TP_OK:
         raise TopoError(st, "tp_oc_update_noalloc failed")
@@ -177,7 +225,7 @@ def spd_inverse(a, stream=None):
         raise ValueError("a must be square")
     out = np.empty_like(a)
     st = lib.tp_spd_inverse_f32(a.ctypes.data_as(C.c_void_p), out.ctypes.data_as(C.c_void_p), a.shape[0],
-                                C.c_void_p(0 if stream is None else int(stream)))
+                                C.c_void_p(_stream_handle(stream)))
     if st != TP_OK:
         raise TopoError(st, "tp_spd_inverse_f32 failed")
     return out
@@ -188,12 +236,20 @@ P1_DIAGONALS = {"right": 0, "left": 1, "right/left": 2, "kuhn": 0}
 
 def p1_matvec(dim, nelx, nely, nelz, diagonal, lam, mu, Emin, penal, rho, fixed, u, y, stream=None):
     """y = K(rho) u for the paper's P1 cells (tp_p1_matvec in include/topo.h).
-    rho (float64), fixed (uint8), u and y (float64, [ncases, n_dof]): CUDA
-    tensors; diagonal: "right", "left", "right/left" (2D) or "kuhn" (3D)."""
+    rho (float64, one per cell), fixed (uint8, n_dof), u and y (float64,
+    [ncases, n_dof] or [n_dof]): contiguous CUDA tensors on the current device;
+    diagonal: "right", "left", "right/left" (2D) or "kuhn" (3D)."""
+    import torch
+    nn = (nelx + 1) * (nely + 1) * ((nelz + 1) if dim == 3 else 1)
+    n_dof = dim * nn
+    n_cells = (2 * nelx * nely) if dim == 2 else 6 * nelx * nely * nelz
+    if not isinstance(u, torch.Tensor) or u.dim() not in (1, 2):
+        raise ValueError("u: a 1D or 2D torch tensor is required")
     nc = u.shape[0] if u.dim() == 2 else 1
+    pu, py, pr, pf = _device_tensors((u, "u", torch.float64, nc * n_dof), (y, "y", torch.float64, nc * n_dof),
+                                     (rho, "rho", torch.float64, n_cells), (fixed, "fixed", torch.uint8, n_dof))
     st = lib.tp_p1_matvec(dim, nelx, nely, nelz, P1_DIAGONALS[diagonal], lam, mu, Emin, penal,
-                          C.c_void_p(rho.data_ptr()), C.c_void_p(fixed.data_ptr()), C.c_void_p(u.data_ptr()),
-                          C.c_void_p(y.data_ptr()), nc, C.c_void_p(0 if stream is None else int(stream)))
+                          pr, pf, pu, py, nc, C.c_void_p(_stream_handle(stream)))
     if st != TP_OK:
         raise TopoError(st, "tp_p1_matvec failed")
     return y
@@ -264,7 +320,7 @@ class Problem:
 
     def __init__(self, params: tp_params, stream=None):
         h = C.c_void_p()
-        s = C.c_void_p(0 if stream is None else int(stream))
+        s = C.c_void_p(_stream_handle(stream))
         st = lib.tp_create_problem(C.byref(params), s, C.byref(h))
         if st != TP_OK:
             raise TopoError(st, "tp_create_problem rejected the parameters")
@@ -314,6 +370,10 @@ class Problem:
 
     def set_trace(self, enable=True):
         self._check(lib.tp_set_trace(self.h, 1 if enable else 0))
+
+    def set_wait_budget(self, cycles=0):
+        """Grid-barrier wait limit in SM cycles (0 = the default, about 1 s)."""
+        self._check(lib.tp_set_wait_budget(self.h, int(cycles)))
 
     def get_trace(self):
         out = np.zeros((32, 8), dtype=np.int64)
@@ -452,7 +512,7 @@ class Batch:
                                              w.volfrac, w.rmin, w.move, w.dmin, w.n_cases)
                                  for w in workloads_list])
         h = C.c_void_p()
-        st = lib.tp_batch_create(n, arr, C.c_void_p(0 if stream is None else int(stream)), C.byref(h))
+        st = lib.tp_batch_create(n, arr, C.c_void_p(_stream_handle(stream)), C.byref(h))
         if st != TP_OK:
             raise TopoError(st, "tp_batch_create rejected the parameters")
         self.h = h
@@ -552,7 +612,7 @@ class Net:
     def __init__(self, c_in=TPNN_FEATURES, widths=(16, 32, 64, 64), stream=None):
         h = C.c_void_p()
         wd = (C.c_int * 4)(*widths)
-        st = lib.tpnn_create(c_in, 3, wd, C.c_void_p(0 if stream is None else int(stream)), C.byref(h))
+        st = lib.tpnn_create(c_in, 3, wd, C.c_void_p(_stream_handle(stream)), C.byref(h))
         if st != TP_OK:
             raise TopoError(st, "tpnn_create rejected the configuration")
         self.h = h

@@ -130,3 +130,51 @@ def test_p1_filter_stencil_rebuilds_the_oracle_weights(lib, dim, diagonal, rmin)
                         e2 = i2 + nx * (j2 + ny * k2)
                         Wg[nc * e + l0, nc * e2 + l] = w[q]
     assert np.allclose(Wg, p1.dense_weights(prob), rtol=0, atol=1e-13)
+
+
+def test_binding_rejects_bad_tensors_before_the_library(lib):
+    """The device-pointer wrappers (oc_update_noalloc, p1_matvec) check each
+    tensor's dtype, contiguity, element count and device before any call, so a
+    wrong tensor raises instead of letting a kernel read or write out of
+    bounds.  CPU tensors reach only the checks (no device work)."""
+    import torch
+    n = 100
+    good = torch.zeros(n, dtype=torch.float64)
+    with pytest.raises(ValueError, match="dtype"):
+        lib.oc_update_noalloc(good, torch.zeros(n, dtype=torch.float32), good.clone(), 0.5)
+    with pytest.raises(ValueError, match="elements"):
+        lib.oc_update_noalloc(good, torch.zeros(n - 1, dtype=torch.float64), good.clone(), 0.5)
+    with pytest.raises(ValueError, match="contiguous"):
+        lib.oc_update_noalloc(good, torch.zeros(2 * n, dtype=torch.float64)[::2], good.clone(), 0.5)
+    with pytest.raises(ValueError, match="dtype"):
+        lib.oc_update_noalloc(good, good.clone(), good.clone(), 0.5, passive=torch.zeros(n, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="CUDA"):
+        lib.oc_update_noalloc(good, good.clone(), good.clone(), 0.5)
+    with pytest.raises(TypeError):
+        lib.oc_update_noalloc(good.numpy(), good, good, 0.5)
+    # P1 operator on a 3 x 2 grid "right": 6 cells, 12 nodes, 24 DOFs
+    rho = torch.full((12,), 0.5, dtype=torch.float64)
+    fixed = torch.zeros(24, dtype=torch.uint8)
+    u = torch.zeros((2, 24), dtype=torch.float64)
+    y = torch.zeros((2, 24), dtype=torch.float64)
+    args = (2, 3, 2, 0, "right", 0.6, 0.4, 1e-9, 3.0)
+    with pytest.raises(ValueError, match="elements"):
+        lib.p1_matvec(*args, rho[:6], fixed, u, y)                       # one density per cell
+    with pytest.raises(ValueError, match="elements"):
+        lib.p1_matvec(*args, rho, fixed, u, y[:1])                       # y shorter than u
+    with pytest.raises(ValueError, match="dtype"):
+        lib.p1_matvec(*args, rho, fixed.to(torch.int32), u, y)
+    with pytest.raises(ValueError, match="dtype"):
+        lib.p1_matvec(*args, rho, fixed, u.float(), y)
+    with pytest.raises(ValueError, match="CUDA"):
+        lib.p1_matvec(*args, rho, fixed, u, y)
+
+
+def test_stream_argument_forms(lib):
+    """A stream may be given as None, a raw handle or an object with a
+    cuda_stream attribute (torch.cuda.Stream)."""
+    class FakeStream:
+        cuda_stream = 12345
+    assert lib._stream_handle(FakeStream()) == 12345
+    assert lib._stream_handle(678) == 678
+    assert isinstance(lib._stream_handle(None), int)

@@ -1,5 +1,6 @@
 """The allocation-free OC update (tp_oc_update_noalloc) gives the same result as
-the regular tp_oc_update.
+the regular tp_oc_update, and both match the oracle's exact multiplier and
+update (Eq. "update": lambda is the root of sum rho_new(lambda) = volfrac n_el).
 
 tp_oc_update_noalloc is for callers that cannot allocate device memory when they
 update the design (their framework's allocator owns the memory budget, or their
@@ -8,12 +9,15 @@ cudaMalloc / cudaFree).  Its scratch is one static device array shared by every
 call, so this test calls it twice in a row, on different inputs, and compares
 each call through the C-ABI with the regular entry point on the same inputs,
 using the tolerances of the OC parity tests (lambda rel 1e-9, densities
-max-abs 1e-6).  This file is named so that pytest collects it last.
+max-abs 1e-6); each call is also compared with the oracle's exact piecewise
+root for lambda and its update at that root.  This file is named so that
+pytest collects it last.
 """
 import numpy as np
 import pytest
 
 import workloads as W
+from oracle import oc
 
 pytestmark = pytest.mark.gpu
 
@@ -60,6 +64,11 @@ def test_noalloc_matches_regular_on_two_calls():
         assert ch == pytest.approx(ch_r, rel=1e-12, abs=1e-15)
         if passive is not None:
             assert np.all(out[passive == 1] == 0.001)
+        # against the oracle: exact root of the volume constraint, update there
+        lam_exact = oc.exact_lambda(rho, dcf, vf, passive=passive)
+        assert lam == pytest.approx(lam_exact, rel=1e-9)
+        assert np.max(np.abs(out - oc.update(rho, dcf, lam_exact, passive=passive))) <= 1e-6
+        assert vol == pytest.approx(vf * n, rel=1e-8)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
