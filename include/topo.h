@@ -364,6 +364,71 @@ tp_status tp_p1_shape_matrices(int dim, double lam, double mu, double* K, int* o
 tp_status tp_p1_filter_stencil(int dim, int diagonal, double rmin, int cap, int* count, int* entries,
                                double* weights, int* n_entries);
 
+/* ---------------------------------------------------------------------------
+ * The SIMP loop on the paper's own elements (Section 4 "Discretization the
+ * problem": triangles, P1 displacements, one density per cell; Section 5
+ * "Working with 3D problems": tetrahedra; the material and form of the
+ * Section 4.3 listing).  The grid and cells are those of tp_p1_matvec: unit
+ * squares cut into 2 triangles (diagonal 0 "right", 1 "left", 2 alternating
+ * by row) or unit cubes cut into the 6 Kuhn tetrahedra (diagonal 0); cell
+ * index = 2 e + l (2D) or 6 e + l (3D) for square / cube e.  Stiffness
+ * sigma = 2 mu eps + lambda tr(eps) I scaled by Emin + rho^penal (1 - Emin).
+ * Calls, conventions and errors as for the Q4 / H8 problem (tp_status,
+ * borrowed pointers, tp_p1_last_error, calls on one handle not thread-safe):
+ *   tp_p1_solve          K(rho) u_k = f_k by Jacobi-preconditioned CG in FP64
+ *                        (opts->precision TP_PREC_F64, opts->precond
+ *                        TP_PRECOND_JACOBI, else TP_ERR_ARG), all cases
+ *                        together, until the TRUE relative residual
+ *                        ||f - K u|| / ||f|| <= opts->tol (recomputed
+ *                        whenever the recurrence meets it);
+ *                        warm_start TP_WARM_ZERO, TP_WARM_PREVIOUS or
+ *                        TP_WARM_USER (the TP_U set by tp_p1_set)
+ *   tp_p1_sensitivities  c = sum_k f_k^T u_k, ce_e = sum_k u_e^T K_e u_e (unit
+ *                        modulus), dc_e = -penal rho_e^(penal-1) (1 - Emin) ce_e
+ *                        (Section 3.2, Section 4.4; the cell energy is a
+ *                        uniform multiple of the paper's DG0 projection)
+ *   tp_p1_filter         dc~_a = sum_b W_ab rho_b dc_b / (rho_a sum_b W_ab),
+ *                        W_ab = max(0, rmin - |m_a - m_b|) between cell
+ *                        centroids, rows truncated at the grid boundary
+ *                        (Eq. "filter", "filter_mat")
+ *   tp_p1_oc_update      the OC update of tp_oc_update on the cells
+ *                        (Eq. "update"; passive cells held at dmin)
+ *   tp_p1_simp_step      solve, sensitivities, filter, OC update
+ *   tp_p1_apply          y = K(rho) u (boundary-conditioned as in tp_matvec)
+ *                        for all cases: u, y [n_cases][n_dof]; with
+ *                        on_device = 1 the call only enqueues the kernel
+ * tp_p1_set_fixed: fixed[n_dof] (host, nonzero = u = 0; at least one).
+ * tp_p1_set_loads: f[n_cases][n_dof] (host, finite; loads on fixed DOFs do not
+ * enter the solve).  tp_p1_set_passive: passive[n_cells] (host, 1 = void).
+ * tp_p1_set_density: rho[n_cells] in (0, 1].  tp_p1_get: TP_RHO (= TP_RHO_PHYS),
+ * TP_U, TP_DC, TP_DCF, TP_CE.  tp_p1_set: TP_U, TP_DC, TP_DCF.
+ * Parameters: dim 2 or 3; nelx, nely >= 1, nelz >= 1 in 3D and 0 in 2D;
+ * mu > 0, lambda + 2 mu / dim > 0; 0 < Emin < 1; 1 <= penal <= 10;
+ * 0 < volfrac <= 1; 0 < rmin <= 4; move > 0; 0 < dmin < 1; 1..8 cases. */
+typedef struct tp_p1_params {
+  int dim, nelx, nely, nelz;
+  int diagonal;
+  double lam, mu, Emin, penal, volfrac, rmin, move, dmin;
+  int n_cases;
+} tp_p1_params;
+typedef struct tp_p1_problem tp_p1_problem;
+tp_status tp_p1_create(const tp_p1_params* params, void* cuda_stream, tp_p1_problem** out);
+void tp_p1_destroy(tp_p1_problem* p);
+const char* tp_p1_last_error(const tp_p1_problem* p);
+long long tp_p1_launch_count(const tp_p1_problem* p);
+tp_status tp_p1_set_fixed(tp_p1_problem* p, const uint8_t* fixed);
+tp_status tp_p1_set_loads(tp_p1_problem* p, const double* f);
+tp_status tp_p1_set_passive(tp_p1_problem* p, const int8_t* passive);
+tp_status tp_p1_set_density(tp_p1_problem* p, const double* rho, int on_device);
+tp_status tp_p1_solve(tp_p1_problem* p, const tp_solve_opts* opts, tp_solve_info* info);
+tp_status tp_p1_sensitivities(tp_p1_problem* p, double* compliance);
+tp_status tp_p1_filter(tp_p1_problem* p);
+tp_status tp_p1_oc_update(tp_p1_problem* p, double* lambda, double* volume, double* change);
+tp_status tp_p1_simp_step(tp_p1_problem* p, const tp_solve_opts* opts, tp_step_info* info);
+tp_status tp_p1_apply(tp_p1_problem* p, const double* u, double* y, int on_device);
+tp_status tp_p1_get(tp_p1_problem* p, int what, void* dst, int on_device);
+tp_status tp_p1_set(tp_p1_problem* p, int what, const void* src, int on_device);
+
 /* Phase tracing of the persistent CG (not in the paper; a profiling aid).
  * When enabled, CTA 0 of every CG launch records %globaltimer (ns) at eight
  * points of each iteration into a ring of 32 iterations: 0 start, 1 operator

@@ -16,28 +16,15 @@
 
 #include "../../include/topo.h"
 #include "common.cuh"
+#include "p1.h"
 
 namespace tp {
-namespace {
-
-constexpr int kMaxTypes = 6;
-constexpr int kMaxNd = 12;  // DOFs of a tetrahedron
-
-// Unit-modulus cell matrices (row-major) and vertex offsets within the square
-// / cube of every cell shape.  They travel with each launch as part of the
-// kernel's __grid_constant__ parameter block (about 7.2 KB, within the 32 KB
-// parameter limit), so concurrent calls with different materials cannot see
-// each other's matrices.
-struct P1Shapes {
-  double K[kMaxTypes][kMaxNd * kMaxNd];
-  int off[kMaxTypes][4][3];
-};
 
 // Vertex offsets of each shape.  2D: 0, 1 = the two cells of a square cut
 // along (0,0)-(1,1); 2, 3 = cut along (1,0)-(0,1) (cell 0 holds (0,0) and
 // (1,0), cell 1 the rest).  3D: the Kuhn path for the axis orderings in
 // lexicographic order.
-void shape_offsets(int dim, int type, int off[4][3]) {
+void p1_shape_offsets(int dim, int type, int off[4][3]) {
   for (int v = 0; v < 4; v++)
     for (int a = 0; a < 3; a++) off[v][a] = 0;
   if (dim == 2) {
@@ -63,7 +50,7 @@ void shape_offsets(int dim, int type, int off[4][3]) {
 // barycentric gradients are the rows 1.. of [1 | X]^-1 (Gauss-Jordan with
 // partial pivoting), the measure |det [1 | X]| / dim!, and
 // K[d i + a][d j + b] = |T| (mu (delta_ab g_i . g_j + g_i[b] g_j[a]) + lambda g_i[a] g_j[b]).
-void simplex_matrix(int dim, const double X[4][3], double lam, double mu, double* K) {
+static void simplex_matrix(int dim, const double X[4][3], double lam, double mu, double* K) {
   const int nv = dim + 1;
   double M[4][8];
   for (int r = 0; r < nv; r++) {
@@ -108,10 +95,11 @@ void simplex_matrix(int dim, const double X[4][3], double lam, double mu, double
 
 // Unit matrices and vertex offsets of every cell shape of the grid (4 in 2D,
 // 6 in 3D), K[t] row-major with dim * (dim + 1) rows.
-int p1_shapes(int dim, double lam, double mu, double K[kMaxTypes][kMaxNd * kMaxNd], int off[kMaxTypes][4][3]) {
+int p1_shapes(int dim, double lam, double mu, double K[kP1MaxTypes][kP1MaxNd * kP1MaxNd],
+              int off[kP1MaxTypes][4][3]) {
   const int ntypes = dim == 2 ? 4 : 6;
   for (int t = 0; t < ntypes; t++) {
-    shape_offsets(dim, t, off[t]);
+    p1_shape_offsets(dim, t, off[t]);
     double X[4][3];
     for (int v = 0; v < 4; v++)
       for (int q = 0; q < 3; q++) X[v][q] = off[t][v][q];
@@ -130,10 +118,10 @@ int p1_shapes(int dim, double lam, double mu, double K[kMaxTypes][kMaxNd * kMaxN
 // when they exceed `cap`.
 int p1_filter_stencil(int dim, int diagonal, double rmin, int cap, int* count, int (*ent)[4], double* w) {
   const int ntypes = dim == 2 ? 4 : 6, ncell = dim == 2 ? 2 : 6;
-  double cen[kMaxTypes][3] = {};
+  double cen[kP1MaxTypes][3] = {};
   for (int t = 0; t < ntypes; t++) {
     int off[4][3];
-    shape_offsets(dim, t, off);
+    p1_shape_offsets(dim, t, off);
     for (int a = 0; a < 3; a++) {
       double sum = 0.0;
       for (int v = 0; v < dim + 1; v++) sum += off[v][a];
@@ -172,6 +160,8 @@ int p1_filter_stencil(int dim, int diagonal, double rmin, int cap, int* count, i
   }
   return n;
 }
+
+namespace {
 
 struct P1Args {
   int nx, ny, nz, diag, nc;
@@ -298,8 +288,8 @@ extern "C" tp_status tp_p1_matvec(int dim, int nelx, int nely, int nelz, int dia
 extern "C" tp_status tp_p1_shape_matrices(int dim, double lam, double mu, double* K, int* offsets) {
   if ((dim != 2 && dim != 3) || !K || !offsets) return TP_ERR_ARG;
   if (!(mu > 0.0) || !(lam + 2.0 * mu / dim > 0.0) || !std::isfinite(lam) || !std::isfinite(mu)) return TP_ERR_ARG;
-  double Kt[tp::kMaxTypes][tp::kMaxNd * tp::kMaxNd] = {};
-  int off[tp::kMaxTypes][4][3] = {};
+  double Kt[tp::kP1MaxTypes][tp::kP1MaxNd * tp::kP1MaxNd] = {};
+  int off[tp::kP1MaxTypes][4][3] = {};
   const int ntypes = tp::p1_shapes(dim, lam, mu, Kt, off);
   const int nd = dim * (dim + 1);
   for (int t = 0; t < ntypes; t++) {

@@ -59,6 +59,13 @@ class tp_step_info(C.Structure):
                 ("volume", C.c_double), ("change", C.c_double), ("oc_passes", C.c_int), ("oc_root", C.c_int)]
 
 
+class tp_p1_params(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nelx", C.c_int), ("nely", C.c_int), ("nelz", C.c_int), ("diagonal", C.c_int),
+                ("lam", C.c_double), ("mu", C.c_double), ("Emin", C.c_double), ("penal", C.c_double),
+                ("volfrac", C.c_double), ("rmin", C.c_double), ("move", C.c_double), ("dmin", C.c_double),
+                ("n_cases", C.c_int)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with "
@@ -105,6 +112,22 @@ def _load():
                                            C.POINTER(C.c_int)]),
         "tp_p1_matvec": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                    C.c_double, C.c_double, P, P, P, P, C.c_int, P]),
+        "tp_p1_create": (C.c_int, [C.POINTER(tp_p1_params), P, C.POINTER(P)]),
+        "tp_p1_destroy": (None, [P]),
+        "tp_p1_last_error": (C.c_char_p, [P]),
+        "tp_p1_launch_count": (C.c_longlong, [P]),
+        "tp_p1_set_fixed": (C.c_int, [P, P]),
+        "tp_p1_set_loads": (C.c_int, [P, P]),
+        "tp_p1_set_passive": (C.c_int, [P, P]),
+        "tp_p1_set_density": (C.c_int, [P, P, C.c_int]),
+        "tp_p1_solve": (C.c_int, [P, C.POINTER(tp_solve_opts), C.POINTER(tp_solve_info)]),
+        "tp_p1_sensitivities": (C.c_int, [P, C.POINTER(C.c_double)]),
+        "tp_p1_filter": (C.c_int, [P]),
+        "tp_p1_oc_update": (C.c_int, [P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "tp_p1_simp_step": (C.c_int, [P, C.POINTER(tp_solve_opts), C.POINTER(tp_step_info)]),
+        "tp_p1_apply": (C.c_int, [P, P, P, C.c_int]),
+        "tp_p1_get": (C.c_int, [P, C.c_int, P, C.c_int]),
+        "tp_p1_set": (C.c_int, [P, C.c_int, P, C.c_int]),
         "tp_get_trace": (C.c_int, [P, P]),
         "tp_set_profile": (C.c_int, [P, C.c_int]),
         "tp_get_profile": (C.c_int, [P, P]),
@@ -141,7 +164,10 @@ lib = _load()
 EXPORTED = ["tp_create_problem", "tp_destroy_problem", "tp_last_error", "tp_launch_count", "tp_set_fixed",
             "tp_set_loads", "tp_set_passive", "tp_set_density", "tp_solve", "tp_sensitivities", "tp_filter",
             "tp_oc_update", "tp_simp_step", "tp_get", "tp_set", "tp_matvec", "tp_set_trace", "tp_get_trace", "tp_set_wait_budget",
-            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_p1_shape_matrices", "tp_p1_filter_stencil", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
+            "tp_oc_update_noalloc", "tp_spd_inverse_f32", "tp_p1_matvec", "tp_p1_shape_matrices", "tp_p1_filter_stencil",
+            "tp_p1_create", "tp_p1_destroy", "tp_p1_last_error", "tp_p1_launch_count", "tp_p1_set_fixed",
+            "tp_p1_set_loads", "tp_p1_set_passive", "tp_p1_set_density", "tp_p1_solve", "tp_p1_sensitivities",
+            "tp_p1_filter", "tp_p1_oc_update", "tp_p1_simp_step", "tp_p1_apply", "tp_p1_get", "tp_p1_set", "tp_set_filter_mode", "tp_set_profile", "tp_get_profile", "tp_batch_create", "tp_batch_destroy", "tp_batch_last_error",
             "tp_batch_set_fixed", "tp_batch_set_loads", "tp_batch_set_density", "tp_batch_set_tiles",
             "tp_batch_autotune", "tp_batch_step", "tp_batch_get", "tp_batch_launch_count",
             "tpnn_create", "tpnn_destroy", "tpnn_last_error", "tpnn_param_count", "tpnn_info",
@@ -500,6 +526,151 @@ class Problem:
         ptr_y, dev2 = _ptr(out)
         assert dev == dev2
         self._check(lib.tp_matvec(self.h, ptr_u, ptr_y, precision, ncopies, dev))
+        return out
+
+
+class P1Problem:
+    """Owns a tp_p1_problem handle: the SIMP loop on the paper's own P1 cells
+    (triangles / Kuhn tetrahedra).  Method names follow the C-ABI."""
+
+    def __init__(self, params: tp_p1_params, stream=None):
+        h = C.c_void_p()
+        st = lib.tp_p1_create(C.byref(params), C.c_void_p(_stream_handle(stream)), C.byref(h))
+        if st != TP_OK:
+            raise TopoError(st, "tp_p1_create rejected the parameters")
+        self.h = h
+        self.params = params
+        self.dim = params.dim
+        nz = (params.nelz + 1) if params.dim == 3 else 1
+        self.n_nodes = (params.nelx + 1) * (params.nely + 1) * nz
+        self.n_dof = self.dim * self.n_nodes
+        self.n_el = (2 * params.nelx * params.nely if params.dim == 2
+                     else 6 * params.nelx * params.nely * params.nelz)
+        self.n_cases = params.n_cases
+
+    @classmethod
+    def from_workload(cls, w, stream=None):
+        """Create and configure from a `workloads.SimplexProblem`."""
+        prm = tp_p1_params(w.dim, w.nelx, w.nely, w.nelz if w.dim == 3 else 0, P1_DIAGONALS[w.diagonal],
+                           w.lam, w.mu, w.Emin, w.penal, w.volfrac, w.rmin, w.move, w.dmin, w.n_cases)
+        p = cls(prm, stream)
+        p.set_fixed(w.fixed)
+        p.set_loads(w.loads)
+        if w.passive is not None:
+            p.set_passive(w.passive)
+        p.set_density(w.initial_density())
+        return p
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.tp_p1_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != TP_OK:
+            raise TopoError(st, lib.tp_p1_last_error(self.h).decode())
+
+    def launch_count(self):
+        return int(lib.tp_p1_launch_count(self.h))
+
+    def set_fixed(self, fixed):
+        a = np.ascontiguousarray(fixed, dtype=np.uint8)
+        if a.size != self.n_dof:
+            raise ValueError(f"fixed: {a.size} entries, expected {self.n_dof}")
+        self._check(lib.tp_p1_set_fixed(self.h, a.ctypes.data_as(C.c_void_p)))
+
+    def set_loads(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float64)
+        if a.size != self.n_cases * self.n_dof:
+            raise ValueError(f"loads: {a.size} entries, expected {self.n_cases * self.n_dof}")
+        self._check(lib.tp_p1_set_loads(self.h, a.ctypes.data_as(C.c_void_p)))
+
+    def set_passive(self, passive):
+        a = np.ascontiguousarray(passive, dtype=np.int8)
+        if a.size != self.n_el:
+            raise ValueError(f"passive: {a.size} entries, expected {self.n_el}")
+        self._check(lib.tp_p1_set_passive(self.h, a.ctypes.data_as(C.c_void_p)))
+
+    def _sized(self, a, n, name):
+        """a as a contiguous float64 array (NumPy) or the float64 tensor itself,
+        after checking its element count."""
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            size = a.size
+        else:
+            import torch
+            if not isinstance(a, torch.Tensor) or a.dtype != torch.float64:
+                raise ValueError(f"{name}: a float64 NumPy array or torch tensor is required")
+            size = a.numel()
+        if size != n:
+            raise ValueError(f"{name}: {size} entries, expected {n}")
+        return a
+
+    def set_density(self, rho):
+        rho = self._sized(rho, self.n_el, "rho")
+        ptr, dev = _ptr(rho)
+        self._check(lib.tp_p1_set_density(self.h, ptr, dev))
+
+    def solve(self, opts: tp_solve_opts, check=True):
+        info = tp_solve_info()
+        st = lib.tp_p1_solve(self.h, C.byref(opts), C.byref(info))
+        if check:
+            self._check(st)
+        return info
+
+    def sensitivities(self):
+        c = C.c_double()
+        self._check(lib.tp_p1_sensitivities(self.h, C.byref(c)))
+        return c.value
+
+    def filter(self):
+        self._check(lib.tp_p1_filter(self.h))
+
+    def oc_update(self):
+        lam, vol, ch = C.c_double(), C.c_double(), C.c_double()
+        self._check(lib.tp_p1_oc_update(self.h, C.byref(lam), C.byref(vol), C.byref(ch)))
+        return lam.value, vol.value, ch.value
+
+    def simp_step(self, opts: tp_solve_opts, check=True):
+        info = tp_step_info()
+        st = lib.tp_p1_simp_step(self.h, C.byref(opts), C.byref(info))
+        if check:
+            self._check(st)
+        return info
+
+    def _size(self, what):
+        return self.n_cases * self.n_dof if what == TP_U else self.n_el
+
+    def get(self, what, out=None):
+        if out is None:
+            out = np.empty(self._size(what), dtype=np.float64)
+        out = self._sized(out, self._size(what), "out") if isinstance(out, np.ndarray) else out
+        ptr, dev = _ptr(out)
+        self._check(lib.tp_p1_get(self.h, what, ptr, dev))
+        return out
+
+    def set(self, what, src):
+        src = self._sized(src, self._size(what), "src")
+        ptr, dev = _ptr(src)
+        self._check(lib.tp_p1_set(self.h, what, ptr, dev))
+
+    def apply(self, u, out=None):
+        """y = K(rho) u for all cases (u [n_cases * n_dof], float64)."""
+        u = self._sized(u, self.n_cases * self.n_dof, "u")
+        if out is None:
+            out = np.empty_like(u) if isinstance(u, np.ndarray) else u.new_empty(u.shape)
+        out = self._sized(out, self.n_cases * self.n_dof, "out")
+        pu, dev = _ptr(u)
+        py, dev2 = _ptr(out)
+        if dev != dev2:
+            raise ValueError("u and out must both be host or both be device memory")
+        self._check(lib.tp_p1_apply(self.h, pu, py, dev))
         return out
 
 

@@ -178,3 +178,19 @@ def test_stream_argument_forms(lib):
     assert lib._stream_handle(FakeStream()) == 12345
     assert lib._stream_handle(678) == 678
     assert isinstance(lib._stream_handle(None), int)
+
+
+def test_p1_create_rejects_bad_params_without_the_gpu(lib):
+    """tp_p1_create validates its parameters before any CUDA call."""
+    import ctypes as C
+    h = C.c_void_p()
+    good = dict(dim=2, nelx=6, nely=3, nelz=0, diagonal=2, lam=0.6, mu=0.4, Emin=1e-9, penal=3.0, volfrac=0.5,
+                rmin=1.5, move=0.2, dmin=1e-3, n_cases=1)
+    for k, v in [("dim", 4), ("nelx", 0), ("nelz", 2), ("diagonal", 3), ("mu", 0.0), ("Emin", 0.0), ("penal", 0.5),
+                 ("volfrac", 0.0), ("rmin", 5.0), ("move", 0.0), ("dmin", 1.0), ("n_cases", 9)]:
+        prm = dict(good, **{k: v})
+        args = lib.tp_p1_params(*[prm[f] for f, _ in lib.tp_p1_params._fields_])
+        assert lib.lib.tp_p1_create(C.byref(args), None, C.byref(h)) == lib.TP_ERR_ARG, k
+    three = dict(good, dim=3, nelz=0, diagonal=0)
+    args = lib.tp_p1_params(*[three[f] for f, _ in lib.tp_p1_params._fields_])
+    assert lib.lib.tp_p1_create(C.byref(args), None, C.byref(h)) == lib.TP_ERR_ARG
