@@ -115,10 +115,12 @@ def matvec_rows(prob, rho, u, dofs, absolute=False):
     return out
 
 
-def solve(prob, rho, method="lu", rtol=1e-13, maxiter=200000, K=None, x0=None):
+def solve(prob, rho, method="lu", rtol=1e-13, maxiter=200000, K=None, x0=None, callback=None):
     """Displacements u[n_cases, n_dof] of K(rho) u_k = f_k with u = 0 on fixed DOFs.
     method 'lu': SuperLU factorisation of K_ff, shared by all load cases.
-    method 'cg': SciPy's Jacobi-preconditioned CG on K_ff to relative residual rtol."""
+    method 'cg': SciPy's Jacobi-preconditioned CG on K_ff to relative residual rtol;
+    `callback` (optional) is handed to SciPy's CG, which calls it once per
+    iteration (e.g. to count iterations)."""
     K = assemble(prob, rho) if K is None else K
     free = np.flatnonzero(prob.fixed == 0)
     Kff = K[free][:, free].tocsc()
@@ -133,7 +135,7 @@ def solve(prob, rho, method="lu", rtol=1e-13, maxiter=200000, K=None, x0=None):
     for c in range(prob.n_cases):
         b = prob.loads[c, free]
         xs = None if x0 is None else x0[c, free]
-        x, info = spla.cg(Kff, b, x0=xs, rtol=rtol, atol=0.0, maxiter=maxiter, M=M)
+        x, info = spla.cg(Kff, b, x0=xs, rtol=rtol, atol=0.0, maxiter=maxiter, M=M, callback=callback)
         if info != 0:
             raise RuntimeError(f"oracle CG did not converge (info={info})")
         U[c, free] = x

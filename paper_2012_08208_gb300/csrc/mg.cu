@@ -44,19 +44,19 @@ __device__ __forceinline__ float kentry(const float* K, const float* E, long lon
   return K ? K[e * ND * ND + a * ND + b] : E[e] * c_K0[a * ND + b];
 }
 
-// Assembled form of a level: per node, the DIM x DIM coupling block to each of
-// its 3^DIM neighbours, S[((nbr * DIM + r) * DIM + s) * n_nodes + node]
-// (structure of arrays: one coalesced load per entry), with the rows and
-// columns of fixed DOFs zeroed.  nbr = (dx+1) + 3 (dy+1) [+ 9 (dz+1)].
+// Assembled form of a level: per node, the DIM x DIM coupling blocks to itself
+// and to its forward neighbours (symmetric storage, mgops::sblock; structure of
+// arrays: one coalesced load per entry), with the rows and columns of fixed
+// DOFs zeroed.
 template <int DIM>
 __global__ void stencil_kernel(Grid g, const float* __restrict__ K, const float* __restrict__ E,
                                const uint8_t* __restrict__ mask, float* __restrict__ S) {
-  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NB = DIM == 2 ? 9 : 27;
+  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NB = DIM == 2 ? 9 : 27, C0 = mgops::Sym<DIM>::kSelf;
   const int nn = (int)g.nn, nxy = g.nx * g.ny;
   for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
     const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
     const uint8_t mk = mask[nd];
-    for (int nbr = 0; nbr < NB; nbr++) {  // one DIM x DIM block at a time, summed in registers
+    for (int nbr = C0; nbr < NB; nbr++) {  // one DIM x DIM block at a time, summed in registers
       const int dx = nbr % 3 - 1, dy = (nbr / 3) % 3 - 1, dz = DIM == 3 ? nbr / 9 - 1 : 0;
       float acc[DIM * DIM];
 #pragma unroll
@@ -86,7 +86,7 @@ __global__ void stencil_kernel(Grid g, const float* __restrict__ K, const float*
             if (((mk >> r) & 1) || ((m2 >> s2) & 1)) acc[r * DIM + s2] = 0.f;
       }
 #pragma unroll
-      for (int q = 0; q < DIM * DIM; q++) S[((long long)nbr * DIM * DIM + q) * nn + nd] = acc[q];
+      for (int q = 0; q < DIM * DIM; q++) S[((long long)(nbr - C0) * DIM * DIM + q) * nn + nd] = acc[q];
     }
   }
 }
@@ -108,18 +108,30 @@ __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const 
 template <int DIM>
 __global__ void diag_stencil_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
                                     float* __restrict__ invd) {
-  constexpr int NB = DIM == 2 ? 9 : 27;
-  const int nn = (int)g.nn;
+  const int nn = (int)g.nn, nxy = g.nx * g.ny;
   for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = DIM == 3 ? nd / nxy : 0, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
     const uint8_t mk = mask[nd];
+    float d[DIM];
 #pragma unroll
-    for (int r = 0; r < DIM; r++) {
-      float d = 0.f;
-      for (int q = 0; q < NB; q++)
+    for (int r = 0; r < DIM; r++) d[r] = 0.f;
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
+      if (k + dz < 0 || k + dz >= g.nz) continue;
+      for (int dy = -1; dy <= 1; dy++) {
+        if (j + dy < 0 || j + dy >= g.ny) continue;
+        for (int dx = -1; dx <= 1; dx++) {
+          if (i + dx < 0 || i + dx >= g.nx) continue;
+          const int nbr = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+          const int n2 = nd + dx + g.nx * dy + nxy * dz;
 #pragma unroll
-        for (int s2 = 0; s2 < DIM; s2++) d += fabsf(S[((long long)(q * DIM + r) * DIM + s2) * nn + nd]);
-      invd[(long long)nd * DIM + r] = ((mk >> r) & 1) || !(d > 0.f) ? 1.f : 1.f / d;
+          for (int r = 0; r < DIM; r++)
+#pragma unroll
+            for (int s2 = 0; s2 < DIM; s2++) d[r] += fabsf(mgops::sblock<DIM>(S, nn, nd, nbr, n2, r, s2));
+        }
+      }
     }
+#pragma unroll
+    for (int r = 0; r < DIM; r++) invd[(long long)nd * DIM + r] = ((mk >> r) & 1) || !(d[r] > 0.f) ? 1.f : 1.f / d[r];
   }
 }
 
@@ -227,6 +239,81 @@ __global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict
   Kc[ec * ND * ND + t] = acc;
 }
 
+// Coarse elements whose footprint holds a fixed fine DOF: touched[ec] = 1
+// when any of the (f + 1)^dim fine nodes inside coarse element ec has a fixed
+// bit (its children's matrices are masked).
+template <int DIM>
+__global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, uint8_t* __restrict__ touched) {
+  const long long ne = gc.ne;
+  for (long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x; ec < ne;
+       ec += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(ec % gc.ex), J = (int)((ec / gc.ex) % gc.ey), Kz = (int)(ec / ((long long)gc.ex * gc.ey));
+    uint8_t any = 0;
+    for (int z = 0; z <= (DIM == 3 ? f : 0); z++)
+      for (int y = 0; y <= f; y++)
+        for (int x = 0; x <= f; x++) any |= mf[node_index(gf, f * I + x, f * J + y, DIM == 3 ? f * Kz + z : 0)];
+    touched[ec] = any ? 1 : 0;
+  }
+}
+
+// Galerkin operator of level 1, whose children are the level-0 elements
+// E_e K0.  With A_ch = P_ch^T K0 P_ch (the unmasked child matrices, formed once
+// per hierarchy), a coarse element no fixed fine DOF touches has
+//   K_E = sum_ch E_ch A_ch            (f^dim FMA per entry);
+// a touched element sums the masked triple product of galerkin_kernel entry by
+// entry.  One thread per entry (flat over elements x ND^2, coalesced stores);
+// rows and columns of fixed coarse DOFs are zeroed as in galerkin_kernel.
+template <int DIM>
+__global__ void galerkin1_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef, const float* __restrict__ A,
+                                 const float* __restrict__ K0g, const uint8_t* __restrict__ mf,
+                                 const uint8_t* __restrict__ mc, const uint8_t* __restrict__ touched,
+                                 float* __restrict__ Kc) {
+  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND;
+  const long long total = gc.ne * ND * ND;
+  const int nch = DIM == 2 ? f * f : f * f * f;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long ec = idx / (ND * ND);
+    const int t = (int)(idx - ec * ND * ND), a = t / ND, b = t % ND;
+    const int I = (int)(ec % gc.ex), J = (int)((ec / gc.ex) % gc.ey), Kz = (int)(ec / ((long long)gc.ex * gc.ey));
+    const int Ca = a / DIM, ra = a % DIM, Cb = b / DIM, rb = b % DIM;
+    float acc = 0.f;
+    if (!touched[ec]) {
+      for (int ch = 0; ch < nch; ch++) {
+        const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+        const long long e = (f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0));
+        acc = fmaf(Ef[e], A[(long long)ch * ND * ND + t], acc);
+      }
+    } else {
+      for (int ch = 0; ch < nch; ch++) {
+        const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+        const int fi = f * I + cx, fj = f * J + cy, fk = DIM == 3 ? f * Kz + cz : 0;
+        const long long e = fi + (long long)gf.ex * (fj + (long long)gf.ey * fk);
+        float sub = 0.f;
+        for (int n = 0; n < NC; n++) {
+          if ((mf[node_index(gf, fi + cofs(n, 0), fj + cofs(n, 1), fk + (DIM == 3 ? cofs(n, 2) : 0))] >> ra) & 1)
+            continue;
+          float pn = w1(cofs(Ca, 0), cx + cofs(n, 0), f) * w1(cofs(Ca, 1), cy + cofs(n, 1), f);
+          if (DIM == 3) pn *= w1(cofs(Ca, 2), cz + cofs(n, 2), f);
+          if (pn == 0.f) continue;
+          for (int m = 0; m < NC; m++) {
+            if ((mf[node_index(gf, fi + cofs(m, 0), fj + cofs(m, 1), fk + (DIM == 3 ? cofs(m, 2) : 0))] >> rb) & 1)
+              continue;
+            float pm = w1(cofs(Cb, 0), cx + cofs(m, 0), f) * w1(cofs(Cb, 1), cy + cofs(m, 1), f);
+            if (DIM == 3) pm *= w1(cofs(Cb, 2), cz + cofs(m, 2), f);
+            sub = fmaf(pn * pm, K0g[(n * DIM + ra) * ND + m * DIM + rb], sub);
+          }
+        }
+        acc = fmaf(Ef[e], sub, acc);
+      }
+    }
+    const uint8_t ma = mc[node_index(gc, I + cofs(Ca, 0), J + cofs(Ca, 1), Kz + (DIM == 3 ? cofs(Ca, 2) : 0))];
+    const uint8_t mb = mc[node_index(gc, I + cofs(Cb, 0), J + cofs(Cb, 1), Kz + (DIM == 3 ? cofs(Cb, 2) : 0))];
+    if (((ma >> ra) & 1) || ((mb >> rb) & 1)) acc = 0.f;
+    Kc[idx] = acc;
+  }
+}
+
 // Restriction (mgops::restrict2_node, restrict_warp) with the coarse level's
 // first smoothing step when x0 is given; blockIdx.y = case.
 template <int DIM>
@@ -303,7 +390,8 @@ Grid coarsen(const Grid& g, int f) {
 
 double MgHierarchy::vcycle_bytes() const {
   const int dim = lv[0].g.dim, L = (int)lv.size();
-  const double nbr = dim == 2 ? 9.0 * 4.0 : 27.0 * 9.0;  // coupling entries per node of an assembled level
+  // stored coupling entries per node of an assembled level (symmetric storage)
+  const double nbr = dim == 2 ? mgops::Sym<2>::kSlots * 4.0 : mgops::Sym<3>::kSlots * 9.0;
   double total = 0.0;
   for (int li = 0; li + 1 < L; li++) {
     const MgLevel& l = lv[li];
@@ -375,6 +463,9 @@ void MgHierarchy::release() {
       if (q) cudaFree(q);
   }
   lv.clear();
+  for (void* q : {(void*)A1, (void*)touched1}) if (q) cudaFree(q);
+  A1 = nullptr;
+  touched1 = nullptr;
   for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32, (void*)d32, (void*)p32b,
                   (void*)dscratch, (void*)dflag})
     if (q) cudaFree(q);
@@ -439,13 +530,19 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
       l.mask_own = true;
     }
     if (e == cudaSuccess && i > 0) {
-      const long long nb = g0.dim == 2 ? 9 * 4 : 27 * 9;
+      const long long nb = g0.dim == 2 ? mgops::Sym<2>::kSlots * 4 : mgops::Sym<3>::kSlots * 9;
       e = cudaMalloc((void**)&l.S, l.g.nn * nb * sizeof(float));
     }
     if (e == cudaSuccess) e = cudaMalloc((void**)&l.invd, ndof * sizeof(float));
     for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMalloc((void**)&l.x[k], nc * ndof * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&l.b, nc * ndof * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&l.t, nc * ndof * sizeof(float));
+  }
+  {
+    const int f1 = lv[1].f, nd = g0.dim == 2 ? 8 : 24;
+    const long long nch = g0.dim == 2 ? f1 * f1 : f1 * f1 * f1;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&A1, nch * nd * nd * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&touched1, std::max<long long>(lv[1].g.ne, 1));
   }
   cn = (int)(lv.back().g.nn * g0.dim);
   if (e == cudaSuccess) e = cudaMalloc((void**)&cinv, (size_t)cn * cn * sizeof(float));
@@ -472,12 +569,52 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
   if (e != cudaSuccess) return e;
   E0 = E32;
   int nl = 0;
+  {  // level-1 child matrices A_ch = P_ch^T K0 P_ch (FP64 sums, stored in FP32)
+    const int f = lv[1].f, NC = dim == 2 ? 4 : 8;
+    const int nch = dim == 2 ? f * f : f * f * f;
+    std::vector<float> Ah((size_t)nch * nd * nd);
+    for (int ch = 0; ch < nch; ch++) {
+      const int cxyz[3] = {ch % f, (ch / f) % f, dim == 3 ? ch / (f * f) : 0};
+      double phi[8][8];
+      for (int n = 0; n < NC; n++)
+        for (int C = 0; C < NC; C++) {
+          double w = 1.0;
+          for (int ax = 0; ax < dim; ax++) {
+            const double t = (double)(cxyz[ax] + cofs(n, ax)) / f;
+            w *= cofs(C, ax) ? t : 1.0 - t;
+          }
+          phi[n][C] = w;
+        }
+      for (int a = 0; a < nd; a++)
+        for (int b = 0; b < nd; b++) {
+          const int C1 = a / dim, r = a % dim, C2 = b / dim, s2 = b % dim;
+          double v = 0.0;
+          for (int n = 0; n < NC; n++)
+            for (int m = 0; m < NC; m++) v += phi[n][C1] * phi[m][C2] * K0[(n * dim + r) * nd + m * dim + s2];
+          Ah[((size_t)ch * nd + a) * nd + b] = (float)v;
+        }
+    }
+    e = cudaMemcpyAsync(A1, Ah.data(), Ah.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+  }
   for (size_t i = 0; i < lv.size(); i++) {
     MgLevel& l = lv[i];
     if (i > 0) {
       const MgLevel& fl = lv[i - 1];
       coarse_mask_kernel<<<blocks(l.g.nn), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, l.mask);
-      if (dim == 2)
+      if (i == 1) {
+        const long long entries = l.g.ne * nd * nd;
+        if (dim == 2) {
+          touched_kernel<2><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
+          galerkin1_kernel<2><<<blocks(entries), 256, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask,
+                                                               touched1, l.K);
+        } else {
+          touched_kernel<3><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
+          galerkin1_kernel<3><<<blocks(entries), 256, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask,
+                                                               touched1, l.K);
+        }
+        nl += 1;  // the touched-element flags (the Galerkin launch is counted below)
+      } else if (dim == 2)
         galerkin_kernel<2><<<(unsigned)l.g.ne, 64, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask,
                                                             l.mask, l.K);
       else

@@ -70,6 +70,8 @@ struct MgHierarchy {
   DenseInverter dinv;
   bool coarse_ok = true;      // the last build's dense inversion met only positive pivots
   float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
+  float* A1 = nullptr;      // level-1 child matrices P_ch^T K0 P_ch [f^dim][ND][ND] (unmasked)
+  uint8_t* touched1 = nullptr;  // level-1 elements whose footprint holds a fixed fine DOF
   const float* E0 = nullptr;
   // Finest-level sweep for all cases on the library's strain-form FP32
   // operator: mode 1 y = a u + c w + om D^-1 (b - A u) (w may be null when

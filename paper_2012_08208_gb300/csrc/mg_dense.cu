@@ -25,6 +25,7 @@
 
 #include "../../include/topo.h"
 #include "mg.h"
+#include "mg_ops.cuh"
 
 namespace tp {
 namespace {
@@ -52,7 +53,7 @@ __global__ void dense_assemble_kernel(Grid g, const float* __restrict__ S, const
           if (i + dx < 0 || i + dx >= g.nx) continue;
           const int nbr = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
           const int n2 = nd + dx + g.nx * dy + nxy * dz;
-          for (int s2 = 0; s2 < DIM; s2++) Ar[n2 * DIM + s2] = S[((long long)(nbr * DIM + r) * DIM + s2) * nn + nd];
+          for (int s2 = 0; s2 < DIM; s2++) Ar[n2 * DIM + s2] = mgops::sblock<DIM>(S, nn, nd, nbr, n2, r, s2);
         }
       }
     }

@@ -28,10 +28,30 @@ __device__ __forceinline__ float ldv(const float* p) {
   else return *p;
 }
 
+// Assembled levels store their coupling blocks once per symmetric pair: node
+// nd's DIM x DIM block to neighbour nbr = (dx+1) + 3 (dy+1) [+ 9 (dz+1)] is
+// kept for the forward half nbr >= kSelf (the node itself and the 4 / 13
+// neighbours after it) in slot h = nbr - kSelf,
+//   S[((h * DIM + r) * DIM + s) * n_nodes + nd],
+// and a backward block (nbr < kSelf) is the transpose of the forward block that
+// the neighbour n2 holds for the opposite direction, slot kSelf - nbr.  The
+// operator is symmetric by construction, and a sweep reads half the bytes.
+template <int DIM>
+struct Sym {
+  static constexpr int kSelf = DIM == 2 ? 4 : 13;      // slot 0: the node itself
+  static constexpr int kSlots = kSelf + 1;             // stored blocks per node
+};
+template <int DIM>
+__device__ __forceinline__ float sblock(const float* __restrict__ S, int nn, int nd, int nbr, int n2, int r, int s) {
+  constexpr int C = Sym<DIM>::kSelf;
+  return nbr >= C ? S[((long long)((nbr - C) * DIM + r) * DIM + s) * nn + nd]
+                  : S[((long long)((C - nbr) * DIM + s) * DIM + r) * nn + n2];
+}
+
 // 1D multilinear weight of coarse corner offset `o` (0 or 1) at fine position t in [0, f].
 __device__ __forceinline__ float w1(int o, int t, int f) { return o ? (float)t / f : 1.f - (float)t / f; }
 
-// Node nd of a level with assembled blocks S[((nbr * DIM + r) * DIM + s) * n_nodes + node]:
+// Node nd of a level with assembled blocks S (symmetric storage, sblock):
 //   mode 1: y = ca u + cc w + om D^-1 (b - A u)   (Chebyshev step; w may be null)
 //   mode 2: y = b - A u                            (residual)
 // A u with fixed entries of u read as 0 (their rows and columns of S are
@@ -62,7 +82,7 @@ __device__ __forceinline__ void stencil_node(const Grid& g, const float* __restr
         for (int s2 = 0; s2 < DIM; s2++) {
           const float v = ldv<CG>(u + off + (long long)n2 * DIM + s2);
 #pragma unroll
-          for (int r = 0; r < DIM; r++) acc[r] = fmaf(S[((long long)(nbr * DIM + r) * DIM + s2) * nn + nd], v, acc[r]);
+          for (int r = 0; r < DIM; r++) acc[r] = fmaf(sblock<DIM>(S, nn, nd, nbr, n2, r, s2), v, acc[r]);
         }
       }
     }
