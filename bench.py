@@ -199,6 +199,7 @@ def run_ours(args):
             extras["batch"] = batch_extra(topo, torch, dev, stream, ws=ws, rank=rank)
         if not args.no_extras and rank == 0:
             extras["simp_configs"] = simp_configs_extra(topo, torch, dev, stream, args.solver)
+            extras["p1"] = p1_extra(topo, torch, dev, stream)
             extras["matvec"] = matvec_roofline(topo, torch, dev, stream, W.cantilever3d_large(),
                                                "cantilever3d_240x80x80 H8 FP32 K(rho)u")
             extras["matvec_2d"] = matvec_roofline(topo, torch, dev, stream, W.cantilever2d(),
@@ -435,6 +436,58 @@ def helmholtz_extra(topo, torch, dev, stream, reps=5, steps=5, warmup=3):
     return out
 
 
+def p1_extra(topo, torch, dev, stream, steps=10, warmup=3):
+    """The paper's own elements (P1 triangles with the "right/left" cut, Kuhn
+    tetrahedra; FP64 Jacobi-PCG to 1e-8): SIMP iterations/s of the 2D cantilever
+    with its traction strip at 60 x 20 and 300 x 100 squares, and of the
+    tetrahedral cantilever at 48 x 16 x 8 cubes; and the FP64 P1 operator at
+    300 x 100 (algorithmic bytes: u read and y written, 16 B per DOF, the cell
+    moduli 8 B per cell, the fixed flags 1 B per DOF)."""
+    import workloads as W
+    out = {}
+    opts = topo.solve_opts(tol=1e-8, max_it=200000, precision=topo.TP_PREC_F64, warm_start=topo.TP_WARM_PREVIOUS,
+                           precond=topo.TP_PRECOND_JACOBI)
+    for key, w in (("p1_cantilever2d_60x20_rightleft", W.p1_cantilever2d(60, 20)),
+                   ("p1_cantilever2d_300x100_rightleft", W.p1_cantilever2d(300, 100, rmin=2.5)),
+                   ("p1_cantilever3d_48x16x8_kuhn", W.p1_cantilever3d(48, 16, 8))):
+        p = topo.P1Problem.from_workload(w, stream=stream)
+        for _ in range(warmup):
+            p.simp_step(opts)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        its = [p.simp_step(opts).solve.iters for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        out[key] = {"cells": w.n_el, "n_dof": w.n_dof, "ms_per_step": round(ms, 3), "simp_iter_s": round(1e3 / ms, 3),
+                    "cg_iters_per_step": float(np.mean(its))}
+        p.close()
+    w = W.p1_cantilever2d(300, 100)
+    p = topo.P1Problem.from_workload(w, stream=stream)
+    u = torch.randn(w.n_dof, dtype=torch.float64, device=dev)
+    y = torch.empty_like(u)
+    for _ in range(3):
+        p.apply(u, out=y)
+    reps = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        p.apply(u, out=y)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    byts = 16 * w.n_dof + 8 * w.n_el + w.n_dof
+    hbm, kind = _peaks()
+    out["p1_operator_300x100"] = {"us_per_apply": round(us, 2), "bytes": byts,
+                                  "achieved_gbs": round(byts / (us * 1e-6) / 1e9, 1), "peak": hbm, "peak_kind": kind,
+                                  "frac": round(byts / (us * 1e-6) / 1e9 / hbm, 4),
+                                  "note": "FP64 node-gather parity operator; L2-resident (1.5 MB)"}
+    p.close()
+    return out
+
+
 def batch_extra(topo, torch, dev, stream, steps=5, warmup=3, ws=1, rank=0):
     """64 uneven 2D cantilevers (batch2d, seed 0) in one persistent graph-captured
     launch per step with the autotuned tile shape: instance SIMP iterations/s.
@@ -476,33 +529,82 @@ def batch_extra(topo, torch, dev, stream, steps=5, warmup=3, ws=1, rank=0):
 # CPU oracle (baseline and reference arm)
 
 
-def _oracle_step_fn(w):
-    from oracle import filt, simp
-    Wm = filt.sparse_weights(w)
-    state = {"rho": w.initial_density()}
+CG_COUNT_FILE = os.path.join(ROOT, "tests", "golden", "cg_iterations_cantilever3d_240x80x80.json")
 
-    def step():
-        out = simp.iteration(w, state["rho"], W=Wm)
-        state["rho"] = out["rho_new"]
-        return out
 
-    return step
+def _oracle_cg_iterations():
+    """The oracle's own Jacobi-CG iteration count to 1e-6 on the 240 x 80 x 80
+    cantilever at the uniform start (written by
+    tests/golden/make_trajectories.py cg_count, which runs oracle/ only)."""
+    with open(CG_COUNT_FILE) as f:
+        return int(json.load(f)["iterations"])
+
+
+def oracle_step_sample(nz_slab=4, cg_iters=40):
+    """One bounded sample of the oracle's SIMP iteration on the 240 x 80 x 80
+    cantilever.  Its phases run on the 240 x 80 x nz_slab slab of the same
+    cantilever (same supports, load and element arithmetic), and their times
+    scale by the element ratio: assembly, sensitivities, the sensitivity filter
+    and the OC bisection once each; SciPy's Jacobi-CG for `cg_iters` iterations,
+    scaled per iteration to the oracle's own iteration count to 1e-6 (the
+    solve of the first SIMP iteration).  Returns (seconds per full-size
+    iteration, description)."""
+    import workloads as W
+    from oracle import fem, filt, oc, sens
+    full = W.cantilever3d_large()
+    slab = W.cantilever3d(full.nelx, full.nely, nz_slab, volfrac=full.volfrac, rmin=full.rmin, tol=full.tol)
+    scale = full.n_el / slab.n_el
+    rho = slab.initial_density()
+    Wm = filt.sparse_weights(slab)  # built once per oracle run, outside its loop
+    t = {}
+    t0 = time.perf_counter()
+    K = fem.assemble(slab, rho)
+    t["assembly"] = time.perf_counter() - t0
+    def cg_run(iters):
+        n = [0]
+        t0 = time.perf_counter()
+        try:
+            fem.solve(slab, rho, method="cg", rtol=1e-30, K=K, maxiter=iters,
+                      callback=lambda xk: n.__setitem__(0, n[0] + 1))
+        except RuntimeError:
+            pass  # stopped at maxiter by design
+        return time.perf_counter() - t0, n[0]
+
+    # two lengths separate the solve's set-up (free-DOF slicing, diagonal) from
+    # the cost of one iteration
+    ta, na = cg_run(cg_iters // 4)
+    tb, nb = cg_run(cg_iters)
+    t["cg_per_iteration"] = max(tb - ta, 0.0) / max(nb - na, 1)
+    t["cg_setup"] = max(ta - na * t["cg_per_iteration"], 0.0)
+    U = np.random.default_rng(3).normal(size=(1, slab.n_dof))
+    U[:, slab.fixed.astype(bool)] = 0.0
+    t0 = time.perf_counter()
+    c, ce, dc = sens.sensitivities(slab, rho, U)
+    t["sensitivities"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dcf = filt.sensitivity_filter(Wm, rho, -np.abs(dc))
+    t["filter"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oc.bisect(rho, dcf, slab.volfrac, slab.move, slab.dmin)
+    t["oc"] = time.perf_counter() - t0
+    n_cg = _oracle_cg_iterations()
+    per_iter = scale * (t["assembly"] + t["cg_setup"] + t["sensitivities"] + t["filter"] + t["oc"]
+                        + n_cg * t["cg_per_iteration"])
+    desc = (f"oracle phases on the 240x80x{nz_slab} slab ({slab.n_el} elements, 1/{scale:.0f} of the workload), "
+            f"scaled by the element ratio: assembly {t['assembly']:.2f} s, sensitivities {t['sensitivities']:.2f} s, "
+            f"filter {t['filter']:.3f} s, OC {t['oc']:.2f} s, CG set-up {t['cg_setup']:.2f} s, "
+            f"SciPy Jacobi-CG {1e3 * t['cg_per_iteration']:.1f} ms "
+            f"per iteration x {n_cg} iterations (the oracle's count to 1e-6 at the uniform start); "
+            f"extrapolated, not a full-size run")
+    return per_iter, desc
 
 
 def cpu_baseline(w, seconds=20.0):
-    """The oracle as it stands (SciPy assembly + SuperLU + NumPy filter/OC),
-    timed on the host for a bounded number of SIMP iterations."""
-    step = _oracle_step_fn(w)
-    n, t = 0, 0.0
-    while t < seconds and n < 3:
-        t0 = time.perf_counter()
-        step()
-        t += time.perf_counter() - t0
-        n += 1
-    return {"value": round(n / t, 5), "unit": "SIMP iter/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} SIMP iteration(s) of the same workload from the uniform start "
-                      f"(SciPy SuperLU, single-threaded), {t:.1f} s",
-            "host_cpus": os.cpu_count()}
+    """The oracle as it stands (SciPy assembly + Jacobi-CG + NumPy filter/OC),
+    timed on the host on a bounded sample of the workload's SIMP iteration."""
+    per_iter, desc = oracle_step_sample()
+    return {"value": round(1.0 / per_iter, 6), "unit": "SIMP iter/s", "cores": 1, "kind": "oracle",
+            "sample": desc, "host_cpus": os.cpu_count()}
 
 
 def run_reference(args):
@@ -510,29 +612,29 @@ def run_reference(args):
     if rank != 0:
         return
     import workloads as W
-    w = W.cantilever2d()
-    step = _oracle_step_fn(w)
-    # warm-up: one step at most (the oracle has no caches worth warming)
+    w = W.cantilever3d_large()
     for _ in range(min(args.warmup, 1)):
-        step()
-    budget = 150.0
-    times = []
+        oracle_step_sample()
+    budget = 240.0
+    per, t_wall, desc = [], 0.0, ""
     for k in range(args.steps):
         t0 = time.perf_counter()
-        step()
-        times.append(time.perf_counter() - t0)
-        if sum(times) > budget:
+        s, desc = oracle_step_sample()
+        t_wall += time.perf_counter() - t0
+        per.append(s)
+        if t_wall > budget:
             break
-    tot = sum(times)
-    value = len(times) / tot
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "SIMP iter/s",
-            "n_gpus": ws, "steps": len(times), "warmup": min(args.warmup, 1),
-            "ms_per_step": round(1e3 * tot / len(times), 2), "higher_is_better": True, "scaling": "weak",
+    tot = float(sum(per))
+    value = len(per) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "SIMP iter/s",
+            "n_gpus": ws, "steps": len(per), "warmup": min(args.warmup, 1),
+            "ms_per_step": round(1e3 * tot / len(per), 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "600x200 Q4", "n_dof": w.n_dof, "n_cases": w.n_cases},
-            "cpu_baseline": {"value": round(value, 5), "unit": "SIMP iter/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} SIMP iterations (steps capped at {budget:.0f} s)"},
-            "e2e": {"value": round(value, 5), "unit": "SIMP iter/s", "h2d_bytes_per_step": 0,
+            "config": {"workload": WORKLOAD, "grid": "240x80x80 H8", "n_dof": w.n_dof, "n_cases": w.n_cases,
+                       "tol": w.tol},
+            "cpu_baseline": {"value": round(value, 6), "unit": "SIMP iter/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(per)} samples, each: {desc}"},
+            "e2e": {"value": round(value, 6), "unit": "SIMP iter/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -566,6 +668,8 @@ def run_only(args):
             p.close()
         elif args.only == "helmholtz":
             out = helmholtz_extra(topo, torch, dev, stream)
+        elif args.only == "p1":
+            out = p1_extra(topo, torch, dev, stream)
         elif args.only == "simp":
             wl = {"mbb2d": W.mbb2d, "cantilever2d": W.cantilever2d, "cantilever3d": W.cantilever3d,
                   "cantilever3d_large": W.cantilever3d_large}[args.workload]()
@@ -586,7 +690,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--only", choices=["matvec3d", "matvec2d", "batch", "learned", "cg2d", "cg3d", "helmholtz",
-                                       "simp"],
+                                       "simp", "p1"],
                     default=None,
                     help="run one extra measurement alone (for profiling)")
     ap.add_argument("--copies", type=int, default=8)

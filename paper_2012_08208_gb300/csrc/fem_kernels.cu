@@ -116,23 +116,36 @@ struct MvArgs {
   CMat<DIM, T> C;
 };
 
-template <int DIM, typename T>
-__global__ void __launch_bounds__(TileOp<DIM, T>::THREADS)
+template <int DIM, typename T, int MINB = 1>
+__global__ void __launch_bounds__(TileOp<DIM, T>::THREADS, MINB)
     matvec_kernel(const __grid_constant__ MvArgs<DIM, T> a) {
   if (halted(a.stop)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const T* u = a.u + blockIdx.y * a.stride;
   T* y = a.y + blockIdx.y * a.stride;
-  TileOp<DIM, T>::template apply<1>(
-      a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1,
-      [&](long long node, int comp, bool) -> T {
-        return ((a.mask[node] >> comp) & 1) ? T(0) : u[node * DIM + comp];
-      },
-      [&](long long node, int, const T(&yv)[DIM], const T(&)[DIM]) {
-        const uint8_t mk = a.mask[node];
+  auto load = [&](long long node, int comp, bool) -> T {
+    return ((a.mask[node] >> comp) & 1) ? T(0) : u[node * DIM + comp];
+  };
+  if constexpr (DIM == 3) {
+    // the fixed bits of the output node are loaded before the layer's arithmetic
+    TileOp<3, T>::apply1_pre(
+        a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, load,
+        [&](long long node) -> uint8_t { return node >= 0 ? a.mask[node] : (uint8_t)0; },
+        [&](long long node, const T(&yv)[3], const T(&)[3], uint8_t mk) {
 #pragma unroll
-        for (int r = 0; r < DIM; r++) y[node * DIM + r] = ((mk >> r) & 1) ? u[node * DIM + r] : yv[r];
-      });
+          for (int r = 0; r < 3; r++) y[node * 3 + r] = ((mk >> r) & 1) ? u[node * 3 + r] : yv[r];
+        });
+  } else {
+    TileOp<DIM, T>::template apply<1>(
+        a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1, [&](long long node, int comp, bool own) {
+          return load(node, comp, own);
+        },
+        [&](long long node, int, const T(&yv)[DIM], const T(&)[DIM]) {
+          const uint8_t mk = a.mask[node];
+#pragma unroll
+          for (int r = 0; r < DIM; r++) y[node * DIM + r] = ((mk >> r) & 1) ? u[node * DIM + r] : yv[r];
+        });
+  }
 }
 
 template <int DIM, typename T>
@@ -150,7 +163,8 @@ static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, c
   a.stop = stop;
   fill_c<DIM, T>(a.C, C);
   const size_t smem = Op::smem_bytes();
-  auto kern = matvec_kernel<DIM, T>;
+  // H8 FP32: 3 resident CTAs per SM (80 registers); measured fastest
+  auto kern = (DIM == 3 && sizeof(T) == 4) ? matvec_kernel<DIM, T, 3> : matvec_kernel<DIM, T, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<dim3(a.tm.ntiles, ncopies), Op::THREADS, smem, s>>>(a);
@@ -194,8 +208,8 @@ struct SweepArgs {
   CMat<DIM, float> C;
 };
 
-template <int DIM>
-__global__ void __launch_bounds__(TileOp<DIM, float>::THREADS)
+template <int DIM, int MINB = 1>
+__global__ void __launch_bounds__(TileOp<DIM, float>::THREADS, MINB)
     mg_sweep_kernel(const __grid_constant__ SweepArgs<DIM> a) {
   if (halted(a.stop)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -203,25 +217,66 @@ __global__ void __launch_bounds__(TileOp<DIM, float>::THREADS)
   const float* b = a.b + blockIdx.y * a.stride;
   const float* w = a.w ? a.w + blockIdx.y * a.stride : nullptr;
   float* y = a.y + blockIdx.y * a.stride;
-  TileOp<DIM, float>::template apply<1>(
-      a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1,
-      [&](long long node, int comp, bool) -> float {
-        return ((a.mask[node] >> comp) & 1) ? 0.f : u[node * DIM + comp];
-      },
-      [&](long long node, int, const float(&kv)[DIM], const float(&us)[DIM]) {
-        const uint8_t mk = a.mask[node];
+  auto load = [&](long long node, int comp, bool) -> float {
+    return ((a.mask[node] >> comp) & 1) ? 0.f : u[node * DIM + comp];
+  };
+  if constexpr (DIM == 3) {
+    // the output node's right-hand side, l1 scale, x_{k-2} term and fixed bits
+    // are loaded before the layer's arithmetic
+    struct Pre {
+      float b[3], d[3], w[3];
+      uint8_t mk;
+    };
+    TileOp<3, float>::apply1_pre(
+        a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, load,
+        [&](long long node) -> Pre {
+          Pre q;
+          q.mk = 0;
 #pragma unroll
-        for (int r = 0; r < DIM; r++) {
-          const long long i = node * DIM + r;
-          const float res = b[i] - kv[r];
-          float out = res;
-          if (a.mode == 1) {
-            out = fmaf(a.a, us[r], a.om * a.invd[i] * res);
-            if (w) out = fmaf(a.c, w[i], out);
+          for (int r = 0; r < 3; r++) q.b[r] = q.d[r] = q.w[r] = 0.f;
+          if (node >= 0) {
+            q.mk = a.mask[node];
+#pragma unroll
+            for (int r = 0; r < 3; r++) {
+              q.b[r] = b[node * 3 + r];
+              if (a.mode == 1) q.d[r] = a.invd[node * 3 + r];
+              if (a.mode == 1 && w) q.w[r] = w[node * 3 + r];
+            }
           }
-          y[i] = ((mk >> r) & 1) ? 0.f : out;
-        }
-      });
+          return q;
+        },
+        [&](long long node, const float(&kv)[3], const float(&us)[3], const Pre& q) {
+#pragma unroll
+          for (int r = 0; r < 3; r++) {
+            const float res = q.b[r] - kv[r];
+            float out = res;
+            if (a.mode == 1) {
+              out = fmaf(a.a, us[r], a.om * q.d[r] * res);
+              if (w) out = fmaf(a.c, q.w[r], out);
+            }
+            y[node * 3 + r] = ((q.mk >> r) & 1) ? 0.f : out;
+          }
+        });
+  } else {
+    TileOp<DIM, float>::template apply<1>(
+        a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1, [&](long long node, int comp, bool own) {
+          return load(node, comp, own);
+        },
+        [&](long long node, int, const float(&kv)[DIM], const float(&us)[DIM]) {
+          const uint8_t mk = a.mask[node];
+#pragma unroll
+          for (int r = 0; r < DIM; r++) {
+            const long long i = node * DIM + r;
+            const float res = b[i] - kv[r];
+            float out = res;
+            if (a.mode == 1) {
+              out = fmaf(a.a, us[r], a.om * a.invd[i] * res);
+              if (w) out = fmaf(a.c, w[i], out);
+            }
+            y[i] = ((mk >> r) & 1) ? 0.f : out;
+          }
+        });
+  }
 }
 
 template <int DIM>
@@ -247,7 +302,9 @@ static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, co
   a.om = om;
   fill_c<DIM, float>(a.C, C);
   const size_t smem = Op::smem_bytes();
-  auto kern = mg_sweep_kernel<DIM>;
+  // H8: 2 resident CTAs per SM (no spills with the pre-loaded emit data);
+  // measured faster than 3 with spills
+  auto kern = DIM == 3 ? mg_sweep_kernel<DIM, 2> : mg_sweep_kernel<DIM, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<dim3(a.tm.ntiles, ncopies), Op::THREADS, smem, s>>>(a);

@@ -261,34 +261,45 @@ __global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
 // per hierarchy), a coarse element no fixed fine DOF touches has
 //   K_E = sum_ch E_ch A_ch            (f^dim FMA per entry);
 // a touched element sums the masked triple product of galerkin_kernel entry by
-// entry.  One thread per entry (flat over elements x ND^2, coalesced stores);
-// rows and columns of fixed coarse DOFs are zeroed as in galerkin_kernel.
+// entry.  One CTA per coarse element (the children's moduli and fixed bits
+// staged in shared memory; the grid strides over the elements), its threads
+// striding over the ND^2 entries
+// (coalesced loads of A and stores of K_E); rows and columns of fixed coarse
+// DOFs are zeroed as in galerkin_kernel.
 template <int DIM>
-__global__ void galerkin1_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef, const float* __restrict__ A,
-                                 const float* __restrict__ K0g, const uint8_t* __restrict__ mf,
-                                 const uint8_t* __restrict__ mc, const uint8_t* __restrict__ touched,
-                                 float* __restrict__ Kc) {
-  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND;
-  const long long total = gc.ne * ND * ND;
+__global__ void __launch_bounds__(256) galerkin1_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
+                                                        const float* __restrict__ A, const float* __restrict__ K0g,
+                                                        const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
+                                                        const uint8_t* __restrict__ touched, float* __restrict__ Kc) {
+  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NE = ND * ND;
+  constexpr int kMaxCh = 343;  // f <= 7
+  __shared__ float sE[kMaxCh];
+  __shared__ uint8_t sMc[NC];
   const int nch = DIM == 2 ? f * f : f * f * f;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long ec = idx / (ND * ND);
-    const int t = (int)(idx - ec * ND * ND), a = t / ND, b = t % ND;
-    const int I = (int)(ec % gc.ex), J = (int)((ec / gc.ex) % gc.ey), Kz = (int)(ec / ((long long)gc.ex * gc.ey));
-    const int Ca = a / DIM, ra = a % DIM, Cb = b / DIM, rb = b % DIM;
+  for (unsigned ec = blockIdx.x; ec < (unsigned)gc.ne; ec += gridDim.x) {
+  __syncthreads();  // the previous element's staged values are no longer read
+  const int I = (int)(ec % (unsigned)gc.ex), J = (int)((ec / (unsigned)gc.ex) % (unsigned)gc.ey);
+  const int Kz = DIM == 3 ? (int)(ec / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
+  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+    const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+    sE[ch] = Ef[(f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0))];
+  }
+  if (threadIdx.x < NC)
+    sMc[threadIdx.x] = mc[node_index(gc, I + cofs(threadIdx.x, 0), J + cofs(threadIdx.x, 1),
+                                     Kz + (DIM == 3 ? cofs(threadIdx.x, 2) : 0))];
+  __syncthreads();
+  const bool tch = touched[ec] != 0;
+  float* out = Kc + (long long)ec * NE;
+  for (int t = threadIdx.x; t < NE; t += blockDim.x) {
+    const int a = t / ND, b = t - (t / ND) * ND;
+    const int Ca = a / DIM, ra = a - Ca * DIM, Cb = b / DIM, rb = b - Cb * DIM;
     float acc = 0.f;
-    if (!touched[ec]) {
-      for (int ch = 0; ch < nch; ch++) {
-        const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-        const long long e = (f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0));
-        acc = fmaf(Ef[e], A[(long long)ch * ND * ND + t], acc);
-      }
+    if (!tch) {
+      for (int ch = 0; ch < nch; ch++) acc = fmaf(sE[ch], __ldg(A + (long long)ch * NE + t), acc);
     } else {
       for (int ch = 0; ch < nch; ch++) {
         const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
         const int fi = f * I + cx, fj = f * J + cy, fk = DIM == 3 ? f * Kz + cz : 0;
-        const long long e = fi + (long long)gf.ex * (fj + (long long)gf.ey * fk);
         float sub = 0.f;
         for (int n = 0; n < NC; n++) {
           if ((mf[node_index(gf, fi + cofs(n, 0), fj + cofs(n, 1), fk + (DIM == 3 ? cofs(n, 2) : 0))] >> ra) & 1)
@@ -304,13 +315,12 @@ __global__ void galerkin1_kernel(Grid gf, Grid gc, int f, const float* __restric
             sub = fmaf(pn * pm, K0g[(n * DIM + ra) * ND + m * DIM + rb], sub);
           }
         }
-        acc = fmaf(Ef[e], sub, acc);
+        acc = fmaf(sE[ch], sub, acc);
       }
     }
-    const uint8_t ma = mc[node_index(gc, I + cofs(Ca, 0), J + cofs(Ca, 1), Kz + (DIM == 3 ? cofs(Ca, 2) : 0))];
-    const uint8_t mb = mc[node_index(gc, I + cofs(Cb, 0), J + cofs(Cb, 1), Kz + (DIM == 3 ? cofs(Cb, 2) : 0))];
-    if (((ma >> ra) & 1) || ((mb >> rb) & 1)) acc = 0.f;
-    Kc[idx] = acc;
+    if (((sMc[Ca] >> ra) & 1) || ((sMc[Cb] >> rb) & 1)) acc = 0.f;
+    out[t] = acc;
+  }
   }
 }
 
@@ -603,15 +613,14 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
       const MgLevel& fl = lv[i - 1];
       coarse_mask_kernel<<<blocks(l.g.nn), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, l.mask);
       if (i == 1) {
-        const long long entries = l.g.ne * nd * nd;
         if (dim == 2) {
           touched_kernel<2><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
-          galerkin1_kernel<2><<<blocks(entries), 256, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask,
-                                                               touched1, l.K);
+          galerkin1_kernel<2><<<blocks(l.g.ne * 4), 64, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
+                                                               l.K);
         } else {
           touched_kernel<3><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
-          galerkin1_kernel<3><<<blocks(entries), 256, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask,
-                                                               touched1, l.K);
+          galerkin1_kernel<3><<<blocks(l.g.ne * 4), 192, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
+                                                                l.K);
         }
         nl += 1;  // the touched-element flags (the Galerkin launch is counted below)
       } else if (dim == 2)
@@ -861,13 +870,36 @@ __global__ void dotscal_kernel(long long n, const TA* __restrict__ a1, const TB*
   const int c = blockIdx.y, nb = gridDim.x;
   const long long base = (long long)c * n;
   using A = acc_t<TA, TB>;
-  A t0 = A(0), t1 = A(0);
-  const int nn = (int)n;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += nb * blockDim.x) {
-    t0 = fma((A)a1[base + i], (A)b1[base + i], t0);
-    if (a2) t1 = fma((A)a2[base + i], (A)b2[base + i], t1);
+  // four independent partial sums per thread keep four loads of each operand
+  // in flight (the grid alone does not cover the latency of HBM)
+  A t0[4] = {A(0), A(0), A(0), A(0)}, t1[4] = {A(0), A(0), A(0), A(0)};
+  const int nn = (int)n, stride = nb * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < nn; i += 4 * stride) {
+    A x[4], y[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      x[k] = (A)a1[base + i + k * stride];
+      y[k] = (A)b1[base + i + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) t0[k] = fma(x[k], y[k], t0[k]);
+    if (a2) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        x[k] = (A)a2[base + i + k * stride];
+        y[k] = (A)b2[base + i + k * stride];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) t1[k] = fma(x[k], y[k], t1[k]);
+    }
   }
-  double acc[2] = {(double)t0, (double)t1};
+  for (; i < nn; i += stride) {
+    t0[0] = fma((A)a1[base + i], (A)b1[base + i], t0[0]);
+    if (a2) t1[0] = fma((A)a2[base + i], (A)b2[base + i], t1[0]);
+  }
+  double acc[2] = {((double)t0[0] + (double)t0[1]) + ((double)t0[2] + (double)t0[3]),
+                   ((double)t1[0] + (double)t1[1]) + ((double)t1[2] + (double)t1[3])};
   block_sum<2>(acc, sred);
   if (threadIdx.x == 0) {
     part[((long long)c * nb + blockIdx.x) * 2] = acc[0];
@@ -1013,7 +1045,9 @@ int vblocks(long long n) { return (int)std::min<long long>(std::max<long long>((
 
 cudaError_t pcg_dot2(cudaStream_t s, long long n, int nc, const double* a1, const double* b1, const double* a2,
                      const double* b2, double* part, int* nblocks) {
-  const int nb = (int)std::min<long long>(std::max<long long>((n + 1023) / 1024, 1), 2 * 152 / nc + 1);
+  // up to 8 CTAs of 256 threads per SM (all cases together), each thread
+  // summing at least 8 products
+  const int nb = (int)std::min<long long>(std::max<long long>((n + 2047) / 2048, 1), 8 * 152 / nc);
   dot2_kernel<<<dim3(nb, nc), 256, 0, s>>>(n, a1, b1, a2, b2, part);
   *nblocks = nb;
   return cudaGetLastError();
@@ -1040,7 +1074,9 @@ cudaError_t mg_prep(cudaStream_t s, long long n, int nc, const double* r, float*
 }
 cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const void* a1, bool a_f32, const void* b1, bool b1_f32,
                        const void* a2, const void* b2, double* part, MgCtl* ctl, int what, int* nblocks) {
-  const int nb = (int)std::min<long long>(std::max<long long>((n + 1023) / 1024, 1), 2 * 152 / nc + 1);
+  // up to 8 CTAs of 256 threads per SM (all cases together), each thread
+  // summing at least 8 products
+  const int nb = (int)std::min<long long>(std::max<long long>((n + 2047) / 2048, 1), 8 * 152 / nc);
   const dim3 grid(nb, nc);
   if (a_f32 && b1_f32)
     dotscal_kernel<float, float><<<grid, 256, 0, s>>>(n, (const float*)a1, (const float*)b1, (const float*)a2,

@@ -143,22 +143,30 @@ __device__ __forceinline__ void h8_strain(const T (&u)[8][3], T (&g)[18]) {
 }
 
 // sigma = C g restricted to the diagonal blocks {0..2}, {3,4}, {5,6}, {7,8},
-// {9,10}, {11,12}, {13,14}, {15..17}.
+// {9,10}, {11,12}, {13,14}, {15..17}.  Each block is its own instantiation, so
+// every index is a compile-time constant for any value type (a runtime index
+// would move g into local memory).
+template <int START, int SIZE, typename T>
+__device__ __forceinline__ void h8_stress_block(const T (&g)[18], const CMat<3, T>& C, T (&s)[18]) {
+#pragma unroll
+  for (int i = 0; i < SIZE; i++) {
+    const int r = START + i;
+    T acc = C.k[r * 18 + START] * g[START];
+#pragma unroll
+    for (int j = 1; j < SIZE; j++) acc = fma(C.k[r * 18 + START + j], g[START + j], acc);
+    s[r] = acc;
+  }
+}
 template <typename T>
 __device__ __forceinline__ void h8_stress(const T (&g)[18], const CMat<3, T>& C, T (&s)[18]) {
-  constexpr int start[8] = {0, 3, 5, 7, 9, 11, 13, 15};
-  constexpr int size[8] = {3, 2, 2, 2, 2, 2, 2, 3};
-#pragma unroll
-  for (int b = 0; b < 8; b++) {
-#pragma unroll
-    for (int i = 0; i < size[b]; i++) {
-      const int r = start[b] + i;
-      T acc = C.k[r * 18 + start[b]] * g[start[b]];
-#pragma unroll
-      for (int j = 1; j < size[b]; j++) acc = fma(C.k[r * 18 + start[b] + j], g[start[b] + j], acc);
-      s[r] = acc;
-    }
-  }
+  h8_stress_block<0, 3>(g, C, s);
+  h8_stress_block<3, 2>(g, C, s);
+  h8_stress_block<5, 2>(g, C, s);
+  h8_stress_block<7, 2>(g, C, s);
+  h8_stress_block<9, 2>(g, C, s);
+  h8_stress_block<11, 2>(g, C, s);
+  h8_stress_block<13, 2>(g, C, s);
+  h8_stress_block<15, 3>(g, C, s);
 }
 
 // Inverse Walsh of one component: F[mode], mode = a + 2b + 4c, F[0] = 0;

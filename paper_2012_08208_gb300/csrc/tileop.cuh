@@ -226,6 +226,19 @@ struct TileOp<3, T> {
   template <class Load, class Emit>
   __device__ static void apply1(const Grid& g, const TileMapG& m, int t, const T* __restrict__ E,
                                 const CMat<3, T>& C, unsigned char* smem, Load load, Emit emit) {
+    apply1_pre(
+        g, m, t, E, C, smem, load, [](long long) { return 0; },
+        [&](long long node, const T(&y)[3], const T(&us)[3], int) { emit(node, y, us); });
+  }
+
+  // The same with a pre-load: pre(node) is called for this thread's output
+  // node of plane kz before the element arithmetic of that layer, and its
+  // result reaches emit(node, y, us, pre_result), so the global loads the
+  // emitter needs (a right-hand side, a scale, the fixed bits) overlap the
+  // arithmetic instead of following the barrier.
+  template <class Load, class Pre, class Emit>
+  __device__ static void apply1_pre(const Grid& g, const TileMapG& m, int t, const T* __restrict__ E,
+                                    const CMat<3, T>& C, unsigned char* smem, Load load, Pre pre, Emit emit) {
     V4<T>* P = reinterpret_cast<V4<T>*>(smem);  // [2][PY][PX] staged node planes
     V4<T>* X = P + 2 * PLANE;                   // [2][LY][LX] y-exchange of corner sums
     int x0, y0, z0, z1;
@@ -294,6 +307,8 @@ struct TileOp<3, T> {
       const bool more = kz + 2 <= z1;  // plane kz + 2 is needed by the next layer
       if (more) prefetch(kz + 2, pf);
       const T Enext = modulus(kz + 1);
+      const bool emits = kz >= z0 && owner;
+      const auto pd = pre(emits ? main_off + nplane * kz : -1LL);
       T f[8][3];
       if (Ee >= T(0)) {
         T u[8][3];
@@ -321,11 +336,11 @@ struct TileOp<3, T> {
       X[(kz & 1) * THREADS + tid] = V4<T>{b[0], b[1], b[2], T(0)};
       if (more) stage(P + (kz & 1) * PLANE, pf);
       __syncthreads();
-      if (kz >= z0 && owner) {
+      if (emits) {
         const V4<T> w = X[(kz & 1) * THREADS + tid - 32];
         T y[3] = {a[0] + w.x, a[1] + w.y, a[2] + w.z};
         T us[3] = {uo[0][0], uo[0][1], uo[0][2]};
-        emit(main_off + nplane * kz, y, us);
+        emit(main_off + nplane * kz, y, us, pd);
       }
 #pragma unroll
       for (int c = 0; c < 4; c++)
