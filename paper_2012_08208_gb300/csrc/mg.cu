@@ -104,6 +104,58 @@ __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const 
     mgops::stencil_node<DIM, false>(g, S, mask, invd, u, w, b, y, mode, ca, cc, om, nd, off);
 }
 
+// The same step on a small assembled 3D level, one warp per node: lane l < 27
+// takes neighbour l = (dx+1) + 3 (dy+1) + 9 (dz+1), the partial rows are summed
+// by a fixed xor butterfly (every lane obtains the same totals), and lanes 0..2
+// finish one component each with mgops::stencil_node's formula.  A small level
+// has too few nodes for one thread per node to cover the latency of its ~200
+// loads; a warp per node runs them in parallel.
+__global__ void apply_stencil_warp_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
+                                          const float* __restrict__ invd, const float* u, const float* w,
+                                          const float* b, float* y, int mode, float ca, float cc, float om,
+                                          const int* __restrict__ stop) {
+  if (halted(stop)) return;
+  const int nn = (int)g.nn, nxy = g.nx * g.ny;
+  const long long off = (long long)blockIdx.y * nn * 3;
+  const int lane = threadIdx.x & 31;
+  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;  // meaningful for lane < 27
+  for (int nd = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; nd < nn; nd += (gridDim.x * blockDim.x) >> 5) {
+    const int k = nd / nxy, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (lane < 27 && i + dx >= 0 && i + dx < g.nx && j + dy >= 0 && j + dy < g.ny && k + dz >= 0 && k + dz < g.nz) {
+      const int n2 = nd + dx + g.nx * dy + nxy * dz;
+#pragma unroll
+      for (int s2 = 0; s2 < 3; s2++) {
+        const float v = u[off + (long long)n2 * 3 + s2];
+        a0 = fmaf(mgops::sblock<3>(S, nn, nd, lane, n2, 0, s2), v, a0);
+        a1 = fmaf(mgops::sblock<3>(S, nn, nd, lane, n2, 1, s2), v, a1);
+        a2 = fmaf(mgops::sblock<3>(S, nn, nd, lane, n2, 2, s2), v, a2);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+      a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+      a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (lane < 3) {
+      const float acc = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+      const long long idx = (long long)nd * 3 + lane;
+      const float res = b[off + idx] - acc;
+      float out = res;
+      if (mode == 1) {
+        out = fmaf(ca, u[off + idx], om * invd[idx] * res);
+        if (w) out = fmaf(cc, w[off + idx], out);
+      }
+      y[off + idx] = ((mask[nd] >> lane) & 1) ? 0.f : out;
+    }
+  }
+}
+
+// Levels with at most this many nodes run their 3D stencil steps and their
+// 2:1 restriction one warp per node.
+constexpr long long kWarpNodes = 65536;
+
 // Inverse l1 row sums from the assembled form (see diag_kernel).
 template <int DIM>
 __global__ void diag_stencil_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
@@ -261,67 +313,91 @@ __global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
 // per hierarchy), a coarse element no fixed fine DOF touches has
 //   K_E = sum_ch E_ch A_ch            (f^dim FMA per entry);
 // a touched element sums the masked triple product of galerkin_kernel entry by
-// entry.  One CTA per coarse element (the children's moduli and fixed bits
-// staged in shared memory; the grid strides over the elements), its threads
-// striding over the ND^2 entries
-// (coalesced loads of A and stores of K_E); rows and columns of fixed coarse
-// DOFs are zeroed as in galerkin_kernel.
+// entry.  The child matrices and the interpolation weights Phi_ch[n][C] (the
+// same for every element) are staged in shared memory once per CTA; one CTA
+// works on one coarse element at a time (the grid strides over the elements),
+// staging its children's moduli and fine-node fixed bits, and its threads
+// stride over the ND^2 entries (coalesced stores).  Rows and columns of fixed
+// coarse DOFs are zeroed as in galerkin_kernel.  Shared memory (dynamic):
+// f^dim (ND^2 + NC^2) floats.
 template <int DIM>
 __global__ void __launch_bounds__(256) galerkin1_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
                                                         const float* __restrict__ A, const float* __restrict__ K0g,
                                                         const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
                                                         const uint8_t* __restrict__ touched, float* __restrict__ Kc) {
   constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NE = ND * ND;
-  constexpr int kMaxCh = 343;  // f <= 7
+  constexpr int kMaxCh = 343, kMaxFine = 512;  // f <= 7
   __shared__ float sE[kMaxCh];
+  __shared__ uint8_t sMf[kMaxFine];  // fine-node fixed bits of the element, (f + 1)^dim nodes x fastest
   __shared__ uint8_t sMc[NC];
+  extern __shared__ __align__(16) float dyn[];
   const int nch = DIM == 2 ? f * f : f * f * f;
-  for (unsigned ec = blockIdx.x; ec < (unsigned)gc.ne; ec += gridDim.x) {
-  __syncthreads();  // the previous element's staged values are no longer read
-  const int I = (int)(ec % (unsigned)gc.ex), J = (int)((ec / (unsigned)gc.ex) % (unsigned)gc.ey);
-  const int Kz = DIM == 3 ? (int)(ec / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
-  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+  const int f1 = f + 1;
+  float* sA = dyn;                            // [nch][NE]
+  float* sPhi = dyn + (long long)nch * NE;    // [nch][NC n][NC C]
+  for (int i = threadIdx.x; i < nch * NE; i += blockDim.x) sA[i] = A[i];
+  for (int i = threadIdx.x; i < nch * NC * NC; i += blockDim.x) {
+    const int ch = i / (NC * NC), n = (i / NC) % NC, C = i % NC;
     const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-    sE[ch] = Ef[(f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0))];
+    float w = w1(cofs(C, 0), cx + cofs(n, 0), f) * w1(cofs(C, 1), cy + cofs(n, 1), f);
+    if (DIM == 3) w *= w1(cofs(C, 2), cz + cofs(n, 2), f);
+    sPhi[i] = w;
   }
-  if (threadIdx.x < NC)
-    sMc[threadIdx.x] = mc[node_index(gc, I + cofs(threadIdx.x, 0), J + cofs(threadIdx.x, 1),
-                                     Kz + (DIM == 3 ? cofs(threadIdx.x, 2) : 0))];
-  __syncthreads();
-  const bool tch = touched[ec] != 0;
-  float* out = Kc + (long long)ec * NE;
-  for (int t = threadIdx.x; t < NE; t += blockDim.x) {
-    const int a = t / ND, b = t - (t / ND) * ND;
-    const int Ca = a / DIM, ra = a - Ca * DIM, Cb = b / DIM, rb = b - Cb * DIM;
-    float acc = 0.f;
-    if (!tch) {
-      for (int ch = 0; ch < nch; ch++) acc = fmaf(sE[ch], __ldg(A + (long long)ch * NE + t), acc);
-    } else {
-      for (int ch = 0; ch < nch; ch++) {
-        const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-        const int fi = f * I + cx, fj = f * J + cy, fk = DIM == 3 ? f * Kz + cz : 0;
-        float sub = 0.f;
-        for (int n = 0; n < NC; n++) {
-          if ((mf[node_index(gf, fi + cofs(n, 0), fj + cofs(n, 1), fk + (DIM == 3 ? cofs(n, 2) : 0))] >> ra) & 1)
-            continue;
-          float pn = w1(cofs(Ca, 0), cx + cofs(n, 0), f) * w1(cofs(Ca, 1), cy + cofs(n, 1), f);
-          if (DIM == 3) pn *= w1(cofs(Ca, 2), cz + cofs(n, 2), f);
-          if (pn == 0.f) continue;
-          for (int m = 0; m < NC; m++) {
-            if ((mf[node_index(gf, fi + cofs(m, 0), fj + cofs(m, 1), fk + (DIM == 3 ? cofs(m, 2) : 0))] >> rb) & 1)
-              continue;
-            float pm = w1(cofs(Cb, 0), cx + cofs(m, 0), f) * w1(cofs(Cb, 1), cy + cofs(m, 1), f);
-            if (DIM == 3) pm *= w1(cofs(Cb, 2), cz + cofs(m, 2), f);
-            sub = fmaf(pn * pm, K0g[(n * DIM + ra) * ND + m * DIM + rb], sub);
-          }
-        }
-        acc = fmaf(sE[ch], sub, acc);
+  for (unsigned ec = blockIdx.x; ec < (unsigned)gc.ne; ec += gridDim.x) {
+    __syncthreads();  // the tables are staged; the previous element's values are no longer read
+    const int I = (int)(ec % (unsigned)gc.ex), J = (int)((ec / (unsigned)gc.ex) % (unsigned)gc.ey);
+    const int Kz = DIM == 3 ? (int)(ec / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
+    const bool tch = touched[ec] != 0;
+    for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+      const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+      sE[ch] = Ef[(f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0))];
+    }
+    if (tch) {
+      const int nf = DIM == 2 ? f1 * f1 : f1 * f1 * f1;
+      for (int i = threadIdx.x; i < nf; i += blockDim.x) {
+        const int x = i % f1, y = (i / f1) % f1, z = DIM == 3 ? i / (f1 * f1) : 0;
+        sMf[i] = mf[node_index(gf, f * I + x, f * J + y, DIM == 3 ? f * Kz + z : 0)];
       }
     }
-    if (((sMc[Ca] >> ra) & 1) || ((sMc[Cb] >> rb) & 1)) acc = 0.f;
-    out[t] = acc;
+    if (threadIdx.x < NC)
+      sMc[threadIdx.x] = mc[node_index(gc, I + cofs(threadIdx.x, 0), J + cofs(threadIdx.x, 1),
+                                       Kz + (DIM == 3 ? cofs(threadIdx.x, 2) : 0))];
+    __syncthreads();
+    float* out = Kc + (long long)ec * NE;
+    for (int t = threadIdx.x; t < NE; t += blockDim.x) {
+      const int a = t / ND, b = t - (t / ND) * ND;
+      const int Ca = a / DIM, ra = a - Ca * DIM, Cb = b / DIM, rb = b - Cb * DIM;
+      float acc = 0.f;
+      if (!tch) {
+        for (int ch = 0; ch < nch; ch++) acc = fmaf(sE[ch], sA[ch * NE + t], acc);
+      } else {
+        for (int ch = 0; ch < nch; ch++) {
+          const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+          const float* phi = sPhi + ch * NC * NC;
+          float sub = 0.f;
+          for (int n = 0; n < NC; n++) {
+            const int ln = (cx + cofs(n, 0)) + f1 * ((cy + cofs(n, 1)) + f1 * (DIM == 3 ? cz + cofs(n, 2) : 0));
+            const float pn = phi[n * NC + Ca];
+            if (pn == 0.f || ((sMf[ln] >> ra) & 1)) continue;
+            for (int m = 0; m < NC; m++) {
+              const int lm = (cx + cofs(m, 0)) + f1 * ((cy + cofs(m, 1)) + f1 * (DIM == 3 ? cz + cofs(m, 2) : 0));
+              if ((sMf[lm] >> rb) & 1) continue;
+              sub = fmaf(pn * phi[m * NC + Cb], K0g[(n * DIM + ra) * ND + m * DIM + rb], sub);
+            }
+          }
+          acc = fmaf(sE[ch], sub, acc);
+        }
+      }
+      if (((sMc[Ca] >> ra) & 1) || ((sMc[Cb] >> rb) & 1)) acc = 0.f;
+      out[t] = acc;
+    }
   }
-  }
+}
+
+// Dynamic shared memory of galerkin1_kernel for coarsening factor f.
+size_t galerkin1_smem(int dim, int f) {
+  const int nd = dim == 2 ? 8 : 24, nc = dim == 2 ? 4 : 8, nch = dim == 2 ? f * f : f * f * f;
+  return (size_t)nch * (nd * nd + nc * nc) * sizeof(float);
 }
 
 // Restriction (mgops::restrict2_node, restrict_warp) with the coarse level's
@@ -612,15 +688,22 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
     if (i > 0) {
       const MgLevel& fl = lv[i - 1];
       coarse_mask_kernel<<<blocks(l.g.nn), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, l.mask);
-      if (i == 1) {
+      // level 1 by the staged child matrices when their tables fit in shared
+      // memory (f = 2, 3 in 3D); otherwise the general kernel below
+      const size_t sm1 = galerkin1_smem(dim, l.f);
+      if (i == 1 && sm1 <= 160 * 1024) {
         if (dim == 2) {
           touched_kernel<2><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
-          galerkin1_kernel<2><<<blocks(l.g.ne * 4), 64, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
-                                                               l.K);
+          e = cudaFuncSetAttribute(galerkin1_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+          if (e != cudaSuccess) return e;
+          galerkin1_kernel<2><<<std::min<long long>(l.g.ne, 152 * 8), 64, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d,
+                                                                                   fl.mask, l.mask, touched1, l.K);
         } else {
           touched_kernel<3><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
-          galerkin1_kernel<3><<<blocks(l.g.ne * 4), 192, 0, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
-                                                                l.K);
+          e = cudaFuncSetAttribute(galerkin1_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+          if (e != cudaSuccess) return e;
+          galerkin1_kernel<3><<<std::min<long long>(l.g.ne, 152 * 4), 192, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d,
+                                                                                    fl.mask, l.mask, touched1, l.K);
         }
         nl += 1;  // the touched-element flags (the Galerkin launch is counted below)
       } else if (dim == 2)
@@ -685,6 +768,9 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
       dim3 grid(blocks(l.g.nn), nc);
       if (dim == 2)
         apply_stencil_kernel<2><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y, mode, a, c, om, stop);
+      else if (l.g.nn <= kWarpNodes)
+        apply_stencil_warp_kernel<<<dim3(blocks(l.g.nn * 32), nc), 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y,
+                                                                              mode, a, c, om, stop);
       else
         apply_stencil_kernel<3><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y, mode, a, c, om, stop);
       e = cudaGetLastError();
@@ -709,7 +795,7 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   MgLevel& c = lv[li + 1];
   const bool coarsest = li + 1 == (int)lv.size() - 1;
   float* cx0 = coarsest ? nullptr : c.x[0];  // the dense solve needs no first sweep
-  if (c.f == 2) {
+  if (c.f == 2 && !(dim == 3 && c.g.nn <= kWarpNodes)) {
     dim3 gr(blocks(c.g.nn), nc);
     if (dim == 2) restrict2_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
     else restrict2_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
