@@ -148,6 +148,40 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS, MINB)
   }
 }
 
+// z-chunk length of a streaming 3D tile kernel: the balanced depth with the
+// fewest rounds x (depth + 3) when `resident` CTAs run at once (a tile streams
+// depth + 1 element layers after a two-plane prologue).
+static int zlen_for(const Grid& g, int resident) {
+  const int tx = (g.nx + 30) / 31, ty = (g.ny + 6) / 7;
+  int best = 16;
+  long long best_cost = -1;
+  for (int zl = 1; zl <= g.nz; zl++) {
+    const int chunks = (g.nz + zl - 1) / zl;
+    const int zb = (g.nz + chunks - 1) / chunks;
+    if (zb != zl) continue;
+    const long long ntiles = (long long)tx * ty * chunks;
+    const long long rounds = (ntiles + resident - 1) / resident;
+    const long long cost = rounds * (zl + 3);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = zl;
+    }
+  }
+  return best;
+}
+
+// CTAs of `kern` (THREADS threads, `smem` bytes) resident on the whole device.
+template <class K>
+static int resident_ctas(K kern, int threads, size_t smem) {
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * nsm;
+}
+
 template <int DIM, typename T>
 static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, const void* E,
                                const uint8_t* mask, const void* u, void* y, int ncopies, int zlen, const int* stop) {
@@ -167,6 +201,11 @@ static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, c
   auto kern = (DIM == 3 && sizeof(T) == 4) ? matvec_kernel<DIM, T, 3> : matvec_kernel<DIM, T, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (DIM == 3) {  // tiles to fill the CTAs this kernel keeps resident
+    static int resident = 0;
+    if (!resident) resident = resident_ctas(kern, Op::THREADS, smem);
+    if (resident > 0) a.tm = Op::map(g, zlen_for(g, resident));
+  }
   kern<<<dim3(a.tm.ntiles, ncopies), Op::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -304,9 +343,15 @@ static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, co
   const size_t smem = Op::smem_bytes();
   // H8: 2 resident CTAs per SM (no spills with the pre-loaded emit data);
   // measured faster than 3 with spills
-  auto kern = DIM == 3 ? mg_sweep_kernel<DIM, 2> : mg_sweep_kernel<DIM, 1>;
+  // H8: 3 resident CTAs per SM, tiles matched to them (measured fastest)
+  auto kern = DIM == 3 ? mg_sweep_kernel<DIM, 3> : mg_sweep_kernel<DIM, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  if (DIM == 3) {  // tiles to fill the CTAs this kernel keeps resident
+    static int res = 0;
+    if (!res) res = resident_ctas(kern, Op::THREADS, smem);
+    if (res > 0) a.tm = Op::map(g, zlen_for(g, res));
+  }
   kern<<<dim3(a.tm.ntiles, ncopies), Op::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -293,9 +293,11 @@ __global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict
 
 // Coarse elements whose footprint holds a fixed fine DOF: touched[ec] = 1
 // when any of the (f + 1)^dim fine nodes inside coarse element ec has a fixed
-// bit (its children's matrices are masked).
+// bit (its children's matrices are masked); those elements are also appended
+// to list[0 .. *count) (*count zeroed before the launch).
 template <int DIM>
-__global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, uint8_t* __restrict__ touched) {
+__global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, uint8_t* __restrict__ touched,
+                               int* __restrict__ list, int* __restrict__ count) {
   const long long ne = gc.ne;
   for (long long ec = blockIdx.x * (long long)blockDim.x + threadIdx.x; ec < ne;
        ec += (long long)gridDim.x * blockDim.x) {
@@ -305,6 +307,7 @@ __global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
       for (int y = 0; y <= f; y++)
         for (int x = 0; x <= f; x++) any |= mf[node_index(gf, f * I + x, f * J + y, DIM == 3 ? f * Kz + z : 0)];
     touched[ec] = any ? 1 : 0;
+    if (any) list[atomicAdd(count, 1)] = (int)ec;  // list order is free: each element is computed alone
   }
 }
 
@@ -315,7 +318,8 @@ __global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
 // a touched element sums the masked triple product of galerkin_kernel entry by
 // entry.  The child matrices and the interpolation weights Phi_ch[n][C] (the
 // same for every element) are staged in shared memory once per CTA; one CTA
-// works on one coarse element at a time (the grid strides over the elements),
+// works on one coarse element at a time (the grid strides over the elements,
+// or over list[0 .. *list_count) when list is given),
 // staging its children's moduli and fine-node fixed bits, and its threads
 // stride over the ND^2 entries (coalesced stores).  Rows and columns of fixed
 // coarse DOFs are zeroed as in galerkin_kernel.  Shared memory (dynamic):
@@ -324,7 +328,8 @@ template <int DIM>
 __global__ void __launch_bounds__(256) galerkin1_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
                                                         const float* __restrict__ A, const float* __restrict__ K0g,
                                                         const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                                                        const uint8_t* __restrict__ touched, float* __restrict__ Kc) {
+                                                        const uint8_t* __restrict__ touched, const int* __restrict__ list,
+                                                        const int* __restrict__ list_count, float* __restrict__ Kc) {
   constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NE = ND * ND;
   constexpr int kMaxCh = 343, kMaxFine = 512;  // f <= 7
   __shared__ float sE[kMaxCh];
@@ -343,7 +348,9 @@ __global__ void __launch_bounds__(256) galerkin1_kernel(Grid gf, Grid gc, int f,
     if (DIM == 3) w *= w1(cofs(C, 2), cz + cofs(n, 2), f);
     sPhi[i] = w;
   }
-  for (unsigned ec = blockIdx.x; ec < (unsigned)gc.ne; ec += gridDim.x) {
+  const int nlist = list ? *list_count : (int)gc.ne;
+  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const unsigned ec = list ? (unsigned)list[li] : (unsigned)li;
     __syncthreads();  // the tables are staged; the previous element's values are no longer read
     const int I = (int)(ec % (unsigned)gc.ex), J = (int)((ec / (unsigned)gc.ex) % (unsigned)gc.ey);
     const int Kz = DIM == 3 ? (int)(ec / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
@@ -391,6 +398,40 @@ __global__ void __launch_bounds__(256) galerkin1_kernel(Grid gf, Grid gc, int f,
       if (((sMc[Ca] >> ra) & 1) || ((sMc[Cb] >> rb) & 1)) acc = 0.f;
       out[t] = acc;
     }
+  }
+}
+
+// The untouched elements of level 1 (K_E = sum_ch E_ch A_ch), one thread per
+// matrix entry over all elements (the element index of an entry is a division
+// by the constant ND^2); the child matrices are staged in shared memory once
+// per CTA.  Touched elements are left to galerkin1_kernel.  Shared memory
+// (dynamic): f^dim ND^2 floats.
+template <int DIM>
+__global__ void __launch_bounds__(256) galerkin1_flat_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
+                                                             const float* __restrict__ A,
+                                                             const uint8_t* __restrict__ touched,
+                                                             float* __restrict__ Kc) {
+  constexpr int ND = MgC<DIM>::ND, NE = ND * ND;
+  extern __shared__ __align__(16) float sA[];  // [nch][NE]
+  const int nch = DIM == 2 ? f * f : f * f * f;
+  for (int i = threadIdx.x; i < nch * NE; i += blockDim.x) sA[i] = A[i];
+  __syncthreads();
+  const long long total = gc.ne * NE;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long ec = idx / NE;
+    const int t = (int)(idx - ec * NE);
+    if (touched[ec]) continue;
+    const unsigned e32 = (unsigned)ec;
+    const int I = (int)(e32 % (unsigned)gc.ex), J = (int)((e32 / (unsigned)gc.ex) % (unsigned)gc.ey);
+    const int Kz = DIM == 3 ? (int)(e32 / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
+    float acc = 0.f;
+    for (int ch = 0; ch < nch; ch++) {
+      const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+      const float Ee = __ldg(Ef + (f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0)));
+      acc = fmaf(Ee, sA[ch * NE + t], acc);
+    }
+    Kc[idx] = acc;
   }
 }
 
@@ -549,9 +590,10 @@ void MgHierarchy::release() {
       if (q) cudaFree(q);
   }
   lv.clear();
-  for (void* q : {(void*)A1, (void*)touched1}) if (q) cudaFree(q);
+  for (void* q : {(void*)A1, (void*)touched1, (void*)touched_list}) if (q) cudaFree(q);
   A1 = nullptr;
   touched1 = nullptr;
+  touched_list = nullptr;
   for (void* q : {(void*)cinv, (void*)K0d, (void*)ctl, (void*)p32, (void*)q32, (void*)d32, (void*)p32b,
                   (void*)dscratch, (void*)dflag})
     if (q) cudaFree(q);
@@ -629,6 +671,7 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
     const long long nch = g0.dim == 2 ? f1 * f1 : f1 * f1 * f1;
     if (e == cudaSuccess) e = cudaMalloc((void**)&A1, nch * nd * nd * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&touched1, std::max<long long>(lv[1].g.ne, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&touched_list, (lv[1].g.ne + 1) * sizeof(int));
   }
   cn = (int)(lv.back().g.nn * g0.dim);
   if (e == cudaSuccess) e = cudaMalloc((void**)&cinv, (size_t)cn * cn * sizeof(float));
@@ -692,20 +735,34 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
       // memory (f = 2, 3 in 3D); otherwise the general kernel below
       const size_t sm1 = galerkin1_smem(dim, l.f);
       if (i == 1 && sm1 <= 160 * 1024) {
+        // flags and the list of touched elements, the untouched ones flat, the
+        // touched ones one CTA each
+        const size_t smf = (size_t)(dim == 2 ? l.f * l.f : l.f * l.f * l.f) * nd * nd * sizeof(float);
+        const long long entries = l.g.ne * nd * nd;
+        e = cudaMemsetAsync(touched_list, 0, sizeof(int), s);
+        if (e != cudaSuccess) return e;
         if (dim == 2) {
-          touched_kernel<2><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
-          e = cudaFuncSetAttribute(galerkin1_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+          touched_kernel<2><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1, touched_list + 1,
+                                                           touched_list);
+          e = cudaFuncSetAttribute(galerkin1_flat_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(galerkin1_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
           if (e != cudaSuccess) return e;
-          galerkin1_kernel<2><<<std::min<long long>(l.g.ne, 152 * 8), 64, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d,
-                                                                                   fl.mask, l.mask, touched1, l.K);
+          galerkin1_flat_kernel<2><<<blocks(entries), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
+          galerkin1_kernel<2><<<152 * 2, 64, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
+                                                      touched_list + 1, touched_list, l.K);
         } else {
-          touched_kernel<3><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1);
-          e = cudaFuncSetAttribute(galerkin1_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+          touched_kernel<3><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1, touched_list + 1,
+                                                           touched_list);
+          e = cudaFuncSetAttribute(galerkin1_flat_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
+          if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(galerkin1_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
           if (e != cudaSuccess) return e;
-          galerkin1_kernel<3><<<std::min<long long>(l.g.ne, 152 * 4), 192, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d,
-                                                                                    fl.mask, l.mask, touched1, l.K);
+          galerkin1_flat_kernel<3><<<blocks(entries), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
+          galerkin1_kernel<3><<<152 * 2, 192, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
+                                                       touched_list + 1, touched_list, l.K);
         }
-        nl += 1;  // the touched-element flags (the Galerkin launch is counted below)
+        nl += 2;  // the touched-element flags and the flat kernel (the staged launch is counted below)
       } else if (dim == 2)
         galerkin_kernel<2><<<(unsigned)l.g.ne, 64, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask,
                                                             l.mask, l.K);

@@ -72,6 +72,7 @@ struct MgHierarchy {
   float* K0d = nullptr;     // level-0 element matrix (unit modulus), device copy
   float* A1 = nullptr;      // level-1 child matrices P_ch^T K0 P_ch [f^dim][ND][ND] (unmasked)
   uint8_t* touched1 = nullptr;  // level-1 elements whose footprint holds a fixed fine DOF
+  int* touched_list = nullptr;  // those elements (entries after the count: touched_list[0] = count)
   const float* E0 = nullptr;
   // Finest-level sweep for all cases on the library's strain-form FP32
   // operator: mode 1 y = a u + c w + om D^-1 (b - A u) (w may be null when
