@@ -175,8 +175,9 @@ tp_status tp_sensitivities(tp_problem* p, double* compliance);
  *   the bilinear / trilinear Laplacian stiffness and mass with natural
  *   (Neumann) boundaries, T the element-to-node integral of the shape
  *   functions, R = rmin / (2 sqrt 3).  H is symmetric, so dc~ = H dc.  Each
- *   application solves the nodal system by Jacobi-PCG in FP64 to relative
- *   residual 1e-14 (TP_ERR_NOT_CONVERGED otherwise) and synchronises.
+ *   application solves the nodal system by FP64 iterative refinement around
+ *   FP32 Jacobi-PCG solves until the FP64 true relative residual is at most
+ *   1e-14 (TP_ERR_NOT_CONVERGED otherwise) and synchronises.
  * `mode` must equal the problem's filter mode (else TP_ERR_STATE). */
 tp_status tp_filter(tp_problem* p, int mode);
 /* Filter mode of the problem (default TP_FILTER_SENSITIVITY); also the mode

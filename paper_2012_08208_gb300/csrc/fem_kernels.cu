@@ -198,7 +198,7 @@ static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, c
   fill_c<DIM, T>(a.C, C);
   const size_t smem = Op::smem_bytes();
   // H8 FP32: 3 resident CTAs per SM (80 registers); measured fastest
-  auto kern = (DIM == 3 && sizeof(T) == 4) ? matvec_kernel<DIM, T, 3> : matvec_kernel<DIM, T, 1>;
+  auto kern = DIM == 3 ? (sizeof(T) == 4 ? matvec_kernel<DIM, T, 3> : matvec_kernel<DIM, T, 2>) : matvec_kernel<DIM, T, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (DIM == 3) {  // tiles to fill the CTAs this kernel keeps resident

@@ -413,8 +413,13 @@ __global__ void __launch_bounds__(256) galerkin1_flat_kernel(Grid gf, Grid gc, i
                                                              float* __restrict__ Kc) {
   constexpr int ND = MgC<DIM>::ND, NE = ND * ND;
   extern __shared__ __align__(16) float sA[];  // [nch][NE]
+  __shared__ long long sOff[343];              // child element offsets from the first child (f <= 7)
   const int nch = DIM == 2 ? f * f : f * f * f;
   for (int i = threadIdx.x; i < nch * NE; i += blockDim.x) sA[i] = A[i];
+  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
+    const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+    sOff[ch] = cx + (long long)gf.ex * (cy + (long long)gf.ey * cz);
+  }
   __syncthreads();
   const long long total = gc.ne * NE;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -425,12 +430,9 @@ __global__ void __launch_bounds__(256) galerkin1_flat_kernel(Grid gf, Grid gc, i
     const unsigned e32 = (unsigned)ec;
     const int I = (int)(e32 % (unsigned)gc.ex), J = (int)((e32 / (unsigned)gc.ex) % (unsigned)gc.ey);
     const int Kz = DIM == 3 ? (int)(e32 / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
+    const long long base = (long long)f * I + (long long)gf.ex * ((long long)f * J + (long long)gf.ey * (DIM == 3 ? f * Kz : 0));
     float acc = 0.f;
-    for (int ch = 0; ch < nch; ch++) {
-      const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-      const float Ee = __ldg(Ef + (f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0)));
-      acc = fmaf(Ee, sA[ch * NE + t], acc);
-    }
+    for (int ch = 0; ch < nch; ch++) acc = fmaf(__ldg(Ef + base + sOff[ch]), sA[ch * NE + t], acc);
     Kc[idx] = acc;
   }
 }
@@ -1055,14 +1057,19 @@ __global__ void dotscal_kernel(long long n, const TA* __restrict__ a1, const TB*
   if (!is_last) return;
   __threadfence();
   const int nc = gridDim.y;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int pr = warp; pr < 2 * nc; pr += blockDim.x >> 5) {
-    const int cc = pr >> 1, k = pr & 1;
-    double sum = 0.0;
-    for (int b = lane; b < nb; b += 32) sum += __ldcg(part + ((long long)cc * nb + b) * 2 + k);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) tot[pr] = sum;
+  // every thread of the last CTA takes a strided share of the partials (a
+  // few loads each, all in flight), then a fixed-order block reduction
+  for (int cc = 0; cc < nc; cc++) {
+    double v2[2] = {0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      v2[0] += __ldcg(part + ((long long)cc * nb + b) * 2);
+      v2[1] += __ldcg(part + ((long long)cc * nb + b) * 2 + 1);
+    }
+    block_sum<2>(v2, sred);
+    if (threadIdx.x == 0) {
+      tot[2 * cc] = v2[0];
+      tot[2 * cc + 1] = v2[1];
+    }
   }
   __syncthreads();
   double* sc = ctl->sc;
