@@ -87,8 +87,7 @@ tp_status ensure_E(tp_problem* p) {
   }
   TPCK(launch_young(p->stream, phys(p), p->E32, p->E64, p->ne, p->prm.E0, p->prm.Emin, p->prm.penal),
        "young kernel");
-  TPCK(launch_diag(p->stream, p->g, p->K0.data(), p->E64, p->mask, p->inv32, p->inv64), "diag kernel");
-  p->launches += 2;
+  p->launches++;
   p->E_dirty = false;
   p->E_version++;
   return TP_OK;
@@ -196,30 +195,64 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   MgLevel& l0 = M.lv[0];
   int nl = 0;
   TPCK(cudaEventRecord(p->ev0, s), "event");
-  if (M.version != p->E_version) {
-    TPCK(M.build(s, p->K0.data(), p->E32, &nl), "multigrid setup");
-    if (!M.coarse_ok) return fail(p, TP_ERR_BREAKDOWN, "multigrid coarsest FP32 inverse met a non-positive pivot");
-    M.version = p->E_version;
-  }
-  TPCK(launch_to_abi(s, p->f, fA, p->nn, p->dim, nc), "layout kernel");
-  if (opts->warm_start == TP_WARM_ZERO || (opts->warm_start == TP_WARM_PREVIOUS && !p->has_u))
-    TPCK(cudaMemsetAsync(x, 0, (size_t)nc * n * sizeof(double), s), "memset");
-  else
-    TPCK(launch_to_abi(s, p->x64, x, p->nn, p->dim, nc), "layout kernel");
-  nl += 2;
-  auto true_rr = [&](double* rr_out) -> tp_status {  // r = f - K x with the FP64 operator, rr per case (synchronises)
-    TPCK(launch_matvec(s, p->g, p->C.data(), true, p->E64, p->mask, x, q, nc, p->zlen), "matvec");
-    TPCK(pcg_residual(s, n, nc, fA, q, p->mask, p->dim, r), "residual kernel");
+  // r = f - K x with the FP64 operator and rr per case into the scalars, on
+  // stream cs; read_rr copies rr to the host (synchronises the problem's stream)
+  auto issue_rr = [&](cudaStream_t cs) -> tp_status {
+    TPCK(launch_matvec(cs, p->g, p->C.data(), true, p->E64, p->mask, x, q, nc, p->zlen), "matvec");
+    TPCK(pcg_residual(cs, n, nc, fA, q, p->mask, p->dim, r), "residual kernel");
     int nb = 0;
-    TPCK(pcg_dot2(s, n, nc, r, r, r, r, p->part, &nb), "dot kernel");
-    TPCK(pcg_scalars(s, nb, nc, p->part, 2, sc), "scalar kernel");
+    TPCK(pcg_dot2(cs, n, nc, r, r, r, r, p->part, &nb), "dot kernel");
+    TPCK(pcg_scalars(cs, nb, nc, p->part, 2, sc), "scalar kernel");
     nl += 4;
+    return TP_OK;
+  };
+  auto read_rr = [&](double* rr_out) -> tp_status {
     double h[64];
     TPCK(cudaMemcpyAsync(h, sc, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
     TPCK(cudaStreamSynchronize(s), "sync");
     for (int c = 0; c < nc; c++) rr_out[c] = h[32 + c];
     return TP_OK;
   };
+  auto true_rr = [&](double* rr_out) -> tp_status {
+    tp_status t = issue_rr(s);
+    return t != TP_OK ? t : read_rr(rr_out);
+  };
+  // The first residual does not depend on the hierarchy (it reads f, x and the
+  // FP64 moduli; the build reads the FP32 moduli and writes only its own
+  // buffers).  When a rebuild is due, the residual runs on a second stream,
+  // forked from and joined back into the problem's stream by events, while the
+  // latency-bound build runs beside the FP64-bound operator.
+  const bool rebuild = M.version != p->E_version;
+  cudaStream_t sr = s;
+  if (rebuild) {
+    if (!M.side) TPCK(cudaStreamCreateWithFlags(&M.side, cudaStreamNonBlocking), "stream");
+    if (!M.fork) TPCK(cudaEventCreateWithFlags(&M.fork, cudaEventDisableTiming), "event");
+    if (!M.join) TPCK(cudaEventCreateWithFlags(&M.join, cudaEventDisableTiming), "event");
+    TPCK(cudaEventRecord(M.fork, s), "event");
+    TPCK(cudaStreamWaitEvent(M.side, M.fork, 0), "stream wait");
+    sr = M.side;
+  }
+  TPCK(launch_to_abi(sr, p->f, fA, p->nn, p->dim, nc), "layout kernel");
+  if (opts->warm_start == TP_WARM_ZERO || (opts->warm_start == TP_WARM_PREVIOUS && !p->has_u))
+    TPCK(cudaMemsetAsync(x, 0, (size_t)nc * n * sizeof(double), sr), "memset");
+  else
+    TPCK(launch_to_abi(sr, p->x64, x, p->nn, p->dim, nc), "layout kernel");
+  nl += 2;
+  st = issue_rr(sr);
+  if (rebuild) {
+    // the join is recorded and waited for on every path, so no work of this
+    // solve is left in flight on the second stream when it returns
+    const cudaError_t ej = cudaEventRecord(M.join, sr);
+    const cudaError_t eb = st == TP_OK ? M.build(s, p->K0.data(), p->E32, &nl) : cudaSuccess;
+    const cudaError_t ew = ej == cudaSuccess ? cudaStreamWaitEvent(s, M.join, 0) : cudaStreamSynchronize(sr);
+    if (st != TP_OK) return st;
+    TPCK(eb, "multigrid setup");
+    TPCK(ej, "event");
+    TPCK(ew, "stream wait");
+    if (!M.coarse_ok) return fail(p, TP_ERR_BREAKDOWN, "multigrid coarsest FP32 inverse met a non-positive pivot");
+    M.version = p->E_version;
+  }
+  if (st != TP_OK) return st;
   // One PCG iteration: q = K p, alpha, the iterate and r, z = V(r), beta and
   // the stopping rule, p.  Default: the segment solves K d = r for a
   // correction d with FP32 vectors and the FP32 operator (FP64 scalars); with
@@ -282,7 +315,7 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     return TP_OK;
   };
   double rr[kMaxCases] = {}, rel0[kMaxCases] = {};
-  st = true_rr(rr);
+  st = read_rr(rr);  // the first residual, issued above
   if (st != TP_OK) return st;
   int fallback = 0;
   for (int c = 0; c < nc; c++) rel0[c] = std::sqrt(rr[c] / p->ff[c]);
@@ -661,6 +694,11 @@ tp_status tp_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_info* info
   }
   tp_status s = ensure_E(p);
   if (s != TP_OK) return s;
+  if (p->diag_version != p->E_version) {  // the Jacobi scaling, formed only for this solver
+    TPCK(launch_diag(p->stream, p->g, p->K0.data(), p->E64, p->mask, p->inv32, p->inv64), "diag kernel");
+    p->launches++;
+    p->diag_version = p->E_version;
+  }
   const bool f64 = opts->precision == TP_PREC_F64;
   const size_t nvals = (size_t)p->nn * p->nv;
   if (opts->warm_start == TP_WARM_ZERO || (opts->warm_start == TP_WARM_PREVIOUS && !p->has_u))

@@ -104,57 +104,76 @@ __global__ void apply_stencil_kernel(Grid g, const float* __restrict__ S, const 
     mgops::stencil_node<DIM, false>(g, S, mask, invd, u, w, b, y, mode, ca, cc, om, nd, off);
 }
 
-// The same step on a small assembled 3D level, one warp per node: lane l < 27
-// takes neighbour l = (dx+1) + 3 (dy+1) + 9 (dz+1), the partial rows are summed
-// by a fixed xor butterfly (every lane obtains the same totals), and lanes 0..2
-// finish one component each with mgops::stencil_node's formula.  A small level
-// has too few nodes for one thread per node to cover the latency of its ~200
-// loads; a warp per node runs them in parallel.
-__global__ void apply_stencil_warp_kernel(Grid g, const float* __restrict__ S, const uint8_t* __restrict__ mask,
-                                          const float* __restrict__ invd, const float* u, const float* w,
-                                          const float* b, float* y, int mode, float ca, float cc, float om,
-                                          const int* __restrict__ stop) {
+// The same step on a small assembled 3D level with G lanes per node (G = 2,
+// 4, 8, 16): lane g of a group takes neighbours g, g + G, ... < 27, the
+// partial rows are summed by a fixed xor butterfly over the group, and lanes
+// 0..2 finish one component each with mgops::stencil_node's formula.  A small
+// level has too few nodes for one thread per node to keep its ~300 loads in
+// flight; a warp per node would leave five lanes idle and take a wave of
+// warps per 9,728 nodes.  Every lane runs the same trip count (the stride is
+// uniform over the grid), so the shuffles always see the whole warp.
+template <int G>
+__global__ void __launch_bounds__(256) apply_stencil_group_kernel(Grid g, const float* __restrict__ S,
+                                                                  const uint8_t* __restrict__ mask,
+                                                                  const float* __restrict__ invd, const float* u,
+                                                                  const float* w, const float* b, float* y, int mode,
+                                                                  float ca, float cc, float om,
+                                                                  const int* __restrict__ stop) {
+  static_assert(G >= 2 && G <= 16 && (G & (G - 1)) == 0, "a power of two up to 16");
+  constexpr int kNbr = (27 + G - 1) / G;
   if (halted(stop)) return;
   const int nn = (int)g.nn, nxy = g.nx * g.ny;
   const long long off = (long long)blockIdx.y * nn * 3;
-  const int lane = threadIdx.x & 31;
-  const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;  // meaningful for lane < 27
-  for (int nd = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; nd < nn; nd += (gridDim.x * blockDim.x) >> 5) {
+  const int sub = threadIdx.x & (G - 1);
+  const int groups = (gridDim.x * blockDim.x) / G;
+  for (int base = 0; base < nn; base += groups) {
+    const int nd = base + (int)((blockIdx.x * blockDim.x + threadIdx.x) / G);
+    const bool active = nd < nn;
     const int k = nd / nxy, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    if (lane < 27 && i + dx >= 0 && i + dx < g.nx && j + dy >= 0 && j + dy < g.ny && k + dz >= 0 && k + dz < g.nz) {
-      const int n2 = nd + dx + g.nx * dy + nxy * dz;
 #pragma unroll
-      for (int s2 = 0; s2 < 3; s2++) {
-        const float v = u[off + (long long)n2 * 3 + s2];
-        a0 = fmaf(mgops::sblock<3>(S, nn, nd, lane, n2, 0, s2), v, a0);
-        a1 = fmaf(mgops::sblock<3>(S, nn, nd, lane, n2, 1, s2), v, a1);
-        a2 = fmaf(mgops::sblock<3>(S, nn, nd, lane, n2, 2, s2), v, a2);
+    for (int q = 0; q < kNbr; q++) {
+      const int nbr = sub + G * q;
+      const int dx = nbr % 3 - 1, dy = (nbr / 3) % 3 - 1, dz = nbr / 9 - 1;
+      if (active && nbr < 27 && i + dx >= 0 && i + dx < g.nx && j + dy >= 0 && j + dy < g.ny && k + dz >= 0 &&
+          k + dz < g.nz) {
+        const int n2 = nd + dx + g.nx * dy + nxy * dz;
+#pragma unroll
+        for (int s2 = 0; s2 < 3; s2++) {
+          const float v = u[off + (long long)n2 * 3 + s2];
+          a0 = fmaf(mgops::sblock<3>(S, nn, nd, nbr, n2, 0, s2), v, a0);
+          a1 = fmaf(mgops::sblock<3>(S, nn, nd, nbr, n2, 1, s2), v, a1);
+          a2 = fmaf(mgops::sblock<3>(S, nn, nd, nbr, n2, 2, s2), v, a2);
+        }
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = G / 2; o > 0; o >>= 1) {
       a0 += __shfl_xor_sync(0xffffffffu, a0, o);
       a1 += __shfl_xor_sync(0xffffffffu, a1, o);
       a2 += __shfl_xor_sync(0xffffffffu, a2, o);
     }
-    if (lane < 3) {
-      const float acc = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
-      const long long idx = (long long)nd * 3 + lane;
+    if (active && sub < 3) {
+      const float acc = sub == 0 ? a0 : (sub == 1 ? a1 : a2);
+      const long long idx = (long long)nd * 3 + sub;
       const float res = b[off + idx] - acc;
       float out = res;
       if (mode == 1) {
         out = fmaf(ca, u[off + idx], om * invd[idx] * res);
         if (w) out = fmaf(cc, w[off + idx], out);
       }
-      y[off + idx] = ((mask[nd] >> lane) & 1) ? 0.f : out;
+      y[off + idx] = ((mask[nd] >> sub) & 1) ? 0.f : out;
     }
   }
 }
 
-// Levels with at most this many nodes run their 3D stencil steps and their
-// 2:1 restriction one warp per node.
+// 3D levels with at most this many nodes run their stencil steps with 8 lanes
+// per node; above, one thread per node (a warp then reads 32 consecutive
+// nodes of each stored coupling entry in one request).
 constexpr long long kWarpNodes = 65536;
+// 3D coarse levels with at most this many nodes are restricted one warp per
+// coarse node (too few nodes for one thread each to keep loads in flight).
+constexpr long long kWarpRestrictNodes = 8192;
 
 // Inverse l1 row sums from the assembled form (see diag_kernel).
 template <int DIM>
@@ -236,59 +255,92 @@ __global__ void coarse_mask_kernel(Grid gf, Grid gc, int f, const uint8_t* __res
 // entry.  For each child c (fine DOFs masked), with Phi_c[n][C] the weight of
 // coarse corner C at the child's node n, in two separable stages:
 //   T = K_c (Phi_c x I),   K_E += (Phi_c x I)^T T.
+// The children are taken kGalChunk at a time: their matrices and fine-node
+// fixed bits are loaded together (all loads of a thread in flight at once),
+// then both stages run over the staged children between three barriers.  The
+// sums keep the order child by child, corner by corner.  With a list, the CTAs
+// stride over the coarse elements list[0 .. *list_count) instead of taking
+// element blockIdx.x.
+constexpr int kGalChunk = 8;
+
 template <int DIM>
-__global__ void galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Kf, const float* __restrict__ Ef,
+__global__ void __launch_bounds__(MgC<DIM>::ND * MgC<DIM>::ND, DIM == 3 ? 3 : 16) galerkin_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Kf, const float* __restrict__ Ef,
                                 const float* __restrict__ K0g, const uint8_t* __restrict__ mf,
-                                const uint8_t* __restrict__ mc, float* __restrict__ Kc) {
-  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND;
-  __shared__ float sK[ND * ND];
-  __shared__ float sT[ND * ND];
-  __shared__ float sK0[ND * ND];  // level-0 children: K0 staged once (divergent constant reads serialise)
-  __shared__ float sPhi[NC * NC];
-  __shared__ uint8_t sM[NC];
+                                const uint8_t* __restrict__ mc, float* __restrict__ Kc,
+                                const int* __restrict__ list = nullptr, const int* __restrict__ list_count = nullptr) {
+  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NE = ND * ND;
+  __shared__ float sK[kGalChunk * NE];
+  __shared__ float sT[kGalChunk * NE];
+  __shared__ float sPhi[kGalChunk * NC * NC];
+  __shared__ uint8_t sM[kGalChunk * NC];
   const int t = threadIdx.x;  // blockDim.x == ND * ND
-  if (!Kf) sK0[t] = K0g[t];
-  const long long ec = blockIdx.x;
+  const float k0t = Kf ? 0.f : K0g[t];
+  const long long nlist = list ? (long long)*list_count : (long long)gridDim.x;
+  for (long long li = blockIdx.x; li < nlist; li += gridDim.x) {
+  const long long ec = list ? (long long)list[li] : li;
   const int I = (int)(ec % gc.ex), J = (int)((ec / gc.ex) % gc.ey), Kz = (int)(ec / ((long long)gc.ex * gc.ey));
   const int a = t / ND, b = t % ND;
   float acc = 0.f;
   const int nch = DIM == 2 ? f * f : f * f * f;
-  for (int ch = 0; ch < nch; ch++) {
-    const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-    const int fi = f * I + cx, fj = f * J + cy, fk = DIM == 3 ? f * Kz + cz : 0;
-    const long long e = fi + (long long)gf.ex * (fj + (long long)gf.ey * fk);
-    __syncthreads();
-    if (t < NC) sM[t] = mf[node_index(gf, fi + cofs(t, 0), fj + cofs(t, 1), fk + (DIM == 3 ? cofs(t, 2) : 0))];
-    if (t < NC * NC) {
-      const int n = t / NC, C = t % NC;
+  for (int ch0 = 0; ch0 < nch; ch0 += kGalChunk) {
+    const int m = min(kGalChunk, nch - ch0);
+    float kv[kGalChunk];
+#pragma unroll
+    for (int q = 0; q < kGalChunk; q++) {
+      kv[q] = 0.f;
+      if (q < m) {
+        const int ch = ch0 + q;
+        const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+        const long long e = (f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0));
+        kv[q] = Kf ? Kf[e * NE + t] : Ef[e] * k0t;
+      }
+    }
+    if (t < m * NC) {
+      const int ch = ch0 + t / NC, n = t % NC;
+      const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+      sM[t] = mf[node_index(gf, f * I + cx + cofs(n, 0), f * J + cy + cofs(n, 1),
+                            DIM == 3 ? f * Kz + cz + cofs(n, 2) : 0)];
+    }
+    for (int i = t; i < m * NC * NC; i += blockDim.x) {
+      const int ch = ch0 + i / (NC * NC), n = (i / NC) % NC, C = i % NC;
+      const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
       float w = w1(cofs(C, 0), cx + cofs(n, 0), f) * w1(cofs(C, 1), cy + cofs(n, 1), f);
       if (DIM == 3) w *= w1(cofs(C, 2), cz + cofs(n, 2), f);
-      sPhi[t] = w;
+      sPhi[i] = w;
     }
+    __syncthreads();  // fixed bits and weights staged; the previous chunk's sT is no longer read
+#pragma unroll
+    for (int q = 0; q < kGalChunk; q++)
+      if (q < m) {
+        const bool fa = (sM[q * NC + a / DIM] >> (a % DIM)) & 1, fb = (sM[q * NC + b / DIM] >> (b % DIM)) & 1;
+        sK[q * NE + t] = (fa || fb) ? 0.f : kv[q];
+      }
     __syncthreads();
-    const bool fa = (sM[a / DIM] >> (a % DIM)) & 1, fb = (sM[b / DIM] >> (b % DIM)) & 1;
-    sK[t] = (fa || fb) ? 0.f : (Kf ? Kf[e * ND * ND + t] : Ef[e] * sK0[t]);
-    __syncthreads();
-    {  // T[a][(C, s)] = sum_n K[a][(n, s)] Phi[n][C]
+    {  // T_q[a][(C, s)] = sum_n K_q[a][(n, s)] Phi_q[n][C]
       const int C = b / DIM, s2 = b % DIM;
-      float v = 0.f;
+      for (int q = 0; q < m; q++) {
+        float v = 0.f;
 #pragma unroll
-      for (int n = 0; n < NC; n++) v = fmaf(sK[a * ND + n * DIM + s2], sPhi[n * NC + C], v);
-      sT[t] = v;
+        for (int n = 0; n < NC; n++) v = fmaf(sK[q * NE + a * ND + n * DIM + s2], sPhi[(q * NC + n) * NC + C], v);
+        sT[q * NE + t] = v;
+      }
     }
     __syncthreads();
-    {  // K_E[(C1, r)][b] += sum_n Phi[n][C1] T[(n, r)][b]
+    {  // K_E[(C1, r)][b] += sum_n Phi_q[n][C1] T_q[(n, r)][b], child by child
       const int C1 = a / DIM, r = a % DIM;
+      for (int q = 0; q < m; q++)
 #pragma unroll
-      for (int n = 0; n < NC; n++) acc = fmaf(sPhi[n * NC + C1], sT[(n * DIM + r) * ND + b], acc);
+        for (int n = 0; n < NC; n++) acc = fmaf(sPhi[(q * NC + n) * NC + C1], sT[q * NE + (n * DIM + r) * ND + b], acc);
     }
+    __syncthreads();  // sK, sPhi and sM are restaged by the next chunk
   }
   // zero rows and columns of fixed coarse DOFs
   const int Ca = a / DIM, ra = a % DIM, Cb = b / DIM, rb = b % DIM;
   const uint8_t ma = mc[node_index(gc, I + cofs(Ca, 0), J + cofs(Ca, 1), Kz + (DIM == 3 ? cofs(Ca, 2) : 0))];
   const uint8_t mb = mc[node_index(gc, I + cofs(Cb, 0), J + cofs(Cb, 1), Kz + (DIM == 3 ? cofs(Cb, 2) : 0))];
   if (((ma >> ra) & 1) || ((mb >> rb) & 1)) acc = 0.f;
-  Kc[ec * ND * ND + t] = acc;
+  Kc[ec * NE + t] = acc;
+  }
 }
 
 // Coarse elements whose footprint holds a fixed fine DOF: touched[ec] = 1
@@ -311,136 +363,53 @@ __global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
   }
 }
 
-// Galerkin operator of level 1, whose children are the level-0 elements
-// E_e K0.  With A_ch = P_ch^T K0 P_ch (the unmasked child matrices, formed once
-// per hierarchy), a coarse element no fixed fine DOF touches has
-//   K_E = sum_ch E_ch A_ch            (f^dim FMA per entry);
-// a touched element sums the masked triple product of galerkin_kernel entry by
-// entry.  The child matrices and the interpolation weights Phi_ch[n][C] (the
-// same for every element) are staged in shared memory once per CTA; one CTA
-// works on one coarse element at a time (the grid strides over the elements,
-// or over list[0 .. *list_count) when list is given),
-// staging its children's moduli and fine-node fixed bits, and its threads
-// stride over the ND^2 entries (coalesced stores).  Rows and columns of fixed
-// coarse DOFs are zeroed as in galerkin_kernel.  Shared memory (dynamic):
-// f^dim (ND^2 + NC^2) floats.
-template <int DIM>
-__global__ void __launch_bounds__(256) galerkin1_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
-                                                        const float* __restrict__ A, const float* __restrict__ K0g,
-                                                        const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
-                                                        const uint8_t* __restrict__ touched, const int* __restrict__ list,
-                                                        const int* __restrict__ list_count, float* __restrict__ Kc) {
-  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NE = ND * ND;
-  constexpr int kMaxCh = 343, kMaxFine = 512;  // f <= 7
-  __shared__ float sE[kMaxCh];
-  __shared__ uint8_t sMf[kMaxFine];  // fine-node fixed bits of the element, (f + 1)^dim nodes x fastest
-  __shared__ uint8_t sMc[NC];
-  extern __shared__ __align__(16) float dyn[];
-  const int nch = DIM == 2 ? f * f : f * f * f;
-  const int f1 = f + 1;
-  float* sA = dyn;                            // [nch][NE]
-  float* sPhi = dyn + (long long)nch * NE;    // [nch][NC n][NC C]
-  for (int i = threadIdx.x; i < nch * NE; i += blockDim.x) sA[i] = A[i];
-  for (int i = threadIdx.x; i < nch * NC * NC; i += blockDim.x) {
-    const int ch = i / (NC * NC), n = (i / NC) % NC, C = i % NC;
-    const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-    float w = w1(cofs(C, 0), cx + cofs(n, 0), f) * w1(cofs(C, 1), cy + cofs(n, 1), f);
-    if (DIM == 3) w *= w1(cofs(C, 2), cz + cofs(n, 2), f);
-    sPhi[i] = w;
-  }
-  const int nlist = list ? *list_count : (int)gc.ne;
-  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
-    const unsigned ec = list ? (unsigned)list[li] : (unsigned)li;
-    __syncthreads();  // the tables are staged; the previous element's values are no longer read
-    const int I = (int)(ec % (unsigned)gc.ex), J = (int)((ec / (unsigned)gc.ex) % (unsigned)gc.ey);
-    const int Kz = DIM == 3 ? (int)(ec / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
-    const bool tch = touched[ec] != 0;
-    for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
-      const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-      sE[ch] = Ef[(f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0))];
-    }
-    if (tch) {
-      const int nf = DIM == 2 ? f1 * f1 : f1 * f1 * f1;
-      for (int i = threadIdx.x; i < nf; i += blockDim.x) {
-        const int x = i % f1, y = (i / f1) % f1, z = DIM == 3 ? i / (f1 * f1) : 0;
-        sMf[i] = mf[node_index(gf, f * I + x, f * J + y, DIM == 3 ? f * Kz + z : 0)];
-      }
-    }
-    if (threadIdx.x < NC)
-      sMc[threadIdx.x] = mc[node_index(gc, I + cofs(threadIdx.x, 0), J + cofs(threadIdx.x, 1),
-                                       Kz + (DIM == 3 ? cofs(threadIdx.x, 2) : 0))];
-    __syncthreads();
-    float* out = Kc + (long long)ec * NE;
-    for (int t = threadIdx.x; t < NE; t += blockDim.x) {
-      const int a = t / ND, b = t - (t / ND) * ND;
-      const int Ca = a / DIM, ra = a - Ca * DIM, Cb = b / DIM, rb = b - Cb * DIM;
-      float acc = 0.f;
-      if (!tch) {
-        for (int ch = 0; ch < nch; ch++) acc = fmaf(sE[ch], sA[ch * NE + t], acc);
-      } else {
-        for (int ch = 0; ch < nch; ch++) {
-          const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-          const float* phi = sPhi + ch * NC * NC;
-          float sub = 0.f;
-          for (int n = 0; n < NC; n++) {
-            const int ln = (cx + cofs(n, 0)) + f1 * ((cy + cofs(n, 1)) + f1 * (DIM == 3 ? cz + cofs(n, 2) : 0));
-            const float pn = phi[n * NC + Ca];
-            if (pn == 0.f || ((sMf[ln] >> ra) & 1)) continue;
-            for (int m = 0; m < NC; m++) {
-              const int lm = (cx + cofs(m, 0)) + f1 * ((cy + cofs(m, 1)) + f1 * (DIM == 3 ? cz + cofs(m, 2) : 0));
-              if ((sMf[lm] >> rb) & 1) continue;
-              sub = fmaf(pn * phi[m * NC + Cb], K0g[(n * DIM + ra) * ND + m * DIM + rb], sub);
-            }
-          }
-          acc = fmaf(sE[ch], sub, acc);
-        }
-      }
-      if (((sMc[Ca] >> ra) & 1) || ((sMc[Cb] >> rb) & 1)) acc = 0.f;
-      out[t] = acc;
-    }
-  }
-}
-
-// The untouched elements of level 1 (K_E = sum_ch E_ch A_ch), one thread per
-// matrix entry over all elements (the element index of an entry is a division
-// by the constant ND^2); the child matrices are staged in shared memory once
-// per CTA.  Touched elements are left to galerkin1_kernel.  Shared memory
-// (dynamic): f^dim ND^2 floats.
+// The untouched elements of level 1 (K_E = sum_ch E_ch A_ch), one warp per
+// element: the element's coordinates and its children's moduli are formed
+// once per warp (child ch's modulus in lane ch mod 32 of one of two registers,
+// broadcast by shuffle), and each lane sums ND^2 / 32 entries, child by child
+// (coalesced stores).  The child matrices are staged in shared memory once per
+// CTA.  Touched elements are left to galerkin_kernel (list mode).  Needs f^dim <= 64;
+// shared memory (dynamic): f^dim ND^2 floats.
 template <int DIM>
 __global__ void __launch_bounds__(256) galerkin1_flat_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
                                                              const float* __restrict__ A,
                                                              const uint8_t* __restrict__ touched,
                                                              float* __restrict__ Kc) {
-  constexpr int ND = MgC<DIM>::ND, NE = ND * ND;
+  constexpr int ND = MgC<DIM>::ND, NE = ND * ND, kPer = NE / 32;
+  static_assert(NE % 32 == 0, "whole entries per lane");
   extern __shared__ __align__(16) float sA[];  // [nch][NE]
-  __shared__ long long sOff[343];              // child element offsets from the first child (f <= 7)
   const int nch = DIM == 2 ? f * f : f * f * f;
   for (int i = threadIdx.x; i < nch * NE; i += blockDim.x) sA[i] = A[i];
-  for (int ch = threadIdx.x; ch < nch; ch += blockDim.x) {
-    const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
-    sOff[ch] = cx + (long long)gf.ex * (cy + (long long)gf.ey * cz);
-  }
   __syncthreads();
-  const long long total = gc.ne * NE;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long ec = idx / NE;
-    const int t = (int)(idx - ec * NE);
-    if (touched[ec]) continue;
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long ec = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); ec < gc.ne; ec += nw) {
+    if (touched[ec]) continue;  // uniform over the warp
     const unsigned e32 = (unsigned)ec;
     const int I = (int)(e32 % (unsigned)gc.ex), J = (int)((e32 / (unsigned)gc.ex) % (unsigned)gc.ey);
     const int Kz = DIM == 3 ? (int)(e32 / ((unsigned)gc.ex * (unsigned)gc.ey)) : 0;
-    const long long base = (long long)f * I + (long long)gf.ex * ((long long)f * J + (long long)gf.ey * (DIM == 3 ? f * Kz : 0));
-    float acc = 0.f;
-    for (int ch = 0; ch < nch; ch++) acc = fmaf(__ldg(Ef + base + sOff[ch]), sA[ch * NE + t], acc);
-    Kc[idx] = acc;
+    float ev[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int ch = lane + 32 * h;
+      if (ch < nch) {
+        const int cx = ch % f, cy = (ch / f) % f, cz = DIM == 3 ? ch / (f * f) : 0;
+        ev[h] = Ef[(f * I + cx) + (long long)gf.ex * ((f * J + cy) + (long long)gf.ey * (DIM == 3 ? f * Kz + cz : 0))];
+      }
+    }
+    float acc[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; q++) acc[q] = 0.f;
+    for (int ch = 0; ch < nch; ch++) {
+      const float ech = __shfl_sync(0xffffffffu, ch < 32 ? ev[0] : ev[1], ch & 31);
+      const float* a = sA + ch * NE + lane;
+#pragma unroll
+      for (int q = 0; q < kPer; q++) acc[q] = fmaf(ech, a[32 * q], acc[q]);
+    }
+    float* out = Kc + ec * NE + lane;
+#pragma unroll
+    for (int q = 0; q < kPer; q++) out[32 * q] = acc[q];
   }
-}
-
-// Dynamic shared memory of galerkin1_kernel for coarsening factor f.
-size_t galerkin1_smem(int dim, int f) {
-  const int nd = dim == 2 ? 8 : 24, nc = dim == 2 ? 4 : 8, nch = dim == 2 ? f * f : f * f * f;
-  return (size_t)nch * (nd * nd + nc * nc) * sizeof(float);
 }
 
 // Restriction (mgops::restrict2_node, restrict_warp) with the coarse level's
@@ -476,6 +445,100 @@ __global__ void prolong_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
   const int nn = (int)gf.nn;
   for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x)
     mgops::prolong_node<DIM, false>(gf, gc, f, mf, xc, xf, nd, offf, offc);
+}
+
+// Restriction and prolongation for f = 2 in 3D, one thread per node on a 3D
+// grid (x by threads, y by blockIdx.y, z and the case by blockIdx.z), so the
+// node coordinates need no division and the weights are constants.  They form
+// the sums of restrict2_node and prolong_node term by term in the same order
+// (a skipped term there is an exact +0 here), so the values are identical.
+// Every load of a thread is unconditional within the grid and independent of
+// the fixed bits, which select afterwards: all of them are in flight at once.
+constexpr int kT2X = 128;  // threads per block along x
+
+__global__ void __launch_bounds__(kT2X)
+    restrict2x_kernel(Grid gf, Grid gc, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
+                      const float* __restrict__ rf, float* __restrict__ bc, float* __restrict__ x0,
+                      const float* __restrict__ invd, float omega, const int* __restrict__ stop) {
+  if (halted(stop)) return;
+  const int I = blockIdx.x * kT2X + threadIdx.x, J = blockIdx.y, K = blockIdx.z % gc.nz, c = blockIdx.z / gc.nz;
+  if (I >= gc.nx) return;
+  const long long offf = (long long)c * gf.nn * 3, offc = (long long)c * gc.nn * 3;
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int dz = -1; dz <= 1; dz++) {
+    const int fk = 2 * K + dz;
+    if (fk < 0 || fk >= gf.nz) continue;  // uniform over the block
+#pragma unroll
+    for (int dy = -1; dy <= 1; dy++) {
+      const int fj = 2 * J + dy;
+      if (fj < 0 || fj >= gf.ny) continue;  // uniform over the block
+      const long long row = (long long)gf.nx * (fj + (long long)gf.ny * fk);
+      float v[3][3];
+      uint8_t m[3];
+#pragma unroll
+      for (int dx = -1; dx <= 1; dx++) {
+        const int fi = 2 * I + dx;
+        const bool in = fi >= 0 && fi < gf.nx;
+        const long long n2 = row + (in ? fi : 0);
+        m[dx + 1] = in ? mf[n2] : (uint8_t)7;
+#pragma unroll
+        for (int s2 = 0; s2 < 3; s2++) v[dx + 1][s2] = in ? rf[offf + n2 * 3 + s2] : 0.f;
+      }
+#pragma unroll
+      for (int dx = -1; dx <= 1; dx++) {
+        const float wgt = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f);
+#pragma unroll
+        for (int s2 = 0; s2 < 3; s2++)
+          acc[s2] = fmaf(wgt, ((m[dx + 1] >> s2) & 1) ? 0.f : v[dx + 1][s2], acc[s2]);
+      }
+    }
+  }
+  const long long nd = I + (long long)gc.nx * (J + (long long)gc.ny * K);
+  const uint8_t mk = mc[nd];
+#pragma unroll
+  for (int s2 = 0; s2 < 3; s2++) {
+    const long long idx = nd * 3 + s2;
+    const float v = ((mk >> s2) & 1) ? 0.f : acc[s2];
+    bc[offc + idx] = v;
+    if (x0) x0[offc + idx] = omega * invd[idx] * v;
+  }
+}
+
+__global__ void __launch_bounds__(kT2X)
+    prolong2x_kernel(Grid gf, Grid gc, const uint8_t* __restrict__ mf, const float* __restrict__ xc,
+                     float* __restrict__ xf, const int* __restrict__ stop) {
+  if (halted(stop)) return;
+  const int i = blockIdx.x * kT2X + threadIdx.x, j = blockIdx.y, k = blockIdx.z % gf.nz, c = blockIdx.z / gf.nz;
+  if (i >= gf.nx) return;
+  const long long offf = (long long)c * gf.nn * 3, offc = (long long)c * gc.nn * 3;
+  const long long nd = i + (long long)gf.nx * (j + (long long)gf.ny * k);
+  const uint8_t mk = mf[nd];
+  float xv[3];
+#pragma unroll
+  for (int s = 0; s < 3; s++) xv[s] = xf[offf + nd * 3 + s];
+  // corner 0 of the coarse element holding the node, and the node's position in it
+  const int I = min(i >> 1, gc.ex - 1), J = min(j >> 1, gc.ey - 1), Kz = min(k >> 1, gc.ez - 1);
+  const int tx = i - 2 * I, ty = j - 2 * J, tz = k - 2 * Kz;
+  float cv[8][3];
+#pragma unroll
+  for (int C = 0; C < 8; C++) {
+    const long long n2 = (I + cofs(C, 0)) + (long long)gc.nx * ((J + cofs(C, 1)) + (long long)gc.ny * (Kz + cofs(C, 2)));
+#pragma unroll
+    for (int s = 0; s < 3; s++) cv[C][s] = xc[offc + n2 * 3 + s];
+  }
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int C = 0; C < 8; C++) {
+    const float wgt = (cofs(C, 0) ? 0.5f * tx : 1.f - 0.5f * tx) * (cofs(C, 1) ? 0.5f * ty : 1.f - 0.5f * ty) *
+                      (cofs(C, 2) ? 0.5f * tz : 1.f - 0.5f * tz);
+    if (wgt == 0.f) continue;
+#pragma unroll
+    for (int s = 0; s < 3; s++) acc[s] = fmaf(wgt, cv[C][s], acc[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < 3; s++)
+    if (!((mk >> s) & 1)) xf[offf + nd * 3 + s] = xv[s] + acc[s];
 }
 
 // Coarsest solve: x = A^-1 b with the dense inverse (mgops::dense_row), all
@@ -579,6 +642,12 @@ void MgHierarchy::release() {
   drop_graphs();
   if (cap) cudaStreamDestroy(cap);
   cap = nullptr;
+  if (side) cudaStreamDestroy(side);
+  side = nullptr;
+  for (cudaEvent_t* e : {&fork, &join}) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
   for (auto& e : ev) {
     if (e) cudaEventDestroy(e);
     e = nullptr;
@@ -733,38 +802,33 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
     if (i > 0) {
       const MgLevel& fl = lv[i - 1];
       coarse_mask_kernel<<<blocks(l.g.nn), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, l.mask);
-      // level 1 by the staged child matrices when their tables fit in shared
-      // memory (f = 2, 3 in 3D); otherwise the general kernel below
-      const size_t sm1 = galerkin1_smem(dim, l.f);
-      if (i == 1 && sm1 <= 160 * 1024) {
-        // flags and the list of touched elements, the untouched ones flat, the
-        // touched ones one CTA each
-        const size_t smf = (size_t)(dim == 2 ? l.f * l.f : l.f * l.f * l.f) * nd * nd * sizeof(float);
-        const long long entries = l.g.ne * nd * nd;
+      // Level 1: K_E = sum_ch E_ch A_ch for the coarse elements that no fixed
+      // fine DOF touches (warp per element, child matrices staged in shared
+      // memory, f^dim <= 64); the touched ones by the masked triple product of
+      // galerkin_kernel over their list.  Otherwise galerkin_kernel for all.
+      const int nch1 = dim == 2 ? l.f * l.f : l.f * l.f * l.f;
+      const size_t smf = (size_t)nch1 * nd * nd * sizeof(float);
+      if (i == 1 && nch1 <= 64 && smf <= 160 * 1024) {
         e = cudaMemsetAsync(touched_list, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
         if (dim == 2) {
           touched_kernel<2><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1, touched_list + 1,
                                                            touched_list);
           e = cudaFuncSetAttribute(galerkin1_flat_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-          if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(galerkin1_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
           if (e != cudaSuccess) return e;
-          galerkin1_flat_kernel<2><<<blocks(entries), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
-          galerkin1_kernel<2><<<152 * 2, 64, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
-                                                      touched_list + 1, touched_list, l.K);
+          galerkin1_flat_kernel<2><<<blocks(l.g.ne * 32), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
+          galerkin_kernel<2><<<152 * 16, 64, 0, s>>>(fl.g, l.g, l.f, nullptr, E32, K0d, fl.mask, l.mask, l.K,
+                                                     touched_list + 1, touched_list);
         } else {
           touched_kernel<3><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1, touched_list + 1,
                                                            touched_list);
           e = cudaFuncSetAttribute(galerkin1_flat_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-          if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(galerkin1_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
           if (e != cudaSuccess) return e;
-          galerkin1_flat_kernel<3><<<blocks(entries), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
-          galerkin1_kernel<3><<<152 * 2, 192, sm1, s>>>(fl.g, l.g, l.f, E32, A1, K0d, fl.mask, l.mask, touched1,
-                                                       touched_list + 1, touched_list, l.K);
+          galerkin1_flat_kernel<3><<<blocks(l.g.ne * 32), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
+          galerkin_kernel<3><<<152 * 3, 576, 0, s>>>(fl.g, l.g, l.f, nullptr, E32, K0d, fl.mask, l.mask, l.K,
+                                                     touched_list + 1, touched_list);
         }
-        nl += 2;  // the touched-element flags and the flat kernel (the staged launch is counted below)
+        nl += 2;  // the touched-element flags and the flat kernel (the list launch is counted below)
       } else if (dim == 2)
         galerkin_kernel<2><<<(unsigned)l.g.ne, 64, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask,
                                                             l.mask, l.K);
@@ -828,8 +892,8 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
       if (dim == 2)
         apply_stencil_kernel<2><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y, mode, a, c, om, stop);
       else if (l.g.nn <= kWarpNodes)
-        apply_stencil_warp_kernel<<<dim3(blocks(l.g.nn * 32), nc), 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y,
-                                                                              mode, a, c, om, stop);
+        apply_stencil_group_kernel<8><<<dim3(blocks(l.g.nn * 8), nc), 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b,
+                                                                                 y, mode, a, c, om, stop);
       else
         apply_stencil_kernel<3><<<grid, 256, 0, s>>>(l.g, l.S, l.mask, l.invd, u, w, l.b, y, mode, a, c, om, stop);
       e = cudaGetLastError();
@@ -854,7 +918,10 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   MgLevel& c = lv[li + 1];
   const bool coarsest = li + 1 == (int)lv.size() - 1;
   float* cx0 = coarsest ? nullptr : c.x[0];  // the dense solve needs no first sweep
-  if (c.f == 2 && !(dim == 3 && c.g.nn <= kWarpNodes)) {
+  if (c.f == 2 && dim == 3 && c.g.nn > kWarpRestrictNodes && c.g.ny <= 65535 && c.g.nz * nc <= 65535) {
+    dim3 gr((c.g.nx + kT2X - 1) / kT2X, c.g.ny, c.g.nz * nc);
+    restrict2x_kernel<<<gr, kT2X, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
+  } else if (c.f == 2 && !(dim == 3 && c.g.nn <= kWarpNodes)) {
     dim3 gr(blocks(c.g.nn), nc);
     if (dim == 2) restrict2_kernel<2><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
     else restrict2_kernel<3><<<gr, 256, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
@@ -870,7 +937,10 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   e = vcycle(s, li + 1, nlaunch, stop, &xc);
   if (e != cudaSuccess) return e;
   dim3 gp(blocks(l.g.nn), nc);
-  if (dim == 2) prolong_kernel<2><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
+  if (dim == 3 && c.f == 2 && l.g.ny <= 65535 && l.g.nz * nc <= 65535)
+    prolong2x_kernel<<<dim3((l.g.nx + kT2X - 1) / kT2X, l.g.ny, l.g.nz * nc), kT2X, 0, s>>>(l.g, c.g, l.mask, xc,
+                                                                                          l.x[cur], stop);
+  else if (dim == 2) prolong_kernel<2><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
   else prolong_kernel<3><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
   (*nlaunch)++;
   // post-smoothing with the same polynomial from the corrected iterate
@@ -1015,33 +1085,75 @@ __global__ void dotscal_kernel(long long n, const TA* __restrict__ a1, const TB*
   const int c = blockIdx.y, nb = gridDim.x;
   const long long base = (long long)c * n;
   using A = acc_t<TA, TB>;
-  // four independent partial sums per thread keep four loads of each operand
-  // in flight (the grid alone does not cover the latency of HBM)
+  // four independent partial sums per thread; the loads of a pass are
+  // predicated rather than left to a remainder loop, so every thread issues
+  // all of them at once (a grid of 8 CTAs per SM covers the vector in one pass
+  // of 128-bit loads)
   A t0[4] = {A(0), A(0), A(0), A(0)}, t1[4] = {A(0), A(0), A(0), A(0)};
-  const int nn = (int)n, stride = nb * blockDim.x;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + 3 * stride < nn; i += 4 * stride) {
+  const int nn = (int)n, stride = nb * blockDim.x, i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool sq = a2 != nullptr && (const void*)a2 == (const void*)a1 && b2 == a2;  // second product a1 . a1
+  int done = 0;  // elements covered by the vector pass
+  if constexpr (sizeof(TA) == 4 && sizeof(TB) == 4) {
+    auto al = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+    if (al(a1 + base) && al(b1 + base) && (a2 == nullptr || sq || (al(a2 + base) && al(b2 + base)))) {
+      const int n4 = nn >> 2;
+      const float4* A1 = reinterpret_cast<const float4*>(a1 + base);
+      const float4* B1 = reinterpret_cast<const float4*>(b1 + base);
+      for (int i = i0; i < n4; i += 4 * stride) {
+        float4 x[4], y[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          const bool in = i + k * stride < n4;
+          x[k] = in ? A1[i + k * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+          y[k] = in ? B1[i + k * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          t0[k] = fmaf(x[k].w, y[k].w, fmaf(x[k].z, y[k].z, fmaf(x[k].y, y[k].y, fmaf(x[k].x, y[k].x, t0[k]))));
+        if (sq) {
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            t1[k] = fmaf(x[k].w, x[k].w, fmaf(x[k].z, x[k].z, fmaf(x[k].y, x[k].y, fmaf(x[k].x, x[k].x, t1[k]))));
+        } else if (a2) {
+          const float4* A2 = reinterpret_cast<const float4*>(a2 + base);
+          const float4* B2 = reinterpret_cast<const float4*>(b2 + base);
+#pragma unroll
+          for (int k = 0; k < 4; k++) {
+            const bool in = i + k * stride < n4;
+            x[k] = in ? A2[i + k * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+            y[k] = in ? B2[i + k * stride] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            t1[k] = fmaf(x[k].w, y[k].w, fmaf(x[k].z, y[k].z, fmaf(x[k].y, y[k].y, fmaf(x[k].x, y[k].x, t1[k]))));
+        }
+      }
+      done = n4 << 2;
+    }
+  }
+  for (int i = done + i0; i < nn; i += 4 * stride) {
     A x[4], y[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      x[k] = (A)a1[base + i + k * stride];
-      y[k] = (A)b1[base + i + k * stride];
+      const bool in = i + k * stride < nn;
+      x[k] = in ? (A)a1[base + i + k * stride] : A(0);
+      y[k] = in ? (A)b1[base + i + k * stride] : A(0);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) t0[k] = fma(x[k], y[k], t0[k]);
-    if (a2) {
+    if (sq) {
+#pragma unroll
+      for (int k = 0; k < 4; k++) t1[k] = fma(x[k], x[k], t1[k]);
+    } else if (a2) {
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        x[k] = (A)a2[base + i + k * stride];
-        y[k] = (A)b2[base + i + k * stride];
+        const bool in = i + k * stride < nn;
+        x[k] = in ? (A)a2[base + i + k * stride] : A(0);
+        y[k] = in ? (A)b2[base + i + k * stride] : A(0);
       }
 #pragma unroll
       for (int k = 0; k < 4; k++) t1[k] = fma(x[k], y[k], t1[k]);
     }
-  }
-  for (; i < nn; i += stride) {
-    t0[0] = fma((A)a1[base + i], (A)b1[base + i], t0[0]);
-    if (a2) t1[0] = fma((A)a2[base + i], (A)b2[base + i], t1[0]);
   }
   double acc[2] = {((double)t0[0] + (double)t0[1]) + ((double)t0[2] + (double)t0[3]),
                    ((double)t1[0] + (double)t1[1]) + ((double)t1[2] + (double)t1[3])};
@@ -1224,9 +1336,22 @@ cudaError_t mg_prep(cudaStream_t s, long long n, int nc, const double* r, float*
 }
 cudaError_t mg_dotscal(cudaStream_t s, long long n, int nc, const void* a1, bool a_f32, const void* b1, bool b1_f32,
                        const void* a2, const void* b2, double* part, MgCtl* ctl, int what, int* nblocks) {
-  // up to 8 CTAs of 256 threads per SM (all cases together), each thread
-  // summing at least 8 products
-  const int nb = (int)std::min<long long>(std::max<long long>((n + 2047) / 2048, 1), 8 * 152 / nc);
+  // the CTAs of 256 threads that are resident at once on the device (all
+  // cases together), each thread summing at least 8 products
+  static int resident[3] = {0, 0, 0};
+  const int kind = a_f32 && b1_f32 ? 0 : (b1_f32 ? 1 : 2);
+  if (!resident[kind]) {
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = kind == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dotscal_kernel<float, float>, 256, 0)
+          : kind == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dotscal_kernel<double, float>, 256, 0)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dotscal_kernel<double, double>, 256, 0);
+    if (e != cudaSuccess) return e;
+    resident[kind] = std::max(nsm * per_sm, 1);
+  }
+  const int nb = (int)std::min<long long>(std::max<long long>((n + 2047) / 2048, 1), std::max(resident[kind] / nc, 1));
   const dim3 grid(nb, nc);
   if (a_f32 && b1_f32)
     dotscal_kernel<float, float><<<grid, 256, 0, s>>>(n, (const float*)a1, (const float*)b1, (const float*)a2,

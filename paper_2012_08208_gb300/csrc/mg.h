@@ -93,6 +93,10 @@ struct MgHierarchy {
   cudaGraphExec_t gx[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int gx_launches[2][2] = {{0, 0}, {0, 0}};
   cudaStream_t cap = nullptr;   // capture stream of the graphs
+  // second stream of a solve that rebuilds the hierarchy: the first FP64
+  // residual runs there while the build runs on the problem's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
   // Smoother: Chebyshev iteration of degree nu on D_l1^-1 A, whose spectrum
   // lies in (0, 1] (l1 row sums), for the interval [1 / cheb_ratio, 1].
   // Step 1 from x: x + omega D^-1 (b - A x); step k >= 2 (x_k from x_{k-1}, x_{k-2}):
