@@ -38,8 +38,11 @@ METRIC = "SIMP iter/s; K(rho)u GDOF/s vs HBM roofline; learned+mixed vs plain PC
 WORKLOAD = "cantilever3d_240x80x80_line_load"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM read + write of one finest-level 3D sweep launch at 240 x 80 x 80, from
-# an ncu capture of the same kernel (None until captured for the current kernel)
-TRAFFIC_FINE_SWEEP_3D = None
+# an ncu capture of the same kernel at the same size: the mean of three
+# consecutive launches of a SIMP step (68.1, 45.7 and 65.5 MB; below the
+# 82.0 MB of algorithmic bytes because the outputs stay in L2 for the next
+# kernel).  None once the kernel changes, until it is captured again.
+TRAFFIC_FINE_SWEEP_3D = 59.8e6
 
 
 def _peaks():

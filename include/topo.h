@@ -55,7 +55,7 @@ typedef struct tp_params {
   int n_cases;
 } tp_params;
 
-enum { TP_PREC_F64 = 0, TP_PREC_MIXED = 1 };
+enum { TP_PREC_F64 = 0, TP_PREC_MIXED = 1, TP_PREC_DW = 2 };
 enum { TP_WARM_ZERO = 0, TP_WARM_PREVIOUS = 1, TP_WARM_USER = 2 };
 /* Preconditioner of tp_solve.  TP_PRECOND_JACOBI: the persistent Jacobi-PCG
  * described above.  TP_PRECOND_MG: CG preconditioned by one geometric
@@ -204,7 +204,10 @@ tp_status tp_set(tp_problem* p, int what, const void* src, int on_device);
 
 /* Apply the boundary-conditioned operator: y = K(rho) u on free DOFs with the
  * fixed entries of u read as 0, and y_i = u_i on fixed DOFs.  precision
- * TP_PREC_F64: u, y are double[n_dof]; TP_PREC_MIXED: float[n_dof] (FP32 operator).
+ * TP_PREC_F64: u, y are double[n_dof]; TP_PREC_MIXED: float[n_dof] (FP32 operator);
+ * TP_PREC_DW: double[n_dof], the operator in double-word FP32 arithmetic
+ * (about 48 significant bits; the form of the multigrid solver's true
+ * residual at tolerances >= 1e-8 in 3D).
  * `ncopies` > 1 applies it to that many consecutive vectors (stride n_dof). */
 tp_status tp_matvec(tp_problem* p, const void* u, void* y, int precision, int ncopies,
                     int on_device);

@@ -8,6 +8,7 @@
 // penalisation of Eq. "simp_fn"; the element energy u_e^T K0 u_e enters the
 // sensitivity of Section 3.2.
 #include "pcg_common.cuh"
+#include "df32.cuh"
 
 namespace tp {
 
@@ -217,6 +218,105 @@ cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f
                : matvec_impl<2, float>(s, g, C, E, mask, u, y, ncopies, zlen, stop);
   return f64 ? matvec_impl<3, double>(s, g, C, E, mask, u, y, ncopies, zlen, stop)
              : matvec_impl<3, float>(s, g, C, E, mask, u, y, ncopies, zlen, stop);
+}
+
+// ---------------------------------------------------------------------------
+// The same operator in double-word FP32 arithmetic (df32.cuh) on FP64 data:
+// u and y are double, the moduli and C are double-words (about 48 significant
+// bits).  Each operation runs on the FP32 pipes (about 20 FP32 operations per
+// addition, 9 per multiplication) instead of GB300's FP64 pipe at 1/64 of the
+// FP32 rate; the result agrees with the FP64 operator to about 1e-13 of the
+// element force scale.
+
+__global__ void dw_moduli_kernel(const double* __restrict__ E64, df32* __restrict__ Edw, long long ne) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
+       e += (long long)gridDim.x * blockDim.x)
+    Edw[e] = df32::of(E64[e]);
+}
+
+template <int DIM>
+struct MvDwArgs {
+  Grid g;
+  TileMapG tm;
+  const df32* E;
+  const uint8_t* mask;
+  const double* u;
+  double* y;
+  long long stride;
+  const int* stop;
+  CMat<DIM, df32> C;
+};
+
+template <int DIM, int MINB = 1>
+__global__ void __launch_bounds__(TileOp<DIM, df32>::THREADS, MINB)
+    matvec_dw_kernel(const __grid_constant__ MvDwArgs<DIM> a) {
+  if (halted(a.stop)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const double* u = a.u + blockIdx.y * a.stride;
+  double* y = a.y + blockIdx.y * a.stride;
+  auto load = [&](long long node, int comp, bool) -> df32 {
+    return ((a.mask[node] >> comp) & 1) ? df32() : df32::of(u[node * DIM + comp]);
+  };
+  if constexpr (DIM == 3) {
+    TileOp<3, df32>::apply1_pre(
+        a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, load,
+        [&](long long node) -> uint8_t { return node >= 0 ? a.mask[node] : (uint8_t)0; },
+        [&](long long node, const df32(&yv)[3], const df32(&)[3], uint8_t mk) {
+#pragma unroll
+          for (int r = 0; r < 3; r++) y[node * 3 + r] = ((mk >> r) & 1) ? u[node * 3 + r] : yv[r].to_double();
+        });
+  } else {
+    TileOp<DIM, df32>::template apply<1>(
+        a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1, [&](long long node, int comp, bool own) {
+          return load(node, comp, own);
+        },
+        [&](long long node, int, const df32(&yv)[DIM], const df32(&)[DIM]) {
+          const uint8_t mk = a.mask[node];
+#pragma unroll
+          for (int r = 0; r < DIM; r++)
+            y[node * DIM + r] = ((mk >> r) & 1) ? u[node * DIM + r] : yv[r].to_double();
+        });
+  }
+}
+
+template <int DIM>
+static cudaError_t matvec_dw_impl(cudaStream_t s, const Grid& g, const double* C, const df32* E,
+                                  const uint8_t* mask, const double* u, double* y, int ncopies, int zlen,
+                                  const int* stop) {
+  using Op = TileOp<DIM, df32>;
+  MvDwArgs<DIM> a;
+  a.g = g;
+  a.tm = Op::map(g, zlen);
+  a.E = E;
+  a.mask = mask;
+  a.u = u;
+  a.y = y;
+  a.stride = g.nn * DIM;
+  a.stop = stop;
+  constexpr int n = DIM == 2 ? 25 : 324;
+  for (int i = 0; i < n; i++) a.C.k[i] = df32::of(C[i]);
+  const size_t smem = Op::smem_bytes();
+  auto kern = DIM == 3 ? matvec_dw_kernel<DIM, 2> : matvec_dw_kernel<DIM, 1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (DIM == 3) {
+    static int resident = 0;
+    if (!resident) resident = resident_ctas(kern, Op::THREADS, smem);
+    if (resident > 0) a.tm = Op::map(g, zlen_for(g, resident));
+  }
+  kern<<<dim3(a.tm.ntiles, ncopies), Op::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dw_moduli(cudaStream_t s, const double* E64, void* Edw, long long ne) {
+  dw_moduli_kernel<<<grid_for(ne), 256, 0, s>>>(E64, (df32*)Edw, ne);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_matvec_dw(cudaStream_t s, const Grid& g, const double* C, const void* Edw, const uint8_t* mask,
+                             const double* u, double* y, int ncopies, int zlen, const int* stop) {
+  if (g.dim == 2) return matvec_dw_impl<2>(s, g, C, (const df32*)Edw, mask, u, y, ncopies, zlen, stop);
+  return matvec_dw_impl<3>(s, g, C, (const df32*)Edw, mask, u, y, ncopies, zlen, stop);
 }
 
 // ---------------------------------------------------------------------------

@@ -68,6 +68,11 @@ cudaError_t launch_diag(cudaStream_t s, const Grid& g, const double* K0, const d
 cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f64, const void* E,
                           const uint8_t* mask, const void* u, void* y, int ncopies, int zlen,
                           const int* stop = nullptr);
+// The same operator in double-word FP32 arithmetic: u, y double; Edw the moduli
+// as double-words (launch_dw_moduli converts E64).
+cudaError_t launch_dw_moduli(cudaStream_t s, const double* E64, void* Edw, long long ne);
+cudaError_t launch_matvec_dw(cudaStream_t s, const Grid& g, const double* C, const void* Edw, const uint8_t* mask,
+                             const double* u, double* y, int ncopies, int zlen, const int* stop = nullptr);
 // Multigrid finest-level sweep on the FP32 operator (mode 1: smoothing step
 // y = ca u + cc w + om D^-1 (b - K u), w optional and y may alias w; mode 2:
 // residual y = b - K u; 0 on fixed DOFs), ncopies vectors of stride n_dof;

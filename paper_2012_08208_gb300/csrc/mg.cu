@@ -33,6 +33,7 @@ struct MgC {
 };
 
 __constant__ float c_K0[24 * 24];  // level-0 element matrix (unit modulus), row-major
+__constant__ float c_K0abs[24];    // its l1 row sums, sum_b |K0[a][b]|
 
 using mgops::node_index;
 using mgops::w1;
@@ -226,6 +227,18 @@ __global__ void diag_kernel(Grid g, const float* __restrict__ K, const float* __
       if (ei < 0 || ej < 0 || ek < 0 || ei >= g.ex || ej >= g.ey || ek >= g.ez) continue;
       const long long e = ei + (long long)g.ex * (ej + (long long)g.ey * ek);
       constexpr int ND = MgC<DIM>::ND;
+      if (!K) {  // level 0: with no fixed node in the element, row (c, r) sums to E_e sum_b |K0|
+        uint8_t any = 0;
+#pragma unroll
+        for (int n = 0; n < NC; n++)
+          any |= mask[node_index(g, ei + cofs(n, 0), ej + cofs(n, 1), ek + (DIM == 3 ? cofs(n, 2) : 0))];
+        if (!any) {
+          const float Ee = E[e];
+#pragma unroll
+          for (int r = 0; r < DIM; r++) d[r] = fmaf(Ee, c_K0abs[c * DIM + r], d[r]);
+          continue;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < DIM; r++)
         for (int b = 0; b < ND; b++) {
@@ -764,6 +777,13 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
   std::vector<float> k0f(nd * nd);
   for (int i = 0; i < nd * nd; i++) k0f[i] = (float)K0[i];
   cudaError_t e = cudaMemcpyToSymbolAsync(c_K0, k0f.data(), nd * nd * sizeof(float), 0, cudaMemcpyHostToDevice, s);
+  k0abs.assign(nd, 0.f);
+  for (int a = 0; a < nd; a++) {
+    double r = 0.0;
+    for (int b = 0; b < nd; b++) r += std::fabs((double)k0f[a * nd + b]);
+    k0abs[a] = (float)r;
+  }
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_K0abs, k0abs.data(), nd * sizeof(float), 0, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && !K0d) e = cudaMalloc((void**)&K0d, nd * nd * sizeof(float));
   if (e == cudaSuccess) e = cudaMemcpyAsync(K0d, k0f.data(), nd * nd * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return e;

@@ -96,6 +96,7 @@ struct MgHierarchy {
   // second stream of a solve that rebuilds the hierarchy: the first FP64
   // residual runs there while the build runs on the problem's stream
   cudaStream_t side = nullptr;
+  std::vector<float> k0abs;  // host copy of the l1 row sums of K0 (the source of an async upload)
   cudaEvent_t fork = nullptr, join = nullptr;
   // Smoother: Chebyshev iteration of degree nu on D_l1^-1 A, whose spectrum
   // lies in (0, 1] (l1 row sums), for the interval [1 / cheb_ratio, 1].

@@ -59,6 +59,8 @@ struct tp_problem {
   tp::MgHierarchy* mg = nullptr; // multigrid preconditioner (built on first use)
   long long E_version = 0;       // bumped whenever the moduli are recomputed
   long long diag_version = -1;   // moduli version of inv32 / inv64 (the Jacobi scaling)
+  void* Edw = nullptr;           // moduli as double-words (float pairs), formed on first use
+  long long dw_version = -1;     // moduli version of Edw
   bool profile = false;          // time the multigrid finest-level launches
   int filter_mode = 0;           // TP_FILTER_SENSITIVITY or TP_FILTER_DENSITY
   int oc_passes = 0, oc_root = 0;  // diagnostics of the last OC update

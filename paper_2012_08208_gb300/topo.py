@@ -19,7 +19,7 @@ TP_OK, TP_ERR_ARG, TP_ERR_CUDA, TP_ERR_OOM, TP_ERR_NOT_CONVERGED, TP_ERR_BREAKDO
     TP_ERR_STATE = range(8)
 STATUS_NAMES = ["TP_OK", "TP_ERR_ARG", "TP_ERR_CUDA", "TP_ERR_OOM", "TP_ERR_NOT_CONVERGED",
                 "TP_ERR_BREAKDOWN", "TP_ERR_TIMEOUT", "TP_ERR_STATE"]
-TP_PREC_F64, TP_PREC_MIXED = 0, 1
+TP_PREC_F64, TP_PREC_MIXED, TP_PREC_DW = 0, 1, 2
 TP_WARM_ZERO, TP_WARM_PREVIOUS, TP_WARM_USER = 0, 1, 2
 TP_FILTER_SENSITIVITY = 0
 TP_FILTER_DENSITY = 1
@@ -518,7 +518,7 @@ class Problem:
 
     def matvec(self, u, precision=TP_PREC_F64, ncopies=1, out=None):
         if isinstance(u, np.ndarray):
-            dt = np.float64 if precision == TP_PREC_F64 else np.float32
+            dt = np.float32 if precision == TP_PREC_MIXED else np.float64
             u = np.ascontiguousarray(u, dtype=dt)
             if out is None:
                 out = np.empty_like(u)

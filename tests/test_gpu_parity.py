@@ -2,6 +2,7 @@
 same seeded inputs.  Tolerances (written per test):
   * FP64 operator:   |y - y_ref| <= 1e-12 * (|K| |u|)_i          (rounding order only)
   * FP32 operator:   |y - y_ref| <= 2e-5 * (|K| |u|)_i           (FP32 K0, E and sums)
+  * double-word op.: |y - y_ref| <= 1e-12 * (|K| |u|)_i          (48-bit FP32 pairs, 3u^2 per addition)
   * solve / loop:    compliance rel <= 1e-8, densities max-abs <= 1e-6, lambda rel <= 1e-9
   * filter / sens:   rel <= 1e-12 (FP64 both sides, same formula)
 """
@@ -54,6 +55,26 @@ def test_matvec_f64_and_f32(topo, prob):
     Y = p.matvec(U.ravel(), topo.TP_PREC_F64, ncopies=3).reshape(3, -1)
     for k in range(3):
         assert np.allclose(Y[k], fem.matvec_bc(prob, rho, U[k]), rtol=1e-12, atol=1e-12 * np.abs(Y[k]).max())
+    p.close()
+
+
+@pytest.mark.parametrize("prob", GRIDS, ids=lambda p: p.name + f"_nc{p.n_cases}")
+def test_matvec_double_word(topo, prob):
+    """The double-word FP32 operator (the multigrid solver's true residual at
+    tolerances >= 1e-8 in 3D) against the FP64 oracle, on a density field with
+    the void modulus (Emin = 1e-9) in a third of the elements and on smooth
+    displacements (the case where the element strains cancel most)."""
+    rng = np.random.default_rng(57)
+    rho = np.where(rng.random(prob.n_el) < 0.33, 1e-3, W.random_density(prob.n_el, seed=58))
+    p = topo.Problem.from_workload(prob)
+    p.set_density(rho)
+    xs = np.linspace(0.0, 1.0, prob.n_dof)
+    for u in (W.random_vector(prob.n_dof, seed=59), 1.0 + 1e-3 * np.sin(7.0 * xs)):
+        u = np.where(prob.fixed.astype(bool), 0.0, u)
+        y_ref = fem.matvec_bc(prob, rho, u)
+        bound = _abs_product(prob, rho, u)
+        ydw = p.matvec(u, topo.TP_PREC_DW)
+        assert np.all(np.abs(ydw - y_ref) <= 1e-12 * bound + 1e-300), np.max(np.abs(ydw - y_ref) / (bound + 1e-300))
     p.close()
 
 
