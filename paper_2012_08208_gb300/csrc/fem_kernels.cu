@@ -616,7 +616,10 @@ cudaError_t launch_true_residual(cudaStream_t s, const Solver& S, bool f64, bool
 }
 
 // ---------------------------------------------------------------------------
-// Compliance and sensitivities (FP64).  ce_e = sum_k u_e^T K0 u_e = g^T C g.
+// Compliance and sensitivities.  ce_e = sum_k u_e^T K0 u_e = g^T C g, in FP64
+// in 2D; in 3D in double-word FP32 arithmetic (df32.cuh, about 1e-14 relative:
+// GB300's FP64 pipe made the FP64 energy of 1.5 M elements take 0.53 ms), summed
+// over the cases in FP64.  The compliance f.u stays FP64.
 
 template <int DIM>
 struct SensArgs {
@@ -630,6 +633,7 @@ struct SensArgs {
   double* dc;
   double* part;
   CMat<DIM, double> C;
+  CMat<DIM, df32> Cdw;
 };
 
 template <int DIM>
@@ -652,15 +656,15 @@ __global__ void __launch_bounds__(256) sens_kernel(const __grid_constant__ SensA
         }
         ce += q4_energy(ux, uy, a.C);
       } else {
-        double u[8][3];
+        df32 u[8][3];
 #pragma unroll
         for (int m = 0; m < 8; m++) {
           const long long node = (ex + cofs(m, 0)) +
                                  (long long)g.nx * ((ey + cofs(m, 1)) + (long long)g.ny * (ez + cofs(m, 2)));
 #pragma unroll
-          for (int s = 0; s < 3; s++) u[m][s] = a.x64[(long long)(cs * 3 + s) * g.nn + node];
+          for (int s = 0; s < 3; s++) u[m][s] = df32::of(a.x64[(long long)(cs * 3 + s) * g.nn + node]);
         }
-        ce += h8_energy(u, a.C);
+        ce += h8_energy(u, a.Cdw).to_double();
       }
     }
     const double r = a.rho[e];
@@ -703,6 +707,7 @@ static cudaError_t sens_impl(cudaStream_t s, const Grid& g, int nc, const double
   a.dc = dc;
   a.part = part;
   fill_c<DIM, double>(a.C, C);
+  for (int i = 0; i < (DIM == 2 ? 25 : 324); i++) a.Cdw.k[i] = df32::of(C[i]);
   const int grid = grid_for(g.ne > g.nn * nc * DIM ? g.ne : g.nn * nc * DIM);
   sens_kernel<DIM><<<grid, 256, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();

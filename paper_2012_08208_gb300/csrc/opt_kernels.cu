@@ -31,6 +31,7 @@ struct FilterArgs {
   const double* rho;
   const double* dc;
   double* out;
+  double wsum;  // sum of all weights in tap order: the row sum of an element whose taps all lie inside
   int off[3 * kMaxTaps];
   double w[kMaxTaps];
 };
@@ -70,13 +71,24 @@ __global__ void __launch_bounds__(256) filter_kernel(const __grid_constant__ Fil
     const int gx = x0 + tx, gy = y0 + ty, gz = DIM == 3 ? z0 + tz : 0;
     if (gx >= g.ex || gy >= g.ey || gz >= g.ez) continue;
     double num = 0.0, den = 0.0;
-    for (int k = 0; k < a.ntaps; k++) {
-      const int dx = a.off[3 * k], dy = a.off[3 * k + 1], dz = a.off[3 * k + 2];
-      const int nx = gx + dx, ny = gy + dy, nz = gz + dz;
-      if (nx < 0 || nx >= g.ex || ny < 0 || ny >= g.ey || nz < 0 || nz >= g.ez) continue;
-      const int sidx = ((DIM == 3 ? tz + R + dz : 0) * SY + (ty + R + dy)) * SX + (tx + R + dx);
-      num = fma(a.w[k], sG[sidx], num);
-      den += a.w[k];
+    const bool inside = gx >= R && gx + R < g.ex && gy >= R && gy + R < g.ey &&
+                        (DIM == 2 || (gz >= R && gz + R < g.ez));
+    if (inside) {  // every tap lies in the mesh: the row sum is the precomputed total (same order)
+      for (int k = 0; k < a.ntaps; k++) {
+        const int dx = a.off[3 * k], dy = a.off[3 * k + 1], dz = a.off[3 * k + 2];
+        const int sidx = ((DIM == 3 ? tz + R + dz : 0) * SY + (ty + R + dy)) * SX + (tx + R + dx);
+        num = fma(a.w[k], sG[sidx], num);
+      }
+      den = a.wsum;
+    } else {
+      for (int k = 0; k < a.ntaps; k++) {
+        const int dx = a.off[3 * k], dy = a.off[3 * k + 1], dz = a.off[3 * k + 2];
+        const int nx = gx + dx, ny = gy + dy, nz = gz + dz;
+        if (nx < 0 || nx >= g.ex || ny < 0 || ny >= g.ey || nz < 0 || nz >= g.ez) continue;
+        const int sidx = ((DIM == 3 ? tz + R + dz : 0) * SY + (ty + R + dy)) * SX + (tx + R + dx);
+        num = fma(a.w[k], sG[sidx], num);
+        den += a.w[k];
+      }
     }
     const long long e = gx + (long long)g.ex * (gy + (long long)g.ey * gz);
     a.out[e] = a.mode == 0 ? num / (a.rho[e] * den) : (a.mode == 1 ? num / den : (a.mode == 2 ? num : den));
@@ -97,6 +109,8 @@ cudaError_t launch_filter(cudaStream_t s, const FilterLaunch& Fl, int mode, cons
     }
     a.w[k] = Fl.w[k];
   }
+  a.wsum = 0.0;
+  for (int k = 0; k < Fl.ntaps; k++) a.wsum += Fl.w[k];
   a.R = R;
   a.mode = mode;
   a.rho = rho;

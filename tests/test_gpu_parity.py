@@ -4,7 +4,7 @@ same seeded inputs.  Tolerances (written per test):
   * FP32 operator:   |y - y_ref| <= 2e-5 * (|K| |u|)_i           (FP32 K0, E and sums)
   * double-word op.: |y - y_ref| <= 1e-12 * (|K| |u|)_i          (48-bit FP32 pairs, 3u^2 per addition)
   * solve / loop:    compliance rel <= 1e-8, densities max-abs <= 1e-6, lambda rel <= 1e-9
-  * filter / sens:   rel <= 1e-12 (FP64 both sides, same formula)
+  * filter / sens:   rel <= 1e-12 (FP64 both sides, same formula; 3D element energies in double-word FP32)
 """
 import numpy as np
 import pytest
