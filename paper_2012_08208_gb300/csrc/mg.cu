@@ -356,6 +356,102 @@ __global__ void __launch_bounds__(MgC<DIM>::ND * MgC<DIM>::ND, DIM == 3 ? 3 : 16
   }
 }
 
+// The same Galerkin product for f = 2 (every coarsening of the 2:1 levels):
+// the child offsets are bit fields, the element coordinates 32-bit, and the
+// interpolation weights (the same for every element) are formed once per CTA
+// and stored transposed, Phi_q[C][n], so a thread reads its weight column as
+// 128-bit words.  The CTAs stride over the coarse elements (or the list).  The
+// sums are those of galerkin_kernel, term by term in the same order, so the
+// values are identical; this form issues about a third of the instructions
+// (galerkin_kernel: about 1,900 per thread at level 2 of the 240 x 80 x 80
+// hierarchy, issue slots 72 % busy, 0.93 ms).
+template <int DIM>
+__global__ void __launch_bounds__(MgC<DIM>::ND * MgC<DIM>::ND, DIM == 3 ? 3 : 16)
+    galerkin2_kernel(Grid gf, Grid gc, const float* __restrict__ Kf, const float* __restrict__ Ef,
+                     const float* __restrict__ K0g, const uint8_t* __restrict__ mf, const uint8_t* __restrict__ mc,
+                     float* __restrict__ Kc, const int* __restrict__ list, const int* __restrict__ list_count) {
+  constexpr int NC = MgC<DIM>::NC, ND = MgC<DIM>::ND, NE = ND * ND, NCH = NC;  // 2^dim children
+  __shared__ float sK[NCH * NE];
+  __shared__ float sT[NCH * NE];
+  __shared__ __align__(16) float sPt[NCH * NC * NC];  // [child][C][n]
+  __shared__ uint8_t sM[NCH * NC];
+  const int t = threadIdx.x;  // blockDim.x == NE
+  for (int i = t; i < NCH * NC * NC; i += blockDim.x) {
+    const int q = i / (NC * NC), C = (i / NC) % NC, n = i % NC;
+    const int cx = q & 1, cy = (q >> 1) & 1, cz = q >> 2;
+    auto w2 = [](int o, int p) { return o ? 0.5f * (float)p : 1.f - 0.5f * (float)p; };  // w1 for f = 2
+    float w = w2(cofs(C, 0), cx + cofs(n, 0)) * w2(cofs(C, 1), cy + cofs(n, 1));
+    if (DIM == 3) w *= w2(cofs(C, 2), cz + cofs(n, 2));
+    sPt[i] = w;
+  }
+  const float k0t = Kf ? 0.f : K0g[t];
+  const int a = t / ND, b = t % ND;
+  const int C = b / DIM, s2 = b % DIM;   // stage 1 column
+  const int C1 = a / DIM, r = a % DIM;   // stage 2 row
+  const unsigned ex = (unsigned)gc.ex, ey = (unsigned)gc.ey;
+  const int nlist = list ? *list_count : (int)gc.ne;
+  for (int li = blockIdx.x; li < nlist; li += gridDim.x) {
+    const unsigned ec = list ? (unsigned)list[li] : (unsigned)li;
+    const int I = (int)(ec % ex), J = (int)((ec / ex) % ey), Kz = DIM == 3 ? (int)(ec / (ex * ey)) : 0;
+    float kv[NCH];
+#pragma unroll
+    for (int q = 0; q < NCH; q++) {
+      const long long e = (2 * I + (q & 1)) + (long long)gf.ex * ((2 * J + ((q >> 1) & 1)) +
+                                                                 (long long)gf.ey * (DIM == 3 ? 2 * Kz + (q >> 2) : 0));
+      kv[q] = Kf ? Kf[e * NE + t] : Ef[e] * k0t;
+    }
+    if (t < NCH * NC) {
+      const int q = t / NC, n = t % NC;
+      sM[t] = mf[node_index(gf, 2 * I + (q & 1) + cofs(n, 0), 2 * J + ((q >> 1) & 1) + cofs(n, 1),
+                            DIM == 3 ? 2 * Kz + (q >> 2) + cofs(n, 2) : 0)];
+    }
+    __syncthreads();  // weights and fixed bits staged; the previous element's stage 2 is done
+#pragma unroll
+    for (int q = 0; q < NCH; q++) {
+      const bool fa = (sM[q * NC + a / DIM] >> (a % DIM)) & 1, fb = (sM[q * NC + b / DIM] >> (b % DIM)) & 1;
+      sK[q * NE + t] = (fa || fb) ? 0.f : kv[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NCH; q++) {  // T_q[a][(C, s)] = sum_n K_q[a][(n, s)] Phi_q[n][C]
+      float ph[NC];
+#pragma unroll
+      for (int n4 = 0; n4 < NC; n4 += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(&sPt[(q * NC + C) * NC + n4]);
+        ph[n4] = v.x;
+        ph[n4 + 1] = v.y;
+        ph[n4 + 2] = v.z;
+        ph[n4 + 3] = v.w;
+      }
+      float v = 0.f;
+#pragma unroll
+      for (int n = 0; n < NC; n++) v = fmaf(sK[q * NE + a * ND + n * DIM + s2], ph[n], v);
+      sT[q * NE + t] = v;
+    }
+    __syncthreads();
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < NCH; q++) {  // K_E[(C1, r)][b] += sum_n Phi_q[n][C1] T_q[(n, r)][b]
+      float ph[NC];
+#pragma unroll
+      for (int n4 = 0; n4 < NC; n4 += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(&sPt[(q * NC + C1) * NC + n4]);
+        ph[n4] = v.x;
+        ph[n4 + 1] = v.y;
+        ph[n4 + 2] = v.z;
+        ph[n4 + 3] = v.w;
+      }
+#pragma unroll
+      for (int n = 0; n < NC; n++) acc = fmaf(ph[n], sT[q * NE + (n * DIM + r) * ND + b], acc);
+    }
+    const int Ca = a / DIM, ra = a % DIM, Cb = b / DIM, rb = b % DIM;
+    const uint8_t ma = mc[node_index(gc, I + cofs(Ca, 0), J + cofs(Ca, 1), Kz + (DIM == 3 ? cofs(Ca, 2) : 0))];
+    const uint8_t mb = mc[node_index(gc, I + cofs(Cb, 0), J + cofs(Cb, 1), Kz + (DIM == 3 ? cofs(Cb, 2) : 0))];
+    if (((ma >> ra) & 1) || ((mb >> rb) & 1)) acc = 0.f;
+    Kc[(long long)ec * NE + t] = acc;
+  }
+}
+
 // Coarse elements whose footprint holds a fixed fine DOF: touched[ec] = 1
 // when any of the (f + 1)^dim fine nodes inside coarse element ec has a fixed
 // bit (its children's matrices are masked); those elements are also appended
@@ -837,18 +933,34 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
           e = cudaFuncSetAttribute(galerkin1_flat_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
           if (e != cudaSuccess) return e;
           galerkin1_flat_kernel<2><<<blocks(l.g.ne * 32), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
-          galerkin_kernel<2><<<152 * 16, 64, 0, s>>>(fl.g, l.g, l.f, nullptr, E32, K0d, fl.mask, l.mask, l.K,
-                                                     touched_list + 1, touched_list);
+          if (l.f == 2)
+            galerkin2_kernel<2><<<152 * 16, 64, 0, s>>>(fl.g, l.g, nullptr, E32, K0d, fl.mask, l.mask, l.K,
+                                                        touched_list + 1, touched_list);
+          else
+            galerkin_kernel<2><<<152 * 16, 64, 0, s>>>(fl.g, l.g, l.f, nullptr, E32, K0d, fl.mask, l.mask, l.K,
+                                                       touched_list + 1, touched_list);
         } else {
           touched_kernel<3><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1, touched_list + 1,
                                                            touched_list);
           e = cudaFuncSetAttribute(galerkin1_flat_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
           if (e != cudaSuccess) return e;
           galerkin1_flat_kernel<3><<<blocks(l.g.ne * 32), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
-          galerkin_kernel<3><<<152 * 3, 576, 0, s>>>(fl.g, l.g, l.f, nullptr, E32, K0d, fl.mask, l.mask, l.K,
-                                                     touched_list + 1, touched_list);
+          if (l.f == 2)
+            galerkin2_kernel<3><<<152 * 3, 576, 0, s>>>(fl.g, l.g, nullptr, E32, K0d, fl.mask, l.mask, l.K,
+                                                        touched_list + 1, touched_list);
+          else
+            galerkin_kernel<3><<<152 * 3, 576, 0, s>>>(fl.g, l.g, l.f, nullptr, E32, K0d, fl.mask, l.mask, l.K,
+                                                       touched_list + 1, touched_list);
         }
         nl += 2;  // the touched-element flags and the flat kernel (the list launch is counted below)
+      } else if (l.f == 2) {  // CTAs striding over the elements (weights formed once per CTA)
+        const unsigned gr2 = (unsigned)std::min<long long>(l.g.ne, dim == 2 ? 152 * 16 * 4 : 152 * 3 * 8);
+        if (dim == 2)
+          galerkin2_kernel<2><<<gr2, 64, 0, s>>>(fl.g, l.g, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask, l.mask, l.K,
+                                                 nullptr, nullptr);
+        else
+          galerkin2_kernel<3><<<gr2, 576, 0, s>>>(fl.g, l.g, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask, l.mask, l.K,
+                                                  nullptr, nullptr);
       } else if (dim == 2)
         galerkin_kernel<2><<<(unsigned)l.g.ne, 64, 0, s>>>(fl.g, l.g, l.f, fl.K, i == 1 ? E32 : nullptr, K0d, fl.mask,
                                                             l.mask, l.K);
