@@ -148,10 +148,11 @@ static cudaError_t reset_bar(tp_problem* p) {
 
 // Finest multigrid level: the problem's FP32 strain-form operator on all cases.
 static cudaError_t mg_fine_op(void* ctx, cudaStream_t s, const float* u, const float* w, const float* b,
-                              const float* invd, float* y, int mode, float a, float c, float om, const int* stop) {
+                              const float* invd, float* y, int mode, float a, float c, float om, const int* stop,
+                              int dots) {
   tp_problem* p = (tp_problem*)ctx;
   return launch_mg_sweep(s, p->g, p->C.data(), p->E32, p->mask, invd, u, w, b, y, p->nc, p->zlen, mode, a, c, om,
-                         stop);
+                         stop, dots, p->part, p->mg->ctl);
 }
 
 // CG preconditioned by one FP32 multigrid V-cycle per iteration
@@ -282,28 +283,44 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
   // u64, x, r, p stay FP64 and the operator is FP64.
   float* z32 = nullptr;
   float* r32 = l0.b;  // the V-cycle's right-hand side doubles as the FP32 residual
+  // In 3D the FP32 iteration forms its dot products in the epilogues of the
+  // kernels that produce the vectors: p.q in the operator q = K p, r.z and r.r
+  // in the V-cycle's last finest-level step (which reads r and writes z); the
+  // last CTA of each completes the scalars.  Elsewhere a dot kernel follows.
+  const bool fuse_dots = p->dim == 3;
   auto issue_iter = [&](cudaStream_t cs, bool u64, int* nlk) -> cudaError_t {
     cudaError_t e;
+    const bool fz = !u64 && fuse_dots;
     if (u64) {
       e = launch_matvec(cs, p->g, p->C.data(), true, p->E64, p->mask, pp, q, nc, p->zlen, stop);
       if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, pp, false, q, false, nullptr, nullptr, p->part, ctl, 0, nullptr);
       if (e == cudaSuccess) e = mg_update_xr(cs, n, nc, ctl, x, pp, r, q, false, r32, l0.x[0], l0.invd, M.omega);
+      *nlk += 3;
+    } else if (fz) {
+      e = launch_matvec_dots(cs, p->g, p->C.data(), p->E32, p->mask, M.p32, M.q32, nc, p->zlen, stop, p->part, ctl,
+                             0);
+      if (e == cudaSuccess) e = mg_update32(cs, n, nc, ctl, M.d32, M.p32, r32, M.q32, l0.x[0], l0.invd, M.omega);
+      *nlk += 2;
     } else {
       e = launch_matvec(cs, p->g, p->C.data(), false, p->E32, p->mask, M.p32, M.q32, nc, p->zlen, stop);
       if (e == cudaSuccess)
         e = mg_dotscal(cs, n, nc, M.p32, true, M.q32, true, nullptr, nullptr, p->part, ctl, 0, nullptr);
       if (e == cudaSuccess) e = mg_update32(cs, n, nc, ctl, M.d32, M.p32, r32, M.q32, l0.x[0], l0.invd, M.omega);
+      *nlk += 3;
     }
-    *nlk += 3;
+    M.fine_dots = fz ? 1 : -1;
     if (e == cudaSuccess) e = M.vcycle(cs, 0, nlk, stop, &z32);
+    M.fine_dots = -1;
     if (u64) {
       if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, r, false, z32, true, r, r, p->part, ctl, 1, nullptr);
       if (e == cudaSuccess) e = mg_update_p(cs, n, nc, ctl, pp, M.p32, z32);
+      *nlk += 2;
     } else {
-      if (e == cudaSuccess) e = mg_dotscal(cs, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 1, nullptr);
+      if (e == cudaSuccess && !fz)
+        e = mg_dotscal(cs, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 1, nullptr);
       if (e == cudaSuccess) e = mg_update_p32(cs, n, nc, ctl, M.p32, z32);
+      *nlk += fz ? 1 : 2;
     }
-    *nlk += 2;
     return e;
   };
   // The graph of kGraphIters iterations for u64, with the finest sweeps
@@ -392,16 +409,20 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     } else {
       // segment start z = V(r), p = z (d = 0), then replays of the graph of
       // kGraphIters iterations with the device-side stop flag
-      TPCK(M.vcycle(s, 0, &nl, nullptr, &z32), "v-cycle");
+      const bool fz = !use64 && fuse_dots;
+      M.fine_dots = fz ? 2 : -1;
+      const cudaError_t ev = M.vcycle(s, 0, &nl, nullptr, &z32);
+      M.fine_dots = -1;
+      TPCK(ev, "v-cycle");
       if (use64) {
         TPCK(mg_dotscal(s, n, nc, r, false, z32, true, r, r, p->part, ctl, 2, nullptr), "dot kernel");
         TPCK(mg_update_p(s, n, nc, ctl, pp, M.p32, z32), "update kernel");
       } else {
         TPCK(cudaMemsetAsync(M.d32, 0, (size_t)nc * n * sizeof(float), s), "memset");
-        TPCK(mg_dotscal(s, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 2, nullptr), "dot kernel");
+        if (!fz) TPCK(mg_dotscal(s, n, nc, r32, true, z32, true, r32, r32, p->part, ctl, 2, nullptr), "dot kernel");
         TPCK(mg_update_p32(s, n, nc, ctl, M.p32, z32), "update kernel");
       }
-      nl += 2;
+      nl += fz ? 1 : 2;
       st = graph(use64);
       if (st != TP_OK) return st;
       const int gi = use64 ? 1 : 0, gt = M.timing ? 1 : 0;

@@ -9,6 +9,7 @@
 // sensitivity of Section 3.2.
 #include "pcg_common.cuh"
 #include "df32.cuh"
+#include "mg_dots.cuh"
 
 namespace tp {
 
@@ -114,6 +115,11 @@ struct MvArgs {
   T* y;
   long long stride;
   const int* stop;  // optional: return at once when set
+  // PCG dot product p.q formed in the epilogue (3D FP32): dots >= 0 adds u.y
+  // (u read as 0 on fixed DOFs) and completes it as pcg_dots_complete(what = dots)
+  int dots;
+  double* part;
+  MgCtl* ctl;
   CMat<DIM, T> C;
 };
 
@@ -128,14 +134,23 @@ __global__ void __launch_bounds__(TileOp<DIM, T>::THREADS, MINB)
     return ((a.mask[node] >> comp) & 1) ? T(0) : u[node * DIM + comp];
   };
   if constexpr (DIM == 3) {
+    T d0 = T(0);  // this thread's share of the fused p.q
     // the fixed bits of the output node are loaded before the layer's arithmetic
     TileOp<3, T>::apply1_pre(
         a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, load,
         [&](long long node) -> uint8_t { return node >= 0 ? a.mask[node] : (uint8_t)0; },
-        [&](long long node, const T(&yv)[3], const T(&)[3], uint8_t mk) {
+        [&](long long node, const T(&yv)[3], const T(&us)[3], uint8_t mk) {
 #pragma unroll
-          for (int r = 0; r < 3; r++) y[node * 3 + r] = ((mk >> r) & 1) ? u[node * 3 + r] : yv[r];
+          for (int r = 0; r < 3; r++) {
+            const T v = ((mk >> r) & 1) ? u[node * 3 + r] : yv[r];
+            y[node * 3 + r] = v;
+            if (a.dots >= 0) d0 = fma(us[r], v, d0);
+          }
         });
+    if (a.dots >= 0) {
+      double acc[2] = {(double)d0, 0.0};
+      pcg_dots_complete(acc, a.part, a.ctl, a.dots);
+    }
   } else {
     TileOp<DIM, T>::template apply<1>(
         a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1, [&](long long node, int comp, bool own) {
@@ -185,7 +200,8 @@ static int resident_ctas(K kern, int threads, size_t smem) {
 
 template <int DIM, typename T>
 static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, const void* E,
-                               const uint8_t* mask, const void* u, void* y, int ncopies, int zlen, const int* stop) {
+                               const uint8_t* mask, const void* u, void* y, int ncopies, int zlen, const int* stop,
+                               int dots = -1, double* part = nullptr, MgCtl* ctl = nullptr) {
   using Op = TileOp<DIM, T>;
   MvArgs<DIM, T> a;
   a.g = g;
@@ -196,6 +212,9 @@ static cudaError_t matvec_impl(cudaStream_t s, const Grid& g, const double* C, c
   a.y = (T*)y;
   a.stride = g.nn * DIM;
   a.stop = stop;
+  a.dots = DIM == 3 && sizeof(T) == 4 ? dots : -1;
+  a.part = part;
+  a.ctl = ctl;
   fill_c<DIM, T>(a.C, C);
   const size_t smem = Op::smem_bytes();
   // H8 FP32: 3 resident CTAs per SM (80 registers); measured fastest
@@ -218,6 +237,13 @@ cudaError_t launch_matvec(cudaStream_t s, const Grid& g, const double* C, bool f
                : matvec_impl<2, float>(s, g, C, E, mask, u, y, ncopies, zlen, stop);
   return f64 ? matvec_impl<3, double>(s, g, C, E, mask, u, y, ncopies, zlen, stop)
              : matvec_impl<3, float>(s, g, C, E, mask, u, y, ncopies, zlen, stop);
+}
+
+cudaError_t launch_matvec_dots(cudaStream_t s, const Grid& g, const double* C, const float* E32, const uint8_t* mask,
+                               const float* u, float* y, int ncopies, int zlen, const int* stop, double* part,
+                               MgCtl* ctl, int what) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  return matvec_impl<3, float>(s, g, C, E32, mask, u, y, ncopies, zlen, stop, what, part, ctl);
 }
 
 // ---------------------------------------------------------------------------
@@ -344,6 +370,12 @@ struct SweepArgs {
   const int* stop;
   int mode;
   float a, c, om;
+  // PCG dot products formed in the epilogue (3D): dots >= 0 adds b.y and b.b
+  // (r.z and r.r when b is the finest right-hand side r and y = z) and
+  // completes them as pcg_dots_complete(what = dots)
+  int dots;
+  double* part;
+  MgCtl* ctl;
   CMat<DIM, float> C;
 };
 
@@ -360,6 +392,7 @@ __global__ void __launch_bounds__(TileOp<DIM, float>::THREADS, MINB)
     return ((a.mask[node] >> comp) & 1) ? 0.f : u[node * DIM + comp];
   };
   if constexpr (DIM == 3) {
+    float d0 = 0.f, d1 = 0.f;  // this thread's share of the fused dot products
     // the output node's right-hand side, l1 scale, x_{k-2} term and fixed bits
     // are loaded before the layer's arithmetic
     struct Pre {
@@ -393,9 +426,18 @@ __global__ void __launch_bounds__(TileOp<DIM, float>::THREADS, MINB)
               out = fmaf(a.a, us[r], a.om * q.d[r] * res);
               if (w) out = fmaf(a.c, q.w[r], out);
             }
-            y[node * 3 + r] = ((q.mk >> r) & 1) ? 0.f : out;
+            const float yv = ((q.mk >> r) & 1) ? 0.f : out;
+            y[node * 3 + r] = yv;
+            if (a.dots >= 0) {
+              d0 = fmaf(q.b[r], yv, d0);
+              d1 = fmaf(q.b[r], q.b[r], d1);
+            }
           }
         });
+    if (a.dots >= 0) {
+      double acc[2] = {(double)d0, (double)d1};
+      pcg_dots_complete(acc, a.part, a.ctl, a.dots);
+    }
   } else {
     TileOp<DIM, float>::template apply<1>(
         a.g, a.tm, blockIdx.x, a.E, a.C, smem_raw, 1, [&](long long node, int comp, bool own) {
@@ -421,7 +463,8 @@ __global__ void __launch_bounds__(TileOp<DIM, float>::THREADS, MINB)
 template <int DIM>
 static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
                               const float* invd, const float* u, const float* w, const float* b, float* y,
-                              int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop) {
+                              int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop,
+                              int dots, double* part, MgCtl* ctl) {
   using Op = TileOp<DIM, float>;
   SweepArgs<DIM> a;
   a.g = g;
@@ -439,10 +482,11 @@ static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, co
   a.a = ca;
   a.c = cc;
   a.om = om;
+  a.dots = DIM == 3 ? dots : -1;
+  a.part = part;
+  a.ctl = ctl;
   fill_c<DIM, float>(a.C, C);
   const size_t smem = Op::smem_bytes();
-  // H8: 2 resident CTAs per SM (no spills with the pre-loaded emit data);
-  // measured faster than 3 with spills
   // H8: 3 resident CTAs per SM, tiles matched to them (measured fastest)
   auto kern = DIM == 3 ? mg_sweep_kernel<DIM, 3> : mg_sweep_kernel<DIM, 1>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -458,9 +502,12 @@ static cudaError_t sweep_impl(cudaStream_t s, const Grid& g, const double* C, co
 
 cudaError_t launch_mg_sweep(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
                             const float* invd, const float* u, const float* w, const float* b, float* y,
-                            int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop) {
-  return g.dim == 2 ? sweep_impl<2>(s, g, C, E, mask, invd, u, w, b, y, ncopies, zlen, mode, ca, cc, om, stop)
-                    : sweep_impl<3>(s, g, C, E, mask, invd, u, w, b, y, ncopies, zlen, mode, ca, cc, om, stop);
+                            int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop,
+                            int dots, double* part, MgCtl* ctl) {
+  return g.dim == 2 ? sweep_impl<2>(s, g, C, E, mask, invd, u, w, b, y, ncopies, zlen, mode, ca, cc, om, stop, -1,
+                                    part, ctl)
+                    : sweep_impl<3>(s, g, C, E, mask, invd, u, w, b, y, ncopies, zlen, mode, ca, cc, om, stop, dots,
+                                    part, ctl);
 }
 
 // ---------------------------------------------------------------------------

@@ -8,6 +8,8 @@
 
 namespace tp {
 
+struct MgCtl;
+
 constexpr int kMaxCases = 8;
 constexpr int kMaxTaps = 512;
 
@@ -79,7 +81,13 @@ cudaError_t launch_matvec_dw(cudaStream_t s, const Grid& g, const double* C, con
 // returns at once when *stop is set.
 cudaError_t launch_mg_sweep(cudaStream_t s, const Grid& g, const double* C, const float* E, const uint8_t* mask,
                             const float* invd, const float* u, const float* w, const float* b, float* y,
-                            int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop);
+                            int ncopies, int zlen, int mode, float ca, float cc, float om, const int* stop,
+                            int dots = -1, double* part = nullptr, MgCtl* ctl = nullptr);
+// The FP32 3D operator q = K p with p.q formed in its epilogue and completed
+// as the PCG scalar step `what` (pcg_dots_complete).
+cudaError_t launch_matvec_dots(cudaStream_t s, const Grid& g, const double* C, const float* E32, const uint8_t* mask,
+                               const float* u, float* y, int ncopies, int zlen, const int* stop, double* part,
+                               MgCtl* ctl, int what);
 // FP64 update: x64 += x_l, x_l = 0; r = f - K64 x64; z = D^-1 r; CgState update.
 // `init` starts a solve (beta = 0, counters reset).  Returns the number of
 // kernels launched through *nlaunch.

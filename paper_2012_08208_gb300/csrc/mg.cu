@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "mg.h"
+#include "mg_dots.cuh"
 #include "mg_ops.cuh"
 
 namespace tp {
@@ -1013,12 +1014,13 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
     *out = l.x[0];
     return cudaGetLastError();
   }
-  auto sweep = [&](const float* u, const float* w, float* y, int mode, float a, float c, float om) -> cudaError_t {
+  auto sweep = [&](const float* u, const float* w, float* y, int mode, float a, float c, float om,
+                   int dots = -1) -> cudaError_t {
     const bool tm = capture_events && li == 0 && ev_used + 2 <= (int)sweep_ev.size();
     if (tm) cudaEventRecordWithFlags(sweep_ev[ev_used], s, cudaEventRecordExternal);
     cudaError_t e;
     if (li == 0) {
-      e = fine_op_fn(fine_ctx, s, u, w, l.b, l.invd, y, mode, a, c, om, stop);
+      e = fine_op_fn(fine_ctx, s, u, w, l.b, l.invd, y, mode, a, c, om, stop, dots);
     } else {
       dim3 grid(blocks(l.g.nn), nc);
       if (dim == 2)
@@ -1077,8 +1079,9 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   (*nlaunch)++;
   // post-smoothing with the same polynomial from the corrected iterate
   for (int k = 1; k <= nu; k++) {
-    e = k == 1 ? sweep(l.x[cur], nullptr, l.x[cur ^ 1], 1, 1.f, 0.f, omega)
-               : sweep(l.x[cur], l.x[cur ^ 1], l.x[cur ^ 1], 1, ca[k], cc[k], cw[k]);
+    const int dots = li == 0 && k == nu ? fine_dots : -1;  // the step that produces z
+    e = k == 1 ? sweep(l.x[cur], nullptr, l.x[cur ^ 1], 1, 1.f, 0.f, omega, dots)
+               : sweep(l.x[cur], l.x[cur ^ 1], l.x[cur ^ 1], 1, ca[k], cc[k], cw[k], dots);
     if (e != cudaSuccess) return e;
     cur ^= 1;
   }
@@ -1210,9 +1213,6 @@ template <typename TA, typename TB>
 __global__ void dotscal_kernel(long long n, const TA* __restrict__ a1, const TB* __restrict__ b1,
                                const TA* __restrict__ a2, const TA* __restrict__ b2, double* part, MgCtl* ctl,
                                int what) {
-  __shared__ double sred[32 * 2];
-  __shared__ double tot[16];
-  __shared__ int is_last;
   if (what != 2 && ctl->stop) return;  // uniform: the flag changes only in the last block of this kernel
   const int c = blockIdx.y, nb = gridDim.x;
   const long long base = (long long)c * n;
@@ -1289,82 +1289,7 @@ __global__ void dotscal_kernel(long long n, const TA* __restrict__ a1, const TB*
   }
   double acc[2] = {((double)t0[0] + (double)t0[1]) + ((double)t0[2] + (double)t0[3]),
                    ((double)t1[0] + (double)t1[1]) + ((double)t1[2] + (double)t1[3])};
-  block_sum<2>(acc, sred);
-  if (threadIdx.x == 0) {
-    part[((long long)c * nb + blockIdx.x) * 2] = acc[0];
-    part[((long long)c * nb + blockIdx.x) * 2 + 1] = acc[1];
-    __threadfence();
-    const unsigned t = atomicAdd(&ctl->ticket, 1u);
-    is_last = t == gridDim.x * gridDim.y - 1;
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  const int nc = gridDim.y;
-  // every thread of the last CTA takes a strided share of the partials (a
-  // few loads each, all in flight), then a fixed-order block reduction
-  for (int cc = 0; cc < nc; cc++) {
-    double v2[2] = {0.0, 0.0};
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      v2[0] += __ldcg(part + ((long long)cc * nb + b) * 2);
-      v2[1] += __ldcg(part + ((long long)cc * nb + b) * 2 + 1);
-    }
-    block_sum<2>(v2, sred);
-    if (threadIdx.x == 0) {
-      tot[2 * cc] = v2[0];
-      tot[2 * cc + 1] = v2[1];
-    }
-  }
-  __syncthreads();
-  double* sc = ctl->sc;
-  const int cc = threadIdx.x;
-  if (cc < nc) {
-    const double s1 = tot[2 * cc], s2 = tot[2 * cc + 1];
-    if (what == 0) {  // alpha = rz / pq
-      sc[24 + cc] = s1;
-      sc[cc] = (s1 > 0.0 && isfinite(s1)) ? sc[16 + cc] / s1 : 0.0;
-    } else if (what == 1) {  // beta = rz_new / rz
-      sc[8 + cc] = sc[16 + cc] != 0.0 ? s1 / sc[16 + cc] : 0.0;
-      sc[16 + cc] = s1;
-      sc[32 + cc] = s2;
-    } else {  // segment start
-      sc[16 + cc] = s1;
-      sc[32 + cc] = s2;
-      sc[8 + cc] = 0.0;
-      ctl->rr_start[cc] = s2;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (what == 1) {
-      // stop at the tolerance (with margin 1/2 on the recurrence residual),
-      // when the FP32 operator's error may dominate the recurrence (1e-5 of
-      // the segment's starting residual), on stagnation (no halving of the
-      // worst relative residual in 50 iterations), on breakdown, or at the
-      // iteration limit
-      const int it = ctl->it + 1;
-      ctl->it = it;
-      bool brk = false, done = true, inner = ctl->use64 == 0;
-      double worst = 0.0;
-      for (int k = 0; k < nc; k++) {
-        const double rec = sc[32 + k];
-        brk |= !isfinite(rec) || !(sc[24 + k] > 0.0);
-        done &= rec <= 0.25 * ctl->tol2 * ctl->ff[k];
-        inner &= rec <= 1e-10 * ctl->rr_start[k];
-        worst = fmax(worst, rec / ctl->ff[k]);
-      }
-      if (ctl->best == 0.0 || worst < 0.25 * ctl->best) {
-        ctl->best = worst;
-        ctl->best_it = it;
-      }
-      const bool stall = it - ctl->best_it >= 50, limit = it >= ctl->it_limit;
-      const int reason = (done ? MG_STOP_DONE : 0) | (inner ? MG_STOP_INNER : 0) | (stall ? MG_STOP_STALL : 0) |
-                         (brk ? MG_STOP_BREAK : 0) | (limit ? MG_STOP_LIMIT : 0);
-      ctl->reason = reason;
-      ctl->stop = reason != 0;
-    }
-    ctl->ticket = 0u;
-  }
+  pcg_dots_complete(acc, part, ctl, what);
 }
 
 // x += alpha p, r -= alpha q, r32 = (float) r, x0 = omega D^-1 r32.

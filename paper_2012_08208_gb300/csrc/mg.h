@@ -78,10 +78,15 @@ struct MgHierarchy {
   // operator: mode 1 y = a u + c w + om D^-1 (b - A u) (w may be null when
   // c = 0; y may alias w), mode 2 y = b - A u; 0 on fixed DOFs; returns at
   // once when *stop is set.
+  // With dots >= 0 the sweep also forms r.z and r.r (b is the finest r, y = z)
+  // and completes them as the PCG scalar step `dots` (pcg_dots_complete).
   cudaError_t (*fine_op_fn)(void* ctx, cudaStream_t s, const float* u, const float* w, const float* b,
                             const float* invd, float* y, int mode, float a, float c, float om,
-                            const int* stop) = nullptr;
+                            const int* stop, int dots) = nullptr;
   void* fine_ctx = nullptr;
+  // the PCG scalar step that the V-cycle's last finest-level step completes
+  // (-1: none; the caller then launches the dot kernel)
+  int fine_dots = -1;
   MgCtl* ctl = nullptr;     // device control block
   MgCtl* ctl_h = nullptr;   // pinned host mirror
   float* p32 = nullptr;     // FP32 search direction (finest level, all cases)
