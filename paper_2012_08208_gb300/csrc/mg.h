@@ -134,8 +134,9 @@ struct MgHierarchy {
   double vcycle_bytes() const;
   double iter_bytes() const;
 
-  // Level plan for grid g0: 2:1 while possible, then the smallest common odd
-  // factor, until the first level with <= max_coarse_dofs DOFs (coarsening at
+  // Level plan for grid g0: 2:1 while possible (in 3D 4:1 first when every
+  // element count divides by 4), then the smallest common odd factor, until
+  // the first level with <= max_coarse_dofs DOFs (coarsening at
   // least once); that level is solved with a dense inverse.  Allocates all
   // buffers.  cudaErrorInvalidValue when no plan reaches it.
   cudaError_t plan(const Grid& g0, const uint8_t* mask0, int nc, int max_coarse_dofs = 4096);
