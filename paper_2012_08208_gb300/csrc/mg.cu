@@ -616,6 +616,79 @@ __global__ void __launch_bounds__(kT2X)
   }
 }
 
+// Restriction for f = 4 in 3D in two passes.  The weight of fine node
+// (4I + dx, 4J + dy, 4K + dz) in coarse node (I, J, K) is the product of
+// (1 - |d| / 4) over the axes, so the 343-node sum separates: pass 1 sums x
+// and y over the 7 x 7 fine nodes around each (coarse x, coarse y, fine z),
+// fine fixed DOFs read as 0, into r4; pass 2 sums z, zeroes the coarse fixed
+// DOFs and forms the coarse level's first smoothing step.  One thread per
+// output node on a 3D grid (no divisions); the sums of restrict_warp in
+// another order.  A warp per coarse node over the 343 fine nodes took about
+// 60 us at 240 x 80 x 80.
+__device__ __forceinline__ float w4(int d) { return 1.f - 0.25f * (float)(d < 0 ? -d : d); }
+
+__global__ void __launch_bounds__(kT2X)
+    restrict4_xy_kernel(Grid gf, Grid gc, const uint8_t* __restrict__ mf, const float* __restrict__ rf,
+                        float* __restrict__ r4, const int* __restrict__ stop) {
+  if (halted(stop)) return;
+  const int I = blockIdx.x * kT2X + threadIdx.x, J = blockIdx.y, k = blockIdx.z % gf.nz, c = blockIdx.z / gf.nz;
+  if (I >= gc.nx) return;
+  const long long offf = (long long)c * gf.nn * 3;
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int dy = -3; dy <= 3; dy++) {
+    const int fj = 4 * J + dy;
+    if (fj < 0 || fj >= gf.ny) continue;  // uniform over the block
+    const long long row = (long long)gf.nx * (fj + (long long)gf.ny * k);
+    float rs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int dx = -3; dx <= 3; dx++) {
+      const int fi = 4 * I + dx;
+      const bool in = fi >= 0 && fi < gf.nx;
+      const long long n2 = row + (in ? fi : 0);
+      const uint8_t m = in ? mf[n2] : (uint8_t)7;
+#pragma unroll
+      for (int s2 = 0; s2 < 3; s2++) {
+        const float v = in ? rf[offf + n2 * 3 + s2] : 0.f;
+        rs[s2] = fmaf(w4(dx), ((m >> s2) & 1) ? 0.f : v, rs[s2]);
+      }
+    }
+#pragma unroll
+    for (int s2 = 0; s2 < 3; s2++) acc[s2] = fmaf(w4(dy), rs[s2], acc[s2]);
+  }
+  float* out = r4 + ((((long long)c * gf.nz + k) * gc.ny + J) * gc.nx + I) * 3;
+#pragma unroll
+  for (int s2 = 0; s2 < 3; s2++) out[s2] = acc[s2];
+}
+
+__global__ void __launch_bounds__(kT2X)
+    restrict4_z_kernel(Grid gf, Grid gc, const float* __restrict__ r4, const uint8_t* __restrict__ mc,
+                       float* __restrict__ bc, float* __restrict__ x0, const float* __restrict__ invd, float omega,
+                       const int* __restrict__ stop) {
+  if (halted(stop)) return;
+  const int I = blockIdx.x * kT2X + threadIdx.x, J = blockIdx.y, K = blockIdx.z % gc.nz, c = blockIdx.z / gc.nz;
+  if (I >= gc.nx) return;
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int dz = -3; dz <= 3; dz++) {
+    const int fk = 4 * K + dz;
+    if (fk < 0 || fk >= gf.nz) continue;  // uniform over the block
+    const float* in = r4 + ((((long long)c * gf.nz + fk) * gc.ny + J) * gc.nx + I) * 3;
+#pragma unroll
+    for (int s2 = 0; s2 < 3; s2++) acc[s2] = fmaf(w4(dz), in[s2], acc[s2]);
+  }
+  const long long offc = (long long)c * gc.nn * 3;
+  const long long nd = I + (long long)gc.nx * (J + (long long)gc.ny * K);
+  const uint8_t mk = mc[nd];
+#pragma unroll
+  for (int s2 = 0; s2 < 3; s2++) {
+    const long long idx = nd * 3 + s2;
+    const float v = ((mk >> s2) & 1) ? 0.f : acc[s2];
+    bc[offc + idx] = v;
+    if (x0) x0[offc + idx] = omega * invd[idx] * v;
+  }
+}
+
 // The prolongation takes F = 2 or 4 (the weights t / F are exact in FP32).
 template <int F>
 __global__ void __launch_bounds__(kT2X)
@@ -771,7 +844,7 @@ void MgHierarchy::release() {
   sweep_ev.clear();
   ev_used = 0;
   for (auto& l : lv) {
-    void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t};
+    void* ptrs[] = {l.K, l.S, l.mask_own ? (void*)l.mask : nullptr, l.invd, l.x[0], l.x[1], l.b, l.t, l.r4};
     for (void* q : ptrs)
       if (q) cudaFree(q);
   }
@@ -858,6 +931,8 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
     for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaMalloc((void**)&l.x[k], nc * ndof * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&l.b, nc * ndof * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&l.t, nc * ndof * sizeof(float));
+    if (e == cudaSuccess && i > 0 && l.f == 4 && g0.dim == 3)
+      e = cudaMalloc((void**)&l.r4, (size_t)nc * lv[i - 1].g.nz * l.g.ny * l.g.nx * 3 * sizeof(float));
   }
   {
     const int f1 = lv[1].f, nd = g0.dim == 2 ? 8 : 24;
@@ -1064,7 +1139,14 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   MgLevel& c = lv[li + 1];
   const bool coarsest = li + 1 == (int)lv.size() - 1;
   float* cx0 = coarsest ? nullptr : c.x[0];  // the dense solve needs no first sweep
-  if (c.f == 2 && dim == 3 && c.g.nn > kWarpRestrictNodes && c.g.ny <= 65535 && c.g.nz * nc <= 65535) {
+  if (c.f == 4 && dim == 3 && c.r4 && c.g.ny <= 65535 && l.g.nz * nc <= 65535 && c.g.nz * nc <= 65535) {
+    restrict4_xy_kernel<<<dim3((c.g.nx + kT2X - 1) / kT2X, c.g.ny, l.g.nz * nc), kT2X, 0, s>>>(l.g, c.g, l.mask, l.t,
+                                                                                              c.r4, stop);
+    restrict4_z_kernel<<<dim3((c.g.nx + kT2X - 1) / kT2X, c.g.ny, c.g.nz * nc), kT2X, 0, s>>>(l.g, c.g, c.r4, c.mask,
+                                                                                             c.b, cx0, c.invd, omega,
+                                                                                             stop);
+    (*nlaunch)++;  // the second pass (the restriction's launch is counted below)
+  } else if (c.f == 2 && dim == 3 && c.g.nn > kWarpRestrictNodes && c.g.ny <= 65535 && c.g.nz * nc <= 65535) {
     dim3 gr((c.g.nx + kT2X - 1) / kT2X, c.g.ny, c.g.nz * nc);
     restrict2x_kernel<<<gr, kT2X, 0, s>>>(l.g, c.g, l.mask, c.mask, l.t, c.b, cx0, c.invd, omega, stop);
   } else if (c.f == 2 && !(dim == 3 && c.g.nn <= kWarpNodes)) {

@@ -21,6 +21,7 @@ struct MgLevel {
   float* x[2] = {nullptr, nullptr};  // iterates [case][n_nodes * dim]
   float* b = nullptr;       // right-hand side
   float* t = nullptr;       // residual scratch
+  float* r4 = nullptr;      // 3D f = 4: partial restriction sums [case][fine z][coarse y][coarse x][dim]
 };
 
 // Device control block of the multigrid PCG.  The scalar kernels keep the
