@@ -481,8 +481,10 @@ __global__ void touched_kernel(Grid gf, Grid gc, int f, const uint8_t* __restric
 // (coalesced stores).  The child matrices are staged in shared memory once per
 // CTA.  Touched elements are left to galerkin_kernel (list mode).  Needs f^dim <= 64;
 // shared memory (dynamic): f^dim ND^2 floats.
+constexpr int kG1Threads = 1024;  // 32 warps share one staged table (it fills most of shared memory at f = 4)
+
 template <int DIM>
-__global__ void __launch_bounds__(256) galerkin1_flat_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
+__global__ void __launch_bounds__(kG1Threads) galerkin1_flat_kernel(Grid gf, Grid gc, int f, const float* __restrict__ Ef,
                                                              const float* __restrict__ A,
                                                              const uint8_t* __restrict__ touched,
                                                              float* __restrict__ Kc) {
@@ -1015,12 +1017,14 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
       if (i == 1 && nch1 <= 64 && smf <= 160 * 1024) {
         e = cudaMemsetAsync(touched_list, 0, sizeof(int), s);
         if (e != cudaSuccess) return e;
+        const unsigned g1grid =
+            (unsigned)std::max<long long>(1, std::min<long long>((l.g.ne + 31) / 32, 152 * 2));  // warp per element
         if (dim == 2) {
           touched_kernel<2><<<blocks(l.g.ne), 256, 0, s>>>(fl.g, l.g, l.f, fl.mask, touched1, touched_list + 1,
                                                            touched_list);
           e = cudaFuncSetAttribute(galerkin1_flat_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
           if (e != cudaSuccess) return e;
-          galerkin1_flat_kernel<2><<<blocks(l.g.ne * 32), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
+          galerkin1_flat_kernel<2><<<g1grid, kG1Threads, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
           if (l.f == 2)
             galerkin2_kernel<2><<<152 * 16, 64, 0, s>>>(fl.g, l.g, nullptr, E32, K0d, fl.mask, l.mask, l.K,
                                                         touched_list + 1, touched_list);
@@ -1032,7 +1036,7 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
                                                            touched_list);
           e = cudaFuncSetAttribute(galerkin1_flat_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
           if (e != cudaSuccess) return e;
-          galerkin1_flat_kernel<3><<<blocks(l.g.ne * 32), 256, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
+          galerkin1_flat_kernel<3><<<g1grid, kG1Threads, smf, s>>>(fl.g, l.g, l.f, E32, A1, touched1, l.K);
           if (l.f == 2)
             galerkin2_kernel<3><<<152 * 3, 576, 0, s>>>(fl.g, l.g, nullptr, E32, K0d, fl.mask, l.mask, l.K,
                                                         touched_list + 1, touched_list);
