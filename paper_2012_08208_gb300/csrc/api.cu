@@ -329,7 +329,7 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
     const int gi = u64 ? 1 : 0, gt = M.timing ? 1 : 0;
     if (M.gx[gi][gt]) return TP_OK;
     if (gt && M.sweep_ev.empty()) {
-      M.sweep_ev.resize(2 * 2 * M.nu * kIt);  // an event pair per finest-level sweep of the graph
+      M.sweep_ev.resize(2 * 2 * M.nu0 * kIt);  // an event pair per finest-level sweep of the graph
       for (auto& ev : M.sweep_ev) TPCK(cudaEventCreate(&ev), "event");
     }
     // captured on a private stream (the problem's stream may be the legacy
@@ -432,7 +432,7 @@ static tp_status mg_solve(tp_problem* p, const tp_solve_opts* opts, tp_solve_inf
         TPCK(cudaMemcpyAsync(M.ctl_h, ctl, sizeof(MgCtl), cudaMemcpyDeviceToHost, s), "copy");
         TPCK(cudaStreamSynchronize(s), "sync");
         const int now = M.ctl_h->it;
-        if (gt) M.collect_sweeps((now - seg_it) * 2 * M.nu);  // sweeps of the iterations that ran
+        if (gt) M.collect_sweeps((now - seg_it) * 2 * M.nu0);  // sweeps of the iterations that ran
         const bool advanced = now > seg_it;
         seg_it = now;
         if (M.ctl_h->stop) break;

@@ -780,9 +780,10 @@ double MgHierarchy::vcycle_bytes() const {
     const double nodes = (double)l.g.nn, vals = (double)nc * nodes * dim;
     // operator data of one sweep: moduli (finest) or assembled blocks, plus the scale
     const double op = (li == 0 ? 4.0 * l.g.ne : 4.0 * nbr * nodes) + 4.0 * nodes * dim;
-    // Chebyshev steps before (nu - 1), residual, after (nu): u, b read, y
+    // Chebyshev steps before (degree - 1), residual, after (degree): u, b read, y
     // written; w read by the steps that use x_{k-2}
-    const int steps = 2 * nu, w_reads = std::max(0, nu - 2) + (nu - 1);
+    const int nl = degree_at(li);
+    const int steps = 2 * nl, w_reads = std::max(0, nl - 2) + (nl - 1);
     total += steps * (op + 12.0 * vals) + w_reads * 4.0 * vals;
     const MgLevel& c = lv[li + 1];
     const double cvals = (double)nc * c.g.nn * dim;
@@ -892,6 +893,7 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
   release();
   nc = nc_;
   set_smoother(nu, cheb_ratio);
+  nu0 = g0.nn > kDegree1Nodes ? 1 : nu;
   MgLevel l0;
   l0.g = g0;
   l0.f = 1;
@@ -1133,7 +1135,8 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   // pre-smoothing from zero: x[0] already holds step 1, omega D^-1 b; step k
   // needs x_{k-2}, which is 0 for k = 2
   int cur = 0;
-  for (int k = 2; k <= nu; k++) {
+  const int nuL = degree_at(li);
+  for (int k = 2; k <= nuL; k++) {
     cudaError_t e = sweep(l.x[cur], k == 2 ? nullptr : l.x[cur ^ 1], l.x[cur ^ 1], 1, ca[k], cc[k], cw[k]);
     if (e != cudaSuccess) return e;
     cur ^= 1;
@@ -1178,8 +1181,8 @@ cudaError_t MgHierarchy::vcycle(cudaStream_t s, int li, int* nlaunch, const int*
   else prolong_kernel<3><<<gp, 256, 0, s>>>(l.g, c.g, c.f, l.mask, xc, l.x[cur], stop);
   (*nlaunch)++;
   // post-smoothing with the same polynomial from the corrected iterate
-  for (int k = 1; k <= nu; k++) {
-    const int dots = li == 0 && k == nu ? fine_dots : -1;  // the step that produces z
+  for (int k = 1; k <= nuL; k++) {
+    const int dots = li == 0 && k == nuL ? fine_dots : -1;  // the step that produces z
     e = k == 1 ? sweep(l.x[cur], nullptr, l.x[cur ^ 1], 1, 1.f, 0.f, omega, dots)
                : sweep(l.x[cur], l.x[cur ^ 1], l.x[cur ^ 1], 1, ca[k], cc[k], cw[k], dots);
     if (e != cudaSuccess) return e;

@@ -44,7 +44,7 @@ struct MgLevelArgs {
 
 template <int DIM>
 struct MgSegArgs {
-  int nl, nc, nu, cn;
+  int nl, nc, nu, nu0, cn;  // nu0: the degree on the finest level
   MgLevelArgs lv[kMgMaxLevels];
   TileMapG tm;
   const float* E;     // finest-level moduli
@@ -307,7 +307,8 @@ __global__ void __launch_bounds__(256, 2) mg_seg_kernel(const __grid_constant__ 
     for (int li = 0; li < L - 1; li++) {
       const MgLevelArgs& l = a.lv[li];
       int cu = 0;
-      for (int k = 2; k <= a.nu; k++) {
+      const int nuL = li == 0 ? a.nu0 : a.nu;
+      for (int k = 2; k <= nuL; k++) {
         sweep(li, l.x[cu], k == 2 ? nullptr : l.x[cu ^ 1], l.x[cu ^ 1], 1, a.ca[k], a.cc[k], a.cw[k], false);
         sync();
         cu ^= 1;
@@ -329,8 +330,9 @@ __global__ void __launch_bounds__(256, 2) mg_seg_kernel(const __grid_constant__ 
       int cu = curs[li];
       prolong_from(li, xc, l.x[cu]);
       sync();
-      for (int k = 1; k <= a.nu; k++) {
-        const bool last = li == 0 && k == a.nu;
+      const int nuL = li == 0 ? a.nu0 : a.nu;
+      for (int k = 1; k <= nuL; k++) {
+        const bool last = li == 0 && k == nuL;
         if (k == 1) sweep(li, l.x[cu], nullptr, l.x[cu ^ 1], 1, 1.f, 0.f, a.omega, last);
         else sweep(li, l.x[cu], l.x[cu ^ 1], l.x[cu ^ 1], 1, a.ca[k], a.cc[k], a.cw[k], last);
         sync();
@@ -479,6 +481,7 @@ cudaError_t launch_impl(cudaStream_t s, const MgHierarchy& M, const double* C, c
   a.nl = (int)M.lv.size();
   a.nc = M.nc;
   a.nu = M.nu;
+  a.nu0 = M.nu0;
   a.cn = M.cn;
   for (int i = 0; i < a.nl; i++) {
     const MgLevel& l = M.lv[i];
