@@ -5,7 +5,8 @@
 // Dekker's Fast2Sum, the FMA form of TwoProd) combined as in Joldes, Muller
 // and Popescu, "Tight and rigorous error bounds for basic building blocks of
 // double-word arithmetic" (ACM TOMS 44, 2017):
-//   addition        AccurateDWPlusDW, relative error <= 3 u^2 (u = 2^-24);
+//   addition        AccurateDWPlusDW, relative error <= 3 u^2 (u = 2^-24), or
+//                   the sloppy sum (its error bounded by the operands);
 //   multiplication  DWTimesDW with the lo x lo term, relative error <= 5 u^2.
 // Every FP32 operation is an explicit round-to-nearest intrinsic, so the
 // compiler neither contracts nor reassociates them.
@@ -25,20 +26,28 @@ using ::__ldg;
 using ::__shfl_up_sync;
 using ::__shfl_down_sync;
 
-struct df32 {
+// A value is hi + lo.  ACC selects the addition: the accurate double-word sum
+// (relative error <= 3 u^2 of the result, about 20 FP32 operations) or the
+// "sloppy" one (one TwoSum and a renormalisation, 11 operations; its error is
+// bounded by u^2 (|x| + |y|), the operands rather than the result, so it can
+// lose relative accuracy where x + y cancels).
+template <bool ACC>
+struct dword {
   float hi, lo;
-  __host__ __device__ constexpr df32() : hi(0.f), lo(0.f) {}
-  // explicit: no float or double silently becomes a df32 (so fma on doubles
-  // keeps resolving to the FP64 function)
-  __host__ __device__ constexpr explicit df32(float h, float l = 0.f) : hi(h), lo(l) {}
-  __host__ __device__ constexpr explicit df32(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ constexpr dword() : hi(0.f), lo(0.f) {}
+  // explicit: no float or double silently becomes a double-word (so fma on
+  // doubles keeps resolving to the FP64 function)
+  __host__ __device__ constexpr explicit dword(float h, float l = 0.f) : hi(h), lo(l) {}
+  __host__ __device__ constexpr explicit dword(int v) : hi((float)v), lo(0.f) {}
   // nearest double-word of an FP64 value (exact for values with <= 48 significant bits)
-  __host__ __device__ static df32 of(double x) {
+  __host__ __device__ static dword of(double x) {
     const float h = (float)x;
-    return df32(h, (float)(x - (double)h));
+    return dword(h, (float)(x - (double)h));
   }
   __host__ __device__ double to_double() const { return (double)hi + (double)lo; }
 };
+using df32 = dword<true>;    // accurate addition
+using df32f = dword<false>;  // sloppy addition
 
 namespace dw {
 // s + e = a + b exactly (Knuth)
@@ -54,40 +63,59 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
 }
 }  // namespace dw
 
-__device__ __forceinline__ df32 operator+(df32 x, df32 y) {
-  float sh, sl, th, tl, vh, vl, zh, zl;
+template <bool A>
+__device__ __forceinline__ dword<A> operator+(dword<A> x, dword<A> y) {
+  float sh, sl, zh, zl;
   dw::two_sum(x.hi, y.hi, sh, sl);
-  dw::two_sum(x.lo, y.lo, th, tl);
-  dw::fast_two_sum(sh, __fadd_rn(sl, th), vh, vl);
-  dw::fast_two_sum(vh, __fadd_rn(tl, vl), zh, zl);
-  return df32(zh, zl);
+  if constexpr (A) {
+    float th, tl, vh, vl;
+    dw::two_sum(x.lo, y.lo, th, tl);
+    dw::fast_two_sum(sh, __fadd_rn(sl, th), vh, vl);
+    dw::fast_two_sum(vh, __fadd_rn(tl, vl), zh, zl);
+  } else {
+    dw::fast_two_sum(sh, __fadd_rn(sl, __fadd_rn(x.lo, y.lo)), zh, zl);
+  }
+  return dword<A>(zh, zl);
 }
-__device__ __forceinline__ df32 operator-(df32 x) { return df32(-x.hi, -x.lo); }
-__device__ __forceinline__ df32 operator-(df32 x, df32 y) { return x + (-y); }
-__device__ __forceinline__ df32 operator*(df32 x, df32 y) {
+template <bool A>
+__device__ __forceinline__ dword<A> operator-(dword<A> x) { return dword<A>(-x.hi, -x.lo); }
+template <bool A>
+__device__ __forceinline__ dword<A> operator-(dword<A> x, dword<A> y) { return x + (-y); }
+template <bool A>
+__device__ __forceinline__ dword<A> operator*(dword<A> x, dword<A> y) {
   const float ch = __fmul_rn(x.hi, y.hi);
   const float cl1 = __fmaf_rn(x.hi, y.hi, -ch);  // exact low part of hi x hi
   const float tl1 = __fmaf_rn(x.hi, y.lo, __fmul_rn(x.lo, y.lo));
   const float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
   float zh, zl;
   dw::fast_two_sum(ch, __fadd_rn(cl1, cl2), zh, zl);
-  return df32(zh, zl);
+  return dword<A>(zh, zl);
 }
-__device__ __forceinline__ df32& operator+=(df32& x, df32 y) { return x = x + y; }
-__device__ __forceinline__ df32& operator-=(df32& x, df32 y) { return x = x - y; }
-__device__ __forceinline__ df32& operator*=(df32& x, df32 y) { return x = x * y; }
-__device__ __forceinline__ df32 fma(df32 a, df32 b, df32 c) { return a * b + c; }
-__device__ __forceinline__ bool operator>=(df32 x, df32 y) { return x.hi > y.hi || (x.hi == y.hi && x.lo >= y.lo); }
+template <bool A>
+__device__ __forceinline__ dword<A>& operator+=(dword<A>& x, dword<A> y) { return x = x + y; }
+template <bool A>
+__device__ __forceinline__ dword<A>& operator-=(dword<A>& x, dword<A> y) { return x = x - y; }
+template <bool A>
+__device__ __forceinline__ dword<A>& operator*=(dword<A>& x, dword<A> y) { return x = x * y; }
+template <bool A>
+__device__ __forceinline__ dword<A> fma(dword<A> a, dword<A> b, dword<A> c) { return a * b + c; }
+template <bool A>
+__device__ __forceinline__ bool operator>=(dword<A> x, dword<A> y) {
+  return x.hi > y.hi || (x.hi == y.hi && x.lo >= y.lo);
+}
 
-__device__ __forceinline__ df32 __shfl_up_sync(unsigned mask, df32 v, unsigned delta) {
-  return df32(::__shfl_up_sync(mask, v.hi, delta), ::__shfl_up_sync(mask, v.lo, delta));
+template <bool A>
+__device__ __forceinline__ dword<A> __shfl_up_sync(unsigned mask, dword<A> v, unsigned delta) {
+  return dword<A>(::__shfl_up_sync(mask, v.hi, delta), ::__shfl_up_sync(mask, v.lo, delta));
 }
-__device__ __forceinline__ df32 __shfl_down_sync(unsigned mask, df32 v, unsigned delta) {
-  return df32(::__shfl_down_sync(mask, v.hi, delta), ::__shfl_down_sync(mask, v.lo, delta));
+template <bool A>
+__device__ __forceinline__ dword<A> __shfl_down_sync(unsigned mask, dword<A> v, unsigned delta) {
+  return dword<A>(::__shfl_down_sync(mask, v.hi, delta), ::__shfl_down_sync(mask, v.lo, delta));
 }
-__device__ __forceinline__ df32 __ldg(const df32* p) {
+template <bool A>
+__device__ __forceinline__ dword<A> __ldg(const dword<A>* p) {
   const float2 v = ::__ldg(reinterpret_cast<const float2*>(p));
-  return df32(v.x, v.y);
+  return dword<A>(v.x, v.y);
 }
 
 }  // namespace tp
