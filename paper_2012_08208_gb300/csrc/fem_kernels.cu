@@ -249,10 +249,10 @@ cudaError_t launch_matvec_dots(cudaStream_t s, const Grid& g, const double* C, c
 // ---------------------------------------------------------------------------
 // The same operator in double-word FP32 arithmetic (df32.cuh) on FP64 data:
 // u and y are double, the moduli and C are double-words (about 48 significant
-// bits).  Each operation runs on the FP32 pipes (about 20 FP32 operations per
-// addition, 9 per multiplication) instead of GB300's FP64 pipe at 1/64 of the
-// FP32 rate; the result agrees with the FP64 operator to about 1e-13 of the
-// element force scale.
+// bits).  Each operation runs on the FP32 pipes (11 FP32 operations per
+// addition with the sloppy sum below, 9 per multiplication) instead of GB300's
+// FP64 pipe at 1/64 of the FP32 rate; the result agrees with the FP64 operator
+// to about 1e-13 of the element force scale.
 
 __global__ void dw_moduli_kernel(const double* __restrict__ E64, df32* __restrict__ Edw, long long ne) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ne;
