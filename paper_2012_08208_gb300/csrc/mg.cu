@@ -256,6 +256,62 @@ __global__ void diag_kernel(Grid g, const float* __restrict__ K, const float* __
   }
 }
 
+// Corner index of the offsets (x, y, z) in the order of cofs.
+__host__ __device__ constexpr int corner_of(int x, int y, int z) { return (y ? (x ? 2 : 3) : (x ? 1 : 0)) + 4 * z; }
+
+// Inverse l1 row sums of the assembled 3D level-0 operator, sum_j |A_ij| over
+// the free columns j, where the 3 x 3 block A_ij = sum over the elements
+// holding both nodes of E_e K0 (formed here, never stored).  Assembly cancels
+// part of the element-level sums of diag_kernel: these are at most those (0.67
+// to 0.75 of them inside a solid region of the H8 cantilever, equal beside
+// void), and Gershgorin on the assembled rows keeps the spectrum of D^-1 A in
+// (0, 1], so the same Chebyshev interval applies and smooths harder.  The
+// neighbour and corner loops unroll to the 64 (corner, corner) pairs of the 8
+// elements, K0 entries as constant-bank operands.
+__global__ void diag_assembled_kernel(Grid g, const float* __restrict__ E, const uint8_t* __restrict__ mask,
+                                      float* __restrict__ invd) {
+  constexpr int ND = MgC<3>::ND;
+  const int nn = (int)g.nn, nxy = g.nx * g.ny;
+  for (int nd = blockIdx.x * blockDim.x + threadIdx.x; nd < nn; nd += gridDim.x * blockDim.x) {
+    const int k = nd / nxy, rem = nd - k * nxy, j = rem / g.nx, i = rem - j * g.nx;
+    // moduli of the 8 elements around the node (0 outside the grid); the node
+    // is corner c of element c
+    float Ee[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+      const int ei = i - cofs(c, 0), ej = j - cofs(c, 1), ek = k - cofs(c, 2);
+      const bool in = ei >= 0 && ej >= 0 && ek >= 0 && ei < g.ex && ej < g.ey && ek < g.ez;
+      Ee[c] = in ? E[ei + (long long)g.ex * (ej + (long long)g.ey * ek)] : 0.f;
+    }
+    float d[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 27; o++) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+      if (i + ox < 0 || j + oy < 0 || k + oz < 0 || i + ox >= g.nx || j + oy >= g.ny || k + oz >= g.nz) continue;
+      const uint8_t m2 = mask[nd + ox + g.nx * oy + nxy * oz];
+      float blk[3][3] = {};
+#pragma unroll
+      for (int c = 0; c < 8; c++) {
+        const int x2 = cofs(c, 0) + ox, y2 = cofs(c, 1) + oy, z2 = cofs(c, 2) + oz;
+        if (x2 < 0 || x2 > 1 || y2 < 0 || y2 > 1 || z2 < 0 || z2 > 1) continue;  // resolved at compile time
+        const int c2 = corner_of(x2, y2, z2);
+#pragma unroll
+        for (int r = 0; r < 3; r++)
+#pragma unroll
+          for (int s2 = 0; s2 < 3; s2++) blk[r][s2] = fmaf(Ee[c], c_K0[(c * 3 + r) * ND + c2 * 3 + s2], blk[r][s2]);
+      }
+#pragma unroll
+      for (int r = 0; r < 3; r++)
+#pragma unroll
+        for (int s2 = 0; s2 < 3; s2++)
+          if (!((m2 >> s2) & 1)) d[r] += fabsf(blk[r][s2]);
+    }
+    const uint8_t mk = mask[nd];
+#pragma unroll
+    for (int r = 0; r < 3; r++) invd[(long long)nd * 3 + r] = ((mk >> r) & 1) || !(d[r] > 0.f) ? 1.f : 1.f / d[r];
+  }
+}
+
 // Coarse mask: a coarse node takes the fixed bits of the fine node at its place.
 __global__ void coarse_mask_kernel(Grid gf, Grid gc, int f, const uint8_t* __restrict__ mf, uint8_t* __restrict__ mc) {
   const int nn = (int)gc.nn, nxy = gc.nx * gc.ny;
@@ -1074,7 +1130,8 @@ cudaError_t MgHierarchy::build(cudaStream_t s, const double* K0, const float* E3
       nl += 2;
     } else {
       if (dim == 2) diag_kernel<2><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.K, i == 0 ? E32 : nullptr, l.mask, l.invd);
-      else diag_kernel<3><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.K, i == 0 ? E32 : nullptr, l.mask, l.invd);
+      else if (i == 0) diag_assembled_kernel<<<blocks(l.g.nn), 256, 0, s>>>(l.g, E32, l.mask, l.invd);
+      else diag_kernel<3><<<blocks(l.g.nn), 256, 0, s>>>(l.g, l.K, nullptr, l.mask, l.invd);
       nl++;
     }
     e = cudaGetLastError();
