@@ -949,7 +949,7 @@ cudaError_t MgHierarchy::plan(const Grid& g0, const uint8_t* mask0, int nc_, int
   release();
   nc = nc_;
   set_smoother(nu, cheb_ratio);
-  nu0 = g0.nn > kDegree1Nodes ? 1 : nu;
+  nu0 = g0.nn > (g0.dim == 3 ? kDegree1Nodes3D : kDegree1Nodes) ? 1 : nu;
   MgLevel l0;
   l0.g = g0;
   l0.f = 1;

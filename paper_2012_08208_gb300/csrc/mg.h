@@ -111,12 +111,15 @@ struct MgHierarchy {
   // The same polynomial before and after the coarse correction keeps the
   // V-cycle symmetric.
   int nu = 2;
-  // Degree on the finest level: 1 when it holds more than kDegree1Nodes nodes
-  // (then its sweeps dominate an iteration: at 240 x 80 x 80 degree 1 took
-  // 29.3 ms per SIMP step against 33.5 ms, the extra iterations outweighed by
-  // two fewer finest sweeps per iteration; at 120 x 40 x 40 it was 2 % slower)
+  // Degree on the finest level: 1 when it holds more than kDegree1Nodes nodes,
+  // kDegree1Nodes3D in 3D (then its sweeps dominate an iteration: at
+  // 240 x 80 x 80 degree 1 took 29.3 ms per SIMP step against 33.5 ms, the
+  // extra iterations outweighed by two fewer finest sweeps per iteration).  In
+  // 3D the finest level is scaled by the assembled operator's l1 row sums, which
+  // make one step a stronger smoother: at 120 x 40 x 40 degree 1 then took
+  // 9.04 ms against 9.18 ms (it was 2 % slower with the element-level sums).
   int nu0 = 2;
-  static constexpr long long kDegree1Nodes = 1000000;
+  static constexpr long long kDegree1Nodes = 1000000, kDegree1Nodes3D = 100000;
   int degree_at(int li) const { return li == 0 ? nu0 : nu; }
   float cheb_ratio = 60.f;
   float omega = 0.f;
